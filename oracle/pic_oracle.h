@@ -1,0 +1,90 @@
+/* FP64 CPU oracle of the relativistic PIC time step of the Runko paper
+ * (Nattila, arXiv:1906.06306).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the plain, slow, obviously correct
+ * reference that the CUDA path is checked against.  Only the test suite, the
+ * smoke check and the benchmark's CPU-baseline leg may load it; the product
+ * library never links, calls or falls back to it, and it shares no code,
+ * header, table or helper with the CUDA path.
+ *
+ * Conventions (Sect. 2.3, Appendix A): code units with dx = dt = 1; the
+ * Courant number c is the only constant in the field equations.
+ *
+ * Fields: double[9][nz][ny][nx], planes Ex Ey Ez Bx By Bz Jx Jy Jz.  Plane
+ * element [i,j,k] lives at the Yee point of Sect. 2.3.1:
+ *   Ex (i+1/2, j, k)   Ey (i, j+1/2, k)   Ez (i, j, k+1/2)
+ *   Bx (i, j+1/2, k+1/2)   By (i+1/2, j, k+1/2)   Bz (i+1/2, j+1/2, k)
+ *   J shares the points of E; charge density lives on the nodes (i, j, k).
+ * All boundaries are periodic.  In D < 3 the missing dimensions are not
+ * gridded: nothing varies along them and they have extent 1.
+ *
+ * Particles: double x[3][n] (absolute positions, only the first D rows are
+ * used, each in [0, n_d)), double u[3][n] (four-velocity in units of c).
+ */
+#ifndef PIC_ORACLE_H
+#define PIC_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int dim;        /* 1, 2 or 3 gridded dimensions */
+  int nx, ny, nz; /* cells per dimension (1 for non-gridded ones) */
+  double c;       /* Courant number */
+} orc_grid;
+
+/* Field solver, Eq. (fdB) over half a step: B -= (c/2) curl E. */
+void orc_push_half_b(const orc_grid* g, double* F);
+/* Field solver, curl part of Eq. (fdE): E += c curl B. */
+void orc_push_e(const orc_grid* g, double* F);
+/* add_cur of Table 1, current part of Eq. (fdE): E -= J. */
+void orc_add_cur(const orc_grid* g, double* F);
+/* Binomial2 filter (Table 2): `passes` passes of (1/4, 1/2, 1/4) along every
+ * gridded dimension on Jx, Jy, Jz. */
+void orc_filter_binomial(const orc_grid* g, double* F, int passes);
+
+/* LinearInterpolator: E and B at position x (3 values, only the gridded ones
+ * are read) by first-order weighting of each staggered component. */
+void orc_interp(const orc_grid* g, const double* F, const double* x, double* e, double* b);
+/* Relativistic Boris scheme of Appendix C, u (units of c) advanced in place by
+ * one step; qm = q/m of the species (s-hat). */
+void orc_boris(double* u, const double* e, const double* b, double qm, double c);
+/* ZigZag current of Appendix D for one particle moving from x1 to x2
+ * (unwrapped: x2 - x1 is the displacement; rows of non-gridded dimensions
+ * carry only the displacement), charge q, added into the J planes of F. */
+void orc_zigzag(const orc_grid* g, double* F, const double* x1, const double* x2, double q);
+
+/* interp_em + push of Table 1 for every particle of a species: gather, Boris,
+ * position update of Eq. (fdX) with periodic wrap.  The pre-move positions are
+ * written to x_old[3][n] (rows of non-gridded dims are 0) and the
+ * displacements to dx[3][n], both consumed by orc_deposit. */
+void orc_push_particles(const orc_grid* g, const double* F, double* x, double* u, long n,
+                        double qm, double* x_old, double* dx);
+/* comp_curr of Table 1 for one species: ZigZag from x_old to x_old + dx. */
+void orc_deposit(const orc_grid* g, double* F, const double* x_old, const double* dx, long n,
+                 double q);
+
+/* One full time step in the order of Table 1 for `ns` species:
+ * B half, interp_em + push (all species), B half, push_e, clear J and
+ * comp_curr (all species), `passes` Binomial2 passes, add_cur.
+ * x[s], u[s] point to each species' arrays; work must hold 6 * sum(n) doubles. */
+void orc_step(const orc_grid* g, double* F, double** x, double** u, const long* n,
+              const double* q, const double* m, int ns, int passes, double* work);
+
+/* Charge density on the nodes, first-order (cloud-in-cell) shape, added into
+ * rho[nz][ny][nx]. */
+void orc_charge_density(const orc_grid* g, const double* x, long n, double q, double* rho);
+/* Discrete divergence of E on the nodes (backward differences), written to div. */
+void orc_div_e(const orc_grid* g, const double* F, double* div);
+/* Discrete divergence of B at the cell centres (forward differences). */
+void orc_div_b(const orc_grid* g, const double* F, double* div);
+/* Field energies 0.5 sum E^2 and 0.5 sum B^2 (out[0], out[1]). */
+void orc_field_energy(const orc_grid* g, const double* F, double* out);
+/* Kinetic energy sum m c^2 (gamma - 1) of one species. */
+double orc_kinetic_energy(const double* u, long n, double m, double c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,249 @@
+"""Seeded initial conditions for pair-plasma PIC runs.
+
+Layout of what is produced (identical bytes go to the GPU path and the oracle):
+
+* particles, per species, structure of arrays:
+    ``cell``  int32[N]      linear cell index i + nx*(j + ny*k)
+    ``off``   float32[D, N] in-cell offset of each gridded coordinate, in [0, 1)
+    ``u``     float32[3, N] spatial four-velocity in units of c
+* fields: float32[9, nz, ny, nx] planes Ex, Ey, Ez, Bx, By, Bz, Jx, Jy, Jz on
+  the Yee lattice of Sect. 2.3.1 (plane index [i, j, k] of Ex is the point
+  (i+1/2, j, k), of Bx the point (i, j+1/2, k+1/2), and so on).
+
+Code units follow Appendix A: dx = dt = 1, the Courant number c is the only
+constant of the field equations, |q| = m for every macro-particle of a pair
+plasma and the charge is fixed by the skin depth R_p (in cells).
+
+Random numbers come from numpy's Philox counter-based generator, whose stream
+is the same on every platform.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+from scipy import special
+
+ONE_MINUS = np.nextafter(np.float32(1.0), np.float32(0.0))  # largest float32 < 1
+
+
+@dataclasses.dataclass
+class Species:
+    """One particle species: charge q (signed, code units), mass m (code units)."""
+
+    q: float
+    m: float
+    cell: np.ndarray  # int32[N]
+    off: np.ndarray  # float32[D, N]
+    u: np.ndarray  # float32[3, N]
+
+    @property
+    def n(self) -> int:
+        return int(self.cell.shape[0])
+
+
+@dataclasses.dataclass
+class Plasma:
+    """A periodic box: grid, Courant number, species and the 9 field planes."""
+
+    dim: int
+    nx: int
+    ny: int
+    nz: int
+    c: float
+    species: list
+    fields: np.ndarray  # float32[9, nz, ny, nx]
+    meta: dict
+
+    @property
+    def ncells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def nparticles(self) -> int:
+        return sum(s.n for s in self.species)
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(seed))
+
+
+def mj_mean_gamma(theta: float) -> float:
+    """Mean Lorentz factor of a Maxwell-Juettner gas, K1(1/t)/K2(1/t) + 3t."""
+    z = 1.0 / theta
+    if z > 500.0:  # asymptotic form, avoids underflow of kv
+        return 1.0 + 1.5 * theta + 15.0 / 8.0 * theta**2
+    return float(special.kve(1, z) / special.kve(2, z) + 3.0 * theta)
+
+
+def charge_from_skin_depth(c: float, r_p: float, ppc: int, mean_gamma: float,
+                           mass_ratio_sum: float = 2.0) -> float:
+    """|q| fixed by the skin depth (Appendix A): w_p0 = c / R_p and
+    |q| = w_p0^2 <gamma> / (N_ppc (1 + m-/m+))."""
+    wp0 = c / r_p
+    return wp0 * wp0 * mean_gamma / (ppc * mass_ratio_sum)
+
+
+def sample_mj_momenta(gen: np.random.Generator, n: int, theta: float) -> np.ndarray:
+    """Isotropic Maxwell-Juettner four-velocities u (units of c), float64[3, n].
+
+    |u| is drawn by inverting the tabulated cumulative distribution of
+    p^2 exp(-(sqrt(1+p^2)-1)/theta); the direction is uniform on the sphere.
+    The table spans the distribution out to gamma-1 = 60 theta."""
+    pmax = math.sqrt((1.0 + 60.0 * theta) ** 2 - 1.0)
+    p = np.linspace(0.0, pmax, 1 << 17)
+    logg = 2.0 * np.log(np.maximum(p, 1e-300)) - (np.sqrt(1.0 + p * p) - 1.0) / theta
+    g = np.exp(logg - logg.max())
+    g[0] = 0.0
+    cdf = np.concatenate([[0.0], np.cumsum(0.5 * (g[1:] + g[:-1]) * np.diff(p))])
+    cdf /= cdf[-1]
+    mag = np.interp(gen.random(n), cdf, p)
+    cos_t = 2.0 * gen.random(n) - 1.0
+    sin_t = np.sqrt(np.maximum(0.0, 1.0 - cos_t * cos_t))
+    phi = 2.0 * math.pi * gen.random(n)
+    return np.stack([mag * sin_t * np.cos(phi), mag * sin_t * np.sin(phi), mag * cos_t])
+
+
+def boost_flip(gen: np.random.Generator, u: np.ndarray, axis: int, beta: np.ndarray) -> np.ndarray:
+    """Boost rest-frame momenta u (float64[3, n]) to drift velocity beta along
+    `axis` with the flipping method of Zenitani (2015): a particle whose
+    velocity component satisfies -beta v > X (X uniform) has that component
+    reversed first, which reweights the rest-frame sample by (1 + beta v) as the
+    Lorentz transformation of the number density requires; then
+    u' = Gamma (u + beta gamma)."""
+    beta = np.broadcast_to(np.asarray(beta, dtype=np.float64), u.shape[1:])
+    gam = np.sqrt(1.0 + (u * u).sum(axis=0))
+    ua = u[axis].copy()
+    flip = -beta * (ua / gam) > gen.random(ua.shape[0])
+    ua[flip] = -ua[flip]
+    big = 1.0 / np.sqrt(1.0 - beta * beta)
+    out = u.copy()
+    out[axis] = big * (ua + beta * gam)
+    return out
+
+
+_CHUNK = 1 << 22  # particles drawn per chunk; fixed so the streams never change
+
+
+def uniform_plasma(dim: int, nx: int, ny: int, nz: int, c: float, ppc: int,
+                   q_abs: float, theta: float, seed: int,
+                   drift_axis: int = 0, drift_beta_per_slot=None,
+                   meta: dict | None = None) -> Plasma:
+    """Electron-positron plasma, `ppc` particles per cell per species.
+
+    Offsets are uniform in each cell; particle k of the electrons and particle k
+    of the positrons share their position (so the initial charge density is 0
+    exactly), their four-velocities are drawn independently.  The slot of a
+    particle inside its cell (0..ppc-1) selects its drift velocity from
+    `drift_beta_per_slot` (None = at rest), applied along `drift_axis`."""
+    if dim == 1:
+        ny = nz = 1
+    elif dim == 2:
+        nz = 1
+    ncells = nx * ny * nz
+    n = ncells * ppc
+    gen = rng(seed)
+    cell = np.repeat(np.arange(ncells, dtype=np.int32), ppc)
+    off = np.empty((dim, n), dtype=np.float32)
+    us = [np.empty((3, n), dtype=np.float32) for _ in range(2)]
+    slot_beta = None
+    if drift_beta_per_slot is not None:
+        slot_beta = np.asarray(drift_beta_per_slot, dtype=np.float64)
+        assert slot_beta.shape == (ppc,)
+    for lo in range(0, n, _CHUNK):
+        hi = min(n, lo + _CHUNK)
+        o = gen.random((dim, hi - lo)).astype(np.float32)
+        off[:, lo:hi] = np.minimum(o, ONE_MINUS)
+        for s in range(2):
+            u = sample_mj_momenta(gen, hi - lo, theta)
+            if slot_beta is not None:
+                beta = slot_beta[np.arange(lo, hi) % ppc]
+                u = boost_flip(gen, u, drift_axis, beta)
+            us[s][:, lo:hi] = u.astype(np.float32)
+    species = [
+        Species(q=-q_abs, m=q_abs, cell=cell, off=off, u=us[0]),
+        Species(q=+q_abs, m=q_abs, cell=cell.copy(), off=off.copy(), u=us[1]),
+    ]
+    fields = np.zeros((9, nz, ny, nx), dtype=np.float32)
+    return Plasma(dim=dim, nx=nx, ny=ny, nz=nz, c=c, species=species,
+                  fields=fields, meta=dict(meta or {}))
+
+
+def weibel_1d(nx: int = 512, ppc: int = 64, gamma_b: float = 3.0, theta: float = 0.01,
+              r_p: float = 10.0, c: float = 0.45, seed: int = 1234) -> Plasma:
+    """Relativistic Weibel (filamentation) set-up of Sect. 4.1 in 1D3V: wave
+    vector along x, two counter-streaming beams along +-y with Lorentz factor
+    gamma_b, each carrying half of every species; zero initial fields.
+    Charge from Appendix A with <gamma> = gamma_b."""
+    q_abs = charge_from_skin_depth(c, r_p, ppc, gamma_b)
+    beta_b = math.sqrt(1.0 - 1.0 / gamma_b**2)
+    slots = np.where(np.arange(ppc) < ppc // 2, beta_b, -beta_b)
+    return uniform_plasma(1, nx, 1, 1, c, ppc, q_abs, theta, seed,
+                          drift_axis=1, drift_beta_per_slot=slots,
+                          meta=dict(workload="weibel_1d3v", gamma_b=gamma_b, beta_b=beta_b,
+                                    theta=theta, r_p=r_p, ppc=ppc, q_abs=q_abs,
+                                    filter_passes=0))
+
+
+def turbulence_2d(n: int = 1024, ppc: int = 16, r_p: float = 4.0, theta: float = 0.3,
+                  sigma: float = 10.0, db_over_b0: float = 1.0, modes: int = 8,
+                  c: float = 0.45, seed: int = 1235) -> Plasma:
+    """Decaying turbulence set-up of Sect. 4.3 in 2D3V: pair plasma at rest
+    with Maxwell-Juettner temperature theta, guide field B0 z-hat from the
+    magnetization sigma (Appendix A, both species' enthalpy), and in-plane
+    perturbations summed over modes m, n = 1..`modes` with random phases and
+    amplitudes beta_mn = 2 dB / (N sqrt(m^2+n^2)).
+
+    The perturbation is the curl of A_z = sum beta_mn (L/2pi)
+    sin(k_m x + phi) sin(k_n y + psi), differenced on the lattice, which gives the
+    printed dBx, dBy in the continuum limit and a discretely solenoidal B."""
+    mean_g = mj_mean_gamma(theta)
+    q_abs = charge_from_skin_depth(c, r_p, ppc, mean_g)
+    b0 = math.sqrt(sigma * ppc * q_abs * c * c * mean_g * 2.0)
+    pl = uniform_plasma(2, n, n, 1, c, ppc, q_abs, theta, seed,
+                        meta=dict(workload="turbulence_2d3v", theta=theta, sigma=sigma,
+                                  r_p=r_p, ppc=ppc, q_abs=q_abs, b0=b0, mean_gamma=mean_g,
+                                  filter_passes=0))
+    gen = rng(seed + 100000)
+    phi = 2.0 * math.pi * gen.random((modes, modes))
+    psi = 2.0 * math.pi * gen.random((modes, modes))
+    L = float(n)
+    x = np.arange(n, dtype=np.float64)
+    az = np.zeros((n, n), dtype=np.float64)  # [j, i]
+    db = db_over_b0 * b0
+    for m in range(1, modes + 1):
+        for nn in range(1, modes + 1):
+            beta = 2.0 * db / (modes * math.sqrt(m * m + nn * nn))
+            sx = np.sin(2.0 * math.pi * m * x / L + phi[m - 1, nn - 1])
+            sy = np.sin(2.0 * math.pi * nn * x / L + psi[m - 1, nn - 1])
+            az += beta * (L / (2.0 * math.pi)) * np.outer(sy, sx)
+    bx = np.roll(az, -1, axis=0) - az  # at (i, j+1/2)
+    by = -(np.roll(az, -1, axis=1) - az)  # at (i+1/2, j)
+    pl.fields[3, 0] = bx.astype(np.float32)
+    pl.fields[4, 0] = by.astype(np.float32)
+    pl.fields[5, 0] = np.float32(b0)
+    pl.meta["db_rms_over_b0"] = float(np.sqrt((bx * bx + by * by).mean()) / b0)
+    return pl
+
+
+def shock_3d(nx: int = 1024, ny: int = 128, nz: int = 128, ppc: int = 8,
+             gamma_flow: float = 10.0, theta: float = 1e-4, r_p: float = 10.0,
+             c: float = 0.45, seed: int = 1236) -> Plasma:
+    """Periodic stand-in for the shock run of Sect. 4.2 in 3D3V: cold pair
+    plasma streaming toward -x with Lorentz factor gamma_flow, no fields.
+    Charge from Appendix A with <gamma> = gamma_flow; 4 binomial passes."""
+    q_abs = charge_from_skin_depth(c, r_p, ppc, gamma_flow)
+    beta = -math.sqrt(1.0 - 1.0 / gamma_flow**2)
+    return uniform_plasma(3, nx, ny, nz, c, ppc, q_abs, theta, seed,
+                          drift_axis=0, drift_beta_per_slot=np.full(ppc, beta),
+                          meta=dict(workload="shock_3d3v_periodic", gamma_flow=gamma_flow,
+                                    theta=theta, r_p=r_p, ppc=ppc, q_abs=q_abs,
+                                    filter_passes=4))
+
+
+CONFIGS = {
+    "weibel_1d3v": weibel_1d,
+    "turbulence_2d3v": turbulence_2d,
+    "shock_3d3v_periodic": shock_3d,
+}
