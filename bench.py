@@ -1,0 +1,354 @@
+"""Benchmark of the GB300 PIC step on the 2D3V decaying-turbulence workload
+(1024 x 1024 cells, 16 particles per cell per species, theta = 0.3,
+sigma = 10, forcing modes 1..8; Sect. 4.3 of arXiv:1906.06306).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one full pic_step (B half step, fused gather + Boris + move +
+ZigZag deposit, B half step, filter passes, E update, and the tile sort every
+`sort_every` steps), over every particle.  value = particle-steps/s of the
+whole job; for N > 1 (torchrun) every rank steps an independent replica of
+the box ("replicas only": the single-GPU path has no exchange step).
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (gather+push+deposit), FP32 vs FP64 oracle, % HBM roofline"
+WORKLOAD = dict(workload="turbulence_2d3v", grid=[1024, 1024], ppc_per_species=16, species=2,
+                theta=0.3, sigma=10.0, r_p=4.0, modes=8)
+FALLBACK_HBM_GBS = 6800.0
+PROFILE = os.path.join(ROOT, "profiles", "push_turbulence_2d3v.md")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("pic_particles.cu", "pic_dev.cuh", "pic_kernels.h"):
+        with open(os.path.join(ROOT, "paper_1906_06306_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the fused particle kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(steps: int = 0, sample_n: int = 128, target_s: float = 12.0):
+    """The FP64 oracle, as it stands (one host thread), on a sample of the same
+    workload: the turbulence set-up on a sample_n^2 box with the same particles
+    per cell, temperature, magnetization and forcing; `steps` steps, or as many
+    as fit in about target_s seconds."""
+    import oracle
+    import workloads
+
+    oracle.build()
+    pl = workloads.turbulence_2d(n=sample_n, ppc=16, r_p=4.0, theta=0.3, sigma=10.0, modes=8,
+                                 seed=1235)
+    g, F, sp = oracle.from_plasma(pl)
+    t0 = time.perf_counter()
+    oracle.step(g, F, sp)
+    one = time.perf_counter() - t0
+    n = steps if steps > 0 else max(1, int(target_s / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    oracle.step(g, F, sp, nsteps=n)
+    dt = time.perf_counter() - t0
+    return {"value": pl.nparticles * n / dt, "unit": "particle-steps/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"turbulence_2d3v on a {sample_n}x{sample_n} box ({pl.nparticles} particles, "
+                      f"same ppc/theta/sigma/forcing), {n} steps, FP64, 1 host thread",
+            "seconds": dt}
+
+
+def run_reference(args):
+    """The oracle as it stands on the host cores, K timed steps after W warm-up
+    steps; each step runs the turbulence set-up on a box small enough that the
+    whole run stays within about 90 seconds."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import math
+
+    import oracle
+    import workloads
+
+    oracle.build()
+    cal = cpu_baseline(steps=1, sample_n=64)
+    per_particle_step = 1.0 / cal["value"]
+    budget = 90.0 / max(1, args.steps + args.warmup)
+    n = int(math.sqrt(budget / per_particle_step / 32.0))
+    n = max(16, min(256, n))
+    pl = workloads.turbulence_2d(n=n, ppc=16, r_p=4.0, theta=0.3, sigma=10.0, modes=8, seed=1235)
+    g, F, sp = oracle.from_plasma(pl)
+    oracle.step(g, F, sp, nsteps=args.warmup)
+    t0 = time.perf_counter()
+    oracle.step(g, F, sp, nsteps=args.steps)
+    dt = time.perf_counter() - t0
+    value = pl.nparticles * args.steps / dt
+    sample = (f"turbulence_2d3v on a {n}x{n} box ({pl.nparticles} particles, same ppc/theta/"
+              f"sigma/forcing) per step, FP64, 1 host thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, sample=sample),
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def push_bytes_per_launch(pl) -> float:
+    """Algorithmic DRAM bytes of one fused particle launch: every particle's SoA
+    record (int32 cell, D float offsets, 3 float u) read once and written once,
+    the six E and B planes read once and the three J planes written once."""
+    rec = 4 + 4 * pl.dim + 12
+    return float(pl.nparticles * 2 * rec + pl.ncells * (6 + 3) * 4)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import workloads
+    from paper_1906_06306_gb300 import Simulation
+    from paper_1906_06306_gb300 import binding as B
+
+    pl = workloads.turbulence_2d(seed=1235)  # every rank steps its own replica of the box
+    sim = Simulation.from_plasma(pl, device=f"cuda:{local}",
+                                 tuning=dict(sort_every=args.sort_every))
+    tun = sim.tuning()
+    dev = torch.device(f"cuda:{local}")
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize(dev)
+    sim.check()
+
+    # ---- device-resident timed region ----
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    B.pic_kernel_times(sim.ctx)  # reset counters
+    B.pic_timing(sim.ctx, True)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(sim.stream)
+    for _ in range(args.steps):
+        sim.step(1)
+    t1.record(sim.stream)
+    torch.cuda.synchronize(dev)
+    ms = t0.elapsed_time(t1)
+    kt = B.pic_kernel_times(sim.ctx)
+    B.pic_timing(sim.ctx, False)
+    clocks = sampler.stop()
+    if dist is not None:
+        dist.barrier()
+    sim.check()
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * pl.nparticles * args.steps / (ms_max * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if args.e2e_steps > 0:
+        F0, sp0 = sim.download()
+        hs, keep = [], []
+        for s in sp0:
+            arrs = [torch.from_numpy(s[k]).pin_memory() for k in ("cell", "off", "u")]
+            keep.append(arrs)
+            hs.append(B.pic_host_species(*[a.data_ptr() for a in arrs]))
+        hf = torch.from_numpy(F0).pin_memory()
+        h2d = sum(a.numel() * a.element_size() for arrs in keep for a in arrs) + hf.numel() * 4
+        B.pic_step_host(sim.ctx, hs, hf.data_ptr(), 1)  # warm-up
+        if dist is not None:
+            dist.barrier()
+        te = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            B.pic_step_host(sim.ctx, hs, hf.data_ptr(), 1)
+        e_s = time.perf_counter() - te
+        if dist is not None:
+            t = torch.tensor([e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_s = float(t.item())
+        e2e = {"value": world * pl.nparticles * args.e2e_steps / e_s, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d),
+               "steps": args.e2e_steps,
+               "note": "pic_step_host: pinned host particles + fields copied in, one step, copied back"}
+
+    if rank != 0:
+        sim.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    push_ms, push_n = kt["push"]
+    avg_push_s = push_ms * 1e-3 / max(push_n, 1)
+    peak, peak_kind = hbm_peak()
+    alg = push_bytes_per_launch(pl)
+    achieved = alg / avg_push_s / 1e9
+    traffic = profiled_traffic()
+    nsorts = sum(1 for s in range(args.warmup, args.warmup + args.steps)
+                 if s > 0 and s % tun["sort_every"] == 0)
+    launches = args.steps * (4 + tun["filter_passes"]) + nsorts * 3 * sim.nspecies
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": dict(WORKLOAD, particles=pl.nparticles, sort_every=tun["sort_every"],
+                       filter_passes=tun["filter_passes"], tile=tun["tile"][:2], halo=tun["halo"],
+                       parallelism="replicas" if world > 1 else "single-gpu",
+                       l2="inputs larger than L2 (particle SoA %.2f GB), no flush" %
+                          (pl.nparticles * 24 / 1e9)),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_particles<2,0> (gather+push+move+deposit)",
+                     "peak_source": peak_kind, "avg_launch_us": avg_push_s * 1e6,
+                     "alg_bytes_per_launch": alg},
+        "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in kt.items()},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline()
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--sort-every", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/* pic.h - C ABI of a single-GPU relativistic particle-in-cell time step for
+ * NVIDIA GB300 (sm_103a): the hot path of the PIC method of the Runko paper
+ * (Nattila, arXiv:1906.06306, Sect. 2.3, Table 1, Appendices B-D).
+ *
+ * Units and lattice (Sect. 2.3, Appendix A): dx = dt = 1; the Courant number c
+ * is the only constant of the field equations.  All boundaries are periodic.
+ *
+ * Fields: ONE caller-owned device buffer of 9 float planes, each
+ * nz*ny*nx floats, x fastest: Ex Ey Ez Bx By Bz Jx Jy Jz.  Element [i,j,k] of
+ * each plane lives at its Yee point (Sect. 2.3.1):
+ *   Ex (i+1/2,j,k)  Ey (i,j+1/2,k)  Ez (i,j,k+1/2)
+ *   Bx (i,j+1/2,k+1/2)  By (i+1/2,j,k+1/2)  Bz (i+1/2,j+1/2,k)
+ *   J at the E points; charge density (diagnostics) on the nodes (i,j,k).
+ * Time levels: on entry to a step E is at t^n and B at t^(n-1/2); particles
+ * hold x^n and u^(n-1/2).
+ *
+ * Particles, per species, caller-owned device buffers (structure of arrays):
+ *   cell  int32[n]       linear cell index i + nx*(j + ny*k)
+ *   off   float[dim][n]  in-cell offset of each gridded coordinate, in [0,1)
+ *   u     float[3][n]    spatial four-velocity in units of c
+ * The library keeps particles sorted by spatial tile and may reorder them
+ * (pic_sort, pic_step); after every call returns (on the stream) the caller's
+ * buffers hold the current particles.
+ *
+ * Ownership: the caller owns the field and particle buffers and the stream;
+ * the library owns the context, its scratch (sort buffers, tile tables,
+ * pre-move snapshot, filter buffer, diagnostics, status word) and frees them
+ * in pic_destroy.  All calls enqueue work on the context's stream and return
+ * without synchronising, except pic_energies, pic_check, pic_step_host and
+ * pic_kernel_times, which synchronise the stream.  No exception crosses the
+ * ABI: every call returns a pic_status; pic_last_error gives the message of
+ * the last failure on a context.  A context is not thread-safe.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_ctx pic_ctx;
+
+typedef enum {
+  PIC_OK = 0,
+  PIC_ERR_ARG = 1,     /* invalid argument: null pointer, bad size or layout */
+  PIC_ERR_CUDA = 2,    /* a CUDA runtime call failed (message in pic_last_error) */
+  PIC_ERR_OOM = 3,     /* the library could not allocate its device scratch */
+  PIC_ERR_TIMEOUT = 4, /* a bounded device-side wait gave up */
+  PIC_ERR_STATE = 5    /* a kernel met invalid particle data (cell index out of
+                          range, offset outside [0,1), non-finite u) */
+} pic_status;
+
+#define PIC_MAX_SPECIES 4
+
+/* Periodic box: dim = 1, 2 or 3 gridded dimensions; extents of non-gridded
+ * dimensions must be 1.  nx*ny*nz must fit in int32. */
+typedef struct {
+  int dim;
+  int nx, ny, nz;
+} pic_grid;
+
+/* One species.  q is the charge of a macro-particle (signed, code units; the
+ * ZigZag current of Appendix D is proportional to it) and m its mass, so that
+ * q/m is the s-hat of the Boris scheme (Appendix C).  Pointers are device
+ * pointers with the layout above; the caller keeps them alive until
+ * pic_destroy. */
+typedef struct {
+  float q;
+  float m;
+  int64_t n;
+  int32_t* cell;
+  float* off;
+  float* u;
+} pic_species;
+
+/* Host-side particles of one species for pic_step_host (same layout as
+ * pic_species, host pointers; pinned memory gives full copy bandwidth). */
+typedef struct {
+  int32_t* cell;
+  float* off;
+  float* u;
+} pic_host_species;
+
+/* Launch and layout parameters (not physics).  Zero fields keep their current
+ * value.  tile: cells per tile per gridded dimension; halo: extra cells staged
+ * on each side of a tile (>= 1; a particle that has drifted further than
+ * halo-1 cells from its tile since the last sort takes the global-memory
+ * path); sort_every: steps between tile sorts inside pic_step; filter_passes:
+ * Binomial2 passes applied to J inside pic_step (Sect. 4.2 uses 8, the
+ * 3D shock-shaped workload 4); chunk: target particles per thread block. */
+typedef struct {
+  int tile[3];
+  int halo;
+  int sort_every;
+  int filter_passes;
+  int chunk;
+} pic_tuning;
+
+/* Which field update pic_field_update performs. */
+#define PIC_FIELD_B_HALF 0 /* Eq. (fdB) over half a step: B -= (c/2) curl E */
+#define PIC_FIELD_E 1      /* Eq. (fdE) with add_cur (Table 1): E += c curl B - J */
+
+/* Kernel kinds reported by pic_kernel_times. */
+#define PIC_KERNEL_PUSH 0   /* gather + push + move + deposit (fused) */
+#define PIC_KERNEL_BHALF 1  /* B half step */
+#define PIC_KERNEL_EUPD 2   /* E update with -J */
+#define PIC_KERNEL_FILTER 3 /* one Binomial2 pass */
+#define PIC_KERNEL_SORT 4   /* tile sort: count + scan + scatter + copy back */
+#define PIC_KERNEL_KINDS 5
+
+/* Create a context for `grid`, `nspecies` (1..PIC_MAX_SPECIES) species, Courant
+ * number c (0 < c < 1 for the explicit scheme, Sect. 2.3) and time step dt,
+ * which must be 1 (code units of Sect. 2.3).  `fields` is the caller's device
+ * buffer of 9 planes; `stream` a cudaStream_t (NULL = legacy default stream).
+ * Validates every argument, allocates the scratch, sorts the particles by
+ * tile (on the stream) and stores the new context in *out.  On failure *out
+ * is NULL and nothing stays allocated. */
+pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* species,
+                    int nspecies, float c, float dt, float* fields, void* stream);
+
+/* Read or change the launch parameters.  Changing tile re-sorts the particles. */
+pic_status pic_get_tuning(pic_ctx* ctx, pic_tuning* out);
+pic_status pic_set_tuning(pic_ctx* ctx, const pic_tuning* t);
+
+/* Counting sort by tile of every species (replaces the particle migration
+ * routines of Table 1, check_outg_prtcls ... del_vir_prtcls, on one GPU).
+ * Particles are grouped by tile; the order inside a tile is not specified. */
+pic_status pic_sort(pic_ctx* ctx);
+
+/* interp_em + push of Table 1 for every species: linear gather of E and B at
+ * x^n (Sect. 2.3.2), relativistic Boris push u^(n-1/2) -> u^(n+1/2)
+ * (Appendix C), position update x^(n+1) = x^n + c u / gamma (Eq. fdX) with
+ * periodic wrap.  The pre-move positions are kept in library scratch for
+ * pic_deposit. */
+pic_status pic_gather_push(pic_ctx* ctx);
+
+/* comp_curr of Table 1: adds the ZigZag current (Appendix D) of every particle's
+ * move since the last pic_gather_push into the J planes (J is not cleared).
+ * PIC_ERR_STATE if no pic_gather_push preceded it. */
+pic_status pic_deposit(pic_ctx* ctx);
+
+/* `passes` (>= 0) passes of the Binomial2 (1/4,1/2,1/4) filter along every
+ * gridded dimension on Jx, Jy, Jz (Table 2).  The result is left in the J
+ * planes. */
+pic_status pic_filter_current(pic_ctx* ctx, int passes);
+
+/* One field update, `which` = PIC_FIELD_B_HALF or PIC_FIELD_E. */
+pic_status pic_field_update(pic_ctx* ctx, int which);
+
+/* `nsteps` full time steps in the order of Table 1: B half step, gather +
+ * push + deposit (fused; J cleared first), B half step, filter_passes
+ * Binomial2 passes on J, E update with -J.  Every sort_every steps (counted
+ * over the life of the context) the particles are re-sorted by tile before
+ * the push.  On return the J planes hold the filtered current of the last
+ * step. */
+pic_status pic_step(pic_ctx* ctx, int nsteps);
+
+/* Diagnostics (synchronising).  out[0] = 0.5 sum E^2, out[1] = 0.5 sum B^2,
+ * out[2+s] = sum m c^2 (gamma - 1) of species s, out[2+ns] = max |div E -
+ * F^p(rho)|, out[3+ns] = rms of the same over the nodes, where rho is the
+ * first-order charge on the nodes and F^p the filter_passes-fold Binomial2
+ * filter (Appendix B: this residual is conserved).  Sums are accumulated in
+ * double precision on the GPU.  nout must be >= 4 + nspecies. */
+pic_status pic_energies(pic_ctx* ctx, double* out, int nout);
+
+/* Synchronise the stream and read the device status word: PIC_ERR_STATE if
+ * any kernel since the last check met invalid particle data (the word is then
+ * cleared), otherwise PIC_OK. */
+pic_status pic_check(pic_ctx* ctx);
+
+/* End-to-end step from host memory: copies every species' particles from
+ * `hs` and the 9 field planes from `host_fields` into the context's device
+ * buffers, runs pic_step(nsteps), copies particles and fields back into the
+ * same host buffers and synchronises. */
+pic_status pic_step_host(pic_ctx* ctx, const pic_host_species* hs, float* host_fields,
+                         int nsteps);
+
+/* Per-kernel timing with CUDA events on the context stream.  While enabled,
+ * every launch of the kinds above is bracketed by events.  pic_kernel_times
+ * synchronises, adds the elapsed milliseconds and launch counts of each kind
+ * since the last reset into ms[PIC_KERNEL_KINDS] and launches[...], and
+ * resets the counters. */
+pic_status pic_timing(pic_ctx* ctx, int enable);
+pic_status pic_kernel_times(pic_ctx* ctx, double* ms, int64_t* launches);
+
+/* Release the context and its scratch (the caller's buffers are untouched). */
+pic_status pic_destroy(pic_ctx* ctx);
+
+/* Message of the last failure on ctx ("" if none); for ctx == NULL, the last
+ * failure of pic_init in this process. */
+const char* pic_last_error(const pic_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

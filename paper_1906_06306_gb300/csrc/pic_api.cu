@@ -1,0 +1,586 @@
+// C ABI of the PIC hot path (see include/pic.h): argument checking, scratch
+// ownership, the order of the time step (Table 1 of arXiv:1906.06306) and
+// event timing.  All device work goes to the context's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pic.h"
+#include "pic_kernels.h"
+
+using namespace pic;
+
+namespace {
+
+struct TimedLaunch {
+  cudaEvent_t a, b;
+  int kind;
+};
+
+thread_local std::string g_init_error;
+
+}  // namespace
+
+struct pic_ctx {
+  pic_grid grid{};
+  int ns = 0;
+  pic_species sp[PIC_MAX_SPECIES]{};
+  float c = 0.f;
+  float* F = nullptr;
+  cudaStream_t st = nullptr;
+  pic_tuning tun{};
+  GridDev g{};
+  TileDev tile{};
+  int splits = 1;
+  long long ntot = 0, nmax = 0;
+  int* d_tstart[PIC_MAX_SPECIES] = {};
+  int* d_count = nullptr;
+  int* d_cursor = nullptr;
+  void* d_sortbuf = nullptr;
+  int* d_cell_old = nullptr;
+  float* d_off_old = nullptr;
+  bool snapshot_valid = false;
+  float* d_jtmp = nullptr;
+  double* d_rho = nullptr;
+  double* d_rho2 = nullptr;
+  double* d_acc = nullptr;
+  int* d_status = nullptr;
+  long long steps = 0;
+  bool timing = false;
+  std::vector<TimedLaunch> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms[PIC_KERNEL_KINDS] = {};
+  int64_t launches[PIC_KERNEL_KINDS] = {};
+  std::string err;
+};
+
+namespace {
+
+pic_status set_err(pic_ctx* ctx, pic_status s, const std::string& msg) {
+  if (ctx)
+    ctx->err = msg;
+  else
+    g_init_error = msg;
+  return s;
+}
+
+pic_status cuda_fail(pic_ctx* ctx, const char* what, cudaError_t e) {
+  const pic_status s = (e == cudaErrorMemoryAllocation) ? PIC_ERR_OOM : PIC_ERR_CUDA;
+  return set_err(ctx, s, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define PIC_CK(ctx, call)                                     \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), #call, e_); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+void free_all(pic_ctx* ctx) {
+  for (int s = 0; s < PIC_MAX_SPECIES; ++s) dfree(ctx->d_tstart[s]);
+  dfree(ctx->d_count);
+  dfree(ctx->d_cursor);
+  dfree(ctx->d_sortbuf);
+  dfree(ctx->d_cell_old);
+  dfree(ctx->d_off_old);
+  dfree(ctx->d_jtmp);
+  dfree(ctx->d_rho);
+  dfree(ctx->d_rho2);
+  dfree(ctx->d_acc);
+  dfree(ctx->d_status);
+  for (auto& t : ctx->pending) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  ctx->pending.clear();
+  for (auto e : ctx->pool) cudaEventDestroy(e);
+  ctx->pool.clear();
+}
+
+int extent(const pic_grid& g, int d) { return d == 0 ? g.nx : d == 1 ? g.ny : g.nz; }
+
+// Tile geometry from the tuning; returns an error message or "".
+std::string derive_tiles(const pic_grid& grid, const pic_tuning& tun, long long ntot,
+                         TileDev* t, int* splits) {
+  if (tun.halo < 1) return "halo must be >= 1";
+  if (tun.chunk < 32) return "chunk must be >= 32";
+  TileDev r{};
+  r.H = tun.halo;
+  long long ntiles = 1, wcells = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (d < grid.dim) {
+      if (tun.tile[d] < 1) return "tile extents must be >= 1";
+      const int n = extent(grid, d);
+      r.T[d] = tun.tile[d] < n ? tun.tile[d] : n;
+      r.nt[d] = (n + r.T[d] - 1) / r.T[d];
+      r.W[d] = r.T[d] + 2 * r.H + 1;
+    } else {
+      r.T[d] = 1;
+      r.nt[d] = 1;
+      r.W[d] = 1;
+    }
+    ntiles *= r.nt[d];
+    wcells *= r.W[d];
+  }
+  if (wcells * 9 * 4 > 200 * 1024) return "tile + halo window exceeds 200 KB of shared memory";
+  if (ntiles > (1LL << 30)) return "too many tiles";
+  r.wcells = (int)wcells;
+  r.ntiles = (int)ntiles;
+  const long long per_tile = (ntot + ntiles - 1) / ntiles;
+  long long sp = (per_tile + tun.chunk - 1) / tun.chunk;
+  if (sp < 1) sp = 1;
+  if (sp > 1024) sp = 1024;
+  *t = r;
+  *splits = (int)sp;
+  return "";
+}
+
+pic_status alloc_tiles(pic_ctx* ctx) {
+  for (int s = 0; s < ctx->ns; ++s) {
+    dfree(ctx->d_tstart[s]);
+    PIC_CK(ctx, dalloc(&ctx->d_tstart[s], (size_t)ctx->tile.ntiles + 1));
+  }
+  dfree(ctx->d_count);
+  dfree(ctx->d_cursor);
+  PIC_CK(ctx, dalloc(&ctx->d_count, (size_t)ctx->tile.ntiles));
+  PIC_CK(ctx, dalloc(&ctx->d_cursor, (size_t)ctx->tile.ntiles));
+  return PIC_OK;
+}
+
+cudaEvent_t take_event(pic_ctx* ctx) {
+  if (!ctx->pool.empty()) {
+    cudaEvent_t e = ctx->pool.back();
+    ctx->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Run `fn` (which enqueues one kind of work) bracketed by timing events when
+// timing is on.
+template <typename Fn>
+cudaError_t timed(pic_ctx* ctx, int kind, Fn fn) {
+  if (!ctx->timing) return fn();
+  TimedLaunch t{take_event(ctx), take_event(ctx), kind};
+  cudaEventRecord(t.a, ctx->st);
+  const cudaError_t e = fn();
+  cudaEventRecord(t.b, ctx->st);
+  ctx->pending.push_back(t);
+  return e;
+}
+
+PushParams make_params(pic_ctx* ctx) {
+  PushParams P{};
+  P.g = ctx->g;
+  P.t = ctx->tile;
+  P.F = ctx->F;
+  P.nspecies = ctx->ns;
+  P.splits = ctx->splits;
+  P.status = ctx->d_status;
+  P.inv_c = 1.0f / ctx->c;
+  P.inv_c2 = 1.0f / (ctx->c * ctx->c);
+  long long o = 0;
+  for (int s = 0; s < ctx->ns; ++s) {
+    SpeciesDev& S = P.sp[s];
+    S.q = ctx->sp[s].q;
+    S.qm = ctx->sp[s].q / ctx->sp[s].m;
+    S.n = ctx->sp[s].n;
+    S.cell = ctx->sp[s].cell;
+    S.off = ctx->sp[s].off;
+    S.u = ctx->sp[s].u;
+    S.tstart = ctx->d_tstart[s];
+    S.cell_old = ctx->d_cell_old ? ctx->d_cell_old + o : nullptr;
+    S.off_old = ctx->d_off_old ? ctx->d_off_old + (long long)ctx->grid.dim * o : nullptr;
+    o += ctx->sp[s].n;
+  }
+  return P;
+}
+
+pic_status do_sort(pic_ctx* ctx) {
+  SortParams P{ctx->g, ctx->tile, ctx->d_status};
+  const int D = ctx->grid.dim;
+  const cudaError_t e = timed(ctx, PIC_KERNEL_SORT, [&]() -> cudaError_t {
+    for (int s = 0; s < ctx->ns; ++s) {
+      const long long n = ctx->sp[s].n;
+      cudaError_t r = cudaMemsetAsync(ctx->d_count, 0, sizeof(int) * ctx->tile.ntiles, ctx->st);
+      if (r != cudaSuccess) return r;
+      r = launch_tile_count(P, ctx->sp[s].cell, n, ctx->d_count, ctx->st);
+      if (r != cudaSuccess) return r;
+      r = launch_tile_scan(ctx->d_count, ctx->tile.ntiles, ctx->d_tstart[s], ctx->d_cursor, ctx->st);
+      if (r != cudaSuccess) return r;
+      if (n == 0) continue;
+      int* cell_out = (int*)ctx->d_sortbuf;
+      float* off_out = (float*)(cell_out + n);
+      float* u_out = off_out + (long long)D * n;
+      r = launch_tile_scatter(P, ctx->sp[s].cell, ctx->sp[s].off, ctx->sp[s].u, n, ctx->d_cursor,
+                              cell_out, off_out, u_out, ctx->st);
+      if (r != cudaSuccess) return r;
+      r = cudaMemcpyAsync(ctx->sp[s].cell, cell_out, sizeof(int) * n, cudaMemcpyDeviceToDevice, ctx->st);
+      if (r != cudaSuccess) return r;
+      r = cudaMemcpyAsync(ctx->sp[s].off, off_out, sizeof(float) * D * n, cudaMemcpyDeviceToDevice,
+                          ctx->st);
+      if (r != cudaSuccess) return r;
+      r = cudaMemcpyAsync(ctx->sp[s].u, u_out, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, ctx->st);
+      if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+  });
+  if (e != cudaSuccess) return cuda_fail(ctx, "tile sort", e);
+  ctx->snapshot_valid = false;
+  return PIC_OK;
+}
+
+pic_status do_filter(pic_ctx* ctx, int passes) {
+  if (passes <= 0) return PIC_OK;
+  float* J = ctx->F + JX * ctx->g.plane;
+  if (!ctx->d_jtmp) PIC_CK(ctx, dalloc(&ctx->d_jtmp, 3 * (size_t)ctx->g.plane));
+  float* a = J;
+  float* b = ctx->d_jtmp;
+  for (int p = 0; p < passes; ++p) {
+    const cudaError_t e = timed(ctx, PIC_KERNEL_FILTER,
+                                [&]() { return launch_filter_f32(ctx->g, a, b, 3, ctx->st); });
+    if (e != cudaSuccess) return cuda_fail(ctx, "binomial filter", e);
+    float* t = a;
+    a = b;
+    b = t;
+  }
+  if (a != J)
+    PIC_CK(ctx, cudaMemcpyAsync(J, a, sizeof(float) * 3 * ctx->g.plane, cudaMemcpyDeviceToDevice,
+                                ctx->st));
+  return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* species, int nspecies,
+                    float c, float dt, float* fields, void* stream) {
+  g_init_error.clear();
+  if (!out) return set_err(nullptr, PIC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grid || !species || !fields) return set_err(nullptr, PIC_ERR_ARG, "grid, species or fields is NULL");
+  if (grid->dim < 1 || grid->dim > 3) return set_err(nullptr, PIC_ERR_ARG, "dim must be 1, 2 or 3");
+  long long ncell = 1;
+  for (int d = 0; d < 3; ++d) {
+    const int n = extent(*grid, d);
+    if (n < 1) return set_err(nullptr, PIC_ERR_ARG, "grid extents must be >= 1");
+    if (d >= grid->dim && n != 1)
+      return set_err(nullptr, PIC_ERR_ARG, "extents of non-gridded dimensions must be 1");
+    ncell *= n;
+  }
+  if (ncell > 0x7fffffffLL) return set_err(nullptr, PIC_ERR_ARG, "nx*ny*nz must fit in int32");
+  if (nspecies < 1 || nspecies > PIC_MAX_SPECIES)
+    return set_err(nullptr, PIC_ERR_ARG, "nspecies must be in 1..4");
+  if (!(c > 0.f && c < 1.f)) return set_err(nullptr, PIC_ERR_ARG, "Courant number must be in (0, 1)");
+  if (dt != 1.0f) return set_err(nullptr, PIC_ERR_ARG, "dt must be 1 (code units)");
+  long long ntot = 0, nmax = 0;
+  for (int s = 0; s < nspecies; ++s) {
+    const pic_species& S = species[s];
+    if (S.n < 0 || S.n > 0x7fffffffLL)
+      return set_err(nullptr, PIC_ERR_ARG, "species n must be in [0, 2^31)");
+    if (S.n > 0 && (!S.cell || !S.off || !S.u))
+      return set_err(nullptr, PIC_ERR_ARG, "species buffers are NULL");
+    if (!(S.m > 0.f) || !std::isfinite(S.m) || !std::isfinite(S.q))
+      return set_err(nullptr, PIC_ERR_ARG, "species mass must be > 0 and charge finite");
+    ntot += S.n;
+    nmax = S.n > nmax ? S.n : nmax;
+  }
+
+  pic_ctx* ctx = new pic_ctx();
+  ctx->grid = *grid;
+  ctx->ns = nspecies;
+  for (int s = 0; s < nspecies; ++s) ctx->sp[s] = species[s];
+  ctx->c = c;
+  ctx->F = fields;
+  ctx->st = (cudaStream_t)stream;
+  ctx->ntot = ntot;
+  ctx->nmax = nmax;
+  ctx->g.dim = grid->dim;
+  ctx->g.n[0] = grid->nx;
+  ctx->g.n[1] = grid->ny;
+  ctx->g.n[2] = grid->nz;
+  ctx->g.plane = ncell;
+  ctx->g.c = c;
+  // defaults: tiles of 64 cells in 1D, 16^2 in 2D, 8^3 in 3D; sort every 20 steps
+  ctx->tun.tile[0] = grid->dim == 1 ? 64 : grid->dim == 2 ? 16 : 8;
+  ctx->tun.tile[1] = grid->dim == 2 ? 16 : 8;
+  ctx->tun.tile[2] = 8;
+  ctx->tun.halo = grid->dim == 3 ? 2 : 3;
+  ctx->tun.sort_every = 20;
+  ctx->tun.filter_passes = 0;
+  ctx->tun.chunk = 8192;
+  const std::string msg = derive_tiles(ctx->grid, ctx->tun, ntot, &ctx->tile, &ctx->splits);
+  if (!msg.empty()) {
+    delete ctx;
+    return set_err(nullptr, PIC_ERR_ARG, msg);
+  }
+  pic_status s = PIC_OK;
+  cudaError_t e = cudaSuccess;
+  if ((e = set_particle_smem_limit(200 * 1024)) != cudaSuccess) {
+    s = cuda_fail(nullptr, "cudaFuncSetAttribute", e);
+  } else if ((e = dalloc(&ctx->d_status, 1)) != cudaSuccess ||
+             (e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->st)) != cudaSuccess) {
+    s = cuda_fail(nullptr, "status word", e);
+  } else if ((e = dalloc((char**)&ctx->d_sortbuf, (size_t)nmax * (4 + 4 * grid->dim + 12))) !=
+             cudaSuccess) {
+    s = cuda_fail(nullptr, "sort buffer", e);
+  } else if ((s = alloc_tiles(ctx)) != PIC_OK || (s = do_sort(ctx)) != PIC_OK) {
+    g_init_error = ctx->err;
+  }
+  if (s != PIC_OK) {
+    cudaStreamSynchronize(ctx->st);
+    free_all(ctx);
+    delete ctx;
+    return s;
+  }
+  *out = ctx;
+  return PIC_OK;
+}
+
+pic_status pic_get_tuning(pic_ctx* ctx, pic_tuning* out) {
+  if (!ctx || !out) return set_err(ctx, PIC_ERR_ARG, "NULL argument");
+  *out = ctx->tun;
+  return PIC_OK;
+}
+
+pic_status pic_set_tuning(pic_ctx* ctx, const pic_tuning* t) {
+  if (!ctx || !t) return set_err(ctx, PIC_ERR_ARG, "NULL argument");
+  pic_tuning nt = ctx->tun;
+  for (int d = 0; d < 3; ++d)
+    if (t->tile[d]) nt.tile[d] = t->tile[d];
+  if (t->halo) nt.halo = t->halo;
+  if (t->sort_every) nt.sort_every = t->sort_every;
+  if (t->filter_passes) nt.filter_passes = t->filter_passes;
+  if (t->chunk) nt.chunk = t->chunk;
+  if (nt.sort_every < 1) return set_err(ctx, PIC_ERR_ARG, "sort_every must be >= 1");
+  if (nt.filter_passes < 0) return set_err(ctx, PIC_ERR_ARG, "filter_passes must be >= 0");
+  TileDev td{};
+  int splits = 1;
+  const std::string msg = derive_tiles(ctx->grid, nt, ctx->ntot, &td, &splits);
+  if (!msg.empty()) return set_err(ctx, PIC_ERR_ARG, msg);
+  const bool retile = std::memcmp(&td, &ctx->tile, sizeof(TileDev)) != 0;
+  ctx->tun = nt;
+  ctx->splits = splits;
+  if (retile) {
+    PIC_CK(ctx, cudaStreamSynchronize(ctx->st));
+    ctx->tile = td;
+    pic_status s = alloc_tiles(ctx);
+    if (s != PIC_OK) return s;
+    return do_sort(ctx);
+  }
+  return PIC_OK;
+}
+
+pic_status pic_sort(pic_ctx* ctx) {
+  if (!ctx) return PIC_ERR_ARG;
+  return do_sort(ctx);
+}
+
+pic_status pic_gather_push(pic_ctx* ctx) {
+  if (!ctx) return PIC_ERR_ARG;
+  if (!ctx->d_cell_old) {
+    PIC_CK(ctx, dalloc(&ctx->d_cell_old, (size_t)ctx->ntot));
+    PIC_CK(ctx, dalloc(&ctx->d_off_old, (size_t)ctx->ntot * ctx->grid.dim));
+  }
+  const PushParams P = make_params(ctx);
+  const cudaError_t e = timed(ctx, PIC_KERNEL_PUSH,
+                              [&]() { return launch_particles(ctx->grid.dim, 1, P, ctx->st); });
+  if (e != cudaSuccess) return cuda_fail(ctx, "gather/push kernel", e);
+  ctx->snapshot_valid = true;
+  return PIC_OK;
+}
+
+pic_status pic_deposit(pic_ctx* ctx) {
+  if (!ctx) return PIC_ERR_ARG;
+  if (!ctx->snapshot_valid)
+    return set_err(ctx, PIC_ERR_STATE, "pic_deposit needs a preceding pic_gather_push");
+  const PushParams P = make_params(ctx);
+  const cudaError_t e = timed(ctx, PIC_KERNEL_PUSH,
+                              [&]() { return launch_particles(ctx->grid.dim, 2, P, ctx->st); });
+  if (e != cudaSuccess) return cuda_fail(ctx, "deposit kernel", e);
+  return PIC_OK;
+}
+
+pic_status pic_filter_current(pic_ctx* ctx, int passes) {
+  if (!ctx) return PIC_ERR_ARG;
+  if (passes < 0) return set_err(ctx, PIC_ERR_ARG, "passes must be >= 0");
+  return do_filter(ctx, passes);
+}
+
+pic_status pic_field_update(pic_ctx* ctx, int which) {
+  if (!ctx) return PIC_ERR_ARG;
+  cudaError_t e;
+  if (which == PIC_FIELD_B_HALF)
+    e = timed(ctx, PIC_KERNEL_BHALF, [&]() { return launch_b_half(ctx->g, ctx->F, 0, ctx->st); });
+  else if (which == PIC_FIELD_E)
+    e = timed(ctx, PIC_KERNEL_EUPD, [&]() { return launch_e_update(ctx->g, ctx->F, ctx->st); });
+  else
+    return set_err(ctx, PIC_ERR_ARG, "which must be PIC_FIELD_B_HALF or PIC_FIELD_E");
+  if (e != cudaSuccess) return cuda_fail(ctx, "field update", e);
+  return PIC_OK;
+}
+
+pic_status pic_step(pic_ctx* ctx, int nsteps) {
+  if (!ctx) return PIC_ERR_ARG;
+  if (nsteps < 0) return set_err(ctx, PIC_ERR_ARG, "nsteps must be >= 0");
+  const PushParams P = make_params(ctx);
+  for (int it = 0; it < nsteps; ++it) {
+    if (ctx->steps > 0 && ctx->steps % ctx->tun.sort_every == 0) {
+      const pic_status s = do_sort(ctx);
+      if (s != PIC_OK) return s;
+    }
+    cudaError_t e = timed(ctx, PIC_KERNEL_BHALF, [&]() { return launch_b_half(ctx->g, ctx->F, 1, ctx->st); });
+    if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
+    e = timed(ctx, PIC_KERNEL_PUSH, [&]() { return launch_particles(ctx->grid.dim, 0, P, ctx->st); });
+    if (e != cudaSuccess) return cuda_fail(ctx, "gather/push/deposit kernel", e);
+    e = timed(ctx, PIC_KERNEL_BHALF, [&]() { return launch_b_half(ctx->g, ctx->F, 0, ctx->st); });
+    if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
+    const pic_status s = do_filter(ctx, ctx->tun.filter_passes);
+    if (s != PIC_OK) return s;
+    e = timed(ctx, PIC_KERNEL_EUPD, [&]() { return launch_e_update(ctx->g, ctx->F, ctx->st); });
+    if (e != cudaSuccess) return cuda_fail(ctx, "E update", e);
+    ++ctx->steps;
+  }
+  ctx->snapshot_valid = false;
+  return PIC_OK;
+}
+
+pic_status pic_energies(pic_ctx* ctx, double* out, int nout) {
+  if (!ctx || !out) return set_err(ctx, PIC_ERR_ARG, "NULL argument");
+  const int ns = ctx->ns;
+  if (nout < 4 + ns) return set_err(ctx, PIC_ERR_ARG, "nout must be >= 4 + nspecies");
+  const long long P = ctx->g.plane;
+  if (!ctx->d_acc) {
+    PIC_CK(ctx, dalloc(&ctx->d_acc, 4 + PIC_MAX_SPECIES));
+    PIC_CK(ctx, dalloc(&ctx->d_rho, (size_t)P));
+    PIC_CK(ctx, dalloc(&ctx->d_rho2, (size_t)P));
+  }
+  PIC_CK(ctx, cudaMemsetAsync(ctx->d_acc, 0, sizeof(double) * (4 + PIC_MAX_SPECIES), ctx->st));
+  PIC_CK(ctx, cudaMemsetAsync(ctx->d_rho, 0, sizeof(double) * P, ctx->st));
+  PIC_CK(ctx, launch_field_energy(ctx->g, ctx->F, ctx->d_acc, ctx->st));
+  const double c2 = (double)ctx->c * (double)ctx->c;
+  for (int s = 0; s < ns; ++s) {
+    PIC_CK(ctx, launch_kinetic(ctx->sp[s].u, ctx->sp[s].n, (double)ctx->sp[s].m * c2,
+                               ctx->d_acc + 2 + s, ctx->st));
+    PIC_CK(ctx, launch_rho(ctx->g, ctx->sp[s].cell, ctx->sp[s].off, ctx->sp[s].n,
+                           (double)ctx->sp[s].q, ctx->d_rho, ctx->st));
+  }
+  double* a = ctx->d_rho;
+  double* b = ctx->d_rho2;
+  for (int p = 0; p < ctx->tun.filter_passes; ++p) {
+    PIC_CK(ctx, launch_filter_f64(ctx->g, a, b, 1, ctx->st));
+    double* t = a;
+    a = b;
+    b = t;
+  }
+  PIC_CK(ctx, launch_gauss(ctx->g, ctx->F, a, (unsigned long long*)(ctx->d_acc + 2 + ns),
+                           ctx->d_acc + 3 + ns, ctx->st));
+  double h[4 + PIC_MAX_SPECIES];
+  PIC_CK(ctx, cudaMemcpyAsync(h, ctx->d_acc, sizeof(double) * (4 + ns), cudaMemcpyDeviceToHost, ctx->st));
+  PIC_CK(ctx, cudaStreamSynchronize(ctx->st));
+  for (int i = 0; i < 3 + ns; ++i) out[i] = h[i];
+  out[3 + ns] = std::sqrt(h[3 + ns] / (double)P);
+  return PIC_OK;
+}
+
+pic_status pic_check(pic_ctx* ctx) {
+  if (!ctx) return PIC_ERR_ARG;
+  int h = 0;
+  PIC_CK(ctx, cudaMemcpyAsync(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  PIC_CK(ctx, cudaStreamSynchronize(ctx->st));
+  if (h == 0) return PIC_OK;
+  PIC_CK(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->st));
+  PIC_CK(ctx, cudaStreamSynchronize(ctx->st));
+  std::string m = "invalid particle data:";
+  if (h & ST_BAD_CELL) m += " cell index out of range;";
+  if (h & ST_BAD_OFF) m += " offset outside [0,1);";
+  if (h & ST_BAD_U) m += " non-finite four-velocity;";
+  return set_err(ctx, PIC_ERR_STATE, m);
+}
+
+pic_status pic_step_host(pic_ctx* ctx, const pic_host_species* hs, float* host_fields, int nsteps) {
+  if (!ctx || !hs || !host_fields) return set_err(ctx, PIC_ERR_ARG, "NULL argument");
+  const int D = ctx->grid.dim;
+  for (int s = 0; s < ctx->ns; ++s)
+    if (ctx->sp[s].n > 0 && (!hs[s].cell || !hs[s].off || !hs[s].u))
+      return set_err(ctx, PIC_ERR_ARG, "host species buffers are NULL");
+  const cudaMemcpyKind h2d = cudaMemcpyHostToDevice, d2h = cudaMemcpyDeviceToHost;
+  for (int s = 0; s < ctx->ns; ++s) {
+    const long long n = ctx->sp[s].n;
+    if (n == 0) continue;
+    PIC_CK(ctx, cudaMemcpyAsync(ctx->sp[s].cell, hs[s].cell, 4 * n, h2d, ctx->st));
+    PIC_CK(ctx, cudaMemcpyAsync(ctx->sp[s].off, hs[s].off, 4 * D * n, h2d, ctx->st));
+    PIC_CK(ctx, cudaMemcpyAsync(ctx->sp[s].u, hs[s].u, 12 * n, h2d, ctx->st));
+  }
+  PIC_CK(ctx, cudaMemcpyAsync(ctx->F, host_fields, 36 * ctx->g.plane, h2d, ctx->st));
+  const pic_status s = pic_step(ctx, nsteps);
+  if (s != PIC_OK) return s;
+  for (int sp = 0; sp < ctx->ns; ++sp) {
+    const long long n = ctx->sp[sp].n;
+    if (n == 0) continue;
+    PIC_CK(ctx, cudaMemcpyAsync(hs[sp].cell, ctx->sp[sp].cell, 4 * n, d2h, ctx->st));
+    PIC_CK(ctx, cudaMemcpyAsync(hs[sp].off, ctx->sp[sp].off, 4 * D * n, d2h, ctx->st));
+    PIC_CK(ctx, cudaMemcpyAsync(hs[sp].u, ctx->sp[sp].u, 12 * n, d2h, ctx->st));
+  }
+  PIC_CK(ctx, cudaMemcpyAsync(host_fields, ctx->F, 36 * ctx->g.plane, d2h, ctx->st));
+  PIC_CK(ctx, cudaStreamSynchronize(ctx->st));
+  return PIC_OK;
+}
+
+pic_status pic_timing(pic_ctx* ctx, int enable) {
+  if (!ctx) return PIC_ERR_ARG;
+  ctx->timing = enable != 0;
+  return PIC_OK;
+}
+
+pic_status pic_kernel_times(pic_ctx* ctx, double* ms, int64_t* launches) {
+  if (!ctx || !ms || !launches) return set_err(ctx, PIC_ERR_ARG, "NULL argument");
+  PIC_CK(ctx, cudaStreamSynchronize(ctx->st));
+  for (auto& t : ctx->pending) {
+    float v = 0.f;
+    PIC_CK(ctx, cudaEventElapsedTime(&v, t.a, t.b));
+    ctx->ms[t.kind] += v;
+    ctx->launches[t.kind] += 1;
+    ctx->pool.push_back(t.a);
+    ctx->pool.push_back(t.b);
+  }
+  ctx->pending.clear();
+  for (int k = 0; k < PIC_KERNEL_KINDS; ++k) {
+    ms[k] = ctx->ms[k];
+    launches[k] = ctx->launches[k];
+    ctx->ms[k] = 0.0;
+    ctx->launches[k] = 0;
+  }
+  return PIC_OK;
+}
+
+pic_status pic_destroy(pic_ctx* ctx) {
+  if (!ctx) return PIC_ERR_ARG;
+  cudaStreamSynchronize(ctx->st);
+  free_all(ctx);
+  delete ctx;
+  return PIC_OK;
+}
+
+const char* pic_last_error(const pic_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,276 @@
+// Device-side building blocks of the PIC step (arXiv:1906.06306): lattice
+// indexing, field accessors, linear gather, Boris push, position update and
+// ZigZag current.  Everything is FP32 in cell-relative coordinates: a particle
+// is (int cell, float offset in [0,1) per gridded axis), so the arithmetic of
+// gather and deposit never sees the absolute position.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pic {
+
+enum { EX = 0, EY, EZ, BX, BY, BZ, JX, JY, JZ };
+
+// device status word bits (pic_check)
+enum : int { ST_BAD_CELL = 1, ST_BAD_OFF = 2, ST_BAD_U = 4 };
+
+struct GridDev {
+  int dim;
+  int n[3];          // cells per axis (1 for non-gridded axes)
+  long long plane;   // n0*n1*n2
+  float c;           // Courant number
+};
+
+struct TileDev {
+  int T[3];    // cells per tile (1 on non-gridded axes)
+  int nt[3];   // tiles per axis
+  int H;       // halo staged on the low side; H+1 on the high side
+  int W[3];    // window extent T + 2H + 1 (1 on non-gridded axes)
+  int wcells;  // W0*W1*W2
+  int ntiles;
+};
+
+struct SpeciesDev {
+  float q;            // macro-particle charge
+  float qm;           // q/m, the s-hat of Appendix C
+  long long n;
+  int* cell;
+  float* off;         // [D][n]
+  float* u;           // [3][n]
+  const int* tstart;  // [ntiles+1] tile bucket offsets
+  int* cell_old;      // pre-move snapshot (split gather/deposit path)
+  float* off_old;     // [D][n]
+};
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+// Periodic image of a lattice index that is at most one period away.
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// Shared-memory window of a tile: 6 field components then Jx, Jy, Jz, each a
+// W0 x W1 x W2 block, x fastest.  Indices are window-local.
+struct SmemAcc {
+  float* s;
+  int W0, W01, wcells;
+  __device__ __forceinline__ float ld(int comp, int i, int j, int k) const {
+    return s[comp * wcells + i + W0 * j + W01 * k];
+  }
+  __device__ __forceinline__ void add(int comp, int i, int j, int k, float v) const {
+    atomicAdd(&s[comp * wcells + i + W0 * j + W01 * k], v);
+  }
+};
+
+// Global field planes with periodic wrap; indices are lattice indices that may
+// lie up to one period outside [0, n).
+struct GlobAcc {
+  float* F;
+  long long plane;
+  int n0, n1, n2;
+  __device__ __forceinline__ long long at(int i, int j, int k) const {
+    return (long long)wrapi(i, n0) + (long long)n0 * (wrapi(j, n1) + (long long)n1 * wrapi(k, n2));
+  }
+  __device__ __forceinline__ float ld(int comp, int i, int j, int k) const {
+    return __ldg(&F[comp * plane + at(i, j, k)]);
+  }
+  __device__ __forceinline__ void add(int comp, int i, int j, int k, float v) const {
+    atomicAdd(&F[comp * plane + at(i, j, k)], v);
+  }
+};
+
+// Linear interpolation (LinearInterpolator, Sect. 2.3.2) of one staggered
+// component.  `stag` has bit d set when the component sits half a cell up axis
+// d (Sect. 2.3.1); b is the particle's cell in accessor coordinates, o its
+// offsets.  A half-staggered axis uses the lattice points below/above x - 1/2.
+template <int D, class Acc>
+__device__ __forceinline__ float interp1(const Acc& A, int comp, int stag, const int* b,
+                                         const float* o) {
+  int i0[3] = {0, 0, 0};
+  float w[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    if (stag & (1 << d)) {
+      const bool up = o[d] >= 0.5f;
+      i0[d] = up ? b[d] : b[d] - 1;
+      w[d] = up ? o[d] - 0.5f : o[d] + 0.5f;
+    } else {
+      i0[d] = b[d];
+      w[d] = o[d];
+    }
+  }
+  if (D == 1) {
+    const float f0 = A.ld(comp, i0[0], 0, 0), f1 = A.ld(comp, i0[0] + 1, 0, 0);
+    return fmaf(w[0], f1 - f0, f0);
+  } else if (D == 2) {
+    const float f00 = A.ld(comp, i0[0], i0[1], 0), f10 = A.ld(comp, i0[0] + 1, i0[1], 0);
+    const float f01 = A.ld(comp, i0[0], i0[1] + 1, 0), f11 = A.ld(comp, i0[0] + 1, i0[1] + 1, 0);
+    const float a = fmaf(w[0], f10 - f00, f00), c = fmaf(w[0], f11 - f01, f01);
+    return fmaf(w[1], c - a, a);
+  } else {
+    float r[2];
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      const int k = i0[2] + kk;
+      const float f00 = A.ld(comp, i0[0], i0[1], k), f10 = A.ld(comp, i0[0] + 1, i0[1], k);
+      const float f01 = A.ld(comp, i0[0], i0[1] + 1, k), f11 = A.ld(comp, i0[0] + 1, i0[1] + 1, k);
+      const float a = fmaf(w[0], f10 - f00, f00), c = fmaf(w[0], f11 - f01, f01);
+      r[kk] = fmaf(w[1], c - a, a);
+    }
+    return fmaf(w[2], r[1] - r[0], r[0]);
+  }
+}
+
+// E and B at the particle: Ex (1/2,0,0) Ey (0,1/2,0) Ez (0,0,1/2)
+// Bx (0,1/2,1/2) By (1/2,0,1/2) Bz (1/2,1/2,0).
+template <int D, class Acc>
+__device__ __forceinline__ void gather(const Acc& A, const int* b, const float* o, float* e,
+                                       float* bf) {
+  e[0] = interp1<D>(A, EX, 1, b, o);
+  e[1] = interp1<D>(A, EY, 2, b, o);
+  e[2] = interp1<D>(A, EZ, 4, b, o);
+  bf[0] = interp1<D>(A, BX, 6, b, o);
+  bf[1] = interp1<D>(A, BY, 5, b, o);
+  bf[2] = interp1<D>(A, BZ, 3, b, o);
+}
+
+// Relativistic Boris scheme, Appendix C: u1 = c u + (s/2) E,
+// gamma1 = sqrt(1 + u1^2/c^2), t = s B / (2 c gamma1), f = 2/(1 + t^2),
+// u2 = f (u1 + u1 x t), u3 = u1 + u2 x t + (s/2) E, u <- u3 / c.
+__device__ __forceinline__ void boris(float* u, const float* e, const float* b, float qm, float c,
+                                      float inv_c, float inv_c2) {
+  const float hs = 0.5f * qm;
+  float u1[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u1[a] = fmaf(c, u[a], hs * e[a]);
+  const float g1 = sqrtf(fmaf(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2], inv_c2, 1.0f));
+  const float tf = hs * inv_c / g1;
+  const float t0 = tf * b[0], t1 = tf * b[1], t2 = tf * b[2];
+  const float f = 2.0f / fmaf(t0, t0, fmaf(t1, t1, fmaf(t2, t2, 1.0f)));
+  const float v0 = f * (u1[0] + (u1[1] * t2 - u1[2] * t1));
+  const float v1 = f * (u1[1] + (u1[2] * t0 - u1[0] * t2));
+  const float v2 = f * (u1[2] + (u1[0] * t1 - u1[1] * t0));
+  u[0] = (u1[0] + (v1 * t2 - v2 * t1) + hs * e[0]) * inv_c;
+  u[1] = (u1[1] + (v2 * t0 - v0 * t2) + hs * e[1]) * inv_c;
+  u[2] = (u1[2] + (v0 * t1 - v1 * t0) + hs * e[2]) * inv_c;
+}
+
+// Position update of Eq. (fdX), x += c u / gamma, on the offsets, with every
+// operation rounded separately (no contraction) so the cell bookkeeping can be
+// replayed bit for bit: gamma = sqrt(((1 + ux^2) + uy^2) + uz^2),
+// dx = (c u) / gamma, o2 = o1 + dx; o2 < 0 moves one cell down (o2 += 1), o2 >= 1
+// one cell up (o2 -= 1); an o2 + 1 that rounds to 1 is the lower cell face, so
+// the particle stays with offset 0.  dn receives dx of every axis.
+template <int D>
+__device__ __forceinline__ void move(const float* u, const float* o1, float c, float* o2, int* dc,
+                                     float* dn) {
+  const float g2 = __fadd_rn(__fadd_rn(__fadd_rn(1.0f, __fmul_rn(u[0], u[0])), __fmul_rn(u[1], u[1])),
+                             __fmul_rn(u[2], u[2]));
+  const float gam = __fsqrt_rn(g2);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dn[a] = __fdiv_rn(__fmul_rn(c, u[a]), gam);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    float o = __fadd_rn(o1[d], dn[d]);
+    int k = 0;
+    if (o < 0.0f) {
+      o = __fadd_rn(o, 1.0f);
+      k = -1;
+      if (o >= 1.0f) {
+        o = 0.0f;
+        k = 0;
+      }
+    } else if (o >= 1.0f) {
+      o = __fadd_rn(o, -1.0f);
+      k = 1;
+    }
+    o2[d] = o;
+    dc[d] = k;
+  }
+}
+
+// One ZigZag segment (Appendix D) from the cell with lower corner I: flux
+// q*Dl, weights W (segment midpoint minus I).  A current component goes to
+// index I along its own axis and is split (1-W, W) along every other gridded
+// axis.  In 3D the transverse product is the average along the straight
+// segment, midpoint product +- Dl_b Dl_c / 12, which keeps the first-order
+// charge exactly conserved.
+template <int D, class Acc>
+__device__ __forceinline__ void zz_segment(const Acc& A, const int* I, const float* Dl,
+                                           const float* W, float q) {
+  const float f0 = q * Dl[0], f1 = q * Dl[1], f2 = q * Dl[2];
+  if (D == 1) {
+    A.add(JX, I[0], 0, 0, f0);
+    A.add(JY, I[0], 0, 0, f1 * (1.0f - W[0]));
+    A.add(JY, I[0] + 1, 0, 0, f1 * W[0]);
+    A.add(JZ, I[0], 0, 0, f2 * (1.0f - W[0]));
+    A.add(JZ, I[0] + 1, 0, 0, f2 * W[0]);
+  } else if (D == 2) {
+    const float wx = W[0], wy = W[1], mx = 1.0f - W[0], my = 1.0f - W[1];
+    A.add(JX, I[0], I[1], 0, f0 * my);
+    A.add(JX, I[0], I[1] + 1, 0, f0 * wy);
+    A.add(JY, I[0], I[1], 0, f1 * mx);
+    A.add(JY, I[0] + 1, I[1], 0, f1 * wx);
+    A.add(JZ, I[0], I[1], 0, f2 * (mx * my));
+    A.add(JZ, I[0] + 1, I[1], 0, f2 * (wx * my));
+    A.add(JZ, I[0], I[1] + 1, 0, f2 * (mx * wy));
+    A.add(JZ, I[0] + 1, I[1] + 1, 0, f2 * (wx * wy));
+  } else {
+    const float wx = W[0], wy = W[1], wz = W[2];
+    const float mx = 1.0f - wx, my = 1.0f - wy, mz = 1.0f - wz;
+    const float cyz = Dl[1] * Dl[2] * (1.0f / 12.0f);
+    const float czx = Dl[2] * Dl[0] * (1.0f / 12.0f);
+    const float cxy = Dl[0] * Dl[1] * (1.0f / 12.0f);
+    // Jx: transverse axes (y, z)
+    A.add(JX, I[0], I[1], I[2], f0 * (my * mz + cyz));
+    A.add(JX, I[0], I[1] + 1, I[2], f0 * (wy * mz - cyz));
+    A.add(JX, I[0], I[1], I[2] + 1, f0 * (my * wz - cyz));
+    A.add(JX, I[0], I[1] + 1, I[2] + 1, f0 * (wy * wz + cyz));
+    // Jy: transverse axes (z, x)
+    A.add(JY, I[0], I[1], I[2], f1 * (mz * mx + czx));
+    A.add(JY, I[0], I[1], I[2] + 1, f1 * (wz * mx - czx));
+    A.add(JY, I[0] + 1, I[1], I[2], f1 * (mz * wx - czx));
+    A.add(JY, I[0] + 1, I[1], I[2] + 1, f1 * (wz * wx + czx));
+    // Jz: transverse axes (x, y)
+    A.add(JZ, I[0], I[1], I[2], f2 * (mx * my + cxy));
+    A.add(JZ, I[0] + 1, I[1], I[2], f2 * (wx * my - cxy));
+    A.add(JZ, I[0], I[1] + 1, I[2], f2 * (mx * wy - cxy));
+    A.add(JZ, I[0] + 1, I[1] + 1, I[2], f2 * (wx * wy + cxy));
+  }
+}
+
+// ZigZag current of one move (Appendix D), in coordinates relative to the
+// lower corner b of the old cell: x1 = o1, x2 = dc + o2 on gridded axes; the
+// relay point x_r = min(min(0, dc) + 1, max(max(0, dc), (x1 + x2)/2)); the
+// segments carry x_r - x1 and x2 - x_r with weights (x1 + x_r)/2 and
+// (x2 + x_r)/2 - dc.  A non-gridded axis moves by dn, split evenly.
+template <int D, class Acc>
+__device__ __forceinline__ void zigzag(const Acc& A, const int* b, const int* dc, const float* o1,
+                                       const float* o2, const float* dn, float q) {
+  float D1[3], D2[3], W1[3] = {0.f, 0.f, 0.f}, W2[3] = {0.f, 0.f, 0.f};
+  int b2[3] = {b[0], b[1], b[2]};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (d < D) {
+      const float x1 = o1[d];
+      const float x2 = (float)dc[d] + o2[d];
+      const float lo = (float)(dc[d] < 0 ? dc[d] : 0) + 1.0f;
+      const float hi = (float)(dc[d] > 0 ? dc[d] : 0);
+      const float xr = fminf(lo, fmaxf(hi, 0.5f * (x1 + x2)));
+      D1[d] = xr - x1;
+      D2[d] = x2 - xr;
+      W1[d] = 0.5f * (x1 + xr);
+      W2[d] = 0.5f * (x2 + xr) - (float)dc[d];
+      b2[d] = b[d] + dc[d];
+    } else {
+      D1[d] = 0.5f * dn[d];
+      D2[d] = D1[d];
+    }
+  }
+  zz_segment<D>(A, b, D1, W1, q);
+  zz_segment<D>(A, b2, D2, W2, q);
+}
+
+}  // namespace pic

@@ -1,0 +1,173 @@
+// FDTD2 field update and Binomial2 current filter (arXiv:1906.06306,
+// Sect. 2.3.1, Eqs. (fdE), (fdB), Table 2) on periodic Yee planes.
+// One thread per lattice point, x fastest, so every plane is streamed with
+// coalesced loads; neighbours one point away come from the same or adjacent
+// rows and hit L1/L2.
+#include "pic_kernels.h"
+
+namespace pic {
+
+static unsigned grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > (1LL << 20)) b = 1LL << 20;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+// B -= (c/2) curl+ E (forward differences: B sits half a cell above E), and,
+// when zero_j is set, clear J for the deposit that follows.
+template <int D>
+__global__ void k_b_half(float* __restrict__ F, const GridDev g, float hc, int zero_j) {
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const long long P = g.plane;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n0);
+    const long long r = idx / n0;
+    const int j = (int)(r % n1), k = (int)(r / n1);
+    const long long sx = (i + 1 < n0) ? 1 : 1 - n0;
+    const long long sy = (D >= 2) ? ((j + 1 < n1) ? n0 : (long long)n0 * (1 - n1)) : 0;
+    const long long sz = (D >= 3) ? ((k + 1 < n2) ? (long long)n0 * n1 : (long long)n0 * n1 * (1 - n2)) : 0;
+    const float* Ex = F + EX * P;
+    const float* Ey = F + EY * P;
+    const float* Ez = F + EZ * P;
+    const float ex = Ex[idx], ey = Ey[idx], ez = Ez[idx];
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    cy -= Ez[idx + sx] - ez;
+    cz += Ey[idx + sx] - ey;
+    if (D >= 2) {
+      cx += Ez[idx + sy] - ez;
+      cz -= Ex[idx + sy] - ex;
+    }
+    if (D >= 3) {
+      cx -= Ey[idx + sz] - ey;
+      cy += Ex[idx + sz] - ex;
+    }
+    F[BX * P + idx] = fmaf(-hc, cx, F[BX * P + idx]);
+    F[BY * P + idx] = fmaf(-hc, cy, F[BY * P + idx]);
+    F[BZ * P + idx] = fmaf(-hc, cz, F[BZ * P + idx]);
+    if (zero_j) {
+      F[JX * P + idx] = 0.f;
+      F[JY * P + idx] = 0.f;
+      F[JZ * P + idx] = 0.f;
+    }
+  }
+}
+
+// E += c curl- B - J (backward differences: E sits half a cell below B).
+template <int D>
+__global__ void k_e_update(float* __restrict__ F, const GridDev g, float c) {
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const long long P = g.plane;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n0);
+    const long long r = idx / n0;
+    const int j = (int)(r % n1), k = (int)(r / n1);
+    const long long sx = (i > 0) ? 1 : 1 - n0;
+    const long long sy = (D >= 2) ? ((j > 0) ? n0 : (long long)n0 * (1 - n1)) : 0;
+    const long long sz = (D >= 3) ? ((k > 0) ? (long long)n0 * n1 : (long long)n0 * n1 * (1 - n2)) : 0;
+    const float* Bx = F + BX * P;
+    const float* By = F + BY * P;
+    const float* Bz = F + BZ * P;
+    const float bx = Bx[idx], by = By[idx], bz = Bz[idx];
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    cy -= bz - Bz[idx - sx];
+    cz += by - By[idx - sx];
+    if (D >= 2) {
+      cx += bz - Bz[idx - sy];
+      cz -= bx - Bx[idx - sy];
+    }
+    if (D >= 3) {
+      cx -= by - By[idx - sz];
+      cy += bx - Bx[idx - sz];
+    }
+    F[EX * P + idx] = fmaf(c, cx, F[EX * P + idx]) - F[JX * P + idx];
+    F[EY * P + idx] = fmaf(c, cy, F[EY * P + idx]) - F[JY * P + idx];
+    F[EZ * P + idx] = fmaf(c, cz, F[EZ * P + idx]) - F[JZ * P + idx];
+  }
+}
+
+// One Binomial2 pass: (1/4, 1/2, 1/4) along x, then y, then z (gridded axes),
+// evaluated as the separable 3^D stencil in that order.
+template <int D, typename T>
+__global__ void k_filter(const T* __restrict__ src, T* __restrict__ dst, const GridDev g,
+                         int ncomp) {
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const long long P = g.plane;
+  const T q = T(0.25), h = T(0.5);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P * ncomp;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long comp = idx / P, cidx = idx - comp * P;
+    const int i = (int)(cidx % n0);
+    const long long r = cidx / n0;
+    const int j = (int)(r % n1), k = (int)(r / n1);
+    const T* s = src + comp * P;
+    const int im = i > 0 ? i - 1 : n0 - 1, ip = i + 1 < n0 ? i + 1 : 0;
+    auto row = [&](int jj, int kk) -> T {
+      const long long base = (long long)n0 * (jj + (long long)n1 * kk);
+      return q * s[base + im] + h * s[base + i] + q * s[base + ip];
+    };
+    T out;
+    if (D == 1) {
+      out = row(0, 0);
+    } else {
+      const int jm = j > 0 ? j - 1 : n1 - 1, jp = j + 1 < n1 ? j + 1 : 0;
+      auto plane_ = [&](int kk) -> T { return q * row(jm, kk) + h * row(j, kk) + q * row(jp, kk); };
+      if (D == 2) {
+        out = plane_(0);
+      } else {
+        const int km = k > 0 ? k - 1 : n2 - 1, kp = k + 1 < n2 ? k + 1 : 0;
+        out = q * plane_(km) + h * plane_(k) + q * plane_(kp);
+      }
+    }
+    dst[idx] = out;
+  }
+}
+
+cudaError_t launch_b_half(const GridDev& g, float* F, int zero_j, cudaStream_t st) {
+  const unsigned nb = grid_for(g.plane, 256);
+  const float hc = 0.5f * g.c;
+  switch (g.dim) {
+    case 1: k_b_half<1><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
+    case 2: k_b_half<2><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
+    case 3: k_b_half<3><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_e_update(const GridDev& g, float* F, cudaStream_t st) {
+  const unsigned nb = grid_for(g.plane, 256);
+  switch (g.dim) {
+    case 1: k_e_update<1><<<nb, 256, 0, st>>>(F, g, g.c); break;
+    case 2: k_e_update<2><<<nb, 256, 0, st>>>(F, g, g.c); break;
+    case 3: k_e_update<3><<<nb, 256, 0, st>>>(F, g, g.c); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_filter(const GridDev& g, const T* src, T* dst, int ncomp,
+                                 cudaStream_t st) {
+  const unsigned nb = grid_for(g.plane * ncomp, 256);
+  switch (g.dim) {
+    case 1: k_filter<1, T><<<nb, 256, 0, st>>>(src, dst, g, ncomp); break;
+    case 2: k_filter<2, T><<<nb, 256, 0, st>>>(src, dst, g, ncomp); break;
+    case 3: k_filter<3, T><<<nb, 256, 0, st>>>(src, dst, g, ncomp); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_filter_f32(const GridDev& g, const float* src, float* dst, int ncomp,
+                              cudaStream_t st) {
+  return launch_filter<float>(g, src, dst, ncomp, st);
+}
+
+cudaError_t launch_filter_f64(const GridDev& g, const double* src, double* dst, int ncomp,
+                              cudaStream_t st) {
+  return launch_filter<double>(g, src, dst, ncomp, st);
+}
+
+}  // namespace pic

@@ -1,0 +1,60 @@
+// Host-side launchers of the PIC kernels (internal to libpic).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pic_dev.cuh"
+
+namespace pic {
+
+constexpr int kMaxSpecies = 4;
+constexpr int kPushThreads = 256;
+
+struct PushParams {
+  GridDev g;
+  TileDev t;
+  float* F;
+  int nspecies;
+  SpeciesDev sp[kMaxSpecies];
+  int splits;   // thread blocks per tile
+  int* status;
+  float inv_c, inv_c2;
+};
+
+// mode 0: fused gather + push + move + deposit; 1: gather + push + move and
+// pre-move snapshot; 2: deposit from the snapshot and the stored new u.
+cudaError_t launch_particles(int dim, int mode, const PushParams& P, cudaStream_t st);
+cudaError_t set_particle_smem_limit(int bytes);
+size_t particle_smem_bytes(const TileDev& t);
+
+cudaError_t launch_b_half(const GridDev& g, float* F, int zero_j, cudaStream_t st);
+cudaError_t launch_e_update(const GridDev& g, float* F, cudaStream_t st);
+// one Binomial2 pass over ncomp consecutive planes src -> dst
+cudaError_t launch_filter_f32(const GridDev& g, const float* src, float* dst, int ncomp,
+                              cudaStream_t st);
+cudaError_t launch_filter_f64(const GridDev& g, const double* src, double* dst, int ncomp,
+                              cudaStream_t st);
+
+struct SortParams {
+  GridDev g;
+  TileDev t;
+  int* status;
+};
+cudaError_t launch_tile_count(const SortParams& P, const int* cell, long long n, int* count,
+                              cudaStream_t st);
+cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* cursor,
+                             cudaStream_t st);
+cudaError_t launch_tile_scatter(const SortParams& P, const int* cell, const float* off,
+                                const float* u, long long n, int* cursor, int* cell_out,
+                                float* off_out, float* u_out, cudaStream_t st);
+
+// diagnostics: acc[0] += 0.5 sum E^2, acc[1] += 0.5 sum B^2
+cudaError_t launch_field_energy(const GridDev& g, const float* F, double* acc, cudaStream_t st);
+cudaError_t launch_kinetic(const float* u, long long n, double mc2, double* acc, cudaStream_t st);
+cudaError_t launch_rho(const GridDev& g, const int* cell, const float* off, long long n, double q,
+                       double* rho, cudaStream_t st);
+// acc_max (as the bit pattern of a non-negative double), acc_sq += sum res^2
+cudaError_t launch_gauss(const GridDev& g, const float* F, const double* rho,
+                         unsigned long long* acc_max, double* acc_sq, cudaStream_t st);
+
+}  // namespace pic

@@ -1,0 +1,147 @@
+// Counting sort of particles by spatial tile: the single-GPU stand-in for the
+// particle communication routines of Table 1 (arXiv:1906.06306), which move
+// particles to the tile that owns them.  count -> exclusive scan -> scatter.
+// Lanes of a warp that share a tile combine their atomic (match_any), so a
+// sorted or nearly sorted array costs about one global atomic per warp.
+#include "pic_kernels.h"
+
+namespace pic {
+
+__device__ __forceinline__ int tile_key(const SortParams& P, int cell) {
+  if (cell < 0 || (long long)cell >= P.g.plane) {
+    atomicOr(P.status, ST_BAD_CELL);
+    return 0;  // kept (in tile 0) so that no particle is lost
+  }
+  const int i = cell % P.g.n[0];
+  const int r = cell / P.g.n[0];
+  const int j = r % P.g.n[1], k = r / P.g.n[1];
+  return i / P.t.T[0] + P.t.nt[0] * (j / P.t.T[1] + P.t.nt[1] * (k / P.t.T[2]));
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Reserve `1` slot of counter[key] for every active lane; returns this lane's
+// slot.  Lanes with equal keys share one atomic.
+__device__ __forceinline__ int warp_reserve(int* counter, int key, unsigned active) {
+  const unsigned peers = __match_any_sync(active, key);
+  const int leader = __ffs(peers) - 1;
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&counter[key], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  return base + __popc(peers & lanemask_lt());
+}
+
+__global__ void k_tile_count(const SortParams P, const int* __restrict__ cell, long long n,
+                             int* count) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const long long p = base + threadIdx.x;
+    const bool act = p < n;
+    const unsigned active = __ballot_sync(0xffffffffu, act);
+    if (act) warp_reserve(count, tile_key(P, cell[p]), active);
+  }
+}
+
+// Exclusive scan of count[0..ntiles) into start[0..ntiles] (start[ntiles] =
+// total) and cursor = start, in one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_tile_scan(const int* __restrict__ count, int ntiles,
+                                                    int* start, int* cursor) {
+  __shared__ int warp_sums[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < ntiles; base += 1024) {
+    const int t = base + threadIdx.x;
+    const int v = t < ntiles ? count[t] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int s = warp_sums[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const int incl = x + (wid > 0 ? warp_sums[wid - 1] : 0) + carry;
+    if (t < ntiles) {
+      start[t] = incl - v;
+      cursor[t] = incl - v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) start[ntiles] = carry;
+}
+
+template <int D>
+__global__ void k_tile_scatter(const SortParams P, const int* __restrict__ cell,
+                               const float* __restrict__ off, const float* __restrict__ u,
+                               long long n, int* cursor, int* __restrict__ cell_out,
+                               float* __restrict__ off_out, float* __restrict__ u_out) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const long long p = base + threadIdx.x;
+    const bool act = p < n;
+    const unsigned active = __ballot_sync(0xffffffffu, act);
+    if (act) {
+      const int c = cell[p];
+      const long long q = warp_reserve(cursor, tile_key(P, c), active);
+      cell_out[q] = c;
+#pragma unroll
+      for (int d = 0; d < D; ++d) off_out[d * n + q] = off[d * n + p];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) u_out[a * n + q] = u[a * n + p];
+    }
+  }
+}
+
+static unsigned blocks_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 64) b = 152LL * 64;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_tile_count(const SortParams& P, const int* cell, long long n, int* count,
+                              cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_tile_count<<<blocks_for(n), 256, 0, st>>>(P, cell, n, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* cursor,
+                             cudaStream_t st) {
+  k_tile_scan<<<1, 1024, 0, st>>>(count, ntiles, start, cursor);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_scatter(const SortParams& P, const int* cell, const float* off,
+                                const float* u, long long n, int* cursor, int* cell_out,
+                                float* off_out, float* u_out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const unsigned nb = blocks_for(n);
+  switch (P.g.dim) {
+    case 1: k_tile_scatter<1><<<nb, 256, 0, st>>>(P, cell, off, u, n, cursor, cell_out, off_out, u_out); break;
+    case 2: k_tile_scatter<2><<<nb, 256, 0, st>>>(P, cell, off, u, n, cursor, cell_out, off_out, u_out); break;
+    case 3: k_tile_scatter<3><<<nb, 256, 0, st>>>(P, cell, off, u, n, cursor, cell_out, off_out, u_out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace pic

@@ -1,0 +1,169 @@
+"""Kernel-level parity of the CUDA path (through the C ABI) with the FP64
+oracle: FDTD2 updates, Binomial2 filter, gather + Boris + move, ZigZag deposit
+and the tile sort.  Sizes span several tiles with ragged edges."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+from gpu_helpers import (compare_fields, compare_particles, oracle_from_sim, periodic_dx,
+                         random_fields, rel_err)
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = {1: (37, 1, 1), 2: (29, 23, 1), 3: (13, 11, 9)}
+
+
+def _sim(dim, shape, fields, species, **tun):
+    from paper_1906_06306_gb300 import Simulation
+
+    nx, ny, nz = shape
+    return Simulation(dim, nx, ny, nz, 0.45, fields, species, tuning=tun or None)
+
+
+def _empty_species(dim):
+    return [dict(q=-1.0, m=1.0, cell=np.zeros(0, np.int32), off=np.zeros((dim, 0), np.float32),
+                 u=np.zeros((3, 0), np.float32))]
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_field_updates_match_oracle(dim):
+    from paper_1906_06306_gb300 import PIC_FIELD_B_HALF, PIC_FIELD_E
+
+    nx, ny, nz = SHAPES[dim]
+    rs = np.random.default_rng(100 + dim)
+    F32 = random_fields((nz, ny, nx), rs)
+    F32[6:9] = (0.01 * rs.normal(size=(3, nz, ny, nx))).astype(np.float32)
+    sim = _sim(dim, SHAPES[dim], F32, _empty_species(dim))
+    g = oracle.Grid(dim, nx, ny, nz, 0.45)
+    F = F32.astype(np.float64)
+    sim.field_update(PIC_FIELD_B_HALF)
+    oracle.push_half_b(g, F)
+    compare_fields(sim.download()[0], F, tol=1e-6)
+    sim.field_update(PIC_FIELD_E)
+    oracle.push_e(g, F)
+    oracle.add_cur(g, F)
+    compare_fields(sim.download()[0], F, tol=1e-6)
+    sim.close()
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("passes", [1, 2, 3])
+def test_binomial_filter_matches_oracle(dim, passes):
+    nx, ny, nz = SHAPES[dim]
+    rs = np.random.default_rng(200 + dim)
+    F32 = np.zeros((9, nz, ny, nx), np.float32)
+    F32[6:9] = rs.normal(size=(3, nz, ny, nx)).astype(np.float32)
+    sim = _sim(dim, SHAPES[dim], F32, _empty_species(dim))
+    g = oracle.Grid(dim, nx, ny, nz, 0.45)
+    F = F32.astype(np.float64)
+    sim.filter_current(passes)
+    oracle.filter_binomial(g, F, passes)
+    compare_fields(sim.download()[0], F, tol=1e-6)
+    sim.close()
+
+
+def _plasma(dim, shape, ppc, theta, seed):
+    nx, ny, nz = shape
+    return workloads.uniform_plasma(dim, nx, ny, nz, 0.45, ppc, 0.02, theta, seed)
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_gather_push_matches_oracle_and_move_replays_bit_exact(dim):
+    nx, ny, nz = SHAPES[dim]
+    pl = _plasma(dim, SHAPES[dim], 6, 0.5, 300 + dim)
+    pl.fields[:] = random_fields((nz, ny, nx), np.random.default_rng(301))
+    from paper_1906_06306_gb300 import Simulation
+
+    sim = Simulation.from_plasma(pl, tuning=dict(sort_every=1000))
+    g, F, osp, sp0 = oracle_from_sim(sim)
+    sim.gather_push()
+    sim.check()
+    _, spg = sim.download()
+    for o in osp:
+        oracle.push_particles(g, F, o)
+    compare_particles(g, spg, osp, xtol=2e-6, utol=2e-6)
+    # cell bookkeeping: replay the documented FP32 position update on the CPU
+    f32 = np.float32
+    c = f32(0.45)
+    for s0, s1 in zip(sp0, spg):
+        u = s1["u"]
+        g2 = ((f32(1) + u[0] * u[0]) + u[1] * u[1]) + u[2] * u[2]
+        gam = np.sqrt(g2, dtype=f32)
+        idx = [s0["cell"] % nx, (s0["cell"] // nx) % ny, s0["cell"] // (nx * ny)]
+        for d in range(dim):
+            dn = (c * u[d]) / gam
+            o = s0["off"][d] + dn
+            k = np.zeros_like(s0["cell"])
+            lo, hi = o < 0, o >= 1
+            o = np.where(lo, o + f32(1), np.where(hi, o - f32(1), o)).astype(f32)
+            k[lo], k[hi] = -1, 1
+            edge = lo & (o >= 1)
+            o[edge], k[edge] = 0, 0
+            assert np.array_equal(o.view(np.int32), s1["off"][d].view(np.int32))
+            idx[d] = (idx[d] + k) % (nx, ny, nz)[d]
+        assert np.array_equal(idx[0] + nx * (idx[1] + ny * idx[2]), s1["cell"])
+    sim.close()
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_deposit_matches_oracle_zigzag_of_the_same_moves(dim):
+    """J of pic_deposit equals the oracle's ZigZag current of the moves the GPU
+    made (old position, new position, out-of-plane displacement c u / gamma)."""
+    nx, ny, nz = SHAPES[dim]
+    pl = _plasma(dim, SHAPES[dim], 8, 1.0, 400 + dim)
+    pl.fields[:] = random_fields((nz, ny, nx), np.random.default_rng(401))
+    from paper_1906_06306_gb300 import Simulation
+
+    sim = Simulation.from_plasma(pl, tuning=dict(sort_every=1000))
+    g, F, osp, sp0 = oracle_from_sim(sim)
+    sim.gather_push()
+    sim.deposit()
+    sim.check()
+    Fg, spg = sim.download()
+    Fo = np.zeros_like(F)
+    for s0, s1 in zip(sp0, spg):
+        x_old = oracle.positions(g, s0["cell"], s0["off"])
+        x_new = oracle.positions(g, s1["cell"], s1["off"])
+        dx = np.zeros_like(x_old)
+        dx[:dim] = periodic_dx(g, x_new, x_old)
+        u = s1["u"].astype(np.float64)
+        gam = np.sqrt(1.0 + (u * u).sum(axis=0))
+        dx[dim:] = 0.45 * u[dim:] / gam
+        oracle.deposit(g, Fo, np.ascontiguousarray(x_old), np.ascontiguousarray(dx), s0["q"])
+    for c in range(6, 9):
+        assert rel_err(Fg[c], Fo[c]) < 1e-5, c
+    sim.close()
+
+
+@pytest.mark.parametrize("dim,tile", [(1, (8,)), (2, (8, 4)), (3, (4, 4, 2))])
+def test_sort_groups_particles_by_tile(dim, tile):
+    nx, ny, nz = SHAPES[dim]
+    pl = _plasma(dim, SHAPES[dim], 5, 0.3, 500 + dim)
+    rs = np.random.default_rng(501)
+    for s in pl.species:  # scramble the input order
+        p = rs.permutation(s.n)
+        s.cell, s.off, s.u = s.cell[p].copy(), s.off[:, p].copy(), s.u[:, p].copy()
+    from paper_1906_06306_gb300 import Simulation
+
+    sim = Simulation.from_plasma(pl, tuning=dict(tile=list(tile) + [1] * (3 - dim)))
+    _, spg = sim.download()
+    t3 = tuple(tile) + (1,) * (3 - dim)
+    for s_in, s_out in zip(pl.species, spg):
+        key_out = oracle.tile_keys(s_out["cell"], nx, ny, nz, t3)
+        _, start = oracle.tile_sort_reference(s_in.cell, nx, ny, nz, t3)
+        # bit-exact grouping: the key sequence is the sorted key sequence
+        assert np.array_equal(key_out, np.sort(oracle.tile_keys(s_in.cell, nx, ny, nz, t3)))
+        assert np.array_equal(np.searchsorted(key_out, np.arange(len(start) - 1)), start[:-1])
+        # same particles (bytes) in every tile
+        def rows(s):
+            return np.concatenate([s["cell"][None].view(np.float32), s["off"], s["u"]]).T.copy()
+        a = rows(s_out)
+        b = rows(dict(cell=s_in.cell, off=s_in.off, u=s_in.u))
+        for t in range(len(start) - 1):
+            sa = a[start[t]:start[t + 1]].view(np.int32)
+            kb = oracle.tile_keys(s_in.cell, nx, ny, nz, t3) == t
+            sb = b[kb].view(np.int32)
+            assert np.array_equal(np.unique(sa, axis=0), np.unique(sb, axis=0))
+    sim.close()

@@ -1,0 +1,192 @@
+"""Whole-step parity of pic_step (fused gather + push + deposit, field updates,
+filter) with the FP64 oracle, plus edge cases and invariants."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+from gpu_helpers import (REL_TOL, compare_fields, compare_particles, oracle_from_sim,
+                         periodic_dx, rel_err)
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_configs():
+    return {
+        "weibel_1d": (workloads.weibel_1d(nx=200, ppc=16, seed=21), 0, {}),
+        "turb_2d": (workloads.turbulence_2d(n=40, ppc=4, r_p=4.0, theta=0.3, sigma=10.0,
+                                            modes=4, seed=22), 0, dict(tile=[16, 16, 1])),
+        "shock_3d": (workloads.shock_3d(nx=20, ny=12, nz=10, ppc=2, seed=23), 2,
+                     dict(tile=[8, 8, 4])),
+        "turb_2d_filtered": (workloads.turbulence_2d(n=36, ppc=4, r_p=4.0, theta=0.3, sigma=1.0,
+                                                     modes=4, seed=24), 3, dict(tile=[8, 8, 1])),
+    }
+
+
+@pytest.mark.parametrize("name", list(_small_configs()))
+def test_step_matches_oracle_over_short_run(name):
+    from paper_1906_06306_gb300 import Simulation
+
+    pl, passes, tun = _small_configs()[name]
+    sim = Simulation.from_plasma(pl, tuning=dict(tun, sort_every=1000, filter_passes=passes))
+    g, F, osp, _ = oracle_from_sim(sim)
+    for _ in range(8):
+        sim.step(1)
+        oracle.step(g, F, osp, passes=passes)
+        Fg, spg = sim.download()
+        compare_fields(Fg, F)
+        compare_particles(g, spg, osp)
+    sim.check()
+    en = sim.energies()
+    ref = oracle.energies(g, F, osp)
+    for a, b in zip(en[:2 + len(osp)], ref):
+        assert abs(a - b) <= REL_TOL * max(abs(b), 1e-12 * sum(ref)), (a, b)
+    sim.close()
+
+
+def test_step_with_frequent_sorts_and_strays_matches_oracle_fields():
+    """A hot plasma, halo 1 and a sort every 5 steps: many particles leave
+    their tile window between sorts and take the global-memory path; the
+    fields still follow the oracle (particle order differs, fields do not)."""
+    from paper_1906_06306_gb300 import Simulation
+
+    pl = workloads.uniform_plasma(2, 34, 30, 1, 0.45, 4, 0.01, 2.0, seed=25)
+    sim = Simulation.from_plasma(pl, tuning=dict(tile=[8, 8, 1], halo=1, sort_every=5))
+    g, F, osp, _ = oracle_from_sim(sim)
+    for _ in range(20):
+        sim.step(1)
+        oracle.step(g, F, osp)
+    Fg, spg = sim.download()
+    compare_fields(Fg, F, tol=5e-5)
+    # same particles, in another order: compare sorted kinetic energies
+    for s, o in zip(spg, osp):
+        ug = np.sort((s["u"].astype(np.float64) ** 2).sum(0))
+        uo = np.sort((o.u ** 2).sum(0))
+        assert np.abs(ug - uo).max() < 1e-4 * max(1.0, uo.max())
+    sim.check()
+    sim.close()
+
+
+def test_edge_cases_tiny_grid_offsets_and_empty_species():
+    """Grid smaller than a tile window (every particle takes the global path),
+    offsets exactly 0 and just below 1, and an empty third species."""
+    from paper_1906_06306_gb300 import Simulation
+
+    rs = np.random.default_rng(26)
+    nx, ny = 3, 2
+    n = 40
+    cell = rs.integers(0, nx * ny, size=n).astype(np.int32)
+    off = rs.random((2, n)).astype(np.float32)
+    off[:, :5] = 0.0
+    off[:, 5:10] = workloads.plasma.ONE_MINUS
+    u = rs.normal(scale=2.0, size=(3, n)).astype(np.float32)
+    fields = np.zeros((9, 1, ny, nx), np.float32)
+    fields[:6] = rs.normal(scale=0.1, size=(6, 1, ny, nx)).astype(np.float32)
+    sp = [dict(q=-0.01, m=0.01, cell=cell, off=off, u=u),
+          dict(q=0.01, m=0.01, cell=cell.copy(), off=off.copy(), u=-u),
+          dict(q=0.01, m=0.01, cell=np.zeros(0, np.int32), off=np.zeros((2, 0), np.float32),
+               u=np.zeros((3, 0), np.float32))]
+    sim = Simulation(2, nx, ny, 1, 0.45, fields, sp, tuning=dict(sort_every=1000))
+    g, F, osp, _ = oracle_from_sim(sim)
+    for _ in range(5):
+        sim.step(1)
+        oracle.step(g, F, osp)
+    Fg, spg = sim.download()
+    compare_fields(Fg, F)
+    compare_particles(g, spg[:2], osp[:2])
+    assert spg[2]["cell"].shape == (0,)
+    sim.check()
+    sim.close()
+
+
+def test_invalid_particle_data_is_reported_not_used():
+    from paper_1906_06306_gb300 import PicError, Simulation
+
+    pl = workloads.uniform_plasma(2, 16, 16, 1, 0.45, 2, 0.01, 0.1, seed=27)
+    pl.species[0].u[0, 3] = np.nan
+    pl.species[1].off[0, 7] = 1.5
+    sim = Simulation.from_plasma(pl)
+    sim.step(1)
+    with pytest.raises(PicError) as ei:
+        sim.check()
+    assert ei.value.status == 5
+    assert "offset" in str(ei.value) and "four-velocity" in str(ei.value)
+    sim.check()  # the status word was cleared
+    sim.close()
+
+
+def test_gauss_residual_stays_at_fp32_round_off():
+    """Appendix B: with the charge-conserving deposit div E - rho keeps its
+    initial value (0 for co-located pairs and E = 0).  In FP32 the residual is
+    a random walk of round-off, far below the charge-separation signal."""
+    from paper_1906_06306_gb300 import Simulation
+
+    pl = workloads.turbulence_2d(n=64, ppc=8, r_p=4.0, theta=0.3, sigma=10.0, modes=4, seed=28)
+    sim = Simulation.from_plasma(pl, tuning=dict(sort_every=10))
+    sim.step(50)
+    en = sim.energies()
+    ns = sim.nspecies
+    gauss_max = en[2 + ns]
+    Fg, _ = sim.download()
+    g = oracle.Grid(2, 64, 64, 1, 0.45)
+    div_scale = np.abs(oracle.div_e(g, Fg.astype(np.float64))).max()
+    assert div_scale > 1e-4
+    assert gauss_max < 1e-4 * div_scale, (gauss_max, div_scale)
+    sim.close()
+
+
+def test_filtered_gauss_residual_3d():
+    from paper_1906_06306_gb300 import Simulation
+
+    pl = workloads.shock_3d(nx=24, ny=16, nz=16, ppc=2, seed=29)
+    pl.species[0].u *= 0.1  # slow the flow so charge separates visibly
+    sim = Simulation.from_plasma(pl, tuning=dict(tile=[8, 8, 8], filter_passes=2))
+    sim.step(20)
+    en = sim.energies()
+    Fg, _ = sim.download()
+    g = oracle.Grid(3, 24, 16, 16, 0.45)
+    div_scale = np.abs(oracle.div_e(g, Fg.astype(np.float64))).max()
+    assert en[2 + sim.nspecies] < 1e-4 * div_scale
+    sim.close()
+
+
+def test_full_size_turbulence_step_sampled_against_oracle():
+    """The 1024^2, 16 particles per cell per species turbulence box in the
+    benchmark's launch configuration: one fused pic_step; a sample of particles
+    checked against the oracle's gather + Boris + move from the same state, and
+    the full J lattice against the oracle's ZigZag of every GPU move."""
+    from paper_1906_06306_gb300 import Simulation
+
+    pl = workloads.turbulence_2d()
+    sim = Simulation.from_plasma(pl)
+    g, F, osp, sp0 = oracle_from_sim(sim)
+    sim.step(1)
+    sim.check()
+    Fg, spg = sim.download()
+    Fb = F.copy()
+    oracle.push_half_b(g, Fb)
+    rs = np.random.default_rng(30)
+    for s0, s1, o in zip(sp0, spg, osp):
+        pick = rs.choice(o.n, size=20000, replace=False)
+        sub = oracle.Species(o.q, o.m, o.x[:, pick], o.u[:, pick])
+        x_old, _ = oracle.push_particles(g, Fb, sub)
+        u1 = s1["u"][:, pick].astype(np.float64)
+        assert (np.abs(u1 - sub.u) <= 1e-5 * np.maximum(1.0, np.abs(sub.u))).all()
+        x1 = oracle.positions(g, s1["cell"][pick], s1["off"][:, pick])
+        assert np.abs(periodic_dx(g, x1, sub.x)).max() < 2e-5
+    Jo = np.zeros_like(F)
+    for s0, s1 in zip(sp0, spg):
+        x_old = oracle.positions(g, s0["cell"], s0["off"])
+        dx = np.zeros_like(x_old)
+        dx[:2] = periodic_dx(g, oracle.positions(g, s1["cell"], s1["off"]), x_old)
+        u = s1["u"].astype(np.float64)
+        dx[2] = 0.45 * u[2] / np.sqrt(1.0 + (u * u).sum(0))
+        oracle.deposit(g, Jo, x_old, dx, s0["q"])
+    for c in range(6, 9):
+        assert rel_err(Fg[c], Jo[c]) < 1e-5, c
+    en = sim.energies()
+    assert en[2 + sim.nspecies] < 1e-5 * max(1e-3, np.abs(Fg[6:9]).max())
+    sim.close()
