@@ -1,12 +1,25 @@
 """GB300-native relativistic PIC hot path (Runko, arXiv:1906.06306).
 
-Importing the package loads libpic.so (the CUDA kernels behind the C ABI of
-include/pic.h); there is no CPU fallback.
+The API names below resolve on first use by loading libpic.so (the CUDA
+kernels behind the C ABI of include/pic.h); if the library is missing that
+access raises -- there is no CPU fallback.  The `build` submodule imports
+without the library so that it can compile it.
 """
-from . import binding  # noqa: F401  (raises if libpic.so is missing)
-from .binding import (  # noqa: F401
-    PicError, pic_init, pic_get_tuning, pic_set_tuning, pic_sort, pic_gather_push, pic_deposit,
-    pic_filter_current, pic_field_update, pic_step, pic_energies, pic_check, pic_step_host,
-    pic_timing, pic_kernel_times, pic_destroy, pic_last_error, PIC_FIELD_B_HALF, PIC_FIELD_E,
-)
-from .sim import Simulation  # noqa: F401
+_API = {
+    "PicError", "pic_init", "pic_get_tuning", "pic_set_tuning", "pic_sort", "pic_gather_push",
+    "pic_deposit", "pic_filter_current", "pic_field_update", "pic_step", "pic_energies",
+    "pic_check", "pic_step_host", "pic_timing", "pic_kernel_times", "pic_destroy",
+    "pic_last_error", "PIC_FIELD_B_HALF", "PIC_FIELD_E",
+}
+
+
+def __getattr__(name):
+    if name in _API:
+        from . import binding
+
+        return getattr(binding, name)
+    if name == "Simulation":
+        from .sim import Simulation
+
+        return Simulation
+    raise AttributeError(name)
