@@ -30,13 +30,33 @@ def periodic_dx(g, xa, xb):
     return d - np.round(d / ext) * ext
 
 
-def compare_fields(Fg, Fo, tol=REL_TOL, comps=range(9)):
+def current_scale(g, species):
+    """c * sum_s |q_s| n_s / ncells: the current density of all particles
+    streaming at c along one axis with the charges counted in absolute value.
+    FP32 sums the per-particle ZigZag terms at this scale; when the species'
+    currents cancel (co-moving pairs), the net field is far smaller than the
+    terms and only this scale measures the rounding."""
+    return g.c * sum(abs(s.q) * s.n for s in species) / g.ncells
+
+
+def compare_fields(Fg, Fo, tol=REL_TOL, comps=range(9), floor=None):
+    """Per component: max |GPU - oracle| <= tol * max(max |oracle|, floor[c])."""
     for c in comps:
-        if np.abs(Fo[c]).max() == 0.0:
+        scale = np.abs(Fo[c]).max()
+        if floor is not None:
+            scale = max(scale, floor[c])
+        if scale == 0.0:
             assert np.abs(Fg[c]).max() == 0.0, c
             continue
-        e = rel_err(Fg[c], Fo[c])
-        assert e < tol, (c, e)
+        e = np.abs(np.asarray(Fg[c], dtype=np.float64) - Fo[c]).max() / scale
+        assert e < tol, (c, e, float(np.abs(Fo[c]).max()), scale)
+
+
+def step_floor(g, species, k):
+    """Floors for compare_fields after k steps: the E and J planes accumulate
+    k current-scale terms, B is driven by c curl E over k steps."""
+    j = current_scale(g, species)
+    return [k * j] * 3 + [2 * g.dim * g.c * k * j] * 3 + [j] * 3
 
 
 def compare_particles(g, spg, osp, xtol=2e-5, utol=1e-5):

@@ -9,7 +9,7 @@ import oracle
 import workloads
 
 from gpu_helpers import (REL_TOL, compare_fields, compare_particles, oracle_from_sim,
-                         periodic_dx, rel_err)
+                         periodic_dx, rel_err, step_floor)
 
 pytestmark = pytest.mark.gpu
 
@@ -33,17 +33,20 @@ def test_step_matches_oracle_over_short_run(name):
     pl, passes, tun = _small_configs()[name]
     sim = Simulation.from_plasma(pl, tuning=dict(tun, sort_every=1000, filter_passes=passes))
     g, F, osp, _ = oracle_from_sim(sim)
-    for _ in range(8):
+    for k in range(1, 9):
         sim.step(1)
         oracle.step(g, F, osp, passes=passes)
         Fg, spg = sim.download()
-        compare_fields(Fg, F)
+        compare_fields(Fg, F, floor=step_floor(g, osp, k))
         compare_particles(g, spg, osp)
     sim.check()
     en = sim.energies()
     ref = oracle.energies(g, F, osp)
+    # field energies that are a negligible part of the total (cancelled
+    # currents of co-moving pairs) are compared at 1e-6 of the total energy
+    total = sum(ref)
     for a, b in zip(en[:2 + len(osp)], ref):
-        assert abs(a - b) <= REL_TOL * max(abs(b), 1e-12 * sum(ref)), (a, b)
+        assert abs(a - b) <= REL_TOL * max(abs(b), 1e-6 * total), (a, b, total)
     sim.close()
 
 
@@ -60,7 +63,7 @@ def test_step_with_frequent_sorts_and_strays_matches_oracle_fields():
         sim.step(1)
         oracle.step(g, F, osp)
     Fg, spg = sim.download()
-    compare_fields(Fg, F, tol=5e-5)
+    compare_fields(Fg, F, floor=step_floor(g, osp, 20))
     # same particles, in another order: compare sorted kinetic energies
     for s, o in zip(spg, osp):
         ug = np.sort((s["u"].astype(np.float64) ** 2).sum(0))
@@ -95,7 +98,7 @@ def test_edge_cases_tiny_grid_offsets_and_empty_species():
         sim.step(1)
         oracle.step(g, F, osp)
     Fg, spg = sim.download()
-    compare_fields(Fg, F)
+    compare_fields(Fg, F, floor=step_floor(g, osp, 5))
     compare_particles(g, spg[:2], osp[:2])
     assert spg[2]["cell"].shape == (0,)
     sim.check()
