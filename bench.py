@@ -221,7 +221,8 @@ def run_ours(args):
     from paper_1906_06306_gb300 import Simulation
     from paper_1906_06306_gb300 import binding as B
 
-    pl = workloads.turbulence_2d(seed=1235)  # every rank steps its own replica of the box
+    # every rank steps its own replica of the box; --grid shrinks it for profiling runs
+    pl = workloads.turbulence_2d(n=args.grid, seed=1235)
     sim = Simulation.from_plasma(pl, device=f"cuda:{local}",
                                  tuning=dict(sort_every=args.sort_every))
     tun = sim.tuning()
@@ -303,12 +304,13 @@ def run_ours(args):
     nsorts = sum(1 for s in range(args.warmup, args.warmup + args.steps)
                  if s > 0 and s % tun["sort_every"] == 0)
     launches = args.steps * (4 + tun["filter_passes"]) + nsorts * 3 * sim.nspecies
+    wl = dict(WORKLOAD, grid=[args.grid, args.grid])
     line = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": dict(WORKLOAD, particles=pl.nparticles, sort_every=tun["sort_every"],
+        "config": dict(wl, particles=pl.nparticles, sort_every=tun["sort_every"],
                        filter_passes=tun["filter_passes"], tile=tun["tile"][:2], halo=tun["halo"],
                        parallelism="replicas" if world > 1 else "single-gpu",
                        l2="inputs larger than L2 (particle SoA %.2f GB), no flush" %
@@ -342,6 +344,8 @@ def main():
     ap.add_argument("--sort-every", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=1024,
+                    help="box side; the benchmark workload is 1024 (smaller only for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
