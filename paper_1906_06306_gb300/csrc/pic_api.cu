@@ -136,7 +136,9 @@ std::string derive_tiles(const pic_grid& grid, const pic_tuning& tun, long long 
     ntiles *= r.nt[d];
     wcells *= r.W[d];
   }
-  if (wcells * 9 * 4 > 200 * 1024) return "tile + halo window exceeds 200 KB of shared memory";
+  if ((long long)particle_smem_bytes(grid.dim, TileDev{{0, 0, 0}, {0, 0, 0}, 0, {0, 0, 0}, (int)wcells, 0}) >
+      200 * 1024)
+    return "tile + halo window exceeds 200 KB of shared memory";
   if (ntiles > (1LL << 30)) return "too many tiles";
   r.wcells = (int)wcells;
   r.ntiles = (int)ntiles;
@@ -195,6 +197,15 @@ PushParams make_params(pic_ctx* ctx) {
   P.status = ctx->d_status;
   P.inv_c = 1.0f / ctx->c;
   P.inv_c2 = 1.0f / (ctx->c * ctx->c);
+  P.div0 = make_fastdiv(ctx->g.n[0]);
+  P.div1 = make_fastdiv(ctx->g.n[1]);
+  P.wrap_fast = 1;
+  for (int d = 0; d < ctx->grid.dim; ++d)
+    if (ctx->g.n[d] < ctx->tile.W[d]) P.wrap_fast = 0;
+  float maxq = 0.f;
+  for (int s = 0; s < ctx->ns; ++s) maxq = std::fmax(maxq, std::fabs(ctx->sp[s].q));
+  P.jq = current_quantum(maxq, kPushThreads);
+  P.jq_inv = 1.0f / P.jq;
   long long o = 0;
   for (int s = 0; s < ctx->ns; ++s) {
     SpeciesDev& S = P.sp[s];
@@ -225,11 +236,13 @@ pic_status do_sort(pic_ctx* ctx) {
       r = launch_tile_scan(ctx->d_count, ctx->tile.ntiles, ctx->d_tstart[s], ctx->d_cursor, ctx->st);
       if (r != cudaSuccess) return r;
       if (n == 0) continue;
+      r = launch_tile_mult(ctx->d_tstart[s], ctx->tile.ntiles, ctx->d_count, ctx->st);
+      if (r != cudaSuccess) return r;
       int* cell_out = (int*)ctx->d_sortbuf;
       float* off_out = (float*)(cell_out + n);
       float* u_out = off_out + (long long)D * n;
       r = launch_tile_scatter(P, ctx->sp[s].cell, ctx->sp[s].off, ctx->sp[s].u, n, ctx->d_cursor,
-                              cell_out, off_out, u_out, ctx->st);
+                              ctx->d_tstart[s], ctx->d_count, cell_out, off_out, u_out, ctx->st);
       if (r != cudaSuccess) return r;
       r = cudaMemcpyAsync(ctx->sp[s].cell, cell_out, sizeof(int) * n, cudaMemcpyDeviceToDevice, ctx->st);
       if (r != cudaSuccess) return r;

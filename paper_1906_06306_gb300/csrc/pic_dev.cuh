@@ -43,6 +43,21 @@ struct SpeciesDev {
   float* off_old;     // [D][n]
 };
 
+// Exact division of 0 <= x < 2^31 by a fixed divisor d >= 1 by multiply and
+// shift (Granlund and Montgomery, 1994): with l = ceil(log2 d), s = 31 + l and
+// M = ceil(2^s / d) < 2^32, floor(x / d) = (x * M) >> s.  M exceeds 2^s / d by
+// less than 1, so x M / 2^s exceeds x / d by less than x / 2^s < 2^-l <= 1/d,
+// which cannot carry the fractional part of x / d (at most 1 - 1/d) past 1.
+struct FastDiv {
+  unsigned long long M;
+  int s;
+  int d;
+};
+
+__device__ __forceinline__ int fdiv(int x, const FastDiv& f) {
+  return (int)(((unsigned long long)(unsigned)x * f.M) >> f.s);
+}
+
 __device__ __forceinline__ int wrapi(int i, int n) {
   i %= n;
   return i < 0 ? i + n : i;
@@ -61,6 +76,18 @@ struct SmemAcc {
   }
   __device__ __forceinline__ void add(int comp, int i, int j, int k, float v) const {
     atomicAdd(&s[comp * wcells + i + W0 * j + W01 * k], v);
+  }
+};
+
+// Shared-memory current window in int32 fixed point: the caller passes values
+// already divided by the quantum; integer shared atomics are native and
+// unaffected by lanes that hit the same word.  Planes Jx, Jy, Jz of
+// W0 x W1 x W2 ints.
+struct SmemJ {
+  int* ji;
+  int W0, W01, wc;
+  __device__ __forceinline__ void add(int comp, int i, int j, int k, float v) const {
+    atomicAdd(&ji[(comp - JX) * wc + i + W0 * j + W01 * k], __float2int_rn(v));
   }
 };
 
@@ -139,16 +166,18 @@ __device__ __forceinline__ void gather(const Acc& A, const int* b, const float* 
 // Relativistic Boris scheme, Appendix C: u1 = c u + (s/2) E,
 // gamma1 = sqrt(1 + u1^2/c^2), t = s B / (2 c gamma1), f = 2/(1 + t^2),
 // u2 = f (u1 + u1 x t), u3 = u1 + u2 x t + (s/2) E, u <- u3 / c.
+// 1/gamma1 and f use the hardware reciprocal square root and fast divide
+// (a few ulp; far inside the FP32-vs-FP64 tolerance).
 __device__ __forceinline__ void boris(float* u, const float* e, const float* b, float qm, float c,
                                       float inv_c, float inv_c2) {
   const float hs = 0.5f * qm;
   float u1[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) u1[a] = fmaf(c, u[a], hs * e[a]);
-  const float g1 = sqrtf(fmaf(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2], inv_c2, 1.0f));
-  const float tf = hs * inv_c / g1;
+  const float ig1 = rsqrtf(fmaf(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2], inv_c2, 1.0f));
+  const float tf = hs * inv_c * ig1;
   const float t0 = tf * b[0], t1 = tf * b[1], t2 = tf * b[2];
-  const float f = 2.0f / fmaf(t0, t0, fmaf(t1, t1, fmaf(t2, t2, 1.0f)));
+  const float f = __fdividef(2.0f, fmaf(t0, t0, fmaf(t1, t1, fmaf(t2, t2, 1.0f))));
   const float v0 = f * (u1[0] + (u1[1] * t2 - u1[2] * t1));
   const float v1 = f * (u1[1] + (u1[2] * t0 - u1[0] * t2));
   const float v2 = f * (u1[2] + (u1[0] * t1 - u1[1] * t0));
@@ -158,19 +187,20 @@ __device__ __forceinline__ void boris(float* u, const float* e, const float* b, 
 }
 
 // Position update of Eq. (fdX), x += c u / gamma, on the offsets, with every
-// operation rounded separately (no contraction) so the cell bookkeeping can be
-// replayed bit for bit: gamma = sqrt(((1 + ux^2) + uy^2) + uz^2),
-// dx = (c u) / gamma, o2 = o1 + dx; o2 < 0 moves one cell down (o2 += 1), o2 >= 1
-// one cell up (o2 -= 1); an o2 + 1 that rounds to 1 is the lower cell face, so
-// the particle stays with offset 0.  dn receives dx of every axis.
+// operation correctly rounded and none contracted, so the cell bookkeeping can
+// be replayed bit for bit: gamma = sqrt(((1 + ux^2) + uy^2) + uz^2),
+// r = 1 / gamma, dx = (c u) r, o2 = o1 + dx; o2 < 0 moves one cell down
+// (o2 += 1), o2 >= 1 one cell up (o2 -= 1); an o2 + 1 that rounds to 1 is the
+// lower cell face, so the particle stays with offset 0.  dn receives dx of
+// every axis.
 template <int D>
 __device__ __forceinline__ void move(const float* u, const float* o1, float c, float* o2, int* dc,
                                      float* dn) {
   const float g2 = __fadd_rn(__fadd_rn(__fadd_rn(1.0f, __fmul_rn(u[0], u[0])), __fmul_rn(u[1], u[1])),
                              __fmul_rn(u[2], u[2]));
-  const float gam = __fsqrt_rn(g2);
+  const float r = __frcp_rn(__fsqrt_rn(g2));
 #pragma unroll
-  for (int a = 0; a < 3; ++a) dn[a] = __fdiv_rn(__fmul_rn(c, u[a]), gam);
+  for (int a = 0; a < 3; ++a) dn[a] = __fmul_rn(__fmul_rn(c, u[a]), r);
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     float o = __fadd_rn(o1[d], dn[d]);

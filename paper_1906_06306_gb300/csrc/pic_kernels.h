@@ -19,13 +19,24 @@ struct PushParams {
   int splits;   // thread blocks per tile
   int* status;
   float inv_c, inv_c2;
+  FastDiv div0, div1;  // by n0 and n1: cell -> (i, j, k)
+  int wrap_fast;       // every axis has n >= window extent: one conditional wrap suffices
+  float jq;            // quantum of the int32 shared-memory current (a power of 2)
+  float jq_inv;        // 1 / jq
 };
+
+// Quantum of the fixed-point shared-memory current for charges up to max_abs_q
+// and batches of `batch` particles between spills: one particle adds at most
+// 2.2 |q| to any current word in a step (two segments, 3D weights <= 1 + 1/12),
+// so 4 * batch * max|q| < 2^31 quanta can never overflow.
+float current_quantum(float max_abs_q, int batch);
+FastDiv make_fastdiv(int d);
 
 // mode 0: fused gather + push + move + deposit; 1: gather + push + move and
 // pre-move snapshot; 2: deposit from the snapshot and the stored new u.
 cudaError_t launch_particles(int dim, int mode, const PushParams& P, cudaStream_t st);
 cudaError_t set_particle_smem_limit(int bytes);
-size_t particle_smem_bytes(const TileDev& t);
+size_t particle_smem_bytes(int dim, const TileDev& t);
 
 cudaError_t launch_b_half(const GridDev& g, float* F, int zero_j, cudaStream_t st);
 cudaError_t launch_e_update(const GridDev& g, float* F, cudaStream_t st);
@@ -44,9 +55,12 @@ cudaError_t launch_tile_count(const SortParams& P, const int* cell, long long n,
                               cudaStream_t st);
 cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* cursor,
                              cudaStream_t st);
+// per-tile multiplier inverse used to spread each tile's particles (see pic_sort.cu)
+cudaError_t launch_tile_mult(const int* start, int ntiles, int* minv, cudaStream_t st);
 cudaError_t launch_tile_scatter(const SortParams& P, const int* cell, const float* off,
-                                const float* u, long long n, int* cursor, int* cell_out,
-                                float* off_out, float* u_out, cudaStream_t st);
+                                const float* u, long long n, int* cursor, const int* start,
+                                const int* minv, int* cell_out, float* off_out, float* u_out,
+                                cudaStream_t st);
 
 // diagnostics: acc[0] += 0.5 sum E^2, acc[1] += 0.5 sum B^2
 cudaError_t launch_field_energy(const GridDev& g, const float* F, double* acc, cudaStream_t st);

@@ -1,21 +1,91 @@
 // Particle kernel of the PIC step: interp_em + push + comp_curr of Table 1
 // (arXiv:1906.06306), one thread block per (tile, split).
 //
-// Particles are sorted by tile.  A block stages its tile's E and B plus a
-// halo into shared memory, runs every particle of the tile's bucket (all
-// species) through gather -> Boris -> move -> ZigZag, accumulating the current
-// in a shared-memory J window, and finally adds that window into the global J
-// planes.  A particle whose stencil is not inside the window (it drifted more
-// than halo-1 cells since the last sort) reads and deposits through global
-// memory instead, so correctness never depends on the sort cadence.
+// Particles are sorted by tile.  A block stages its tile's E and B plus a halo
+// into shared memory, runs every particle of the tile's bucket (all species)
+// through gather -> Boris -> move -> ZigZag and accumulates the current in a
+// shared-memory window, which it finally adds into the global J planes.
+//
+// Shared-memory layout (x fastest inside each plane, wc = window cells):
+//   1D: float4 (Ex, By, Bz, -) [half-staggered points], float4 (Ey, Ez, Bx, -)
+//   2D: float2 (Ex, By) [(1/2,0)], float2 (Ey, Bx) [(0,1/2)], Ez [(0,0)], Bz [(1/2,1/2)]
+//   3D: Ex Ey Ez Bx By Bz
+//   then int32 Jx Jy Jz (fixed point) and float Jx Jy Jz (running sums).
+// Components that share a stencil share their loads.  The current goes into
+// the int32 window with native integer atomics (same-address lanes do not
+// serialise) and is folded into the float window after every batch of
+// blockDim particles, before any int32 word can overflow.
+//
+// A particle whose stencil is not inside the window (it drifted more than
+// halo-1 cells since the last sort) reads and deposits through global memory
+// instead, so correctness never depends on the sort cadence.
+#include <cmath>
+
 #include "pic_kernels.h"
 
 namespace pic {
 
+template <int D>
+__host__ __device__ constexpr int field_floats() {
+  return D == 1 ? 8 : 6;
+}
+
+__device__ __forceinline__ float lerp(float a, float b, float w) { return fmaf(w, b - a, a); }
+
+__device__ __forceinline__ float bilerp(float f00, float f10, float f01, float f11, float wx,
+                                        float wy) {
+  return lerp(lerp(f00, f10, wx), lerp(f01, f11, wx), wy);
+}
+
+// Linear gather from the staged window (layout above), window-local cell l.
+template <int D>
+__device__ __forceinline__ void gather_smem(const float* sm, int wc, int W0, int W01, const int* l,
+                                            const float* o, float* e, float* b) {
+  if (D == 1) {
+    const float4* FA = reinterpret_cast<const float4*>(sm);
+    const float4* FB = reinterpret_cast<const float4*>(sm + 4 * wc);
+    const bool hx = o[0] >= 0.5f;
+    const int bh = hx ? l[0] : l[0] - 1;
+    const float wh = hx ? o[0] - 0.5f : o[0] + 0.5f;
+    const float4 a0 = FA[bh], a1 = FA[bh + 1];
+    const float4 c0 = FB[l[0]], c1 = FB[l[0] + 1];
+    e[0] = lerp(a0.x, a1.x, wh);
+    b[1] = lerp(a0.y, a1.y, wh);
+    b[2] = lerp(a0.z, a1.z, wh);
+    e[1] = lerp(c0.x, c1.x, o[0]);
+    e[2] = lerp(c0.y, c1.y, o[0]);
+    b[0] = lerp(c0.z, c1.z, o[0]);
+  } else if (D == 2) {
+    const float2* FA = reinterpret_cast<const float2*>(sm);
+    const float2* FB = reinterpret_cast<const float2*>(sm + 2 * wc);
+    const float* FC = sm + 4 * wc;
+    const float* FD = sm + 5 * wc;
+    const bool hx = o[0] >= 0.5f, hy = o[1] >= 0.5f;
+    const int bxh = hx ? l[0] : l[0] - 1, byh = hy ? l[1] : l[1] - 1;
+    const float wxh = hx ? o[0] - 0.5f : o[0] + 0.5f;
+    const float wyh = hy ? o[1] - 0.5f : o[1] + 0.5f;
+    int i = bxh + W0 * l[1];  // (1/2, 0): Ex, By
+    const float2 a00 = FA[i], a10 = FA[i + 1], a01 = FA[i + W0], a11 = FA[i + W0 + 1];
+    e[0] = bilerp(a00.x, a10.x, a01.x, a11.x, wxh, o[1]);
+    b[1] = bilerp(a00.y, a10.y, a01.y, a11.y, wxh, o[1]);
+    i = l[0] + W0 * byh;  // (0, 1/2): Ey, Bx
+    const float2 c00 = FB[i], c10 = FB[i + 1], c01 = FB[i + W0], c11 = FB[i + W0 + 1];
+    e[1] = bilerp(c00.x, c10.x, c01.x, c11.x, o[0], wyh);
+    b[0] = bilerp(c00.y, c10.y, c01.y, c11.y, o[0], wyh);
+    i = l[0] + W0 * l[1];  // (0, 0): Ez
+    e[2] = bilerp(FC[i], FC[i + 1], FC[i + W0], FC[i + W0 + 1], o[0], o[1]);
+    i = bxh + W0 * byh;  // (1/2, 1/2): Bz
+    b[2] = bilerp(FD[i], FD[i + 1], FD[i + W0], FD[i + W0 + 1], wxh, wyh);
+  } else {
+    const SmemAcc A{const_cast<float*>(sm), W0, W01, wc};
+    gather<3>(A, l, o, e, b);
+  }
+}
+
 template <int D, int MODE>
 __device__ __forceinline__ void one_particle(const PushParams& P, const SpeciesDev& S,
-                                             long long p, const SmemAcc& SA, const GlobAcc& GA,
-                                             const int* w0) {
+                                             long long p, const float* sm, const SmemJ& SJ,
+                                             const GlobAcc& GA, const int* w0, float qs) {
   const long long n = S.n;
   int cell;
   float o1[3] = {0.f, 0.f, 0.f};
@@ -48,23 +118,34 @@ __device__ __forceinline__ void one_particle(const PushParams& P, const SpeciesD
     return;
   }
 
-  int ijk[3];
-  ijk[0] = cell % P.g.n[0];
-  const int r = cell / P.g.n[0];
-  ijk[1] = r % P.g.n[1];
-  ijk[2] = r / P.g.n[1];
+  int ijk[3] = {0, 0, 0};
+  {
+    const int r = fdiv(cell, P.div0);
+    ijk[0] = cell - r * P.g.n[0];
+    if (D >= 2) {
+      ijk[2] = fdiv(r, P.div1);
+      ijk[1] = r - ijk[2] * P.g.n[1];
+    }
+  }
   int l[3] = {0, 0, 0};
   bool inwin = true;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    l[d] = wrapi(ijk[d] - w0[d], P.g.n[d]);
-    inwin &= (l[d] >= 1) && (l[d] <= P.t.W[d] - 3);
+    int v = ijk[d] - w0[d];
+    if (P.wrap_fast) {
+      v += (v < 0) ? P.g.n[d] : 0;
+      v -= (v >= P.g.n[d]) ? P.g.n[d] : 0;
+    } else {
+      v = wrapi(v, P.g.n[d]);
+    }
+    l[d] = v;
+    inwin &= (v >= 1) && (v <= P.t.W[d] - 3);
   }
 
   if (MODE != 2) {
     float e[3], b[3];
     if (inwin)
-      gather<D>(SA, l, o1, e, b);
+      gather_smem<D>(sm, P.t.wcells, P.t.W[0], P.t.W[0] * P.t.W[1], l, o1, e, b);
     else
       gather<D>(GA, ijk, o1, e, b);
     boris(u, e, b, S.qm, P.g.c, P.inv_c, P.inv_c2);
@@ -91,7 +172,7 @@ __device__ __forceinline__ void one_particle(const PushParams& P, const SpeciesD
   }
   if (MODE != 1) {
     if (inwin)
-      zigzag<D>(SA, l, dc, o1, o2, dn, S.q);
+      zigzag<D>(SJ, l, dc, o1, o2, dn, qs);
     else
       zigzag<D>(GA, ijk, dc, o1, o2, dn, S.q);
   }
@@ -99,7 +180,7 @@ __device__ __forceinline__ void one_particle(const PushParams& P, const SpeciesD
 
 template <int D, int MODE>
 __global__ void __launch_bounds__(kPushThreads) k_particles(const PushParams P) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   const int tile = blockIdx.x / P.splits;
   const int split = blockIdx.x - tile * P.splits;
   const int tc[3] = {tile % P.t.nt[0], (tile / P.t.nt[0]) % P.t.nt[1],
@@ -109,19 +190,42 @@ __global__ void __launch_bounds__(kPushThreads) k_particles(const PushParams P) 
   for (int d = 0; d < D; ++d) w0[d] = tc[d] * P.t.T[d] - P.t.H;
   const int wc = P.t.wcells;
   const int W0 = P.t.W[0], W1 = P.t.W[1];
+  constexpr int NF = field_floats<D>();
+  int* ji = reinterpret_cast<int*>(sm + NF * wc);
+  float* jf = sm + (NF + 3) * wc;
   const GlobAcc GA{P.F, P.g.plane, P.g.n[0], P.g.n[1], P.g.n[2]};
-  const SmemAcc SA{sm, W0, W0 * W1, wc};
+  const SmemJ SJ{ji, W0, W0 * W1, wc};
 
   for (int w = threadIdx.x; w < wc; w += blockDim.x) {
     const int lx = w % W0, rr = w / W0, ly = rr % W1, lz = rr / W1;
     const long long gi = GA.at(w0[0] + lx, w0[1] + ly, w0[2] + lz);
     if (MODE != 2) {
-#pragma unroll
-      for (int comp = EX; comp <= BZ; ++comp) sm[comp * wc + w] = __ldg(&P.F[comp * P.g.plane + gi]);
+      const float ex = __ldg(&P.F[EX * P.g.plane + gi]), ey = __ldg(&P.F[EY * P.g.plane + gi]);
+      const float ez = __ldg(&P.F[EZ * P.g.plane + gi]), bx = __ldg(&P.F[BX * P.g.plane + gi]);
+      const float by = __ldg(&P.F[BY * P.g.plane + gi]), bz = __ldg(&P.F[BZ * P.g.plane + gi]);
+      if (D == 1) {
+        reinterpret_cast<float4*>(sm)[w] = make_float4(ex, by, bz, 0.f);
+        reinterpret_cast<float4*>(sm + 4 * wc)[w] = make_float4(ey, ez, bx, 0.f);
+      } else if (D == 2) {
+        reinterpret_cast<float2*>(sm)[w] = make_float2(ex, by);
+        reinterpret_cast<float2*>(sm + 2 * wc)[w] = make_float2(ey, bx);
+        sm[4 * wc + w] = ez;
+        sm[5 * wc + w] = bz;
+      } else {
+        sm[EX * wc + w] = ex;
+        sm[EY * wc + w] = ey;
+        sm[EZ * wc + w] = ez;
+        sm[BX * wc + w] = bx;
+        sm[BY * wc + w] = by;
+        sm[BZ * wc + w] = bz;
+      }
     }
     if (MODE != 1) {
 #pragma unroll
-      for (int comp = JX; comp <= JZ; ++comp) sm[comp * wc + w] = 0.0f;
+      for (int c = 0; c < 3; ++c) {
+        ji[c * wc + w] = 0;
+        jf[c * wc + w] = 0.0f;
+      }
     }
   }
   __syncthreads();
@@ -132,25 +236,59 @@ __global__ void __launch_bounds__(kPushThreads) k_particles(const PushParams P) 
     const long long len = hi - lo;
     const long long a = lo + len * split / P.splits;
     const long long b = lo + len * (split + 1) / P.splits;
-    for (long long p = a + threadIdx.x; p < b; p += blockDim.x)
-      one_particle<D, MODE>(P, S, p, SA, GA, w0);
+    const float qs = S.q * P.jq_inv;
+    for (long long base = a; base < b; base += blockDim.x) {  // block-uniform trip count
+      const long long p = base + threadIdx.x;
+      if (p < b) one_particle<D, MODE>(P, S, p, sm, SJ, GA, w0, qs);
+      if (MODE != 1) {
+        __syncthreads();
+        for (int w = threadIdx.x; w < 3 * wc; w += blockDim.x) {
+          const int v = ji[w];
+          if (v != 0) {
+            jf[w] = fmaf((float)v, P.jq, jf[w]);
+            ji[w] = 0;
+          }
+        }
+        __syncthreads();
+      }
+    }
   }
 
   if (MODE != 1) {
-    __syncthreads();
     for (int w = threadIdx.x; w < wc; w += blockDim.x) {
       const int lx = w % W0, rr = w / W0, ly = rr % W1, lz = rr / W1;
       const long long gi = GA.at(w0[0] + lx, w0[1] + ly, w0[2] + lz);
 #pragma unroll
-      for (int comp = JX; comp <= JZ; ++comp) {
-        const float v = sm[comp * wc + w];
-        if (v != 0.0f) atomicAdd(&P.F[comp * P.g.plane + gi], v);
+      for (int c = 0; c < 3; ++c) {
+        const float v = jf[c * wc + w];
+        if (v != 0.0f) atomicAdd(&P.F[(JX + c) * P.g.plane + gi], v);
       }
     }
   }
 }
 
-size_t particle_smem_bytes(const TileDev& t) { return sizeof(float) * 9 * (size_t)t.wcells; }
+size_t particle_smem_bytes(int dim, const TileDev& t) {
+  const int nf = dim == 1 ? field_floats<1>() : field_floats<2>();
+  return sizeof(float) * (size_t)(nf + 6) * (size_t)t.wcells;
+}
+
+float current_quantum(float max_abs_q, int batch) {
+  const double bound = 4.0 * (double)batch * (double)max_abs_q;
+  const int e = (int)std::ceil(std::log2(bound > 0 ? bound : 1.0));
+  return (float)std::ldexp(1.0, e - 31);
+}
+
+FastDiv make_fastdiv(int d) {
+  int l = 0;
+  while ((1LL << l) < (long long)d) ++l;  // ceil(log2 d)
+  const int s = 31 + l;
+  const unsigned long long two_s = 1ULL << s;
+  FastDiv f;
+  f.M = (two_s + (unsigned long long)d - 1) / (unsigned long long)d;
+  f.s = s;
+  f.d = d;
+  return f;
+}
 
 template <int D, int MODE>
 static cudaError_t set_limit(int bytes) {
@@ -160,9 +298,9 @@ static cudaError_t set_limit(int bytes) {
 
 cudaError_t set_particle_smem_limit(int bytes) {
   cudaError_t e = cudaSuccess;
-#define PIC_SET(D)                                          \
-  if (e == cudaSuccess) e = set_limit<D, 0>(bytes);         \
-  if (e == cudaSuccess) e = set_limit<D, 1>(bytes);         \
+#define PIC_SET(D)                                  \
+  if (e == cudaSuccess) e = set_limit<D, 0>(bytes); \
+  if (e == cudaSuccess) e = set_limit<D, 1>(bytes); \
   if (e == cudaSuccess) e = set_limit<D, 2>(bytes);
   PIC_SET(1)
   PIC_SET(2)
@@ -174,7 +312,7 @@ cudaError_t set_particle_smem_limit(int bytes) {
 template <int D, int MODE>
 static void launch(const PushParams& P, cudaStream_t st) {
   const unsigned nblocks = (unsigned)P.t.ntiles * (unsigned)P.splits;
-  k_particles<D, MODE><<<nblocks, kPushThreads, particle_smem_bytes(P.t), st>>>(P);
+  k_particles<D, MODE><<<nblocks, kPushThreads, particle_smem_bytes(D, P.t), st>>>(P);
 }
 
 cudaError_t launch_particles(int dim, int mode, const PushParams& P, cudaStream_t st) {

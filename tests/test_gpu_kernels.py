@@ -90,10 +90,10 @@ def test_gather_push_matches_oracle_and_move_replays_bit_exact(dim):
     for s0, s1 in zip(sp0, spg):
         u = s1["u"]
         g2 = ((f32(1) + u[0] * u[0]) + u[1] * u[1]) + u[2] * u[2]
-        gam = np.sqrt(g2, dtype=f32)
+        r = f32(1) / np.sqrt(g2, dtype=f32)
         idx = [s0["cell"] % nx, (s0["cell"] // nx) % ny, s0["cell"] // (nx * ny)]
         for d in range(dim):
-            dn = (c * u[d]) / gam
+            dn = (c * u[d]) * r
             o = s0["off"][d] + dn
             k = np.zeros_like(s0["cell"])
             lo, hi = o < 0, o >= 1
