@@ -38,7 +38,8 @@ struct pic_ctx {
   int* d_tstart[PIC_MAX_SPECIES] = {};
   int* d_count = nullptr;
   int* d_cursor = nullptr;
-  void* d_sortbuf = nullptr;
+  void* d_sortbuf = nullptr;   // sorted particles of every species (one record layout each)
+  bool sorted_pending = false;  // the next push reads the sorted buffer (no copy back)
   int* d_cell_old = nullptr;
   float* d_off_old = nullptr;
   bool snapshot_valid = false;
@@ -187,6 +188,13 @@ cudaError_t timed(pic_ctx* ctx, int kind, Fn fn) {
   return e;
 }
 
+// offset (in 4-byte words) of species s in the sorted buffer
+long long sortbuf_offset(const pic_ctx* ctx, int s) {
+  long long o = 0;
+  for (int r = 0; r < s; ++r) o += ctx->sp[r].n * (1 + ctx->grid.dim + 3);
+  return o;
+}
+
 PushParams make_params(pic_ctx* ctx) {
   PushParams P{};
   P.g = ctx->g;
@@ -204,7 +212,7 @@ PushParams make_params(pic_ctx* ctx) {
     if (ctx->g.n[d] < ctx->tile.W[d]) P.wrap_fast = 0;
   float maxq = 0.f;
   for (int s = 0; s < ctx->ns; ++s) maxq = std::fmax(maxq, std::fabs(ctx->sp[s].q));
-  P.jq = current_quantum(maxq, kPushThreads);
+  P.jq = current_quantum(maxq, ctx->c, kPushThreads * kSpillEvery);
   P.jq_inv = 1.0f / P.jq;
   long long o = 0;
   for (int s = 0; s < ctx->ns; ++s) {
@@ -215,6 +223,15 @@ PushParams make_params(pic_ctx* ctx) {
     S.cell = ctx->sp[s].cell;
     S.off = ctx->sp[s].off;
     S.u = ctx->sp[s].u;
+    S.rcell = S.cell;
+    S.roff = S.off;
+    S.ru = S.u;
+    if (ctx->sorted_pending) {
+      int* c = (int*)ctx->d_sortbuf + sortbuf_offset(ctx, s);
+      S.rcell = c;
+      S.roff = (const float*)(c + S.n);
+      S.ru = (const float*)(c + S.n) + (long long)ctx->grid.dim * S.n;
+    }
     S.tstart = ctx->d_tstart[s];
     S.cell_old = ctx->d_cell_old ? ctx->d_cell_old + o : nullptr;
     S.off_old = ctx->d_off_old ? ctx->d_off_old + (long long)ctx->grid.dim * o : nullptr;
@@ -223,7 +240,10 @@ PushParams make_params(pic_ctx* ctx) {
   return P;
 }
 
-pic_status do_sort(pic_ctx* ctx) {
+// Sort every species by tile into the sorted buffer.  With copy_back the
+// sorted particles are copied into the caller's arrays; without, the next push
+// reads them from the buffer and writes the caller's arrays (pic_step).
+pic_status do_sort(pic_ctx* ctx, bool copy_back) {
   SortParams P{ctx->g, ctx->tile, ctx->d_status};
   const int D = ctx->grid.dim;
   const cudaError_t e = timed(ctx, PIC_KERNEL_SORT, [&]() -> cudaError_t {
@@ -236,14 +256,13 @@ pic_status do_sort(pic_ctx* ctx) {
       r = launch_tile_scan(ctx->d_count, ctx->tile.ntiles, ctx->d_tstart[s], ctx->d_cursor, ctx->st);
       if (r != cudaSuccess) return r;
       if (n == 0) continue;
-      r = launch_tile_mult(ctx->d_tstart[s], ctx->tile.ntiles, ctx->d_count, ctx->st);
-      if (r != cudaSuccess) return r;
-      int* cell_out = (int*)ctx->d_sortbuf;
+      int* cell_out = (int*)ctx->d_sortbuf + sortbuf_offset(ctx, s);
       float* off_out = (float*)(cell_out + n);
       float* u_out = off_out + (long long)D * n;
       r = launch_tile_scatter(P, ctx->sp[s].cell, ctx->sp[s].off, ctx->sp[s].u, n, ctx->d_cursor,
-                              ctx->d_tstart[s], ctx->d_count, cell_out, off_out, u_out, ctx->st);
+                              cell_out, off_out, u_out, ctx->st);
       if (r != cudaSuccess) return r;
+      if (!copy_back) continue;
       r = cudaMemcpyAsync(ctx->sp[s].cell, cell_out, sizeof(int) * n, cudaMemcpyDeviceToDevice, ctx->st);
       if (r != cudaSuccess) return r;
       r = cudaMemcpyAsync(ctx->sp[s].off, off_out, sizeof(float) * D * n, cudaMemcpyDeviceToDevice,
@@ -256,6 +275,7 @@ pic_status do_sort(pic_ctx* ctx) {
   });
   if (e != cudaSuccess) return cuda_fail(ctx, "tile sort", e);
   ctx->snapshot_valid = false;
+  ctx->sorted_pending = !copy_back;
   return PIC_OK;
 }
 
@@ -351,10 +371,10 @@ pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* spec
   } else if ((e = dalloc(&ctx->d_status, 1)) != cudaSuccess ||
              (e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->st)) != cudaSuccess) {
     s = cuda_fail(nullptr, "status word", e);
-  } else if ((e = dalloc((char**)&ctx->d_sortbuf, (size_t)nmax * (4 + 4 * grid->dim + 12))) !=
+  } else if ((e = dalloc((char**)&ctx->d_sortbuf, (size_t)ntot * (4 + 4 * grid->dim + 12))) !=
              cudaSuccess) {
     s = cuda_fail(nullptr, "sort buffer", e);
-  } else if ((s = alloc_tiles(ctx)) != PIC_OK || (s = do_sort(ctx)) != PIC_OK) {
+  } else if ((s = alloc_tiles(ctx)) != PIC_OK || (s = do_sort(ctx, true)) != PIC_OK) {
     g_init_error = ctx->err;
   }
   if (s != PIC_OK) {
@@ -396,14 +416,14 @@ pic_status pic_set_tuning(pic_ctx* ctx, const pic_tuning* t) {
     ctx->tile = td;
     pic_status s = alloc_tiles(ctx);
     if (s != PIC_OK) return s;
-    return do_sort(ctx);
+    return do_sort(ctx, true);
   }
   return PIC_OK;
 }
 
 pic_status pic_sort(pic_ctx* ctx) {
   if (!ctx) return PIC_ERR_ARG;
-  return do_sort(ctx);
+  return do_sort(ctx, true);
 }
 
 pic_status pic_gather_push(pic_ctx* ctx) {
@@ -453,12 +473,13 @@ pic_status pic_field_update(pic_ctx* ctx, int which) {
 pic_status pic_step(pic_ctx* ctx, int nsteps) {
   if (!ctx) return PIC_ERR_ARG;
   if (nsteps < 0) return set_err(ctx, PIC_ERR_ARG, "nsteps must be >= 0");
-  const PushParams P = make_params(ctx);
   for (int it = 0; it < nsteps; ++it) {
     if (ctx->steps > 0 && ctx->steps % ctx->tun.sort_every == 0) {
-      const pic_status s = do_sort(ctx);
+      const pic_status s = do_sort(ctx, false);
       if (s != PIC_OK) return s;
     }
+    const PushParams P = make_params(ctx);
+    ctx->sorted_pending = false;
     cudaError_t e = timed(ctx, PIC_KERNEL_BHALF, [&]() { return launch_b_half(ctx->g, ctx->F, 1, ctx->st); });
     if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
     e = timed(ctx, PIC_KERNEL_PUSH, [&]() { return launch_particles(ctx->grid.dim, 0, P, ctx->st); });

@@ -35,9 +35,12 @@ struct SpeciesDev {
   float q;            // macro-particle charge
   float qm;           // q/m, the s-hat of Appendix C
   long long n;
-  int* cell;
+  int* cell;          // particle arrays written by the push
   float* off;         // [D][n]
   float* u;           // [3][n]
+  const int* rcell;   // particle arrays read by the push (the sorted buffer right
+  const float* roff;  // after a sort inside the step, else the same as cell/off/u)
+  const float* ru;
   const int* tstart;  // [ntiles+1] tile bucket offsets
   int* cell_old;      // pre-move snapshot (split gather/deposit path)
   float* off_old;     // [D][n]

@@ -9,6 +9,7 @@ namespace pic {
 
 constexpr int kMaxSpecies = 4;
 constexpr int kPushThreads = 256;
+constexpr int kSpillEvery = 2;  // batches of kPushThreads particles between current spills
 
 struct PushParams {
   GridDev g;
@@ -25,11 +26,13 @@ struct PushParams {
   float jq_inv;        // 1 / jq
 };
 
-// Quantum of the fixed-point shared-memory current for charges up to max_abs_q
-// and batches of `batch` particles between spills: one particle adds at most
-// 2.2 |q| to any current word in a step (two segments, 3D weights <= 1 + 1/12),
-// so 4 * batch * max|q| < 2^31 quanta can never overflow.
-float current_quantum(float max_abs_q, int batch);
+// Quantum of the fixed-point shared-memory current (a power of 2) for charges
+// up to max_abs_q, Courant number c and `batch` particles between spills.  In
+// one step a particle adds to any current word at most |q| times the sum of
+// its two segments' displacements along that component (|dx| < c) times a
+// transverse weight (<= 1, or 1 + c^2/12 in 3D), i.e. less than 1.02 c |q|;
+// a bound of 1.25 c * batch * max|q| < 2^31 quanta can never overflow.
+float current_quantum(float max_abs_q, float c, int batch);
 FastDiv make_fastdiv(int d);
 
 // mode 0: fused gather + push + move + deposit; 1: gather + push + move and
@@ -55,12 +58,9 @@ cudaError_t launch_tile_count(const SortParams& P, const int* cell, long long n,
                               cudaStream_t st);
 cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* cursor,
                              cudaStream_t st);
-// per-tile multiplier inverse used to spread each tile's particles (see pic_sort.cu)
-cudaError_t launch_tile_mult(const int* start, int ntiles, int* minv, cudaStream_t st);
 cudaError_t launch_tile_scatter(const SortParams& P, const int* cell, const float* off,
-                                const float* u, long long n, int* cursor, const int* start,
-                                const int* minv, int* cell_out, float* off_out, float* u_out,
-                                cudaStream_t st);
+                                const float* u, long long n, int* cursor, int* cell_out,
+                                float* off_out, float* u_out, cudaStream_t st);
 
 // diagnostics: acc[0] += 0.5 sum E^2, acc[1] += 0.5 sum B^2
 cudaError_t launch_field_energy(const GridDev& g, const float* F, double* acc, cudaStream_t st);

@@ -13,8 +13,8 @@
 //   then int32 Jx Jy Jz (fixed point) and float Jx Jy Jz (running sums).
 // Components that share a stencil share their loads.  The current goes into
 // the int32 window with native integer atomics (same-address lanes do not
-// serialise) and is folded into the float window after every batch of
-// blockDim particles, before any int32 word can overflow.
+// serialise) and is folded into the float window after every kSpillEvery
+// batches of blockDim particles, before any int32 word can overflow.
 //
 // A particle whose stencil is not inside the window (it drifted more than
 // halo-1 cells since the last sort) reads and deposits through global memory
@@ -95,12 +95,12 @@ __device__ __forceinline__ void one_particle(const PushParams& P, const SpeciesD
 #pragma unroll
     for (int d = 0; d < D; ++d) o1[d] = S.off_old[d * n + p];
   } else {
-    cell = S.cell[p];
+    cell = S.rcell[p];
 #pragma unroll
-    for (int d = 0; d < D; ++d) o1[d] = S.off[d * n + p];
+    for (int d = 0; d < D; ++d) o1[d] = S.roff[d * n + p];
   }
 #pragma unroll
-  for (int a = 0; a < 3; ++a) u[a] = S.u[a * n + p];
+  for (int a = 0; a < 3; ++a) u[a] = MODE == 2 ? S.u[a * n + p] : S.ru[a * n + p];
 
   if (cell < 0 || (long long)cell >= P.g.plane) {
     atomicOr(P.status, ST_BAD_CELL);
@@ -230,6 +230,20 @@ __global__ void __launch_bounds__(kPushThreads) k_particles(const PushParams P) 
   }
   __syncthreads();
 
+  // fold the int32 window into the float window and clear it
+  auto spill = [&]() {
+    __syncthreads();
+    for (int w = threadIdx.x; w < 3 * wc; w += blockDim.x) {
+      const int v = ji[w];
+      if (v != 0) {
+        jf[w] = fmaf((float)v, P.jq, jf[w]);
+        ji[w] = 0;
+      }
+    }
+    __syncthreads();
+  };
+
+  int batches = 0;
   for (int s = 0; s < P.nspecies; ++s) {
     const SpeciesDev& S = P.sp[s];
     const long long lo = S.tstart[tile], hi = S.tstart[tile + 1];
@@ -240,21 +254,15 @@ __global__ void __launch_bounds__(kPushThreads) k_particles(const PushParams P) 
     for (long long base = a; base < b; base += blockDim.x) {  // block-uniform trip count
       const long long p = base + threadIdx.x;
       if (p < b) one_particle<D, MODE>(P, S, p, sm, SJ, GA, w0, qs);
-      if (MODE != 1) {
-        __syncthreads();
-        for (int w = threadIdx.x; w < 3 * wc; w += blockDim.x) {
-          const int v = ji[w];
-          if (v != 0) {
-            jf[w] = fmaf((float)v, P.jq, jf[w]);
-            ji[w] = 0;
-          }
-        }
-        __syncthreads();
+      if (MODE != 1 && ++batches == kSpillEvery) {
+        batches = 0;
+        spill();
       }
     }
   }
 
   if (MODE != 1) {
+    spill();
     for (int w = threadIdx.x; w < wc; w += blockDim.x) {
       const int lx = w % W0, rr = w / W0, ly = rr % W1, lz = rr / W1;
       const long long gi = GA.at(w0[0] + lx, w0[1] + ly, w0[2] + lz);
@@ -272,8 +280,8 @@ size_t particle_smem_bytes(int dim, const TileDev& t) {
   return sizeof(float) * (size_t)(nf + 6) * (size_t)t.wcells;
 }
 
-float current_quantum(float max_abs_q, int batch) {
-  const double bound = 4.0 * (double)batch * (double)max_abs_q;
+float current_quantum(float max_abs_q, float c, int batch) {
+  const double bound = 1.25 * (double)c * (double)batch * (double)max_abs_q;
   const int e = (int)std::ceil(std::log2(bound > 0 ? bound : 1.0));
   return (float)std::ldexp(1.0, e - 31);
 }

@@ -89,56 +89,10 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int* __restrict__ coun
   if (threadIdx.x == 0) start[ntiles] = carry;
 }
 
-// Per tile, a multiplier m coprime with the tile's count n (near 0.618 n)
-// and its inverse modulo n.  The scatter places the particle that took slot s
-// of its tile at slot s * m^-1 mod n, so neighbouring slots in memory come
-// from input slots about 0.618 n apart: the lanes of a warp then belong to
-// different cells, which keeps their shared-memory current atomics apart.
-__global__ void k_tile_mult(const int* __restrict__ start, int ntiles, int* minv) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ntiles) return;
-  const long long n = (long long)start[t + 1] - start[t];
-  if (n <= 2) {
-    minv[t] = 1;
-    return;
-  }
-  long long m = (long long)(0.6180339887498949 * (double)n);
-  if (m < 1) m = 1;
-  // a coprime multiplier: at most 64 candidates, then n - 1 (always coprime)
-  int tries = 0;
-  for (;; ++m, ++tries) {
-    long long a = m, b = n;
-    while (b) {
-      const long long r = a % b;
-      a = b;
-      b = r;
-    }
-    if (a == 1) break;
-    if (tries >= 64) {
-      m = n - 1;
-      break;
-    }
-  }
-  // inverse of m modulo n (extended Euclid)
-  long long r0 = n, r1 = m, t0 = 0, t1 = 1;
-  while (r1) {
-    const long long qq = r0 / r1;
-    long long tmp = r0 - qq * r1;
-    r0 = r1;
-    r1 = tmp;
-    tmp = t0 - qq * t1;
-    t0 = t1;
-    t1 = tmp;
-  }
-  if (t0 < 0) t0 += n;
-  minv[t] = (int)t0;
-}
-
 template <int D>
 __global__ void k_tile_scatter(const SortParams P, const int* __restrict__ cell,
                                const float* __restrict__ off, const float* __restrict__ u,
-                               long long n, int* cursor, const int* __restrict__ start,
-                               const int* __restrict__ minv, int* __restrict__ cell_out,
+                               long long n, int* cursor, int* __restrict__ cell_out,
                                float* __restrict__ off_out, float* __restrict__ u_out) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -147,11 +101,7 @@ __global__ void k_tile_scatter(const SortParams P, const int* __restrict__ cell,
     const unsigned active = __ballot_sync(0xffffffffu, act);
     if (act) {
       const int c = cell[p];
-      const int key = tile_key(P, c);
-      const long long s0 = start[key];
-      const long long cnt = (long long)start[key + 1] - s0;
-      const long long slot = warp_reserve(cursor, key, active) - s0;
-      const long long q = s0 + (slot * (long long)minv[key]) % cnt;
+      const long long q = warp_reserve(cursor, tile_key(P, c), active);
       cell_out[q] = c;
 #pragma unroll
       for (int d = 0; d < D; ++d) off_out[d * n + q] = off[d * n + p];
@@ -180,21 +130,15 @@ cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* curs
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_mult(const int* start, int ntiles, int* minv, cudaStream_t st) {
-  k_tile_mult<<<(ntiles + 255) / 256, 256, 0, st>>>(start, ntiles, minv);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_tile_scatter(const SortParams& P, const int* cell, const float* off,
-                                const float* u, long long n, int* cursor, const int* start,
-                                const int* minv, int* cell_out, float* off_out, float* u_out,
-                                cudaStream_t st) {
+                                const float* u, long long n, int* cursor, int* cell_out,
+                                float* off_out, float* u_out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const unsigned nb = blocks_for(n);
   switch (P.g.dim) {
-    case 1: k_tile_scatter<1><<<nb, 256, 0, st>>>(P, cell, off, u, n, cursor, start, minv, cell_out, off_out, u_out); break;
-    case 2: k_tile_scatter<2><<<nb, 256, 0, st>>>(P, cell, off, u, n, cursor, start, minv, cell_out, off_out, u_out); break;
-    case 3: k_tile_scatter<3><<<nb, 256, 0, st>>>(P, cell, off, u, n, cursor, start, minv, cell_out, off_out, u_out); break;
+    case 1: k_tile_scatter<1><<<nb, 256, 0, st>>>(P, cell, off, u, n, cursor, cell_out, off_out, u_out); break;
+    case 2: k_tile_scatter<2><<<nb, 256, 0, st>>>(P, cell, off, u, n, cursor, cell_out, off_out, u_out); break;
+    case 3: k_tile_scatter<3><<<nb, 256, 0, st>>>(P, cell, off, u, n, cursor, cell_out, off_out, u_out); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

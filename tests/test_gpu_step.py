@@ -190,6 +190,8 @@ def test_full_size_turbulence_step_sampled_against_oracle():
         oracle.deposit(g, Jo, x_old, dx, s0["q"])
     for c in range(6, 9):
         assert rel_err(Fg[c], Jo[c]) < 1e-5, c
+    # Gauss residual after one step: FP32 rounding of E and of the current
+    # terms, far below the field scale
     en = sim.energies()
-    assert en[2 + sim.nspecies] < 1e-5 * max(1e-3, np.abs(Fg[6:9]).max())
+    assert en[2 + sim.nspecies] < 1e-5 * max(np.abs(Fg[0:3]).max(), np.abs(Fg[6:9]).max())
     sim.close()
