@@ -177,6 +177,12 @@ pic_status pic_check(pic_ctx* ctx);
 pic_status pic_step_host(pic_ctx* ctx, const pic_host_species* hs, float* host_fields,
                          int nsteps);
 
+/* Synchronise and report, in *strays, how many particle updates since the
+ * last call found the particle outside its tile's shared-memory window and
+ * went through global memory instead (then reset the count).  The fraction
+ * strays / (particles * steps) is what the sort cadence trades against. */
+pic_status pic_stats(pic_ctx* ctx, int64_t* strays);
+
 /* Per-kernel timing with CUDA events on the context stream.  While enabled,
  * every launch of the kinds above is bracketed by events.  pic_kernel_times
  * synchronises, adds the elapsed milliseconds and launch counts of each kind

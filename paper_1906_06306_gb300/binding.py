@@ -54,6 +54,7 @@ SIGNATURES = {
     "pic_energies": (c_int, [_P, ctypes.POINTER(c_double), c_int]),
     "pic_check": (c_int, [_P]),
     "pic_step_host": (c_int, [_P, ctypes.POINTER(pic_host_species), c_void_p, c_int]),
+    "pic_stats": (c_int, [_P, ctypes.POINTER(c_int64)]),
     "pic_timing": (c_int, [_P, c_int]),
     "pic_kernel_times": (c_int, [_P, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     "pic_destroy": (c_int, [_P]),
@@ -148,6 +149,13 @@ def pic_check(ctx) -> None:
 def pic_step_host(ctx, host_species, host_fields_ptr: int, nsteps: int) -> None:
     arr = (pic_host_species * len(host_species))(*host_species)
     _check(_lib.pic_step_host(ctx, arr, c_void_p(host_fields_ptr), nsteps), ctx)
+
+
+def pic_stats(ctx) -> int:
+    """Particle updates that took the global-memory path since the last call."""
+    v = c_int64()
+    _check(_lib.pic_stats(ctx, ctypes.byref(v)), ctx)
+    return int(v.value)
 
 
 def pic_timing(ctx, enable: bool) -> None:

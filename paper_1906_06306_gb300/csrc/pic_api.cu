@@ -36,8 +36,8 @@ struct pic_ctx {
   int splits = 1;
   long long ntot = 0, nmax = 0;
   int* d_tstart[PIC_MAX_SPECIES] = {};
-  int* d_count = nullptr;
-  int* d_cursor = nullptr;
+  int* d_count = nullptr;   // per tile
+  int* d_cursor = nullptr;  // per tile
   void* d_sortbuf = nullptr;   // sorted particles of every species (one record layout each)
   bool sorted_pending = false;  // the next push reads the sorted buffer (no copy back)
   int* d_cell_old = nullptr;
@@ -48,6 +48,7 @@ struct pic_ctx {
   double* d_rho2 = nullptr;
   double* d_acc = nullptr;
   int* d_status = nullptr;
+  unsigned long long* d_strays = nullptr;  // particles that took the global path
   long long steps = 0;
   bool timing = false;
   std::vector<TimedLaunch> pending;
@@ -103,6 +104,7 @@ void free_all(pic_ctx* ctx) {
   dfree(ctx->d_rho2);
   dfree(ctx->d_acc);
   dfree(ctx->d_status);
+  dfree(ctx->d_strays);
   for (auto& t : ctx->pending) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
@@ -137,11 +139,12 @@ std::string derive_tiles(const pic_grid& grid, const pic_tuning& tun, long long 
     ntiles *= r.nt[d];
     wcells *= r.W[d];
   }
-  if ((long long)particle_smem_bytes(grid.dim, TileDev{{0, 0, 0}, {0, 0, 0}, 0, {0, 0, 0}, (int)wcells, 0}) >
-      200 * 1024)
+  if (wcells > (1LL << 24)) return "tile + halo window too large";
+  r.wcells = (int)wcells;
+  r.wstride = (int)((wcells + 3) / 4 * 4);
+  if ((long long)particle_smem_bytes(grid.dim, r) > 200 * 1024)
     return "tile + halo window exceeds 200 KB of shared memory";
   if (ntiles > (1LL << 30)) return "too many tiles";
-  r.wcells = (int)wcells;
   r.ntiles = (int)ntiles;
   const long long per_tile = (ntot + ntiles - 1) / ntiles;
   long long sp = (per_tile + tun.chunk - 1) / tun.chunk;
@@ -203,6 +206,7 @@ PushParams make_params(pic_ctx* ctx) {
   P.nspecies = ctx->ns;
   P.splits = ctx->splits;
   P.status = ctx->d_status;
+  P.strays = ctx->d_strays;
   P.inv_c = 1.0f / ctx->c;
   P.inv_c2 = 1.0f / (ctx->c * ctx->c);
   P.div0 = make_fastdiv(ctx->g.n[0]);
@@ -351,12 +355,12 @@ pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* spec
   ctx->g.n[2] = grid->nz;
   ctx->g.plane = ncell;
   ctx->g.c = c;
-  // defaults: tiles of 64 cells in 1D, 16^2 in 2D, 8^3 in 3D; sort every 20 steps
+  // defaults: tiles of 64 cells in 1D, 16^2 in 2D, 8^3 in 3D; sort every 10 steps
   ctx->tun.tile[0] = grid->dim == 1 ? 64 : grid->dim == 2 ? 16 : 8;
   ctx->tun.tile[1] = grid->dim == 2 ? 16 : 8;
   ctx->tun.tile[2] = 8;
   ctx->tun.halo = grid->dim == 3 ? 2 : 3;
-  ctx->tun.sort_every = 20;
+  ctx->tun.sort_every = 10;
   ctx->tun.filter_passes = 0;
   ctx->tun.chunk = 8192;
   const std::string msg = derive_tiles(ctx->grid, ctx->tun, ntot, &ctx->tile, &ctx->splits);
@@ -369,7 +373,10 @@ pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* spec
   if ((e = set_particle_smem_limit(200 * 1024)) != cudaSuccess) {
     s = cuda_fail(nullptr, "cudaFuncSetAttribute", e);
   } else if ((e = dalloc(&ctx->d_status, 1)) != cudaSuccess ||
-             (e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->st)) != cudaSuccess) {
+             (e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->st)) != cudaSuccess ||
+             (e = dalloc(&ctx->d_strays, 1)) != cudaSuccess ||
+             (e = cudaMemsetAsync(ctx->d_strays, 0, sizeof(unsigned long long), ctx->st)) !=
+                 cudaSuccess) {
     s = cuda_fail(nullptr, "status word", e);
   } else if ((e = dalloc((char**)&ctx->d_sortbuf, (size_t)ntot * (4 + 4 * grid->dim + 12))) !=
              cudaSuccess) {
@@ -575,6 +582,16 @@ pic_status pic_step_host(pic_ctx* ctx, const pic_host_species* hs, float* host_f
   }
   PIC_CK(ctx, cudaMemcpyAsync(host_fields, ctx->F, 36 * ctx->g.plane, d2h, ctx->st));
   PIC_CK(ctx, cudaStreamSynchronize(ctx->st));
+  return PIC_OK;
+}
+
+pic_status pic_stats(pic_ctx* ctx, int64_t* strays) {
+  if (!ctx || !strays) return set_err(ctx, PIC_ERR_ARG, "NULL argument");
+  unsigned long long h = 0;
+  PIC_CK(ctx, cudaMemcpyAsync(&h, ctx->d_strays, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
+  PIC_CK(ctx, cudaMemsetAsync(ctx->d_strays, 0, sizeof(h), ctx->st));
+  PIC_CK(ctx, cudaStreamSynchronize(ctx->st));
+  *strays = (int64_t)h;
   return PIC_OK;
 }
 

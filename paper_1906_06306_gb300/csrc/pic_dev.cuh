@@ -27,7 +27,8 @@ struct TileDev {
   int nt[3];   // tiles per axis
   int H;       // halo staged on the low side; H+1 on the high side
   int W[3];    // window extent T + 2H + 1 (1 on non-gridded axes)
-  int wcells;  // W0*W1*W2
+  int wcells;   // W0*W1*W2
+  int wstride;  // wcells rounded up to a multiple of 4 (16-byte aligned planes)
   int ntiles;
 };
 

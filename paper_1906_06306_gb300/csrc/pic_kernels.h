@@ -10,6 +10,7 @@ namespace pic {
 constexpr int kMaxSpecies = 4;
 constexpr int kPushThreads = 256;
 constexpr int kSpillEvery = 2;  // batches of kPushThreads particles between current spills
+constexpr int kQueueCap = 2048;  // shared-memory queue of particles outside the tile window
 
 struct PushParams {
   GridDev g;
@@ -24,6 +25,7 @@ struct PushParams {
   int wrap_fast;       // every axis has n >= window extent: one conditional wrap suffices
   float jq;            // quantum of the int32 shared-memory current (a power of 2)
   float jq_inv;        // 1 / jq
+  unsigned long long* strays;  // running count of particles that took the global path
 };
 
 // Quantum of the fixed-point shared-memory current (a power of 2) for charges

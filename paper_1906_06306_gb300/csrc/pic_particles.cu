@@ -17,8 +17,10 @@
 // batches of blockDim particles, before any int32 word can overflow.
 //
 // A particle whose stencil is not inside the window (it drifted more than
-// halo-1 cells since the last sort) reads and deposits through global memory
-// instead, so correctness never depends on the sort cadence.
+// halo-1 cells since the last sort) is put on a shared-memory queue and
+// processed later, in full warps, through global memory: warps of in-window
+// particles never diverge into the global path, and correctness never
+// depends on the sort cadence.
 #include <cmath>
 
 #include "pic_kernels.h"
@@ -29,6 +31,10 @@ template <int D>
 __host__ __device__ constexpr int field_floats() {
   return D == 1 ? 8 : 6;
 }
+
+// Words of the staged field region, rounded up so that the current planes
+// that follow start on a 16-byte boundary (they are accessed as int4/float4).
+__host__ __device__ inline int field_words(int nf, int wc) { return (nf * wc + 3) / 4 * 4; }
 
 __device__ __forceinline__ float lerp(float a, float b, float w) { return fmaf(w, b - a, a); }
 
@@ -82,72 +88,89 @@ __device__ __forceinline__ void gather_smem(const float* sm, int wc, int W0, int
   }
 }
 
+// Particle record as read from memory.
+struct PRec {
+  int cell;
+  float o[3];
+  float u[3];
+};
+
 template <int D, int MODE>
-__device__ __forceinline__ void one_particle(const PushParams& P, const SpeciesDev& S,
-                                             long long p, const float* sm, const SmemJ& SJ,
+__device__ __forceinline__ void load_rec(const SpeciesDev& S, int p, PRec& r) {
+  const long long n = S.n;
+  if (MODE == 2) {
+    r.cell = S.cell_old[p];
+#pragma unroll
+    for (int d = 0; d < D; ++d) r.o[d] = S.off_old[d * n + p];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) r.u[a] = S.u[a * n + p];
+  } else {
+    r.cell = S.rcell[p];
+#pragma unroll
+    for (int d = 0; d < D; ++d) r.o[d] = S.roff[d * n + p];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) r.u[a] = S.ru[a * n + p];
+  }
+#pragma unroll
+  for (int d = D; d < 3; ++d) r.o[d] = 0.f;
+}
+
+// One particle through gather -> Boris -> move -> ZigZag.  GLOBAL = false:
+// the shared-memory window is used and a particle whose stencil leaves the
+// window is not touched (returns false, the caller queues it).  GLOBAL = true:
+// everything goes through global memory (the deferred pass over the queue).
+template <int D, int MODE, bool GLOBAL>
+__device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesDev& S, int p,
+                                             PRec r, const float* sm, const SmemJ& SJ,
                                              const GlobAcc& GA, const int* w0, float qs) {
   const long long n = S.n;
-  int cell;
-  float o1[3] = {0.f, 0.f, 0.f};
-  float u[3];
-  if (MODE == 2) {
-    cell = S.cell_old[p];
+  // invalid data: cell outside the lattice, offset outside [0,1), non-finite u
+  bool bad_off = false;
 #pragma unroll
-    for (int d = 0; d < D; ++d) o1[d] = S.off_old[d * n + p];
-  } else {
-    cell = S.rcell[p];
-#pragma unroll
-    for (int d = 0; d < D; ++d) o1[d] = S.roff[d * n + p];
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) u[a] = MODE == 2 ? S.u[a * n + p] : S.ru[a * n + p];
-
-  if (cell < 0 || (long long)cell >= P.g.plane) {
-    atomicOr(P.status, ST_BAD_CELL);
-    return;
-  }
-  bool bad = false;
-#pragma unroll
-  for (int d = 0; d < D; ++d) bad |= !(o1[d] >= 0.0f && o1[d] < 1.0f);
-  if (bad) {
-    atomicOr(P.status, ST_BAD_OFF);
-    return;
-  }
-  if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]))) {
-    atomicOr(P.status, ST_BAD_U);
-    return;
+  for (int d = 0; d < D; ++d) bad_off |= !(r.o[d] >= 0.0f && r.o[d] < 1.0f);
+  const bool bad_cell = (unsigned)r.cell >= (unsigned long long)P.g.plane;
+  const bool bad_u = !(isfinite(r.u[0]) && isfinite(r.u[1]) && isfinite(r.u[2]));
+  if (bad_cell | bad_off | bad_u) {
+    atomicOr(P.status, (bad_cell ? ST_BAD_CELL : 0) | (bad_off ? ST_BAD_OFF : 0) |
+                           (bad_u ? ST_BAD_U : 0));
+    return true;
   }
 
   int ijk[3] = {0, 0, 0};
   {
-    const int r = fdiv(cell, P.div0);
-    ijk[0] = cell - r * P.g.n[0];
+    const int q = fdiv(r.cell, P.div0);
+    ijk[0] = r.cell - q * P.g.n[0];
     if (D >= 2) {
-      ijk[2] = fdiv(r, P.div1);
-      ijk[1] = r - ijk[2] * P.g.n[1];
+      ijk[2] = fdiv(q, P.div1);
+      ijk[1] = q - ijk[2] * P.g.n[1];
     }
   }
   int l[3] = {0, 0, 0};
-  bool inwin = true;
+  if (!GLOBAL) {
+    bool inwin = true;
 #pragma unroll
-  for (int d = 0; d < D; ++d) {
-    int v = ijk[d] - w0[d];
-    if (P.wrap_fast) {
-      v += (v < 0) ? P.g.n[d] : 0;
-      v -= (v >= P.g.n[d]) ? P.g.n[d] : 0;
-    } else {
-      v = wrapi(v, P.g.n[d]);
+    for (int d = 0; d < D; ++d) {
+      int v = ijk[d] - w0[d];
+      if (P.wrap_fast) {
+        v += (v < 0) ? P.g.n[d] : 0;
+        v -= (v >= P.g.n[d]) ? P.g.n[d] : 0;
+      } else {
+        v = wrapi(v, P.g.n[d]);
+      }
+      l[d] = v;
+      inwin &= (unsigned)(v - 1) <= (unsigned)(P.t.W[d] - 4);
     }
-    l[d] = v;
-    inwin &= (v >= 1) && (v <= P.t.W[d] - 3);
+    if (!inwin) return false;
   }
 
+  float* u = r.u;
+  const float* o1 = r.o;
   if (MODE != 2) {
     float e[3], b[3];
-    if (inwin)
-      gather_smem<D>(sm, P.t.wcells, P.t.W[0], P.t.W[0] * P.t.W[1], l, o1, e, b);
-    else
+    if (GLOBAL)
       gather<D>(GA, ijk, o1, e, b);
+    else
+      gather_smem<D>(sm, P.t.wcells, P.t.W[0], P.t.W[0] * P.t.W[1], l, o1, e, b);
     boris(u, e, b, S.qm, P.g.c, P.inv_c, P.inv_c2);
   }
   float o2[3] = {0.f, 0.f, 0.f}, dn[3];
@@ -165,22 +188,24 @@ __device__ __forceinline__ void one_particle(const PushParams& P, const SpeciesD
     for (int d = 0; d < D; ++d) S.off[d * n + p] = o2[d];
     S.cell[p] = cell2;
     if (MODE == 1) {
-      S.cell_old[p] = cell;
+      S.cell_old[p] = r.cell;
 #pragma unroll
       for (int d = 0; d < D; ++d) S.off_old[d * n + p] = o1[d];
     }
   }
   if (MODE != 1) {
-    if (inwin)
-      zigzag<D>(SJ, l, dc, o1, o2, dn, qs);
-    else
+    if (GLOBAL)
       zigzag<D>(GA, ijk, dc, o1, o2, dn, S.q);
+    else
+      zigzag<D>(SJ, l, dc, o1, o2, dn, qs);
   }
+  return true;
 }
 
 template <int D, int MODE>
 __global__ void __launch_bounds__(kPushThreads) k_particles(const PushParams P) {
   extern __shared__ __align__(16) float sm[];
+  __shared__ int q_n;  // entries in the stray queue
   const int tile = blockIdx.x / P.splits;
   const int split = blockIdx.x - tile * P.splits;
   const int tc[3] = {tile % P.t.nt[0], (tile / P.t.nt[0]) % P.t.nt[1],
@@ -189,13 +214,17 @@ __global__ void __launch_bounds__(kPushThreads) k_particles(const PushParams P) 
 #pragma unroll
   for (int d = 0; d < D; ++d) w0[d] = tc[d] * P.t.T[d] - P.t.H;
   const int wc = P.t.wcells;
+  const int ws = P.t.wstride;  // plane stride of the current windows (wc rounded up to 4)
   const int W0 = P.t.W[0], W1 = P.t.W[1];
   constexpr int NF = field_floats<D>();
-  int* ji = reinterpret_cast<int*>(sm + NF * wc);
-  float* jf = sm + (NF + 3) * wc;
+  const int fw = field_words(NF, wc);
+  int* ji = reinterpret_cast<int*>(sm + fw);
+  float* jf = sm + fw + 3 * ws;
+  int* queue = reinterpret_cast<int*>(sm + fw + 6 * ws);
   const GlobAcc GA{P.F, P.g.plane, P.g.n[0], P.g.n[1], P.g.n[2]};
-  const SmemJ SJ{ji, W0, W0 * W1, wc};
+  const SmemJ SJ{ji, W0, W0 * W1, ws};
 
+  if (threadIdx.x == 0) q_n = 0;
   for (int w = threadIdx.x; w < wc; w += blockDim.x) {
     const int lx = w % W0, rr = w / W0, ly = rr % W1, lz = rr / W1;
     const long long gi = GA.at(w0[0] + lx, w0[1] + ly, w0[2] + lz);
@@ -220,55 +249,88 @@ __global__ void __launch_bounds__(kPushThreads) k_particles(const PushParams P) 
         sm[BZ * wc + w] = bz;
       }
     }
-    if (MODE != 1) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        ji[c * wc + w] = 0;
-        jf[c * wc + w] = 0.0f;
-      }
-    }
+  }
+  if (MODE != 1) {
+    int4* j4 = reinterpret_cast<int4*>(ji);
+    for (int w = threadIdx.x; w < 6 * ws / 4; w += blockDim.x) j4[w] = make_int4(0, 0, 0, 0);
   }
   __syncthreads();
 
-  // fold the int32 window into the float window and clear it
+  // between barriers: fold the int32 window into the float window, clear it
   auto spill = [&]() {
-    __syncthreads();
-    for (int w = threadIdx.x; w < 3 * wc; w += blockDim.x) {
-      const int v = ji[w];
-      if (v != 0) {
-        jf[w] = fmaf((float)v, P.jq, jf[w]);
-        ji[w] = 0;
+    int4* i4 = reinterpret_cast<int4*>(ji);
+    float4* f4 = reinterpret_cast<float4*>(jf);
+    for (int w = threadIdx.x; w < 3 * ws / 4; w += blockDim.x) {
+      const int4 v = i4[w];
+      if ((v.x | v.y | v.z | v.w) != 0) {
+        float4 f = f4[w];
+        f.x = fmaf((float)v.x, P.jq, f.x);
+        f.y = fmaf((float)v.y, P.jq, f.y);
+        f.z = fmaf((float)v.z, P.jq, f.z);
+        f.w = fmaf((float)v.w, P.jq, f.w);
+        f4[w] = f;
+        i4[w] = make_int4(0, 0, 0, 0);
       }
     }
+  };
+  // process the queued strays through global memory, then empty the queue
+  auto drain = [&](const SpeciesDev& S, int cnt) {
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      PRec r;
+      load_rec<D, MODE>(S, queue[i], r);
+      one_particle<D, MODE, true>(P, S, queue[i], r, sm, SJ, GA, w0, 0.f);
+    }
+    if (threadIdx.x == 0) atomicAdd(P.strays, (unsigned long long)cnt);
+    __syncthreads();
+    if (threadIdx.x == 0) q_n = 0;
     __syncthreads();
   };
 
+  // Particles kPushThreads at a time; the record of the next batch is loaded
+  // while the current one is processed.  Every kSpillEvery batches (and only
+  // there) the block synchronises, folds the current and, if the stray queue
+  // could overflow in the next round, drains it.
   int batches = 0;
   for (int s = 0; s < P.nspecies; ++s) {
     const SpeciesDev& S = P.sp[s];
     const long long lo = S.tstart[tile], hi = S.tstart[tile + 1];
     const long long len = hi - lo;
-    const long long a = lo + len * split / P.splits;
-    const long long b = lo + len * (split + 1) / P.splits;
+    const int a = (int)(lo + len * split / P.splits);
+    const int b = (int)(lo + len * (split + 1) / P.splits);
     const float qs = S.q * P.jq_inv;
-    for (long long base = a; base < b; base += blockDim.x) {  // block-uniform trip count
-      const long long p = base + threadIdx.x;
-      if (p < b) one_particle<D, MODE>(P, S, p, sm, SJ, GA, w0, qs);
-      if (MODE != 1 && ++batches == kSpillEvery) {
+    PRec cur, nxt;
+    if (a + (int)threadIdx.x < b) load_rec<D, MODE>(S, a + threadIdx.x, cur);
+    for (int base = a; base < b; base += blockDim.x) {  // block-uniform trip count
+      const int p = base + threadIdx.x;
+      if (p + (int)blockDim.x < b) load_rec<D, MODE>(S, p + blockDim.x, nxt);
+      if (p < b && !one_particle<D, MODE, false>(P, S, p, cur, sm, SJ, GA, w0, qs))
+        queue[atomicAdd(&q_n, 1)] = p;
+      cur = nxt;
+      if (++batches == kSpillEvery) {
         batches = 0;
-        spill();
+        __syncthreads();
+        const int qn = q_n;  // read by every thread before anyone can queue again
+        if (MODE != 1) spill();
+        __syncthreads();
+        if (qn > kQueueCap - kSpillEvery * (int)blockDim.x) drain(S, qn);
       }
     }
+    // end of species: everything queued for it is processed before the next
+    __syncthreads();
+    const int qn = q_n;
+    __syncthreads();
+    if (qn > 0) drain(S, qn);
   }
 
   if (MODE != 1) {
     spill();
+    __syncthreads();
     for (int w = threadIdx.x; w < wc; w += blockDim.x) {
       const int lx = w % W0, rr = w / W0, ly = rr % W1, lz = rr / W1;
       const long long gi = GA.at(w0[0] + lx, w0[1] + ly, w0[2] + lz);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float v = jf[c * wc + w];
+        const float v = jf[c * ws + w];
         if (v != 0.0f) atomicAdd(&P.F[(JX + c) * P.g.plane + gi], v);
       }
     }
@@ -277,7 +339,8 @@ __global__ void __launch_bounds__(kPushThreads) k_particles(const PushParams P) 
 
 size_t particle_smem_bytes(int dim, const TileDev& t) {
   const int nf = dim == 1 ? field_floats<1>() : field_floats<2>();
-  return sizeof(float) * (size_t)(nf + 6) * (size_t)t.wcells;
+  return sizeof(float) * ((size_t)field_words(nf, t.wcells) + 6 * (size_t)t.wstride) +
+         sizeof(int) * kQueueCap;
 }
 
 float current_quantum(float max_abs_q, float c, int batch) {
