@@ -191,11 +191,40 @@ pic_status pic_stats(pic_ctx* ctx, int64_t* strays);
 pic_status pic_timing(pic_ctx* ctx, int enable);
 pic_status pic_kernel_times(pic_ctx* ctx, double* ms, int64_t* launches);
 
+/* Allocation-free variant of pic_filter_current.  The paper has no
+ * counterpart; this entry point exists for callers that cannot let a library
+ * allocate device memory: applications whose memory manager (for instance a
+ * framework's caching allocator) owns the device and forbids raw cudaMalloc,
+ * code that must stay inside a fixed memory budget, and latency-critical loops
+ * where the device-wide synchronisation that cudaFree implies would stall
+ * other streams.  It needs no context and calls no allocator: its scratch is
+ * a fixed array of PIC_FILTER_STATIC_MAX_FLOATS floats (16 MiB) compiled into
+ * the library, which every GPU that loads the library holds until the process
+ * exits.
+ *
+ * grid: as for pic_init.  J: device pointer to the caller's three current
+ * planes Jx, Jy, Jz, contiguous, nx*ny*nz floats each (the layout of planes
+ * 6-8 of the field buffer), filtered in place by `passes` (>= 0) Binomial2
+ * passes, enqueued on `stream` (a cudaStream_t, NULL = legacy default) without
+ * synchronising.  3*nx*ny*nz larger than PIC_FILTER_STATIC_MAX_FLOATS is
+ * rejected with PIC_ERR_ARG; CUDA failures give PIC_ERR_CUDA; the message is
+ * in pic_last_error(NULL).
+ *
+ * The first call on a device looks up the device address of the scratch array
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call uses the same array, which keeps the last
+ * call's contents; each pass writes the whole part it later reads, so nothing
+ * needs clearing.  Calls whose GPU work overlaps (on different streams or from
+ * different host threads, on the same device) race on the array: the caller
+ * must order them. */
+#define PIC_FILTER_STATIC_MAX_FLOATS 4194304
+pic_status pic_filter_current_static(const pic_grid* grid, float* J, int passes, void* stream);
+
 /* Release the context and its scratch (the caller's buffers are untouched). */
 pic_status pic_destroy(pic_ctx* ctx);
 
 /* Message of the last failure on ctx ("" if none); for ctx == NULL, the last
- * failure of pic_init in this process. */
+ * failure of pic_init or pic_filter_current_static in the calling thread. */
 const char* pic_last_error(const pic_ctx* ctx);
 
 #ifdef __cplusplus

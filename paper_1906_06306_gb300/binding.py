@@ -57,6 +57,7 @@ SIGNATURES = {
     "pic_stats": (c_int, [_P, ctypes.POINTER(c_int64)]),
     "pic_timing": (c_int, [_P, c_int]),
     "pic_kernel_times": (c_int, [_P, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
+    "pic_filter_current_static": (c_int, [ctypes.POINTER(pic_grid), c_void_p, c_int, c_void_p]),
     "pic_destroy": (c_int, [_P]),
     "pic_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -167,6 +168,16 @@ def pic_kernel_times(ctx):
     n = (c_int64 * len(KERNEL_KINDS))()
     _check(_lib.pic_kernel_times(ctx, ms, n), ctx)
     return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+PIC_FILTER_STATIC_MAX_FLOATS = 4194304
+
+
+def pic_filter_current_static(grid: pic_grid, j_ptr: int, passes: int, stream: int) -> None:
+    """Allocation-free Binomial2 filter of the three J planes at device address
+    j_ptr (in place, on `stream`); see include/pic.h for the size limit."""
+    _check(_lib.pic_filter_current_static(ctypes.byref(grid), c_void_p(j_ptr), passes,
+                                          c_void_p(stream)), None)
 
 
 def pic_destroy(ctx) -> None:

@@ -23,6 +23,10 @@ thread_local std::string g_init_error;
 
 }  // namespace
 
+namespace pic {
+void set_global_error(const char* msg) { g_init_error = msg; }
+}  // namespace pic
+
 struct pic_ctx {
   pic_grid grid{};
   int ns = 0;

@@ -37,6 +37,9 @@ struct PushParams {
 float current_quantum(float max_abs_q, float c, int batch);
 FastDiv make_fastdiv(int d);
 
+// message returned by pic_last_error(NULL) in the calling thread
+void set_global_error(const char* msg);
+
 // mode 0: fused gather + push + move + deposit; 1: gather + push + move and
 // pre-move snapshot; 2: deposit from the snapshot and the stored new u.
 cudaError_t launch_particles(int dim, int mode, const PushParams& P, cudaStream_t st);
