@@ -366,7 +366,7 @@ pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* spec
   ctx->tun.halo = grid->dim == 3 ? 2 : 3;
   ctx->tun.sort_every = 10;
   ctx->tun.filter_passes = 0;
-  ctx->tun.chunk = 8192;
+  ctx->tun.chunk = 4096;
   const std::string msg = derive_tiles(ctx->grid, ctx->tun, ntot, &ctx->tile, &ctx->splits);
   if (!msg.empty()) {
     delete ctx;

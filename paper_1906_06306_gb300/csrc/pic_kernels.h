@@ -8,8 +8,20 @@
 namespace pic {
 
 constexpr int kMaxSpecies = 4;
-constexpr int kPushThreads = 256;
-constexpr int kSpillEvery = 2;  // batches of kPushThreads particles between current spills
+#ifndef PIC_PUSH_THREADS
+#define PIC_PUSH_THREADS 256
+#endif
+#ifndef PIC_SPILL_EVERY
+#define PIC_SPILL_EVERY 8
+#endif
+#ifndef PIC_PUSH_MIN_BLOCKS
+#define PIC_PUSH_MIN_BLOCKS 5
+#endif
+#ifndef PIC_PREFETCH
+#define PIC_PREFETCH 0
+#endif
+constexpr int kPushThreads = PIC_PUSH_THREADS;
+constexpr int kSpillEvery = PIC_SPILL_EVERY;  // batches of kPushThreads particles between spills
 constexpr int kQueueCap = 2048;  // shared-memory queue of particles outside the tile window
 
 struct PushParams {

@@ -203,7 +203,7 @@ __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesD
 }
 
 template <int D, int MODE>
-__global__ void __launch_bounds__(kPushThreads) k_particles(const PushParams P) {
+__global__ void __launch_bounds__(kPushThreads, PIC_PUSH_MIN_BLOCKS) k_particles(const PushParams P) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int q_n;  // entries in the stray queue
   const int tile = blockIdx.x / P.splits;
@@ -299,13 +299,17 @@ __global__ void __launch_bounds__(kPushThreads) k_particles(const PushParams P) 
     const int b = (int)(lo + len * (split + 1) / P.splits);
     const float qs = S.q * P.jq_inv;
     PRec cur, nxt;
-    if (a + (int)threadIdx.x < b) load_rec<D, MODE>(S, a + threadIdx.x, cur);
+    if (PIC_PREFETCH && a + (int)threadIdx.x < b) load_rec<D, MODE>(S, a + threadIdx.x, cur);
     for (int base = a; base < b; base += blockDim.x) {  // block-uniform trip count
       const int p = base + threadIdx.x;
-      if (p + (int)blockDim.x < b) load_rec<D, MODE>(S, p + blockDim.x, nxt);
+      if (PIC_PREFETCH) {
+        if (p + (int)blockDim.x < b) load_rec<D, MODE>(S, p + blockDim.x, nxt);
+      } else if (p < b) {
+        load_rec<D, MODE>(S, p, cur);
+      }
       if (p < b && !one_particle<D, MODE, false>(P, S, p, cur, sm, SJ, GA, w0, qs))
         queue[atomicAdd(&q_n, 1)] = p;
-      cur = nxt;
+      if (PIC_PREFETCH) cur = nxt;
       if (++batches == kSpillEvery) {
         batches = 0;
         __syncthreads();
