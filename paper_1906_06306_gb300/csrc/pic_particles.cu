@@ -203,7 +203,8 @@ __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesD
 }
 
 template <int D, int MODE>
-__global__ void __launch_bounds__(kPushThreads, PIC_PUSH_MIN_BLOCKS) k_particles(const PushParams P) {
+__global__ void __launch_bounds__(kPushThreads, D == 3 ? 2 : PIC_PUSH_MIN_BLOCKS)
+    k_particles(const PushParams P) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int q_n;  // entries in the stray queue
   const int tile = blockIdx.x / P.splits;

@@ -1,0 +1,72 @@
+"""Physics of the FP32 GPU path over long runs, against the paper and the FP64
+oracle: the relativistic Weibel growth rate of Sect. 4.1, energy exchange,
+and the Gauss law of Appendix B over hundreds of steps with sorts."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _fit_rate(eb):
+    eb = np.asarray(eb)
+    t = np.arange(1, len(eb) + 1)
+    sat = eb.max()
+    end = np.argmax(eb > 0.5 * sat)
+    win = (eb > 3e-4 * sat) & (eb < 3e-2 * sat) & (t < t[end])
+    assert win.sum() > 30
+    return np.polyfit(t[win], np.log(eb[win]), 1)[0]
+
+
+def test_weibel_growth_rate_fp32_matches_theory_and_oracle():
+    """1D3V Weibel box of Sect. 4.1 (512 cells, 64 particles per cell per
+    species, gamma_b = 3, theta = 0.01): the FP32 run grows the magnetic energy
+    at 2 delta, delta = beta_b sqrt(2/gamma_b) c/R_p, within the band the oracle
+    is pinned to, and within 3 % of the FP64 oracle's fitted rate from the same
+    initial state."""
+    from paper_1906_06306_gb300 import Simulation
+
+    pl = workloads.weibel_1d()
+    m = pl.meta
+    delta = m["beta_b"] * math.sqrt(2.0 / m["gamma_b"]) * pl.c / m["r_p"]
+    sim = Simulation.from_plasma(pl)
+    g = oracle.Grid(1, pl.nx, 1, 1, pl.c)
+    _, F, osp = oracle.from_plasma(pl)
+    eb_gpu, eb_orc, tot = [], [], []
+    for _ in range(230):
+        sim.step(1)
+        en = sim.energies()
+        eb_gpu.append(en[1])
+        tot.append(sum(en[:4]))
+        oracle.step(g, F, osp)
+        eb_orc.append(oracle.field_energy(g, F)[1])
+    sim.check()
+    r_gpu, r_orc = _fit_rate(eb_gpu), _fit_rate(eb_orc)
+    assert 0.85 * 2 * delta < r_gpu < 1.02 * 2 * delta, (r_gpu, 2 * delta)
+    assert abs(r_gpu - r_orc) < 0.03 * r_orc, (r_gpu, r_orc)
+    # energy: drift of the total far below the energy moved into the field
+    assert abs(tot[-1] - tot[0]) < 0.05 * max(eb_gpu)
+    sim.close()
+
+
+def test_gauss_law_over_long_run_with_sorts():
+    """500 steps of a 2D turbulence box with a tile sort every 10 steps and the
+    default halo: particles cross tiles, take the stray path and are re-sorted;
+    div E - rho stays at FP32 round-off relative to the charge-separation
+    signal."""
+    from paper_1906_06306_gb300 import Simulation
+
+    pl = workloads.turbulence_2d(n=96, ppc=8, r_p=4.0, theta=0.3, sigma=10.0, modes=4, seed=31)
+    sim = Simulation.from_plasma(pl)
+    sim.step(500)
+    sim.check()
+    en = sim.energies()
+    Fg, _ = sim.download()
+    g = oracle.Grid(2, 96, 96, 1, 0.45)
+    div_scale = np.abs(oracle.div_e(g, Fg.astype(np.float64))).max()
+    assert en[2 + sim.nspecies] < 1e-3 * div_scale, (en[2 + sim.nspecies], div_scale)
+    sim.close()
