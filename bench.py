@@ -263,10 +263,14 @@ def run_ours(args):
     # every rank steps its own replica of the box; --grid changes its size for profiling runs
     w = WORKLOADS[args.workload]
     pl = w["make"](args.grid or w["grid"])
-    tuning = dict(sort_every=args.sort_every, filter_passes=w["filter_passes"])
+    tuning = dict(filter_passes=w["filter_passes"])
+    if args.sort_every:
+        tuning["sort_every"] = args.sort_every
     sim = Simulation.from_plasma(pl, device=f"cuda:{local}", tuning=tuning)
-    tun = sim.tuning()
     dev = torch.device(f"cuda:{local}")
+    if args.autotune:  # untimed: real steps under candidate tunings, keeps the fastest
+        sim.autotune(None, steps=20)
+    tun = sim.tuning()
     for _ in range(args.warmup):
         sim.step(1)
     torch.cuda.synchronize(dev)
@@ -341,9 +345,8 @@ def run_ours(args):
     alg = push_bytes_per_launch(pl)
     achieved = alg / avg_push_s / 1e9
     traffic = profiled_traffic() if args.workload == "turbulence_2d3v" and pl.nx == 1024 else None
-    nsorts = sum(1 for s in range(args.warmup, args.warmup + args.steps)
-                 if s > 0 and s % tun["sort_every"] == 0)
-    launches = args.steps * (4 + tun["filter_passes"]) + nsorts * 3 * sim.nspecies
+    nsorts = -(-args.steps // tun["sort_every"])  # at most one sort per cadence in the loop
+    launches = args.steps * (4 + tun["filter_passes"] * pl.dim) + nsorts * 3 * sim.nspecies
     wl = workload_config(args.workload, pl)
     line = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
@@ -351,7 +354,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": dict(wl, particles=pl.nparticles, sort_every=tun["sort_every"],
-                       tile=tun["tile"][: pl.dim], halo=tun["halo"],
+                       tile=tun["tile"][: pl.dim], halo=tun["halo"], autotuned=bool(args.autotune),
                        parallelism="replicas" if world > 1 else "single-gpu",
                        l2=("inputs larger than L2 (particle SoA %.2f GB), no flush" if
                            pl.nparticles * (16 + 4 * pl.dim) > 2 * 129e6 else
@@ -383,7 +386,9 @@ def main():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--sort-every", type=int, default=10)
+    ap.add_argument("--sort-every", type=int, default=0, help="0 = library default / autotuned")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default tuning instead of autotuning before the timed region")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=0,

@@ -55,7 +55,8 @@ typedef enum {
 #define PIC_MAX_SPECIES 4
 
 /* Periodic box: dim = 1, 2 or 3 gridded dimensions; extents of non-gridded
- * dimensions must be 1.  nx*ny*nz must fit in int32. */
+ * dimensions must be 1.  nx*ny*nz must fit in int32, ny <= 65535 and
+ * nz <= 21845 (launch-grid limits of the filter). */
 typedef struct {
   int dim;
   int nx, ny, nz;
@@ -176,6 +177,19 @@ pic_status pic_check(pic_ctx* ctx);
  * same host buffers and synchronises. */
 pic_status pic_step_host(pic_ctx* ctx, const pic_host_species* hs, float* host_fields,
                          int nsteps);
+
+/* Autotuner of the launch parameters (tile size, halo, sort cadence; the
+ * filter passes are physics and are kept).  Runs real time steps, which
+ * advance the simulation exactly as pic_step does: for each candidate it
+ * re-sorts if the tiles change, takes one step, then times
+ * max(steps, 2*sort_every) steps (rounded up to whole sort cycles) with CUDA
+ * events, and finally keeps the fastest candidate.  candidates == NULL selects
+ * a built-in set of 18 for the grid's dimension (three tile shapes around the
+ * default, halos 2 and 3, three cadences).  *best_index (may be NULL) receives
+ * the chosen candidate's index.  Synchronises.  Candidates that pic_set_tuning
+ * rejects are skipped; PIC_ERR_ARG if none is valid. */
+pic_status pic_autotune(pic_ctx* ctx, const pic_tuning* candidates, int ncandidates, int steps,
+                        int* best_index);
 
 /* Synchronise and report, in *strays, how many particle updates since the
  * last call found the particle outside its tile's shared-memory window and

@@ -54,6 +54,7 @@ SIGNATURES = {
     "pic_energies": (c_int, [_P, ctypes.POINTER(c_double), c_int]),
     "pic_check": (c_int, [_P]),
     "pic_step_host": (c_int, [_P, ctypes.POINTER(pic_host_species), c_void_p, c_int]),
+    "pic_autotune": (c_int, [_P, ctypes.POINTER(pic_tuning), c_int, c_int, ctypes.POINTER(c_int)]),
     "pic_stats": (c_int, [_P, ctypes.POINTER(c_int64)]),
     "pic_timing": (c_int, [_P, c_int]),
     "pic_kernel_times": (c_int, [_P, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
@@ -150,6 +151,18 @@ def pic_check(ctx) -> None:
 def pic_step_host(ctx, host_species, host_fields_ptr: int, nsteps: int) -> None:
     arr = (pic_host_species * len(host_species))(*host_species)
     _check(_lib.pic_step_host(ctx, arr, c_void_p(host_fields_ptr), nsteps), ctx)
+
+
+def pic_autotune(ctx, candidates=None, steps: int = 20) -> int:
+    """Run real steps under each candidate tuning (None: the built-in set) and keep
+    the fastest; returns the chosen candidate's index."""
+    best = c_int(-1)
+    if candidates:
+        arr = (pic_tuning * len(candidates))(*candidates)
+        _check(_lib.pic_autotune(ctx, arr, len(candidates), steps, ctypes.byref(best)), ctx)
+    else:
+        _check(_lib.pic_autotune(ctx, None, 0, steps, ctypes.byref(best)), ctx)
+    return int(best.value)
 
 
 def pic_stats(ctx) -> int:

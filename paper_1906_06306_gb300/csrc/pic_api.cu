@@ -1,6 +1,7 @@
 // C ABI of the PIC hot path (see include/pic.h): argument checking, scratch
 // ownership, the order of the time step (Table 1 of arXiv:1906.06306) and
 // event timing.  All device work goes to the context's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -294,12 +295,14 @@ pic_status do_filter(pic_ctx* ctx, int passes) {
   float* a = J;
   float* b = ctx->d_jtmp;
   for (int p = 0; p < passes; ++p) {
-    const cudaError_t e = timed(ctx, PIC_KERNEL_FILTER,
-                                [&]() { return launch_filter_f32(ctx->g, a, b, 3, ctx->st); });
-    if (e != cudaSuccess) return cuda_fail(ctx, "binomial filter", e);
-    float* t = a;
-    a = b;
-    b = t;
+    for (int axis = 0; axis < ctx->grid.dim; ++axis) {
+      const cudaError_t e = timed(
+          ctx, PIC_KERNEL_FILTER, [&]() { return launch_filter_f32(ctx->g, a, b, 3, axis, ctx->st); });
+      if (e != cudaSuccess) return cuda_fail(ctx, "binomial filter", e);
+      float* t = a;
+      a = b;
+      b = t;
+    }
   }
   if (a != J)
     PIC_CK(ctx, cudaMemcpyAsync(J, a, sizeof(float) * 3 * ctx->g.plane, cudaMemcpyDeviceToDevice,
@@ -327,6 +330,8 @@ pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* spec
     ncell *= n;
   }
   if (ncell > 0x7fffffffLL) return set_err(nullptr, PIC_ERR_ARG, "nx*ny*nz must fit in int32");
+  if (grid->ny > 65535 || grid->nz > 21845)
+    return set_err(nullptr, PIC_ERR_ARG, "ny must be <= 65535 and nz <= 21845");
   if (nspecies < 1 || nspecies > PIC_MAX_SPECIES)
     return set_err(nullptr, PIC_ERR_ARG, "nspecies must be in 1..4");
   if (!(c > 0.f && c < 1.f)) return set_err(nullptr, PIC_ERR_ARG, "Courant number must be in (0, 1)");
@@ -359,12 +364,13 @@ pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* spec
   ctx->g.n[2] = grid->nz;
   ctx->g.plane = ncell;
   ctx->g.c = c;
-  // defaults: tiles of 64 cells in 1D, 16^2 in 2D, 8^3 in 3D; sort every 10 steps
+  // defaults: tiles of 64 cells in 1D, 16^2 in 2D, 8x8x4 in 3D; sort every 10 steps
+  // (3 in 3D, where a 2-cell halo is all the shared memory affords)
   ctx->tun.tile[0] = grid->dim == 1 ? 64 : grid->dim == 2 ? 16 : 8;
   ctx->tun.tile[1] = grid->dim == 2 ? 16 : 8;
-  ctx->tun.tile[2] = 8;
+  ctx->tun.tile[2] = 4;
   ctx->tun.halo = grid->dim == 3 ? 2 : 3;
-  ctx->tun.sort_every = 10;
+  ctx->tun.sort_every = grid->dim == 3 ? 3 : 10;
   ctx->tun.filter_passes = 0;
   ctx->tun.chunk = 4096;
   const std::string msg = derive_tiles(ctx->grid, ctx->tun, ntot, &ctx->tile, &ctx->splits);
@@ -530,10 +536,12 @@ pic_status pic_energies(pic_ctx* ctx, double* out, int nout) {
   double* a = ctx->d_rho;
   double* b = ctx->d_rho2;
   for (int p = 0; p < ctx->tun.filter_passes; ++p) {
-    PIC_CK(ctx, launch_filter_f64(ctx->g, a, b, 1, ctx->st));
-    double* t = a;
-    a = b;
-    b = t;
+    for (int axis = 0; axis < ctx->grid.dim; ++axis) {
+      PIC_CK(ctx, launch_filter_f64(ctx->g, a, b, 1, axis, ctx->st));
+      double* t = a;
+      a = b;
+      b = t;
+    }
   }
   PIC_CK(ctx, launch_gauss(ctx->g, ctx->F, a, (unsigned long long*)(ctx->d_acc + 2 + ns),
                            ctx->d_acc + 3 + ns, ctx->st));
@@ -597,6 +605,77 @@ pic_status pic_stats(pic_ctx* ctx, int64_t* strays) {
   PIC_CK(ctx, cudaStreamSynchronize(ctx->st));
   *strays = (int64_t)h;
   return PIC_OK;
+}
+
+pic_status pic_autotune(pic_ctx* ctx, const pic_tuning* candidates, int ncandidates, int steps,
+                        int* best_index) {
+  if (!ctx) return PIC_ERR_ARG;
+  if (steps < 1) return set_err(ctx, PIC_ERR_ARG, "steps must be >= 1");
+  if (candidates && ncandidates < 1) return set_err(ctx, PIC_ERR_ARG, "ncandidates must be >= 1");
+  std::vector<pic_tuning> cs;
+  if (candidates) {
+    cs.assign(candidates, candidates + ncandidates);
+  } else {
+    // built-in candidates: tile shapes around the default, two halos, cadences
+    const int D = ctx->grid.dim;
+    const int tiles1[][3] = {{32, 1, 1}, {64, 1, 1}, {128, 1, 1}};
+    const int tiles2[][3] = {{16, 16, 1}, {8, 16, 1}, {16, 8, 1}};
+    const int tiles3[][3] = {{8, 8, 4}, {8, 8, 8}, {8, 4, 4}};
+    const int (*tiles)[3] = D == 1 ? tiles1 : D == 2 ? tiles2 : tiles3;
+    const int cad2[] = {5, 10, 20}, cad3[] = {2, 3, 5};
+    const int* cad = D == 3 ? cad3 : cad2;
+    for (int t = 0; t < 3; ++t)
+      for (int h = 2; h <= 3; ++h)
+        for (int k = 0; k < 3; ++k) {
+          pic_tuning c{};
+          for (int d = 0; d < 3; ++d) c.tile[d] = tiles[t][d];
+          c.halo = h;
+          c.sort_every = cad[k];
+          cs.push_back(c);
+        }
+  }
+  const pic_tuning orig = ctx->tun;
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  PIC_CK(ctx, cudaEventCreate(&ea));
+  PIC_CK(ctx, cudaEventCreate(&eb));
+  double best_ms = 1e300;
+  int best = -1;
+  pic_status st = PIC_OK;
+  for (size_t i = 0; i < cs.size() && st == PIC_OK; ++i) {
+    pic_tuning t = cs[i];
+    t.filter_passes = orig.filter_passes;  // physics, not a launch parameter
+    if (t.chunk == 0) t.chunk = orig.chunk;
+    if (pic_set_tuning(ctx, &t) != PIC_OK) continue;  // e.g. window too large: skip
+    const int k = ((std::max(steps, 2 * ctx->tun.sort_every) + ctx->tun.sort_every - 1) /
+                   ctx->tun.sort_every) * ctx->tun.sort_every;
+    if ((st = pic_step(ctx, 1)) != PIC_OK) break;
+    cudaEventRecord(ea, ctx->st);
+    if ((st = pic_step(ctx, k)) != PIC_OK) break;
+    cudaEventRecord(eb, ctx->st);
+    if (cudaEventSynchronize(eb) != cudaSuccess) {
+      st = cuda_fail(ctx, "autotune timing", cudaGetLastError());
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ea, eb);
+    if (ms / k < best_ms) {
+      best_ms = ms / k;
+      best = (int)i;
+    }
+  }
+  cudaEventDestroy(ea);
+  cudaEventDestroy(eb);
+  if (st != PIC_OK) return st;
+  if (best < 0) {
+    pic_set_tuning(ctx, &orig);
+    return set_err(ctx, PIC_ERR_ARG, "no candidate tuning was valid");
+  }
+  pic_tuning t = cs[best];
+  t.filter_passes = orig.filter_passes;
+  if (t.chunk == 0) t.chunk = orig.chunk;
+  st = pic_set_tuning(ctx, &t);
+  if (st == PIC_OK && best_index) *best_index = best;
+  return st;
 }
 
 pic_status pic_timing(pic_ctx* ctx, int enable) {

@@ -2,7 +2,8 @@
 // Sect. 2.3.1, Eqs. (fdE), (fdB), Table 2) on periodic Yee planes.
 // One thread per lattice point, x fastest, so every plane is streamed with
 // coalesced loads; neighbours one point away come from the same or adjacent
-// rows and hit L1/L2.
+// rows and hit L1/L2.  The filter runs as one 3-point sub-pass per gridded
+// axis (x, then y, then z), the order in which the paper's filter is applied.
 #include "pic_kernels.h"
 
 namespace pic {
@@ -87,41 +88,26 @@ __global__ void k_e_update(float* __restrict__ F, const GridDev g, float c) {
   }
 }
 
-// One Binomial2 pass: (1/4, 1/2, 1/4) along x, then y, then z (gridded axes),
-// evaluated as the separable 3^D stencil in that order.
-template <int D, typename T>
-__global__ void k_filter(const T* __restrict__ src, T* __restrict__ dst, const GridDev g,
-                         int ncomp) {
-  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+// One Binomial2 sub-pass along one axis: dst = (1/4, 1/2, 1/4) * src along
+// `axis`, periodic.  Thread (x, y, z*ncomp) of a 3D launch grid owns one
+// lattice value, so neighbours along every axis are coalesced loads.
+template <typename T>
+__global__ void k_filter_axis(const T* __restrict__ src, T* __restrict__ dst, const GridDev g,
+                              int axis) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n[0]) return;
+  const int j = blockIdx.y;
+  const int k = blockIdx.z % g.n[2];
+  const long long comp = blockIdx.z / g.n[2];
   const long long P = g.plane;
-  const T q = T(0.25), h = T(0.5);
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P * ncomp;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long comp = idx / P, cidx = idx - comp * P;
-    const int i = (int)(cidx % n0);
-    const long long r = cidx / n0;
-    const int j = (int)(r % n1), k = (int)(r / n1);
-    const T* s = src + comp * P;
-    const int im = i > 0 ? i - 1 : n0 - 1, ip = i + 1 < n0 ? i + 1 : 0;
-    auto row = [&](int jj, int kk) -> T {
-      const long long base = (long long)n0 * (jj + (long long)n1 * kk);
-      return q * s[base + im] + h * s[base + i] + q * s[base + ip];
-    };
-    T out;
-    if (D == 1) {
-      out = row(0, 0);
-    } else {
-      const int jm = j > 0 ? j - 1 : n1 - 1, jp = j + 1 < n1 ? j + 1 : 0;
-      auto plane_ = [&](int kk) -> T { return q * row(jm, kk) + h * row(j, kk) + q * row(jp, kk); };
-      if (D == 2) {
-        out = plane_(0);
-      } else {
-        const int km = k > 0 ? k - 1 : n2 - 1, kp = k + 1 < n2 ? k + 1 : 0;
-        out = q * plane_(km) + h * plane_(k) + q * plane_(kp);
-      }
-    }
-    dst[idx] = out;
-  }
+  const long long idx = (long long)i + (long long)g.n[0] * (j + (long long)g.n[1] * k);
+  const T* s = src + comp * P;
+  const int a = axis == 0 ? i : axis == 1 ? j : k;
+  const int na = g.n[axis];
+  const long long stride = axis == 0 ? 1 : axis == 1 ? (long long)g.n[0] : (long long)g.n[0] * g.n[1];
+  const long long lo = a > 0 ? idx - stride : idx + (long long)(na - 1) * stride;
+  const long long hi = a + 1 < na ? idx + stride : idx - (long long)(na - 1) * stride;
+  dst[comp * P + idx] = T(0.25) * s[lo] + T(0.5) * s[idx] + T(0.25) * s[hi];
 }
 
 cudaError_t launch_b_half(const GridDev& g, float* F, int zero_j, cudaStream_t st) {
@@ -148,26 +134,23 @@ cudaError_t launch_e_update(const GridDev& g, float* F, cudaStream_t st) {
 }
 
 template <typename T>
-static cudaError_t launch_filter(const GridDev& g, const T* src, T* dst, int ncomp,
+static cudaError_t launch_filter(const GridDev& g, const T* src, T* dst, int ncomp, int axis,
                                  cudaStream_t st) {
-  const unsigned nb = grid_for(g.plane * ncomp, 256);
-  switch (g.dim) {
-    case 1: k_filter<1, T><<<nb, 256, 0, st>>>(src, dst, g, ncomp); break;
-    case 2: k_filter<2, T><<<nb, 256, 0, st>>>(src, dst, g, ncomp); break;
-    case 3: k_filter<3, T><<<nb, 256, 0, st>>>(src, dst, g, ncomp); break;
-    default: return cudaErrorInvalidValue;
-  }
+  if (axis < 0 || axis >= g.dim || g.n[1] > 65535 || (long long)g.n[2] * ncomp > 65535)
+    return cudaErrorInvalidValue;
+  const dim3 grid((g.n[0] + 127) / 128, g.n[1], g.n[2] * ncomp);
+  k_filter_axis<T><<<grid, 128, 0, st>>>(src, dst, g, axis);
   return cudaGetLastError();
 }
 
-cudaError_t launch_filter_f32(const GridDev& g, const float* src, float* dst, int ncomp,
+cudaError_t launch_filter_f32(const GridDev& g, const float* src, float* dst, int ncomp, int axis,
                               cudaStream_t st) {
-  return launch_filter<float>(g, src, dst, ncomp, st);
+  return launch_filter<float>(g, src, dst, ncomp, axis, st);
 }
 
 cudaError_t launch_filter_f64(const GridDev& g, const double* src, double* dst, int ncomp,
-                              cudaStream_t st) {
-  return launch_filter<double>(g, src, dst, ncomp, st);
+                              int axis, cudaStream_t st) {
+  return launch_filter<double>(g, src, dst, ncomp, axis, st);
 }
 
 }  // namespace pic

@@ -60,11 +60,12 @@ size_t particle_smem_bytes(int dim, const TileDev& t);
 
 cudaError_t launch_b_half(const GridDev& g, float* F, int zero_j, cudaStream_t st);
 cudaError_t launch_e_update(const GridDev& g, float* F, cudaStream_t st);
-// one Binomial2 pass over ncomp consecutive planes src -> dst
-cudaError_t launch_filter_f32(const GridDev& g, const float* src, float* dst, int ncomp,
+// one Binomial2 sub-pass along gridded axis `axis` over ncomp consecutive planes,
+// src -> dst (a full pass is one sub-pass per gridded axis, x first)
+cudaError_t launch_filter_f32(const GridDev& g, const float* src, float* dst, int ncomp, int axis,
                               cudaStream_t st);
 cudaError_t launch_filter_f64(const GridDev& g, const double* src, double* dst, int ncomp,
-                              cudaStream_t st);
+                              int axis, cudaStream_t st);
 
 struct SortParams {
   GridDev g;

@@ -70,6 +70,22 @@ class Simulation:
         return dict(tile=list(t.tile), halo=t.halo, sort_every=t.sort_every,
                     filter_passes=t.filter_passes, chunk=t.chunk)
 
+    def autotune(self, candidates=None, steps=20):
+        """Pick tile size, halo and sort cadence by timing real steps (they advance
+        the simulation); returns the chosen tuning."""
+        cs = None
+        if candidates:
+            cs = []
+            for c in candidates:
+                t = B.pic_tuning()
+                for d, v in enumerate(c.get("tile", [0, 0, 0])):
+                    t.tile[d] = int(v)
+                t.halo, t.sort_every = c.get("halo", 0), c.get("sort_every", 0)
+                t.chunk = c.get("chunk", 0)
+                cs.append(t)
+        B.pic_autotune(self.ctx, cs, steps)
+        return self.tuning()
+
     def step(self, n=1):
         B.pic_step(self.ctx, n)
 

@@ -64,6 +64,7 @@ def _species(lib, n=4, q=-1.0, m=1.0, ptr=0x1000):
     (dict(null_cell=True), "NULL"),
     (dict(null_fields=True), "NULL"),
     (dict(dim=3, nx=2048, ny=2048, nz=1024), "int32"),
+    (dict(dim=2, nx=4, ny=70000), "65535"),
 ])
 def test_pic_init_rejects_bad_arguments(lib, case, msg):
     dim = case.get("dim", 2)
