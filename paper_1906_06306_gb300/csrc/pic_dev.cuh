@@ -87,11 +87,21 @@ struct SmemAcc {
 // already divided by the quantum; integer shared atomics are native and
 // unaffected by lanes that hit the same word.  Planes Jx, Jy, Jz of
 // W0 x W1 x W2 ints.
+#ifndef PIC_MAGIC_F2I
+#define PIC_MAGIC_F2I 1
+#endif
 struct SmemJ {
   int* ji;
   int W0, W01, wc;
   __device__ __forceinline__ void add(int comp, int i, int j, int k, float v) const {
-    atomicAdd(&ji[(comp - JX) * wc + i + W0 * j + W01 * k], __float2int_rn(v));
+#if PIC_MAGIC_F2I
+    // round to nearest integer by adding 1.5 * 2^23 (exact for |v| < 2^22, which
+    // the quantum guarantees for a single term) and reading the low mantissa
+    const int iv = __float_as_int(v + 12582912.0f) - 0x4B400000;
+#else
+    const int iv = __float2int_rn(v);
+#endif
+    atomicAdd(&ji[(comp - JX) * wc + i + W0 * j + W01 * k], iv);
   }
 };
 
@@ -225,53 +235,93 @@ __device__ __forceinline__ void move(const float* u, const float* o1, float c, f
   }
 }
 
-// One ZigZag segment (Appendix D) from the cell with lower corner I: flux
-// q*Dl, weights W (segment midpoint minus I).  A current component goes to
-// index I along its own axis and is split (1-W, W) along every other gridded
-// axis.  In 3D the transverse product is the average along the straight
-// segment, midpoint product +- Dl_b Dl_c / 12, which keeps the first-order
-// charge exactly conserved.
-template <int D, class Acc>
-__device__ __forceinline__ void zz_segment(const Acc& A, const int* I, const float* Dl,
-                                           const float* W, float q) {
+// Number of current words one ZigZag segment touches in D dimensions.
+template <int D>
+__host__ __device__ constexpr int zz_words() {
+  return D == 1 ? 5 : D == 2 ? 8 : 12;
+}
+
+// Values that one ZigZag segment (Appendix D) adds to its current words: flux
+// q*Dl, weights W (segment midpoint minus the lower corner of its cell).  A
+// current component goes to its cell's index along its own axis and is split
+// (1-W, W) along every other gridded axis.  In 3D the transverse product is the
+// average along the straight segment, midpoint product +- Dl_b Dl_c / 12,
+// which keeps the first-order charge exactly conserved.  Order of the words:
+//   1D: Jx(i) Jy(i) Jy(i+1) Jz(i) Jz(i+1)
+//   2D: Jx(i,j) Jx(i,j+1) Jy(i,j) Jy(i+1,j) Jz(i,j) Jz(i+1,j) Jz(i,j+1) Jz(i+1,j+1)
+//   3D: Jx at (i, j+{0,1}, k+{0,1}), Jy at (i+{0,1}, j, k+{0,1}),
+//       Jz at (i+{0,1}, j+{0,1}, k), second index fastest in each group
+template <int D>
+__device__ __forceinline__ void zz_values(const float* Dl, const float* W, float q, float* v) {
   const float f0 = q * Dl[0], f1 = q * Dl[1], f2 = q * Dl[2];
   if (D == 1) {
-    A.add(JX, I[0], 0, 0, f0);
-    A.add(JY, I[0], 0, 0, f1 * (1.0f - W[0]));
-    A.add(JY, I[0] + 1, 0, 0, f1 * W[0]);
-    A.add(JZ, I[0], 0, 0, f2 * (1.0f - W[0]));
-    A.add(JZ, I[0] + 1, 0, 0, f2 * W[0]);
+    v[0] = f0;
+    v[1] = f1 * (1.0f - W[0]);
+    v[2] = f1 * W[0];
+    v[3] = f2 * (1.0f - W[0]);
+    v[4] = f2 * W[0];
   } else if (D == 2) {
     const float wx = W[0], wy = W[1], mx = 1.0f - W[0], my = 1.0f - W[1];
-    A.add(JX, I[0], I[1], 0, f0 * my);
-    A.add(JX, I[0], I[1] + 1, 0, f0 * wy);
-    A.add(JY, I[0], I[1], 0, f1 * mx);
-    A.add(JY, I[0] + 1, I[1], 0, f1 * wx);
-    A.add(JZ, I[0], I[1], 0, f2 * (mx * my));
-    A.add(JZ, I[0] + 1, I[1], 0, f2 * (wx * my));
-    A.add(JZ, I[0], I[1] + 1, 0, f2 * (mx * wy));
-    A.add(JZ, I[0] + 1, I[1] + 1, 0, f2 * (wx * wy));
+    v[0] = f0 * my;
+    v[1] = f0 * wy;
+    v[2] = f1 * mx;
+    v[3] = f1 * wx;
+    v[4] = f2 * (mx * my);
+    v[5] = f2 * (wx * my);
+    v[6] = f2 * (mx * wy);
+    v[7] = f2 * (wx * wy);
   } else {
     const float wx = W[0], wy = W[1], wz = W[2];
     const float mx = 1.0f - wx, my = 1.0f - wy, mz = 1.0f - wz;
     const float cyz = Dl[1] * Dl[2] * (1.0f / 12.0f);
     const float czx = Dl[2] * Dl[0] * (1.0f / 12.0f);
     const float cxy = Dl[0] * Dl[1] * (1.0f / 12.0f);
-    // Jx: transverse axes (y, z)
-    A.add(JX, I[0], I[1], I[2], f0 * (my * mz + cyz));
-    A.add(JX, I[0], I[1] + 1, I[2], f0 * (wy * mz - cyz));
-    A.add(JX, I[0], I[1], I[2] + 1, f0 * (my * wz - cyz));
-    A.add(JX, I[0], I[1] + 1, I[2] + 1, f0 * (wy * wz + cyz));
-    // Jy: transverse axes (z, x)
-    A.add(JY, I[0], I[1], I[2], f1 * (mz * mx + czx));
-    A.add(JY, I[0], I[1], I[2] + 1, f1 * (wz * mx - czx));
-    A.add(JY, I[0] + 1, I[1], I[2], f1 * (mz * wx - czx));
-    A.add(JY, I[0] + 1, I[1], I[2] + 1, f1 * (wz * wx + czx));
-    // Jz: transverse axes (x, y)
-    A.add(JZ, I[0], I[1], I[2], f2 * (mx * my + cxy));
-    A.add(JZ, I[0] + 1, I[1], I[2], f2 * (wx * my - cxy));
-    A.add(JZ, I[0], I[1] + 1, I[2], f2 * (mx * wy - cxy));
-    A.add(JZ, I[0] + 1, I[1] + 1, I[2], f2 * (wx * wy + cxy));
+    v[0] = f0 * (my * mz + cyz);
+    v[1] = f0 * (wy * mz - cyz);
+    v[2] = f0 * (my * wz - cyz);
+    v[3] = f0 * (wy * wz + cyz);
+    v[4] = f1 * (mz * mx + czx);
+    v[5] = f1 * (wz * mx - czx);
+    v[6] = f1 * (mz * wx - czx);
+    v[7] = f1 * (wz * wx + czx);
+    v[8] = f2 * (mx * my + cxy);
+    v[9] = f2 * (wx * my - cxy);
+    v[10] = f2 * (mx * wy - cxy);
+    v[11] = f2 * (wx * wy + cxy);
+  }
+}
+
+// Add the words of zz_values for a segment in the cell with lower corner I.
+template <int D, class Acc>
+__device__ __forceinline__ void zz_deposit(const Acc& A, const int* I, const float* v) {
+  if (D == 1) {
+    A.add(JX, I[0], 0, 0, v[0]);
+    A.add(JY, I[0], 0, 0, v[1]);
+    A.add(JY, I[0] + 1, 0, 0, v[2]);
+    A.add(JZ, I[0], 0, 0, v[3]);
+    A.add(JZ, I[0] + 1, 0, 0, v[4]);
+  } else if (D == 2) {
+    A.add(JX, I[0], I[1], 0, v[0]);
+    A.add(JX, I[0], I[1] + 1, 0, v[1]);
+    A.add(JY, I[0], I[1], 0, v[2]);
+    A.add(JY, I[0] + 1, I[1], 0, v[3]);
+    A.add(JZ, I[0], I[1], 0, v[4]);
+    A.add(JZ, I[0] + 1, I[1], 0, v[5]);
+    A.add(JZ, I[0], I[1] + 1, 0, v[6]);
+    A.add(JZ, I[0] + 1, I[1] + 1, 0, v[7]);
+  } else {
+    A.add(JX, I[0], I[1], I[2], v[0]);
+    A.add(JX, I[0], I[1] + 1, I[2], v[1]);
+    A.add(JX, I[0], I[1], I[2] + 1, v[2]);
+    A.add(JX, I[0], I[1] + 1, I[2] + 1, v[3]);
+    A.add(JY, I[0], I[1], I[2], v[4]);
+    A.add(JY, I[0], I[1], I[2] + 1, v[5]);
+    A.add(JY, I[0] + 1, I[1], I[2], v[6]);
+    A.add(JY, I[0] + 1, I[1], I[2] + 1, v[7]);
+    A.add(JZ, I[0], I[1], I[2], v[8]);
+    A.add(JZ, I[0] + 1, I[1], I[2], v[9]);
+    A.add(JZ, I[0], I[1] + 1, I[2], v[10]);
+    A.add(JZ, I[0] + 1, I[1] + 1, I[2], v[11]);
   }
 }
 
@@ -279,12 +329,16 @@ __device__ __forceinline__ void zz_segment(const Acc& A, const int* I, const flo
 // lower corner b of the old cell: x1 = o1, x2 = dc + o2 on gridded axes; the
 // relay point x_r = min(min(0, dc) + 1, max(max(0, dc), (x1 + x2)/2)); the
 // segments carry x_r - x1 and x2 - x_r with weights (x1 + x_r)/2 and
-// (x2 + x_r)/2 - dc.  A non-gridded axis moves by dn, split evenly.
+// (x2 + x_r)/2 - dc.  A non-gridded axis moves by dn, split evenly.  When the
+// particle stays in its cell both segments add to the same words, so their
+// values are summed first and only particles that crossed a face issue the
+// second set of atomics.
 template <int D, class Acc>
 __device__ __forceinline__ void zigzag(const Acc& A, const int* b, const int* dc, const float* o1,
                                        const float* o2, const float* dn, float q) {
   float D1[3], D2[3], W1[3] = {0.f, 0.f, 0.f}, W2[3] = {0.f, 0.f, 0.f};
   int b2[3] = {b[0], b[1], b[2]};
+  bool crossed = false;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (d < D) {
@@ -298,13 +352,21 @@ __device__ __forceinline__ void zigzag(const Acc& A, const int* b, const int* dc
       W1[d] = 0.5f * (x1 + xr);
       W2[d] = 0.5f * (x2 + xr) - (float)dc[d];
       b2[d] = b[d] + dc[d];
+      crossed |= dc[d] != 0;
     } else {
       D1[d] = 0.5f * dn[d];
       D2[d] = D1[d];
     }
   }
-  zz_segment<D>(A, b, D1, W1, q);
-  zz_segment<D>(A, b2, D2, W2, q);
+  float v1[zz_words<D>()], v2[zz_words<D>()];
+  zz_values<D>(D1, W1, q, v1);
+  zz_values<D>(D2, W2, q, v2);
+  if (!crossed) {
+#pragma unroll
+    for (int w = 0; w < zz_words<D>(); ++w) v1[w] += v2[w];
+  }
+  zz_deposit<D>(A, b, v1);
+  if (crossed) zz_deposit<D>(A, b2, v2);
 }
 
 }  // namespace pic
