@@ -380,6 +380,83 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """Ensemble of independent Weibel boxes of uneven sizes (1D lengths 128..4096,
+    2D sides 32..256, 16..128 particles per cell per species, gamma_b 1.5..10,
+    theta 0.001..0.1) stepped with pic_batch_step (one CUDA graph launch per sort
+    cycle of all boxes), compared with stepping the boxes one after the other
+    with pic_step.  Replicas only for N > 1."""
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    import workloads
+    from paper_1906_06306_gb300 import Batch, Simulation
+
+    recipe = workloads.weibel_ensemble(count=args.boxes)
+    plasmas = [workloads.weibel_box(*b) for b in recipe]
+    npart = sum(p.nparticles for p in plasmas)
+    sims = [Simulation.from_plasma(p, device=f"cuda:{local}") for p in plasmas]
+    cands = [dict(sort_every=k, halo=h) for k in (5, 10, 20) for h in (2, 3)]
+    if args.autotune:
+        for sm in sims:
+            sm.autotune(cands, steps=10)
+    batch = Batch(sims)
+    dev = torch.device(f"cuda:{local}")
+    stream = sims[0].stream
+    batch.step(args.warmup)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    batch.step(args.steps)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = t0.elapsed_time(t1)
+    clocks = sampler.stop()
+    # the same steps box by box, one pic_step call per box
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for sm in sims:
+        sm.step(args.steps)
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_seq = s0.elapsed_time(s1)
+    for sm in sims:
+        sm.check()
+    value = npart * args.steps / (ms * 1e-3)
+    alg = sum(float(p.nparticles * 2 * (4 + 4 * p.dim + 12) + p.ncells * 48) for p in plasmas)
+    achieved = alg * args.steps / (ms * 1e-3) / 1e9
+    peak, peak_kind = hbm_peak()
+    cadences = sorted({sm.tuning()["sort_every"] for sm in sims})
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": dict(workload="batched_weibel", boxes=len(sims), particles=npart,
+                       boxes_2d=sum(1 for p in plasmas if p.dim == 2), autotuned=bool(args.autotune),
+                       sort_cadences=cadences, l2="inputs larger than L2, no flush",
+                       parallelism="replicas" if world > 1 else "single-gpu"),
+        "sequential": {"value": npart * args.steps / (ms_seq * 1e-3), "unit": "particle-steps/s",
+                       "ms_per_step": ms_seq / args.steps,
+                       "note": "same boxes and steps, one pic_step(K) call per box in turn"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "whole step of all boxes (graph replay; per-kernel events are not"
+                               " recorded inside graphs)", "peak_source": peak_kind},
+        "clocks": clocks, "e2e": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for sm in sims:
+        sm.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -394,12 +471,21 @@ def main():
     ap.add_argument("--grid", type=int, default=0,
                     help="box size (2D side, 1D length, 3D x-length with y = z = x/8); "
                          "0 = the workload's benchmark size")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="turbulence_2d3v")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched_weibel"],
+                    default="turbulence_2d3v")
+    ap.add_argument("--boxes", type=int, default=256, help="boxes of the batched_weibel ensemble")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
+        if args.workload == "batched_weibel":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the oracle steps one box at a time; time it with "
+                              "--workload weibel_1d3v"}))
+            return 0
         return run_reference(args)
+    if args.workload == "batched_weibel":
+        return run_batched(args)
     return run_ours(args)
 
 

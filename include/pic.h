@@ -234,6 +234,22 @@ pic_status pic_kernel_times(pic_ctx* ctx, double* ms, int64_t* launches);
 #define PIC_FILTER_STATIC_MAX_FLOATS 4194304
 pic_status pic_filter_current_static(const pic_grid* grid, float* J, int passes, void* stream);
 
+/* Ensemble stepping (many independent boxes; the paper steps one box).  A
+ * batch groups existing contexts (independent boxes, any mix of sizes and
+ * dimensions, all on one device and one stream).  pic_batch_step advances
+ * every context by nsteps: the steps of all boxes for one cycle of L steps,
+ * L = lcm of the contexts' sort_every (at most 240), are captured once into a
+ * single CUDA graph in which each box is an independent branch, and that graph
+ * is launched nsteps / L times on `stream`; the remaining steps run through
+ * pic_step.  The graph is rebuilt when a context's tuning or its position in
+ * its sort cycle changed since the capture.  Results are those of pic_step
+ * on each context.  Contexts must not be destroyed before the batch.  Errors:
+ * PIC_ERR_ARG (message in pic_last_error(NULL)), PIC_ERR_CUDA. */
+typedef struct pic_batch pic_batch;
+pic_status pic_batch_create(pic_batch** out, pic_ctx* const* ctxs, int nctx);
+pic_status pic_batch_step(pic_batch* batch, int nsteps, void* stream);
+pic_status pic_batch_destroy(pic_batch* batch);
+
 /* Release the context and its scratch (the caller's buffers are untouched). */
 pic_status pic_destroy(pic_ctx* ctx);
 

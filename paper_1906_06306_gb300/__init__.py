@@ -9,7 +9,8 @@ _API = {
     "PicError", "pic_init", "pic_get_tuning", "pic_set_tuning", "pic_sort", "pic_gather_push",
     "pic_deposit", "pic_filter_current", "pic_field_update", "pic_step", "pic_energies",
     "pic_check", "pic_step_host", "pic_autotune", "pic_stats", "pic_timing", "pic_kernel_times", "pic_destroy",
-    "pic_last_error", "pic_filter_current_static", "PIC_FIELD_B_HALF", "PIC_FIELD_E",
+    "pic_last_error", "pic_filter_current_static", "pic_batch_create", "pic_batch_step",
+    "pic_batch_destroy", "PIC_FIELD_B_HALF", "PIC_FIELD_E",
 }
 
 
@@ -18,8 +19,8 @@ def __getattr__(name):
         from . import binding
 
         return getattr(binding, name)
-    if name == "Simulation":
-        from .sim import Simulation
+    if name in ("Simulation", "Batch"):
+        from . import sim
 
-        return Simulation
+        return getattr(sim, name)
     raise AttributeError(name)

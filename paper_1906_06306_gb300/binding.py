@@ -59,6 +59,9 @@ SIGNATURES = {
     "pic_timing": (c_int, [_P, c_int]),
     "pic_kernel_times": (c_int, [_P, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     "pic_filter_current_static": (c_int, [ctypes.POINTER(pic_grid), c_void_p, c_int, c_void_p]),
+    "pic_batch_create": (c_int, [ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_int]),
+    "pic_batch_step": (c_int, [c_void_p, c_int, c_void_p]),
+    "pic_batch_destroy": (c_int, [c_void_p]),
     "pic_destroy": (c_int, [_P]),
     "pic_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -191,6 +194,21 @@ def pic_filter_current_static(grid: pic_grid, j_ptr: int, passes: int, stream: i
     j_ptr (in place, on `stream`); see include/pic.h for the size limit."""
     _check(_lib.pic_filter_current_static(ctypes.byref(grid), c_void_p(j_ptr), passes,
                                           c_void_p(stream)), None)
+
+
+def pic_batch_create(ctxs):
+    arr = (c_void_p * len(ctxs))(*[c.value if isinstance(c, c_void_p) else c for c in ctxs])
+    b = c_void_p()
+    _check(_lib.pic_batch_create(ctypes.byref(b), arr, len(ctxs)), None)
+    return b
+
+
+def pic_batch_step(batch, nsteps: int, stream: int) -> None:
+    _check(_lib.pic_batch_step(batch, nsteps, c_void_p(stream)), None)
+
+
+def pic_batch_destroy(batch) -> None:
+    _check(_lib.pic_batch_destroy(batch), None)
 
 
 def pic_destroy(ctx) -> None:

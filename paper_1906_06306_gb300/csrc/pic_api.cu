@@ -718,3 +718,196 @@ const char* pic_last_error(const pic_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- batches --
+
+struct pic_batch {
+  std::vector<pic_ctx*> ctxs;
+  std::vector<cudaStream_t> branches;  // capture branches (one per group of boxes)
+  cudaStream_t origin = nullptr;       // capture origin
+  std::vector<cudaEvent_t> events;     // fork (0) and joins (1..)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int cycle = 0;                          // steps per graph launch
+  std::vector<long long> phase;           // steps % sort_every of each context at capture
+  std::vector<pic_tuning> tun;            // tuning of each context at capture
+};
+
+namespace {
+
+constexpr int kBatchBranches = 32;
+constexpr int kMaxCycle = 240;
+
+long long gcd_ll(long long a, long long b) {
+  while (b) {
+    const long long r = a % b;
+    a = b;
+    b = r;
+  }
+  return a;
+}
+
+void batch_free_graph(pic_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+bool batch_graph_current(const pic_batch* b) {
+  if (!b->exec) return false;
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    const pic_ctx* c = b->ctxs[i];
+    if (std::memcmp(&c->tun, &b->tun[i], sizeof(pic_tuning)) != 0) return false;
+    if (c->steps % c->tun.sort_every != b->phase[i]) return false;
+  }
+  return true;
+}
+
+// Capture `cycle` steps of every context into one graph, each context on one
+// of the branch streams forked from the origin stream.
+pic_status batch_capture(pic_batch* b) {
+  batch_free_graph(b);
+  for (pic_ctx* c : b->ctxs)  // no allocation may happen during capture
+    if (c->tun.filter_passes > 0 && !c->d_jtmp) {
+      const cudaError_t ea = dalloc(&c->d_jtmp, 3 * (size_t)c->g.plane);
+      if (ea != cudaSuccess) return cuda_fail(nullptr, "filter buffer", ea);
+    }
+  std::vector<long long> saved_steps(b->ctxs.size());
+  std::vector<cudaStream_t> saved_st(b->ctxs.size());
+  std::vector<bool> saved_timing(b->ctxs.size());
+  cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(nullptr, "batch capture", e);
+  pic_status st = PIC_OK;
+  cudaEventRecord(b->events[0], b->origin);
+  for (cudaStream_t s : b->branches) cudaStreamWaitEvent(s, b->events[0], 0);
+  for (size_t i = 0; i < b->ctxs.size() && st == PIC_OK; ++i) {
+    pic_ctx* c = b->ctxs[i];
+    saved_steps[i] = c->steps;
+    saved_st[i] = c->st;
+    saved_timing[i] = c->timing;
+    c->st = b->branches[i % b->branches.size()];
+    c->timing = false;
+    st = pic_step(c, b->cycle);
+    c->st = saved_st[i];
+    c->timing = saved_timing[i];
+    c->steps = saved_steps[i];  // the captured steps have not run yet
+    if (st != PIC_OK) g_init_error = c->err;
+  }
+  for (size_t k = 0; k < b->branches.size(); ++k) {
+    cudaEventRecord(b->events[k + 1], b->branches[k]);
+    cudaStreamWaitEvent(b->origin, b->events[k + 1], 0);
+  }
+  e = cudaStreamEndCapture(b->origin, &b->graph);
+  if (st != PIC_OK) {
+    batch_free_graph(b);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(nullptr, "batch capture", e);
+  e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) {
+    batch_free_graph(b);
+    return cuda_fail(nullptr, "batch graph instantiation", e);
+  }
+  b->phase.resize(b->ctxs.size());
+  b->tun.resize(b->ctxs.size());
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    b->phase[i] = b->ctxs[i]->steps % b->ctxs[i]->tun.sort_every;
+    b->tun[i] = b->ctxs[i]->tun;
+  }
+  return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_batch_create(pic_batch** out, pic_ctx* const* ctxs, int nctx) {
+  g_init_error.clear();
+  if (!out) return set_err(nullptr, PIC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!ctxs || nctx < 1) return set_err(nullptr, PIC_ERR_ARG, "need at least one context");
+  for (int i = 0; i < nctx; ++i) {
+    if (!ctxs[i]) return set_err(nullptr, PIC_ERR_ARG, "NULL context");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return set_err(nullptr, PIC_ERR_ARG, "a context appears twice");
+  }
+  pic_batch* b = new pic_batch();
+  b->ctxs.assign(ctxs, ctxs + nctx);
+  const int nb = nctx < kBatchBranches ? nctx : kBatchBranches;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  for (int k = 0; k < nb && e == cudaSuccess; ++k) {
+    cudaStream_t s = nullptr;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->branches.push_back(s);
+  }
+  for (int k = 0; k <= nb && e == cudaSuccess; ++k) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->events.push_back(ev);
+  }
+  // buffers that pic_step would otherwise allocate on first use (no
+  // allocation may happen during capture)
+  for (int i = 0; i < nctx && e == cudaSuccess; ++i)
+    if (ctxs[i]->tun.filter_passes > 0 && !ctxs[i]->d_jtmp)
+      e = dalloc(&ctxs[i]->d_jtmp, 3 * (size_t)ctxs[i]->g.plane);
+  if (e != cudaSuccess) {
+    pic_batch_destroy(b);
+    return cuda_fail(nullptr, "batch set-up", e);
+  }
+  *out = b;
+  return PIC_OK;
+}
+
+pic_status pic_batch_step(pic_batch* b, int nsteps, void* stream) {
+  g_init_error.clear();
+  if (!b) return set_err(nullptr, PIC_ERR_ARG, "batch is NULL");
+  if (nsteps < 0) return set_err(nullptr, PIC_ERR_ARG, "nsteps must be >= 0");
+  const cudaStream_t st = (cudaStream_t)stream;
+  long long cycle = 1;
+  for (pic_ctx* c : b->ctxs) {
+    if (c->st != st) return set_err(nullptr, PIC_ERR_ARG, "every context must use the batch's stream");
+    cycle = cycle / gcd_ll(cycle, c->tun.sort_every) * c->tun.sort_every;
+    if (cycle > kMaxCycle) return set_err(nullptr, PIC_ERR_ARG, "lcm of the sort cadences exceeds 240");
+  }
+  const int full = nsteps / (int)cycle, rem = nsteps % (int)cycle;
+  if (full > 0) {
+    if ((int)cycle != b->cycle || !batch_graph_current(b)) {
+      b->cycle = (int)cycle;
+      // work already queued on the contexts' stream must precede the capture's
+      // own ordering (the graph is launched on that stream afterwards)
+      const pic_status s = batch_capture(b);
+      if (s != PIC_OK) return s;
+    }
+    for (int i = 0; i < full; ++i) {
+      const cudaError_t e = cudaGraphLaunch(b->exec, st);
+      if (e != cudaSuccess) return cuda_fail(nullptr, "batch graph launch", e);
+    }
+    for (pic_ctx* c : b->ctxs) {
+      c->steps += (long long)full * cycle;
+      c->snapshot_valid = false;
+    }
+  }
+  for (pic_ctx* c : b->ctxs) {
+    if (rem == 0) break;
+    const pic_status s = pic_step(c, rem);
+    if (s != PIC_OK) {
+      g_init_error = c->err;
+      return s;
+    }
+  }
+  return PIC_OK;
+}
+
+pic_status pic_batch_destroy(pic_batch* b) {
+  if (!b) return PIC_ERR_ARG;
+  batch_free_graph(b);
+  if (b->origin) cudaStreamSynchronize(b->origin);
+  for (cudaStream_t s : b->branches) cudaStreamDestroy(s);
+  for (cudaEvent_t ev : b->events) cudaEventDestroy(ev);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  delete b;
+  return PIC_OK;
+}
+
+}  // extern "C"

@@ -127,3 +127,27 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Ensemble of independent Simulations stepped together: each sort cycle
+    of all boxes is one CUDA graph launch (pic_batch_step).  All simulations
+    must use the same device and stream."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        self.handle = B.pic_batch_create([s.ctx for s in self.sims])
+
+    def step(self, n=1):
+        B.pic_batch_step(self.handle, n, self.sims[0].stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            B.pic_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -16,5 +16,7 @@ from .plasma import (  # noqa: F401
     weibel_1d,
     turbulence_2d,
     shock_3d,
+    weibel_box,
+    weibel_ensemble,
     CONFIGS,
 )

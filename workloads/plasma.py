@@ -242,6 +242,41 @@ def shock_3d(nx: int = 1024, ny: int = 128, nz: int = 128, ppc: int = 8,
                                     filter_passes=4))
 
 
+def weibel_box(dim: int, n: int, ppc: int, gamma_b: float, theta: float, r_p: float = 10.0,
+               c: float = 0.45, seed: int = 0) -> Plasma:
+    """One Weibel box: 1D (n cells, beams along +-y as in weibel_1d) or 2D
+    (n x n cells, beams along +-x in the plane, as in Sect. 4.1)."""
+    if dim == 1:
+        return weibel_1d(nx=n, ppc=ppc, gamma_b=gamma_b, theta=theta, r_p=r_p, c=c, seed=seed)
+    q_abs = charge_from_skin_depth(c, r_p, ppc, gamma_b)
+    beta_b = math.sqrt(1.0 - 1.0 / gamma_b**2)
+    slots = np.where(np.arange(ppc) < ppc // 2, beta_b, -beta_b)
+    return uniform_plasma(2, n, n, 1, c, ppc, q_abs, theta, seed, drift_axis=0,
+                          drift_beta_per_slot=slots,
+                          meta=dict(workload="weibel_2d3v", gamma_b=gamma_b, beta_b=beta_b,
+                                    theta=theta, r_p=r_p, ppc=ppc, q_abs=q_abs,
+                                    filter_passes=0))
+
+
+def weibel_ensemble(count: int = 256, seed: int = 1237, max_1d: int = 4096, max_2d: int = 256):
+    """Recipe of an ensemble of independent Weibel boxes with uneven sizes: half
+    1D, half 2D; 1D lengths log-uniform in 128..max_1d, 2D sides log-uniform in
+    32..max_2d, 16..128 particles per cell per species (even), gamma_b
+    log-uniform in 1.5..10, theta log-uniform in 0.001..0.1.  Returns a list of
+    (dim, n, ppc, gamma_b, theta, seed) tuples; weibel_box builds each."""
+    gen = rng(seed)
+    boxes = []
+    for b in range(count):
+        dim = 1 if gen.random() < 0.5 else 2
+        lo, hi = (128, max_1d) if dim == 1 else (32, max_2d)
+        n = int(round(math.exp(gen.uniform(math.log(lo), math.log(hi)))))
+        ppc = 2 * int(round(math.exp(gen.uniform(math.log(16), math.log(128))) / 2))
+        gamma_b = math.exp(gen.uniform(math.log(1.5), math.log(10.0)))
+        theta = math.exp(gen.uniform(math.log(1e-3), math.log(0.1)))
+        boxes.append((dim, n, ppc, gamma_b, theta, seed * 1000 + b))
+    return boxes
+
+
 CONFIGS = {
     "weibel_1d3v": weibel_1d,
     "turbulence_2d3v": turbulence_2d,
