@@ -125,6 +125,15 @@ pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* spec
 pic_status pic_get_tuning(pic_ctx* ctx, pic_tuning* out);
 pic_status pic_set_tuning(pic_ctx* ctx, const pic_tuning* t);
 
+/* Particle pusher of the context: PIC_PUSHER_BORIS (Appendix C; the default)
+ * or PIC_PUSHER_HIGUERA_CARY (Table 2, the pusher of the paper's shock run,
+ * Higuera and Cary 2017: the Boris steps with the rotation's Lorentz factor
+ * solved so that the E x B drift is exact at any speed).  Takes effect from
+ * the next push; PIC_ERR_ARG for other values. */
+#define PIC_PUSHER_BORIS 0
+#define PIC_PUSHER_HIGUERA_CARY 1
+pic_status pic_set_pusher(pic_ctx* ctx, int pusher);
+
 /* Counting sort by tile of every species (replaces the particle migration
  * routines of Table 1, check_outg_prtcls ... del_vir_prtcls, on one GPU).
  * Particles are grouped by tile; the order inside a tile is not specified. */

@@ -149,6 +149,19 @@ def boris(u, e, b, qm: float, c: float):
     return u
 
 
+def higuera_cary(u, e, b, qm: float, c: float):
+    u = np.array(u, dtype=np.float64)
+    lib().orc_higuera_cary(_p(u), _p(np.ascontiguousarray(e, dtype=np.float64)),
+                           _p(np.ascontiguousarray(b, dtype=np.float64)), ctypes.c_double(qm),
+                           ctypes.c_double(c))
+    return u
+
+
+def set_pusher(name: str):
+    """'boris' (Appendix C) or 'higuera_cary' for push_particles and step."""
+    lib().orc_set_pusher(ctypes.c_int({"boris": 0, "higuera_cary": 1}[name]))
+
+
 def zigzag(g: Grid, F, x1, x2, q: float):
     lib().orc_zigzag(g.c_struct(), _p(F), _p(np.ascontiguousarray(x1, dtype=np.float64)),
                      _p(np.ascontiguousarray(x2, dtype=np.float64)), ctypes.c_double(q))

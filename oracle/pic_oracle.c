@@ -170,6 +170,32 @@ void orc_boris(double* u, const double* e, const double* b, double qm, double c)
   for (int a = 0; a < 3; ++a) u[a] = (u1[a] + x2[a] + 0.5 * qm * e[a]) / c;
 }
 
+/* Higuera-Cary (2017): u1 = c u + s E/2 as in Boris; with tau = s B / (2 c),
+ * u* = (u1 . tau) / c and sigma = gamma1^2 - tau^2, the rotation uses
+ * gamma+ = sqrt((sigma + sqrt(sigma^2 + 4 (tau^2 + u*^2))) / 2) and t = tau / gamma+;
+ * the rotated momentum is the implicit midpoint
+ * um = (u1 + (u1 . t) t + u1 x t) / (1 + t^2), and u3 = um + um x t + s E/2. */
+void orc_higuera_cary(double* u, const double* e, const double* b, double qm, double c) {
+  double u1[3], tau[3], t[3], um[3], x1[3], x2[3];
+  for (int a = 0; a < 3; ++a) u1[a] = c * u[a] + 0.5 * qm * e[a];
+  const double g2 = 1.0 + (u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]) / (c * c);
+  for (int a = 0; a < 3; ++a) tau[a] = qm * b[a] / (2.0 * c);
+  const double tt = tau[0] * tau[0] + tau[1] * tau[1] + tau[2] * tau[2];
+  const double us = (u1[0] * tau[0] + u1[1] * tau[1] + u1[2] * tau[2]) / c;
+  const double sigma = g2 - tt;
+  const double gp = sqrt(0.5 * (sigma + sqrt(sigma * sigma + 4.0 * (tt + us * us))));
+  for (int a = 0; a < 3; ++a) t[a] = tau[a] / gp;
+  const double s = 1.0 / (1.0 + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+  const double ut = u1[0] * t[0] + u1[1] * t[1] + u1[2] * t[2];
+  cross(u1, t, x1);
+  for (int a = 0; a < 3; ++a) um[a] = s * (u1[a] + ut * t[a] + x1[a]);
+  cross(um, t, x2);
+  for (int a = 0; a < 3; ++a) u[a] = (um[a] + x2[a] + 0.5 * qm * e[a]) / c;
+}
+
+static int g_pusher = 0;
+void orc_set_pusher(int pusher) { g_pusher = pusher; }
+
 /* One ZigZag segment: flux Fl from the cell with lower corner I, weights W,
  * displacement Ds of the segment (Appendix D).  Each current component sits
  * half a cell up its own axis (at the E points), so along its own axis it goes
@@ -250,7 +276,10 @@ void orc_push_particles(const orc_grid* g, const double* F, double* x, double* u
     for (int d = 0; d < g->dim; ++d) xp[d] = x[d * n + p];
     orc_interp(g, F, xp, e, b);
     double up[3] = {u[p], u[n + p], u[2 * n + p]};
-    orc_boris(up, e, b, qm, g->c);
+    if (g_pusher == 1)
+      orc_higuera_cary(up, e, b, qm, g->c);
+    else
+      orc_boris(up, e, b, qm, g->c);
     const double gam = sqrt(1.0 + up[0] * up[0] + up[1] * up[1] + up[2] * up[2]);
     for (int d = 0; d < 3; ++d) {
       u[d * n + p] = up[d];

@@ -50,6 +50,14 @@ void orc_interp(const orc_grid* g, const double* F, const double* x, double* e, 
 /* Relativistic Boris scheme of Appendix C, u (units of c) advanced in place by
  * one step; qm = q/m of the species (s-hat). */
 void orc_boris(double* u, const double* e, const double* b, double qm, double c);
+/* Higuera-Cary pusher (Table 2, HigueraCaryPusher; Higuera and Cary 2017), the
+ * alternative the paper uses for its shock run: the Boris steps with the
+ * rotation's Lorentz factor taken from the quadratic that makes the E x B drift
+ * exact.  Same arguments and units as orc_boris. */
+void orc_higuera_cary(double* u, const double* e, const double* b, double qm, double c);
+/* Pusher selection for orc_push_particles / orc_step: 0 Boris, 1 Higuera-Cary. */
+void orc_set_pusher(int pusher);
+
 /* ZigZag current of Appendix D for one particle moving from x1 to x2
  * (unwrapped: x2 - x1 is the displacement; rows of non-gridded dimensions
  * carry only the displacement), charge q, added into the J planes of F. */

@@ -45,6 +45,7 @@ SIGNATURES = {
                          c_int, c_float, c_float, c_void_p, c_void_p]),
     "pic_get_tuning": (c_int, [_P, ctypes.POINTER(pic_tuning)]),
     "pic_set_tuning": (c_int, [_P, ctypes.POINTER(pic_tuning)]),
+    "pic_set_pusher": (c_int, [_P, c_int]),
     "pic_sort": (c_int, [_P]),
     "pic_gather_push": (c_int, [_P]),
     "pic_deposit": (c_int, [_P]),
@@ -114,6 +115,13 @@ def pic_get_tuning(ctx) -> pic_tuning:
 
 def pic_set_tuning(ctx, t: pic_tuning) -> None:
     _check(_lib.pic_set_tuning(ctx, ctypes.byref(t)), ctx)
+
+
+PIC_PUSHER_BORIS, PIC_PUSHER_HIGUERA_CARY = 0, 1
+
+
+def pic_set_pusher(ctx, pusher: int) -> None:
+    _check(_lib.pic_set_pusher(ctx, pusher), ctx)
 
 
 def pic_sort(ctx) -> None:

@@ -54,6 +54,7 @@ struct pic_ctx {
   double* d_acc = nullptr;
   int* d_status = nullptr;
   unsigned long long* d_strays = nullptr;  // particles that took the global path
+  int pusher = 0;                          // PIC_PUSHER_*
   long long steps = 0;
   bool timing = false;
   std::vector<TimedLaunch> pending;
@@ -212,6 +213,7 @@ PushParams make_params(pic_ctx* ctx) {
   P.splits = ctx->splits;
   P.status = ctx->d_status;
   P.strays = ctx->d_strays;
+  P.pusher = ctx->pusher;
   P.inv_c = 1.0f / ctx->c;
   P.inv_c2 = 1.0f / (ctx->c * ctx->c);
   P.div0 = make_fastdiv(ctx->g.n[0]);
@@ -435,6 +437,14 @@ pic_status pic_set_tuning(pic_ctx* ctx, const pic_tuning* t) {
     if (s != PIC_OK) return s;
     return do_sort(ctx, true);
   }
+  return PIC_OK;
+}
+
+pic_status pic_set_pusher(pic_ctx* ctx, int pusher) {
+  if (!ctx) return PIC_ERR_ARG;
+  if (pusher != PIC_PUSHER_BORIS && pusher != PIC_PUSHER_HIGUERA_CARY)
+    return set_err(ctx, PIC_ERR_ARG, "pusher must be PIC_PUSHER_BORIS or PIC_PUSHER_HIGUERA_CARY");
+  ctx->pusher = pusher;
   return PIC_OK;
 }
 

@@ -200,6 +200,41 @@ __device__ __forceinline__ void boris(float* u, const float* e, const float* b, 
   u[2] = (u1[2] + (v0 * t1 - v1 * t0) + hs * e[2]) * inv_c;
 }
 
+// Higuera-Cary pusher (Table 2; Higuera and Cary 2017): the Boris steps with
+// the rotation's Lorentz factor gamma+ solved from
+// gamma+^2 = (sigma + sqrt(sigma^2 + 4 a)) / 2, sigma = gamma1^2 - tau^2,
+// a = tau^2 + (u1 . tau / c)^2, tau = s B / (2 c); for sigma < 0 the same root
+// is evaluated as 2 a / (sqrt(sigma^2 + 4 a) - sigma), free of cancellation.
+// The rotation is the implicit midpoint um = (u1 + (u1.t) t + u1 x t)/(1 + t^2)
+// with t = tau / gamma+, then u3 = um + um x t + (s/2) E.  Keeps the E x B drift
+// exact at any speed.
+__device__ __forceinline__ void higuera_cary(float* u, const float* e, const float* b, float qm,
+                                             float c, float inv_c, float inv_c2) {
+  const float hs = 0.5f * qm;
+  float u1[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u1[a] = fmaf(c, u[a], hs * e[a]);
+  const float g2 = fmaf(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2], inv_c2, 1.0f);
+  const float tf = hs * inv_c;
+  const float ta = tf * b[0], tb = tf * b[1], tc = tf * b[2];
+  const float tt = fmaf(ta, ta, fmaf(tb, tb, tc * tc));
+  const float us = (u1[0] * ta + u1[1] * tb + u1[2] * tc) * inv_c;
+  const float sigma = g2 - tt;
+  const float a4 = 4.0f * fmaf(us, us, tt);
+  const float r = sqrtf(fmaf(sigma, sigma, a4));
+  const float gp2 = sigma >= 0.0f ? 0.5f * (sigma + r) : __fdividef(0.5f * a4, r - sigma);
+  const float ig = rsqrtf(gp2);
+  const float t0 = ta * ig, t1 = tb * ig, t2 = tc * ig;
+  const float sf = __fdividef(1.0f, fmaf(t0, t0, fmaf(t1, t1, fmaf(t2, t2, 1.0f))));
+  const float ut = u1[0] * t0 + u1[1] * t1 + u1[2] * t2;
+  const float m0 = sf * (fmaf(ut, t0, u1[0]) + (u1[1] * t2 - u1[2] * t1));
+  const float m1 = sf * (fmaf(ut, t1, u1[1]) + (u1[2] * t0 - u1[0] * t2));
+  const float m2 = sf * (fmaf(ut, t2, u1[2]) + (u1[0] * t1 - u1[1] * t0));
+  u[0] = (m0 + (m1 * t2 - m2 * t1) + hs * e[0]) * inv_c;
+  u[1] = (m1 + (m2 * t0 - m0 * t2) + hs * e[1]) * inv_c;
+  u[2] = (m2 + (m0 * t1 - m1 * t0) + hs * e[2]) * inv_c;
+}
+
 // Position update of Eq. (fdX), x += c u / gamma, on the offsets, with every
 // operation correctly rounded and none contracted, so the cell bookkeeping can
 // be replayed bit for bit: gamma = sqrt(((1 + ux^2) + uy^2) + uz^2),

@@ -38,6 +38,7 @@ struct PushParams {
   float jq;            // quantum of the int32 shared-memory current (a power of 2)
   float jq_inv;        // 1 / jq
   unsigned long long* strays;  // running count of particles that took the global path
+  int pusher;                  // 0 Boris (Appendix C), 1 Higuera-Cary
 };
 
 // Quantum of the fixed-point shared-memory current (a power of 2) for charges

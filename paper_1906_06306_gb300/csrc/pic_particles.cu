@@ -171,7 +171,10 @@ __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesD
       gather<D>(GA, ijk, o1, e, b);
     else
       gather_smem<D>(sm, P.t.wcells, P.t.W[0], P.t.W[0] * P.t.W[1], l, o1, e, b);
-    boris(u, e, b, S.qm, P.g.c, P.inv_c, P.inv_c2);
+    if (P.pusher == 1)
+      higuera_cary(u, e, b, S.qm, P.g.c, P.inv_c, P.inv_c2);
+    else
+      boris(u, e, b, S.qm, P.g.c, P.inv_c, P.inv_c2);
   }
   float o2[3] = {0.f, 0.f, 0.f}, dn[3];
   int dc[3] = {0, 0, 0};

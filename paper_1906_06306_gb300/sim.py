@@ -86,6 +86,11 @@ class Simulation:
         B.pic_autotune(self.ctx, cs, steps)
         return self.tuning()
 
+    def set_pusher(self, name):
+        """'boris' (default) or 'higuera_cary'."""
+        B.pic_set_pusher(self.ctx, {"boris": B.PIC_PUSHER_BORIS,
+                                    "higuera_cary": B.PIC_PUSHER_HIGUERA_CARY}[name])
+
     def step(self, n=1):
         B.pic_step(self.ctx, n)
 
@@ -137,6 +142,11 @@ class Batch:
     def __init__(self, sims):
         self.sims = list(sims)
         self.handle = B.pic_batch_create([s.ctx for s in self.sims])
+
+    def set_pusher(self, name):
+        """'boris' (default) or 'higuera_cary'."""
+        B.pic_set_pusher(self.ctx, {"boris": B.PIC_PUSHER_BORIS,
+                                    "higuera_cary": B.PIC_PUSHER_HIGUERA_CARY}[name])
 
     def step(self, n=1):
         B.pic_batch_step(self.handle, n, self.sims[0].stream.cuda_stream)

@@ -313,3 +313,36 @@ def test_binomial_fourier_response_and_mean(orc):
     assert np.abs(F[6, 0] - expect6).max() < 1e-13
     assert np.abs(F[7, 0] - (1.5 + fx**3 * np.cos(2 * math.pi * mx * ii / 24))).max() < 1e-13
     assert abs(F[8].sum() - s8) < 1e-11
+
+
+# --------------------------------------------------------- Higuera-Cary ----
+
+@pytest.mark.parametrize("beta_d", [0.3, 0.9, 0.99])
+def test_higuera_cary_keeps_relativistic_exb_drift_exactly(orc, beta_d):
+    """A particle moving with the E x B drift velocity feels no force; the
+    Higuera-Cary rotation factor makes the discrete update keep it exactly,
+    at any drift speed (Boris does not once the drift is relativistic)."""
+    bz = 0.3
+    ey = beta_d * bz  # E + (u/gamma) x B = 0 for u/gamma = beta_d x-hat
+    gam = 1.0 / math.sqrt(1.0 - beta_d**2)
+    u0 = np.array([gam * beta_d, 0.0, 0.0])
+    for qm in (1.0, -1.0):
+        u = u0.copy()
+        for _ in range(200):
+            u = orc.higuera_cary(u, [0, ey, 0], [0, 0, bz], qm, C)
+        assert np.abs(u - u0).max() < 1e-11
+    ub = orc.boris(u0, [0, ey, 0], [0, 0, bz], 1.0, C)
+    if beta_d >= 0.9:
+        assert np.abs(ub - u0).max() > 1e-4  # the closed form separates the two pushers
+
+
+def test_higuera_cary_rotation_and_pure_kick(orc):
+    """E = 0: the update is a rotation (|u| kept); B = 0: the two half kicks
+    add to u + s E / c exactly, as for Boris."""
+    u0 = np.array([1.7, -0.6, 0.4])
+    u = u0.copy()
+    for _ in range(300):
+        u = orc.higuera_cary(u, [0, 0, 0], [0.1, -0.2, 0.9], -1.0, C)
+    assert abs(np.linalg.norm(u) - np.linalg.norm(u0)) < 1e-12
+    e = np.array([0.01, -0.02, 0.03])
+    assert np.allclose(orc.higuera_cary(u0, e, [0, 0, 0], 1.0, C), u0 + e / C, rtol=0, atol=1e-15)
