@@ -125,6 +125,16 @@ pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* spec
 pic_status pic_get_tuning(pic_ctx* ctx, pic_tuning* out);
 pic_status pic_set_tuning(pic_ctx* ctx, const pic_tuning* t);
 
+/* Field solver of the context: PIC_FDTD2 (Eqs. fdE/fdB, second-order Yee; the
+ * default) or PIC_FDTD4 (Table 2; read as the fourth-order staggered
+ * differences (9/8)[f(i+1/2)-f(i-1/2)] - (1/24)[f(i+3/2)-f(i-3/2)] in both
+ * curls, second order in time).  FDTD4 needs c sqrt(dim) 7/6 < 1, else
+ * PIC_ERR_ARG.  The Gauss residual of pic_energies is the second-order one
+ * that the ZigZag deposit conserves; with FDTD4 it is no longer constant. */
+#define PIC_FDTD2 2
+#define PIC_FDTD4 4
+pic_status pic_set_field_solver(pic_ctx* ctx, int order);
+
 /* Particle pusher of the context: PIC_PUSHER_BORIS (Appendix C; the default)
  * or PIC_PUSHER_HIGUERA_CARY (Table 2, the pusher of the paper's shock run,
  * Higuera and Cary 2017: the Boris steps with the rotation's Lorentz factor

@@ -157,6 +157,12 @@ def higuera_cary(u, e, b, qm: float, c: float):
     return u
 
 
+def set_field_order(order: int):
+    """Spatial order of the field solver: 2 (FDTD2) or 4 (FDTD4)."""
+    assert order in (2, 4)
+    lib().orc_set_field_order(ctypes.c_int(order))
+
+
 def set_pusher(name: str):
     """'boris' (Appendix C) or 'higuera_cary' for push_particles and step."""
     lib().orc_set_pusher(ctypes.c_int({"boris": 0, "higuera_cary": 1}[name]))

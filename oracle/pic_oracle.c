@@ -39,6 +39,32 @@ static double dminus(const orc_grid* g, const double* F, int comp, int d, long i
   return val(g, F, comp, i, j, k) - val(g, F, comp, i - (d == 0), j - (d == 1), k - (d == 2));
 }
 
+/* Spatial order of the field solver: 2 (FDTD2, Eqs. fdE/fdB) or 4 (FDTD4 of
+ * Table 2, read as the fourth-order staggered difference
+ * (9/8) [A(p+e/2) - A(p-e/2)] - (1/24) [A(p+3e/2) - A(p-3e/2)]). */
+static int g_order = 2;
+void orc_set_field_order(int order) { g_order = order; }
+
+/* forward difference at the point half a cell up axis d, of the chosen order */
+static double dplus_o(const orc_grid* g, const double* F, int comp, int d, long i, long j, long k) {
+  if (g_order == 2 || d >= g->dim) return dplus(g, F, comp, d, i, j, k);
+  const long di = d == 0, dj = d == 1, dk = d == 2;
+  const double near = val(g, F, comp, i + di, j + dj, k + dk) - val(g, F, comp, i, j, k);
+  const double far = val(g, F, comp, i + 2 * di, j + 2 * dj, k + 2 * dk) -
+                     val(g, F, comp, i - di, j - dj, k - dk);
+  return 9.0 / 8.0 * near - 1.0 / 24.0 * far;
+}
+
+/* backward difference at the point half a cell down axis d, of the chosen order */
+static double dminus_o(const orc_grid* g, const double* F, int comp, int d, long i, long j, long k) {
+  if (g_order == 2 || d >= g->dim) return dminus(g, F, comp, d, i, j, k);
+  const long di = d == 0, dj = d == 1, dk = d == 2;
+  const double near = val(g, F, comp, i, j, k) - val(g, F, comp, i - di, j - dj, k - dk);
+  const double far = val(g, F, comp, i + di, j + dj, k + dk) -
+                     val(g, F, comp, i - 2 * di, j - 2 * dj, k - 2 * dk);
+  return 9.0 / 8.0 * near - 1.0 / 24.0 * far;
+}
+
 /* Eq. (fdB), half a step.  With E on cell edges and B on faces (Sect. 2.3.1)
  * the curl of E at the B points is taken with forward differences:
  *   (curl E)_x = d+_y Ez - d+_z Ey, (curl E)_y = d+_z Ex - d+_x Ez,
@@ -50,9 +76,9 @@ void orc_push_half_b(const orc_grid* g, double* F) {
     for (long j = 0; j < g->ny; ++j)
       for (long i = 0; i < g->nx; ++i) {
         const long p = at(g, i, j, k);
-        const double cx = dplus(g, F, EZ, 1, i, j, k) - dplus(g, F, EY, 2, i, j, k);
-        const double cy = dplus(g, F, EX, 2, i, j, k) - dplus(g, F, EZ, 0, i, j, k);
-        const double cz = dplus(g, F, EY, 0, i, j, k) - dplus(g, F, EX, 1, i, j, k);
+        const double cx = dplus_o(g, F, EZ, 1, i, j, k) - dplus_o(g, F, EY, 2, i, j, k);
+        const double cy = dplus_o(g, F, EX, 2, i, j, k) - dplus_o(g, F, EZ, 0, i, j, k);
+        const double cz = dplus_o(g, F, EY, 0, i, j, k) - dplus_o(g, F, EX, 1, i, j, k);
         F[BX * P + p] -= h * cx;
         F[BY * P + p] -= h * cy;
         F[BZ * P + p] -= h * cz;
@@ -67,9 +93,9 @@ void orc_push_e(const orc_grid* g, double* F) {
     for (long j = 0; j < g->ny; ++j)
       for (long i = 0; i < g->nx; ++i) {
         const long p = at(g, i, j, k);
-        const double cx = dminus(g, F, BZ, 1, i, j, k) - dminus(g, F, BY, 2, i, j, k);
-        const double cy = dminus(g, F, BX, 2, i, j, k) - dminus(g, F, BZ, 0, i, j, k);
-        const double cz = dminus(g, F, BY, 0, i, j, k) - dminus(g, F, BX, 1, i, j, k);
+        const double cx = dminus_o(g, F, BZ, 1, i, j, k) - dminus_o(g, F, BY, 2, i, j, k);
+        const double cy = dminus_o(g, F, BX, 2, i, j, k) - dminus_o(g, F, BZ, 0, i, j, k);
+        const double cz = dminus_o(g, F, BY, 0, i, j, k) - dminus_o(g, F, BX, 1, i, j, k);
         F[EX * P + p] += g->c * cx;
         F[EY * P + p] += g->c * cy;
         F[EZ * P + p] += g->c * cz;

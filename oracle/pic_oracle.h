@@ -36,6 +36,9 @@ typedef struct {
 
 /* Field solver, Eq. (fdB) over half a step: B -= (c/2) curl E. */
 void orc_push_half_b(const orc_grid* g, double* F);
+/* Spatial order of orc_push_half_b / orc_push_e: 2 (FDTD2, default) or 4
+ * (FDTD4: fourth-order staggered differences, coefficients 9/8 and -1/24). */
+void orc_set_field_order(int order);
 /* Field solver, curl part of Eq. (fdE): E += c curl B. */
 void orc_push_e(const orc_grid* g, double* F);
 /* add_cur of Table 1, current part of Eq. (fdE): E -= J. */

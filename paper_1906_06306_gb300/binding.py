@@ -46,6 +46,7 @@ SIGNATURES = {
     "pic_get_tuning": (c_int, [_P, ctypes.POINTER(pic_tuning)]),
     "pic_set_tuning": (c_int, [_P, ctypes.POINTER(pic_tuning)]),
     "pic_set_pusher": (c_int, [_P, c_int]),
+    "pic_set_field_solver": (c_int, [_P, c_int]),
     "pic_sort": (c_int, [_P]),
     "pic_gather_push": (c_int, [_P]),
     "pic_deposit": (c_int, [_P]),
@@ -118,6 +119,13 @@ def pic_set_tuning(ctx, t: pic_tuning) -> None:
 
 
 PIC_PUSHER_BORIS, PIC_PUSHER_HIGUERA_CARY = 0, 1
+
+
+PIC_FDTD2, PIC_FDTD4 = 2, 4
+
+
+def pic_set_field_solver(ctx, order: int) -> None:
+    _check(_lib.pic_set_field_solver(ctx, order), ctx)
 
 
 def pic_set_pusher(ctx, pusher: int) -> None:

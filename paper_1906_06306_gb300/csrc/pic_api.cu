@@ -366,6 +366,7 @@ pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* spec
   ctx->g.n[2] = grid->nz;
   ctx->g.plane = ncell;
   ctx->g.c = c;
+  ctx->g.order = 2;
   // defaults: tiles of 64 cells in 1D, 16^2 in 2D, 8x8x4 in 3D; sort every 10 steps
   // (3 in 3D, where a 2-cell halo is all the shared memory affords)
   ctx->tun.tile[0] = grid->dim == 1 ? 64 : grid->dim == 2 ? 16 : 8;
@@ -437,6 +438,17 @@ pic_status pic_set_tuning(pic_ctx* ctx, const pic_tuning* t) {
     if (s != PIC_OK) return s;
     return do_sort(ctx, true);
   }
+  return PIC_OK;
+}
+
+pic_status pic_set_field_solver(pic_ctx* ctx, int order) {
+  if (!ctx) return PIC_ERR_ARG;
+  if (order != PIC_FDTD2 && order != PIC_FDTD4)
+    return set_err(ctx, PIC_ERR_ARG, "order must be PIC_FDTD2 or PIC_FDTD4");
+  // FDTD4 is stable for c sqrt(D) (9/8 + 1/24) <= 1
+  if (order == PIC_FDTD4 && ctx->c * std::sqrt((double)ctx->grid.dim) * (7.0 / 6.0) >= 1.0)
+    return set_err(ctx, PIC_ERR_ARG, "Courant number too large for FDTD4 in this dimension");
+  ctx->g.order = order;
   return PIC_OK;
 }
 

@@ -20,6 +20,7 @@ struct GridDev {
   int n[3];          // cells per axis (1 for non-gridded axes)
   long long plane;   // n0*n1*n2
   float c;           // Courant number
+  int order;         // spatial order of the field solver: 2 (FDTD2) or 4 (FDTD4)
 };
 
 struct TileDev {

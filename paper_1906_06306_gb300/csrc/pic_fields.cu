@@ -110,13 +110,106 @@ __global__ void k_filter_axis(const T* __restrict__ src, T* __restrict__ dst, co
   dst[comp * P + idx] = T(0.25) * s[lo] + T(0.5) * s[idx] + T(0.25) * s[hi];
 }
 
+// Offsets (elements) of the lattice points a-2, a-1, a+1, a+2 along an axis of
+// n points with stride s, periodic.
+struct Nb {
+  long long m2, m1, p1, p2;
+};
+__device__ __forceinline__ Nb neighbours(int a, int n, long long s) {
+  Nb r;
+  r.m2 = (long long)(wrapi(a - 2, n) - a) * s;
+  r.m1 = (long long)(wrapi(a - 1, n) - a) * s;
+  r.p1 = (long long)(wrapi(a + 1, n) - a) * s;
+  r.p2 = (long long)(wrapi(a + 2, n) - a) * s;
+  return r;
+}
+// fourth-order staggered differences (FDTD4): at the point half a cell up
+// (forward) or down (backward) the axis, coefficients 9/8 and -1/24
+__device__ __forceinline__ float d4p(const float* A, long long i, const Nb& b) {
+  return 1.125f * (A[i + b.p1] - A[i]) - (1.0f / 24.0f) * (A[i + b.p2] - A[i + b.m1]);
+}
+__device__ __forceinline__ float d4m(const float* A, long long i, const Nb& b) {
+  return 1.125f * (A[i] - A[i + b.m1]) - (1.0f / 24.0f) * (A[i + b.p1] - A[i + b.m2]);
+}
+
+// FDTD4 versions of the two updates (same structure as above, wider stencil).
+template <int D>
+__global__ void k_b_half4(float* __restrict__ F, const GridDev g, float hc, int zero_j) {
+  const long long P = g.plane;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % g.n[0]);
+    const long long r = idx / g.n[0];
+    const int j = (int)(r % g.n[1]), k = (int)(r / g.n[1]);
+    const Nb nx = neighbours(i, g.n[0], 1);
+    const Nb ny = neighbours(j, g.n[1], g.n[0]);
+    const Nb nz = neighbours(k, g.n[2], (long long)g.n[0] * g.n[1]);
+    const float* Ex = F + EX * P;
+    const float* Ey = F + EY * P;
+    const float* Ez = F + EZ * P;
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    cy -= d4p(Ez, idx, nx);
+    cz += d4p(Ey, idx, nx);
+    if (D >= 2) {
+      cx += d4p(Ez, idx, ny);
+      cz -= d4p(Ex, idx, ny);
+    }
+    if (D >= 3) {
+      cx -= d4p(Ey, idx, nz);
+      cy += d4p(Ex, idx, nz);
+    }
+    F[BX * P + idx] = fmaf(-hc, cx, F[BX * P + idx]);
+    F[BY * P + idx] = fmaf(-hc, cy, F[BY * P + idx]);
+    F[BZ * P + idx] = fmaf(-hc, cz, F[BZ * P + idx]);
+    if (zero_j) {
+      F[JX * P + idx] = 0.f;
+      F[JY * P + idx] = 0.f;
+      F[JZ * P + idx] = 0.f;
+    }
+  }
+}
+
+template <int D>
+__global__ void k_e_update4(float* __restrict__ F, const GridDev g, float c) {
+  const long long P = g.plane;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % g.n[0]);
+    const long long r = idx / g.n[0];
+    const int j = (int)(r % g.n[1]), k = (int)(r / g.n[1]);
+    const Nb nx = neighbours(i, g.n[0], 1);
+    const Nb ny = neighbours(j, g.n[1], g.n[0]);
+    const Nb nz = neighbours(k, g.n[2], (long long)g.n[0] * g.n[1]);
+    const float* Bx = F + BX * P;
+    const float* By = F + BY * P;
+    const float* Bz = F + BZ * P;
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    cy -= d4m(Bz, idx, nx);
+    cz += d4m(By, idx, nx);
+    if (D >= 2) {
+      cx += d4m(Bz, idx, ny);
+      cz -= d4m(Bx, idx, ny);
+    }
+    if (D >= 3) {
+      cx -= d4m(By, idx, nz);
+      cy += d4m(Bx, idx, nz);
+    }
+    F[EX * P + idx] = fmaf(c, cx, F[EX * P + idx]) - F[JX * P + idx];
+    F[EY * P + idx] = fmaf(c, cy, F[EY * P + idx]) - F[JY * P + idx];
+    F[EZ * P + idx] = fmaf(c, cz, F[EZ * P + idx]) - F[JZ * P + idx];
+  }
+}
+
 cudaError_t launch_b_half(const GridDev& g, float* F, int zero_j, cudaStream_t st) {
   const unsigned nb = grid_for(g.plane, 256);
   const float hc = 0.5f * g.c;
-  switch (g.dim) {
-    case 1: k_b_half<1><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
-    case 2: k_b_half<2><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
-    case 3: k_b_half<3><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
+  switch (g.dim * 10 + g.order) {
+    case 12: k_b_half<1><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
+    case 22: k_b_half<2><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
+    case 32: k_b_half<3><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
+    case 14: k_b_half4<1><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
+    case 24: k_b_half4<2><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
+    case 34: k_b_half4<3><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -124,10 +217,13 @@ cudaError_t launch_b_half(const GridDev& g, float* F, int zero_j, cudaStream_t s
 
 cudaError_t launch_e_update(const GridDev& g, float* F, cudaStream_t st) {
   const unsigned nb = grid_for(g.plane, 256);
-  switch (g.dim) {
-    case 1: k_e_update<1><<<nb, 256, 0, st>>>(F, g, g.c); break;
-    case 2: k_e_update<2><<<nb, 256, 0, st>>>(F, g, g.c); break;
-    case 3: k_e_update<3><<<nb, 256, 0, st>>>(F, g, g.c); break;
+  switch (g.dim * 10 + g.order) {
+    case 12: k_e_update<1><<<nb, 256, 0, st>>>(F, g, g.c); break;
+    case 22: k_e_update<2><<<nb, 256, 0, st>>>(F, g, g.c); break;
+    case 32: k_e_update<3><<<nb, 256, 0, st>>>(F, g, g.c); break;
+    case 14: k_e_update4<1><<<nb, 256, 0, st>>>(F, g, g.c); break;
+    case 24: k_e_update4<2><<<nb, 256, 0, st>>>(F, g, g.c); break;
+    case 34: k_e_update4<3><<<nb, 256, 0, st>>>(F, g, g.c); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

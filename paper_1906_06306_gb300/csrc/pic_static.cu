@@ -72,6 +72,7 @@ extern "C" pic_status pic_filter_current_static(const pic_grid* grid, float* J, 
   g.n[1] = n[1];
   g.n[2] = n[2];
   g.plane = ncell;
+  g.order = 2;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   float* a = J;
   float* b = scratch;

@@ -86,6 +86,10 @@ class Simulation:
         B.pic_autotune(self.ctx, cs, steps)
         return self.tuning()
 
+    def set_field_solver(self, order):
+        """2 (FDTD2, default) or 4 (FDTD4)."""
+        B.pic_set_field_solver(self.ctx, order)
+
     def set_pusher(self, name):
         """'boris' (default) or 'higuera_cary'."""
         B.pic_set_pusher(self.ctx, {"boris": B.PIC_PUSHER_BORIS,
@@ -142,6 +146,10 @@ class Batch:
     def __init__(self, sims):
         self.sims = list(sims)
         self.handle = B.pic_batch_create([s.ctx for s in self.sims])
+
+    def set_field_solver(self, order):
+        """2 (FDTD2, default) or 4 (FDTD4)."""
+        B.pic_set_field_solver(self.ctx, order)
 
     def set_pusher(self, name):
         """'boris' (default) or 'higuera_cary'."""

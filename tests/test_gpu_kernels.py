@@ -219,3 +219,29 @@ def test_higuera_cary_keeps_exb_drift_on_gpu():
         assert np.abs(s["u"][0] - gam * beta).max() < 2e-5 * gam
         assert np.abs(s["u"][1:]).max() < 2e-5 * gam
     sim.close()
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_fdtd4_field_updates_match_oracle(dim):
+    from paper_1906_06306_gb300 import PIC_FIELD_B_HALF, PIC_FIELD_E
+
+    nx, ny, nz = SHAPES[dim]
+    rs = np.random.default_rng(700 + dim)
+    F32 = random_fields((nz, ny, nx), rs)
+    F32[6:9] = (0.01 * rs.normal(size=(3, nz, ny, nx))).astype(np.float32)
+    sim = _sim(dim, SHAPES[dim], F32, _empty_species(dim))
+    sim.set_field_solver(4)
+    g = oracle.Grid(dim, nx, ny, nz, 0.45)
+    F = F32.astype(np.float64)
+    oracle.set_field_order(4)
+    try:
+        sim.field_update(PIC_FIELD_B_HALF)
+        oracle.push_half_b(g, F)
+        compare_fields(sim.download()[0], F, tol=1e-6)
+        sim.field_update(PIC_FIELD_E)
+        oracle.push_e(g, F)
+        oracle.add_cur(g, F)
+        compare_fields(sim.download()[0], F, tol=1e-6)
+    finally:
+        oracle.set_field_order(2)
+    sim.close()

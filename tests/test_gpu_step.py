@@ -195,3 +195,29 @@ def test_full_size_turbulence_step_sampled_against_oracle():
     en = sim.energies()
     assert en[2 + sim.nspecies] < 1e-5 * max(np.abs(Fg[0:3]).max(), np.abs(Fg[6:9]).max())
     sim.close()
+
+
+def test_shock_set_up_with_fdtd4_and_higuera_cary_matches_oracle():
+    """The solver choice of the paper's shock run (Sect. 4.2): FDTD4 fields,
+    Higuera-Cary pusher and Binomial2 filtering, on the cold Gamma = 10 flow."""
+    from paper_1906_06306_gb300 import Simulation
+
+    pl = workloads.shock_3d(nx=24, ny=12, nz=10, ppc=2, seed=32)
+    sim = Simulation.from_plasma(pl, tuning=dict(tile=[8, 8, 4], sort_every=1000, filter_passes=2))
+    sim.set_field_solver(4)
+    sim.set_pusher("higuera_cary")
+    g, F, osp, _ = oracle_from_sim(sim)
+    oracle.set_field_order(4)
+    oracle.set_pusher("higuera_cary")
+    try:
+        for k in range(1, 7):
+            sim.step(1)
+            oracle.step(g, F, osp, passes=2)
+            Fg, spg = sim.download()
+            compare_fields(Fg, F, floor=step_floor(g, osp, k))
+            compare_particles(g, spg, osp)
+    finally:
+        oracle.set_field_order(2)
+        oracle.set_pusher("boris")
+    sim.check()
+    sim.close()

@@ -206,12 +206,22 @@ def test_zigzag_total_current_is_charge_times_displacement(orc):
 
 # ---------------------------------------------------------------- FDTD2 -----
 
-def _plane_wave(g, kvec, e_hat, t_e):
+def _k_operator(kvec, order=2):
+    """Symbol of the staggered difference: 2 sin(k/2) (second order) or
+    2 [(9/8) sin(k/2) - (1/24) sin(3k/2)] (fourth order)."""
+    k = np.asarray(kvec, dtype=np.float64)
+    if order == 2:
+        return 2.0 * np.sin(k / 2.0)
+    return 2.0 * (9.0 / 8.0 * np.sin(k / 2.0) - 1.0 / 24.0 * np.sin(1.5 * k))
+
+
+def _plane_wave(g, kvec, e_hat, t_e, order=2):
     """Discrete plane wave of the Yee scheme at E time t_e (B at t_e - 1/2).
-    With K_d = 2 sin(k_d/2) and Omega = 2 sin(w/2), the update equations of
-    Eqs. (fdE), (fdB) give Omega^2 = c^2 |K|^2 and b = c (K x e) / Omega for e
-    orthogonal to K (the textbook Yee dispersion relation)."""
-    K = 2.0 * np.sin(np.asarray(kvec) / 2.0)
+    With K the symbol of the staggered difference and Omega = 2 sin(w/2), the
+    update equations of Eqs. (fdE), (fdB) give Omega^2 = c^2 |K|^2 and
+    b = c (K x e) / Omega for e orthogonal to K (the textbook Yee dispersion
+    relation for K_d = 2 sin(k_d/2))."""
+    K = _k_operator(kvec, order)
     om = 2.0 * math.asin(C * np.linalg.norm(K) / 2.0)
     b_hat = C * np.cross(K, e_hat) / (2.0 * math.sin(om / 2.0))
     F = g.zeros()
@@ -346,3 +356,32 @@ def test_higuera_cary_rotation_and_pure_kick(orc):
     assert abs(np.linalg.norm(u) - np.linalg.norm(u0)) < 1e-12
     e = np.array([0.01, -0.02, 0.03])
     assert np.allclose(orc.higuera_cary(u0, e, [0, 0, 0], 1.0, C), u0 + e / C, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("dim,modes", [(1, (3, 0, 0)), (2, (2, 5, 0)), (3, (1, 2, 3))])
+def test_fdtd4_vacuum_plane_wave_dispersion(orc, dim, modes):
+    """FDTD4 (Table 2): the fourth-order staggered differences advance a
+    plane wave exactly along sin^2(w/2) = (c^2/4) sum_d K4_d^2,
+    K4 = 2 [(9/8) sin(k/2) - (1/24) sin(3k/2)]."""
+    nx, ny, nz = (32, 24, 16)[:dim] + (1,) * (3 - dim)
+    g = orc.Grid(dim, nx, ny, nz, C)
+    kvec = np.array([2 * math.pi * modes[0] / nx, 2 * math.pi * modes[1] / ny,
+                     2 * math.pi * modes[2] / nz])
+    K = _k_operator(kvec, 4)
+    trial = np.array([0.3, -0.5, 0.8])
+    e_hat = trial - K * (trial @ K) / (K @ K)
+    e_hat /= np.linalg.norm(e_hat)
+    F, _ = _plane_wave(g, kvec, e_hat, 0.0, order=4)
+    orc.set_field_order(4)
+    try:
+        for _ in range(40):
+            orc.push_half_b(g, F)
+            orc.push_half_b(g, F)
+            orc.push_e(g, F)
+    finally:
+        orc.set_field_order(2)
+    expect, _ = _plane_wave(g, kvec, e_hat, 40.0, order=4)
+    assert np.abs(F[:6] - expect[:6]).max() < 1e-11
+    # the second-order wave differs: the test separates the two solvers
+    expect2, _ = _plane_wave(g, kvec, e_hat, 40.0, order=2)
+    assert np.abs(F[:6] - expect2[:6]).max() > 1e-6
