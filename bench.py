@@ -266,6 +266,10 @@ def run_ours(args):
     tuning = dict(filter_passes=w["filter_passes"])
     if args.sort_every:
         tuning["sort_every"] = args.sort_every
+    if args.tile:
+        tuning["tile"] = [int(v) for v in args.tile.split(",")] + [1] * (3 - len(args.tile.split(",")))
+    if args.halo:
+        tuning["halo"] = args.halo
     sim = Simulation.from_plasma(pl, device=f"cuda:{local}", tuning=tuning)
     dev = torch.device(f"cuda:{local}")
     if args.autotune:  # untimed: real steps under candidate tunings, keeps the fastest
@@ -464,6 +468,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sort-every", type=int, default=0, help="0 = library default / autotuned")
+    ap.add_argument("--tile", type=str, default="",
+                    help="tile extents, e.g. 16,8 (with --no-autotune: fix the tuning that "
+                         "autotuning picks, for profiling runs)")
+    ap.add_argument("--halo", type=int, default=0, help="0 = library default / autotuned")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default tuning instead of autotuning before the timed region")
     ap.add_argument("--e2e-steps", type=int, default=20)

@@ -753,6 +753,7 @@ struct pic_batch {
   int cycle = 0;                          // steps per graph launch
   std::vector<long long> phase;           // steps % sort_every of each context at capture
   std::vector<pic_tuning> tun;            // tuning of each context at capture
+  std::vector<int> solver;                // pusher * 16 + field order at capture
 };
 
 namespace {
@@ -782,6 +783,7 @@ bool batch_graph_current(const pic_batch* b) {
     const pic_ctx* c = b->ctxs[i];
     if (std::memcmp(&c->tun, &b->tun[i], sizeof(pic_tuning)) != 0) return false;
     if (c->steps % c->tun.sort_every != b->phase[i]) return false;
+    if (c->pusher * 16 + c->g.order != b->solver[i]) return false;
   }
   return true;
 }
@@ -833,9 +835,11 @@ pic_status batch_capture(pic_batch* b) {
   }
   b->phase.resize(b->ctxs.size());
   b->tun.resize(b->ctxs.size());
+  b->solver.resize(b->ctxs.size());
   for (size_t i = 0; i < b->ctxs.size(); ++i) {
     b->phase[i] = b->ctxs[i]->steps % b->ctxs[i]->tun.sort_every;
     b->tun[i] = b->ctxs[i]->tun;
+    b->solver[i] = b->ctxs[i]->pusher * 16 + b->ctxs[i]->g.order;
   }
   return PIC_OK;
 }

@@ -148,13 +148,14 @@ class Batch:
         self.handle = B.pic_batch_create([s.ctx for s in self.sims])
 
     def set_field_solver(self, order):
-        """2 (FDTD2, default) or 4 (FDTD4)."""
-        B.pic_set_field_solver(self.ctx, order)
+        """Set the field solver of every box (the next step recaptures)."""
+        for s in self.sims:
+            s.set_field_solver(order)
 
     def set_pusher(self, name):
-        """'boris' (default) or 'higuera_cary'."""
-        B.pic_set_pusher(self.ctx, {"boris": B.PIC_PUSHER_BORIS,
-                                    "higuera_cary": B.PIC_PUSHER_HIGUERA_CARY}[name])
+        """Set the pusher of every box (the next step recaptures)."""
+        for s in self.sims:
+            s.set_pusher(name)
 
     def step(self, n=1):
         B.pic_batch_step(self.handle, n, self.sims[0].stream.cuda_stream)

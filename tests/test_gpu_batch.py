@@ -63,6 +63,17 @@ def test_batch_matches_each_box_stepped_alone():
         s.step(20)
     for a, b in zip(batched, alone):
         _same_state(a, b, nsteps + 20)
+    # so does a change of pusher and field solver on every box
+    batch.set_pusher("higuera_cary")
+    batch.set_field_solver(4)
+    for s in alone:
+        s.set_pusher("higuera_cary")
+        s.set_field_solver(4)
+    batch.step(10)
+    for s in alone:
+        s.step(10)
+    for a, b in zip(batched, alone):
+        _same_state(a, b, nsteps + 30)
     batch.close()
     for s in batched + alone:
         s.close()
