@@ -3,14 +3,18 @@
 TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg may import this package.  The product library
 never loads it and shares no code with it.  The arithmetic lives in
-``pic_oracle.c`` (plain C, double precision, periodic boxes); this module
+``pic_oracle.c`` (plain C, double precision, periodic boxes or the shock
+set-up's wall and injector); this module
 compiles it with gcc on first use and marshals numpy arrays through ctypes.
 
 Parity status of each function is pinned in ``tests/test_oracle_pins.py``:
 Boris (closed-form gyration, E x B drift, pure-E kick), gather (exact for
 constant and linear fields), ZigZag (hand sums from ``tests/golden`` and
 discrete continuity), FDTD2 (Yee dispersion relation, div B), Binomial2
-(Fourier response), whole step (Gauss law, energy, Weibel growth rate).
+(Fourier response), whole step (Gauss law, energy, Weibel growth rate);
+``tests/test_oracle_shock.py``: wall (specular reflection, charge continuity of
+reflected particles, conductor standing waves) and injector (the box fills
+with the advected upstream template, no gap and no duplicate).
 """
 from __future__ import annotations
 
@@ -50,6 +54,7 @@ def lib():
     if _lib is None:
         _lib = ctypes.CDLL(build())
         _lib.orc_kinetic_energy.restype = ctypes.c_double
+        _lib.orc_inject.restype = ctypes.c_long
     return _lib
 
 
@@ -199,6 +204,67 @@ def step(g: Grid, F, species, passes: int = 0, nsteps: int = 1):
     for _ in range(nsteps):
         lib().orc_step(g.c_struct(), _p(F), xs, us, n, q, m, ctypes.c_int(ns),
                        ctypes.c_int(passes), _p(work))
+
+
+def set_wall(w: int, i_zero: int = 0):
+    """Conducting wall on the node plane x = w (0: none) for push_particles,
+    deposit and step, with E and B zeroed at i >= i_zero after each field
+    update of step (Sect. 4.2 shock set-up)."""
+    lib().orc_set_wall(ctypes.c_long(w), ctypes.c_long(i_zero))
+
+
+def wall_fields(g: Grid, F, w: int, i_zero: int):
+    lib().orc_wall_fields(g.c_struct(), _p(F), ctypes.c_long(w), ctypes.c_long(i_zero))
+
+
+class Injector:
+    """Receding injector of the shock set-up (Sect. 4.2): `templates` is one
+    (x float64[3, nt], u float64[3, nt]) upstream block per species, x in
+    [0, lt) x ny x nz and sorted by x; it is repeated along x and advected at
+    -v_up, and the injector X(s) = min(x0 + v_inj s, x_max) lets in, during
+    step s, the template particles that cross it."""
+
+    def __init__(self, templates, lt, x0, x_max, v_inj, v_up):
+        self.templates = [(np.ascontiguousarray(x, dtype=np.float64),
+                           np.ascontiguousarray(u, dtype=np.float64)) for x, u in templates]
+        self.lt, self.x0, self.x_max = int(lt), float(x0), float(x_max)
+        self.v_inj, self.v_up = float(v_inj), float(v_up)
+
+    def inject(self, s: int, species):
+        """Append the particles entering during step s to each species."""
+        counts = []
+        for (xt, ut), sp in zip(self.templates, species):
+            nt = xt.shape[1]
+            cap = nt * (2 + int(np.ceil((self.v_inj + self.v_up) / self.lt))) + 16
+            xo, uo = np.zeros((3, cap)), np.zeros((3, cap))
+            k = lib().orc_inject(_p(xt), _p(ut), ctypes.c_long(nt), ctypes.c_long(self.lt),
+                                 ctypes.c_double(self.x0), ctypes.c_double(self.x_max),
+                                 ctypes.c_double(self.v_inj), ctypes.c_double(self.v_up),
+                                 ctypes.c_long(s), _p(xo), _p(uo), ctypes.c_long(cap))
+            assert k >= 0
+            sp.x = np.ascontiguousarray(np.concatenate([sp.x, xo[:, :k]], axis=1))
+            sp.u = np.ascontiguousarray(np.concatenate([sp.u, uo[:, :k]], axis=1))
+            counts.append(int(k))
+        return counts
+
+
+def shock_from_plasma(pl):
+    """(wall, i_zero, Injector) of a workloads.shock_tube plasma; i_zero is the
+    first lattice index past the injector's last position plus one cell."""
+    sh = pl.meta["shock"]
+    tg = Grid(pl.dim, sh["lt"], pl.ny, pl.nz, pl.c)
+    temps = [(positions(tg, t.cell, t.off), t.u.astype(np.float64)) for t in sh["templates"]]
+    inj = Injector(temps, sh["lt"], sh["x_inj"], sh["x_max"], sh["v_inj"], sh["v_up"])
+    return sh["wall"], int(np.floor(sh["x_max"])) + 2, inj
+
+
+def step_shock(g: Grid, F, species, injector, s0: int, passes: int = 0, nsteps: int = 1):
+    """`nsteps` steps of the shock set-up from step index s0: each a full step
+    (with the wall set by set_wall) followed by the injection of that step."""
+    for t in range(nsteps):
+        step(g, F, species, passes=passes, nsteps=1)
+        if injector is not None:
+            injector.inject(s0 + t, species)
 
 
 def charge_density(g: Grid, species):

@@ -293,8 +293,19 @@ void orc_zigzag(const orc_grid* g, double* F, const double* x1, const double* x2
 
 static double extent(const orc_grid* g, int d) { return d == 0 ? g->nx : d == 1 ? g->ny : g->nz; }
 
+/* Conducting wall of the shock set-up (Sect. 4.2) at the node x = g_wall
+ * (0: no wall).  See orc_set_wall. */
+static long g_wall = 0, g_izero = 0;
+void orc_set_wall(long wall, long i_zero) {
+  g_wall = wall;
+  g_izero = i_zero;
+}
+
 /* interp_em and push of Table 1: gather, Boris (Appendix C), then the
- * position update of Eq. (fdX), x += c u / gamma with the new u. */
+ * position update of Eq. (fdX), x += c u / gamma with the new u.  A particle
+ * whose new x lies below the wall is reflected specularly: x -> 2 w - x,
+ * u_x -> -u_x (the displacement written to dx is the unreflected one; the
+ * deposit rebuilds the reflected path from it). */
 void orc_push_particles(const orc_grid* g, const double* F, double* x, double* u, long n,
                         double qm, double* x_old, double* dx) {
   for (long p = 0; p < n; ++p) {
@@ -315,6 +326,10 @@ void orc_push_particles(const orc_grid* g, const double* F, double* x, double* u
     for (int d = 0; d < g->dim; ++d) {
       const double L = extent(g, d);
       double xn = xp[d] + dx[d * n + p];
+      if (d == 0 && g_wall > 0 && xn < (double)g_wall) {
+        xn = 2.0 * (double)g_wall - xn;
+        u[p] = -u[p];
+      }
       if (xn < 0.0) xn += L;
       if (xn >= L) xn -= L;
       x[d * n + p] = xn;
@@ -322,7 +337,10 @@ void orc_push_particles(const orc_grid* g, const double* F, double* x, double* u
   }
 }
 
-/* comp_curr (Table 1) for one species. */
+/* comp_curr (Table 1) for one species.  The current of a particle reflected
+ * at the wall is deposited along its true path: a straight segment to the
+ * point where it meets the wall plane, then the mirrored remainder, each with
+ * the ZigZag rule, so the charge moved is accounted for at every node. */
 void orc_deposit(const orc_grid* g, double* F, const double* x_old, const double* dx, long n,
                  double q) {
   for (long p = 0; p < n; ++p) {
@@ -331,8 +349,94 @@ void orc_deposit(const orc_grid* g, double* F, const double* x_old, const double
       x1[d] = x_old[d * n + p];
       x2[d] = x1[d] + dx[d * n + p];
     }
-    orc_zigzag(g, F, x1, x2, q);
+    if (g_wall > 0 && x2[0] < (double)g_wall) {
+      const double w = (double)g_wall;
+      const double s = (x1[0] - w) / (x1[0] - x2[0]); /* fraction of the step before the wall */
+      double xc[3], xm[3];
+      xc[0] = w;
+      for (int d = 1; d < 3; ++d) xc[d] = x1[d] + s * (x2[d] - x1[d]);
+      xm[0] = 2.0 * w - x2[0];
+      for (int d = 1; d < 3; ++d) xm[d] = x2[d];
+      orc_zigzag(g, F, x1, xc, q);
+      orc_zigzag(g, F, xc, xm, q);
+    } else {
+      orc_zigzag(g, F, x1, x2, q);
+    }
   }
+}
+
+/* Field boundary of the conducting wall at the node x = w (Sect. 4.2): the
+ * tangential E vanishes on the wall plane (Ey = Ez = 0 at i = w) and the cells
+ * behind it (i < w) hold the mirror image of the plasma side, the image of a
+ * perfect conductor (tangential E and normal B odd, normal E and tangential B
+ * even about x = w).  Integer-x components (Ey, Ez, Bx) at i mirror 2w - i;
+ * half-integer ones (Ex, By, Bz, stored at i for x = i + 1/2) mirror
+ * 2w - 1 - i.  Every E and B value at i >= i_zero is set to zero (the vacuum
+ * beyond the injector's last position, which also keeps the periodic wrap from
+ * reaching the wall).  J is not touched. */
+void orc_wall_fields(const orc_grid* g, double* F, long w, long i_zero) {
+  const long P = ncell(g);
+  for (long k = 0; k < g->nz; ++k)
+    for (long j = 0; j < g->ny; ++j) {
+      for (long i = 0; i < w; ++i) {
+        const long a = at(g, i, j, k), ri = at(g, 2 * w - i, j, k), rh = at(g, 2 * w - 1 - i, j, k);
+        F[EX * P + a] = F[EX * P + rh];
+        F[BY * P + a] = F[BY * P + rh];
+        F[BZ * P + a] = F[BZ * P + rh];
+        F[EY * P + a] = -F[EY * P + ri];
+        F[EZ * P + a] = -F[EZ * P + ri];
+        F[BX * P + a] = -F[BX * P + ri];
+      }
+      F[EY * P + at(g, w, j, k)] = 0.0;
+      F[EZ * P + at(g, w, j, k)] = 0.0;
+      for (long i = i_zero; i < g->nx; ++i)
+        for (int comp = EX; comp <= BZ; ++comp) F[comp * P + at(g, i, j, k)] = 0.0;
+    }
+}
+
+/* Receding injector of the shock set-up (Sect. 4.2).  An upstream template
+ * (positions xt[3][nt] in a block [0, lt) x ny x nz, sorted by x; four-
+ * velocities ut[3][nt]) is repeated along x (copy m shifted by m lt) and
+ * advected at -v_up; the injector sits at X(s) = min(x0 + v_inj s, x_max).
+ * In template coordinates the injector is at A(s) = (X(s) - x0) + v_up s, and
+ * in step s (ending at time level s + 1) every copy-m particle with
+ * A(s) - m lt <= xt < A(s+1) - m lt enters the box at
+ * x = xt + ((m lt + x0) - v_up (s + 1)): the particles that crossed the
+ * injector during the step.  The new x offset is rounded to float, as every
+ * initial offset is (an offset that rounds to 1 moves to the next cell).
+ * Writes at most cap particles to xo[3][cap], uo[3][cap] (m ascending, then
+ * template order) and returns their count, or -1 if cap is too small. */
+static double inj_front(double x0, double x_max, double v_inj, double v_up, long s) {
+  const double X = fmin(x0 + v_inj * (double)s, x_max);
+  return (X - x0) + v_up * (double)s;
+}
+
+long orc_inject(const double* xt, const double* ut, long nt, long lt, double x0, double x_max,
+                double v_inj, double v_up, long s, double* xo, double* uo, long cap) {
+  const double a = inj_front(x0, x_max, v_inj, v_up, s);
+  const double b = inj_front(x0, x_max, v_inj, v_up, s + 1);
+  long out = 0;
+  for (long m = (long)floor(a / (double)lt); m <= (long)floor(b / (double)lt); ++m) {
+    const double am = a - (double)m * (double)lt, bm = b - (double)m * (double)lt;
+    const double sh = ((double)m * (double)lt + x0) - v_up * (double)(s + 1);
+    for (long k = 0; k < nt; ++k) {
+      if (!(xt[k] >= am && xt[k] < bm)) continue;
+      if (out >= cap) return -1;
+      const double pos = xt[k] + sh;
+      double cx = floor(pos);
+      double off = (double)(float)(pos - cx);
+      if (off == 1.0) {
+        cx += 1.0;
+        off = 0.0;
+      }
+      xo[out] = cx + off;
+      xo[cap + out] = xt[nt + k];
+      xo[2 * cap + out] = xt[2 * nt + k];
+      for (int d = 0; d < 3; ++d) uo[d * cap + out] = ut[d * nt + k];
+      ++out;
+    }
+  }
+  return out;
 }
 
 /* One time step in the order of Table 1 (halo updates are implicit in the
@@ -342,11 +446,13 @@ void orc_step(const orc_grid* g, double* F, double** x, double** u, const long* 
   const long P = ncell(g);
   long o = 0;
   orc_push_half_b(g, F);                               /* push_half_b1 */
+  if (g_wall > 0) orc_wall_fields(g, F, g_wall, g_izero);
   for (int s = 0; s < ns; ++s) {                       /* interp_em, push */
     orc_push_particles(g, F, x[s], u[s], n[s], q[s] / m[s], work + o, work + o + 3 * n[s]);
     o += 6 * n[s];
   }
   orc_push_half_b(g, F);                               /* push_half_b2 */
+  if (g_wall > 0) orc_wall_fields(g, F, g_wall, g_izero);
   orc_push_e(g, F);                                    /* push_e */
   memset(F + JX * P, 0, sizeof(double) * 3 * P);       /* comp_curr */
   o = 0;
@@ -356,6 +462,7 @@ void orc_step(const orc_grid* g, double* F, double** x, double** u, const long* 
   }
   orc_filter_binomial(g, F, passes);                   /* Binomial2 on J */
   orc_add_cur(g, F);                                   /* add_cur */
+  if (g_wall > 0) orc_wall_fields(g, F, g_wall, g_izero);
 }
 
 /* Charge on the nodes with the first-order shape that the ZigZag weights

@@ -15,11 +15,13 @@
  *   Ex (i+1/2, j, k)   Ey (i, j+1/2, k)   Ez (i, j, k+1/2)
  *   Bx (i, j+1/2, k+1/2)   By (i+1/2, j, k+1/2)   Bz (i+1/2, j+1/2, k)
  *   J shares the points of E; charge density lives on the nodes (i, j, k).
- * All boundaries are periodic.  In D < 3 the missing dimensions are not
+ * In D < 3 the missing dimensions are not
  * gridded: nothing varies along them and they have extent 1.
  *
  * Particles: double x[3][n] (absolute positions, only the first D rows are
  * used, each in [0, n_d)), double u[3][n] (four-velocity in units of c).
+ * All boundaries are periodic unless the shock boundaries are set (a wall
+ * and an injector along x, orc_set_wall / orc_inject).
  */
 #ifndef PIC_ORACLE_H
 #define PIC_ORACLE_H
@@ -75,6 +77,22 @@ void orc_push_particles(const orc_grid* g, const double* F, double* x, double* u
 /* comp_curr of Table 1 for one species: ZigZag from x_old to x_old + dx. */
 void orc_deposit(const orc_grid* g, double* F, const double* x_old, const double* dx, long n,
                  double q);
+
+/* Shock boundaries (Sect. 4.2).  orc_set_wall(w, i_zero) with w >= 1 puts a
+ * conducting wall on the node plane x = w for orc_push_particles, orc_deposit
+ * and orc_step (w = 0: none): particles that cross it are reflected
+ * specularly and their current follows the reflected path; after each field
+ * update orc_step applies orc_wall_fields. */
+void orc_set_wall(long w, long i_zero);
+/* Mirror-image field boundary of a perfect conductor at the node x = w, and
+ * zero E and B at i >= i_zero. */
+void orc_wall_fields(const orc_grid* g, double* F, long w, long i_zero);
+/* Receding injector: the particles of an upstream template (xt[3][nt] in
+ * [0, lt) x ny x nz sorted by x, ut[3][nt]) that cross the injector
+ * X(s) = min(x0 + v_inj s, x_max) during step s, the template moving at -v_up;
+ * written to xo[3][cap], uo[3][cap]; returns the count or -1 (cap too small). */
+long orc_inject(const double* xt, const double* ut, long nt, long lt, double x0, double x_max,
+                double v_inj, double v_up, long s, double* xo, double* uo, long cap);
 
 /* One full time step in the order of Table 1 for `ns` species:
  * B half, interp_em + push (all species), B half, push_e, clear J and

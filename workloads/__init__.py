@@ -16,6 +16,8 @@ from .plasma import (  # noqa: F401
     weibel_1d,
     turbulence_2d,
     shock_3d,
+    shock_tube,
+    injected_count,
     weibel_box,
     weibel_ensemble,
     CONFIGS,

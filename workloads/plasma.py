@@ -242,6 +242,69 @@ def shock_3d(nx: int = 1024, ny: int = 128, nz: int = 128, ppc: int = 8,
                                     filter_passes=4))
 
 
+def _relinearise(cell: np.ndarray, src: tuple, dst: tuple, shift_x: int) -> np.ndarray:
+    """Cell indices of a (sx, sy, sz) block moved into a (nx, ny, nz) box at
+    x offset shift_x."""
+    c = cell.astype(np.int64)
+    i, j, k = c % src[0], (c // src[0]) % src[1], c // (src[0] * src[1])
+    return ((i + shift_x) + dst[0] * (j + dst[1] * k)).astype(np.int32)
+
+
+def shock_tube(dim: int = 3, nx: int = 1024, ny: int = 128, nz: int = 128, ppc: int = 8,
+               gamma_flow: float = 10.0, theta: float = 1e-4, r_p: float = 10.0,
+               c: float = 0.45, wall: int = 2, x_inj: int = 512, x_max: float = 0.0,
+               lt: int = 64, filter_passes: int = 4, seed: int = 1238) -> Plasma:
+    """Shock set-up of Sect. 4.2: cold pair plasma streaming toward -x with
+    Lorentz factor gamma_flow between a conducting wall at the node x = wall
+    and a receding injector that starts at x = x_inj and moves at the speed of
+    light (c cells per step) up to x_max (default nx - 3).  The injector lets
+    in an upstream template: a block of lt cells (full y and z) of the same
+    plasma, drawn independently and sorted by x (pairs stay co-located),
+    advected at the bulk speed v_up = c beta.  Charge from Appendix A with
+    <gamma> = gamma_flow.  meta["shock"] holds the boundary parameters and the
+    template species (cells are indices of the lt x ny x nz block)."""
+    if dim == 1:
+        ny = nz = 1
+    elif dim == 2:
+        nz = 1
+    x_max = float(x_max) if x_max > 0 else float(nx - 3)
+    assert 1 <= wall < x_inj <= x_max <= nx - 3 and 2 * wall < nx
+    q_abs = charge_from_skin_depth(c, r_p, ppc, gamma_flow)
+    beta = math.sqrt(1.0 - 1.0 / gamma_flow**2)
+    drift = np.full(ppc, -beta)
+    fill = uniform_plasma(dim, x_inj - wall, ny, nz, c, ppc, q_abs, theta, seed,
+                          drift_axis=0, drift_beta_per_slot=drift)
+    for s in fill.species:
+        s.cell = _relinearise(s.cell, (x_inj - wall, ny, nz), (nx, ny, nz), wall)
+    tmpl = uniform_plasma(dim, lt, ny, nz, c, ppc, q_abs, theta, seed + 7919,
+                          drift_axis=0, drift_beta_per_slot=drift)
+    xt = (tmpl.species[0].cell.astype(np.int64) % lt).astype(np.float64) + \
+        tmpl.species[0].off[0].astype(np.float64)
+    order = np.argsort(xt, kind="stable")
+    for s in tmpl.species:
+        s.cell = np.ascontiguousarray(s.cell[order])
+        s.off = np.ascontiguousarray(s.off[:, order])
+        s.u = np.ascontiguousarray(s.u[:, order])
+    fields = np.zeros((9, nz, ny, nx), dtype=np.float32)
+    shock = dict(wall=int(wall), x_inj=float(x_inj), x_max=x_max, v_inj=float(c),
+                 v_up=float(c * beta), lt=int(lt), templates=tmpl.species)
+    return Plasma(dim=dim, nx=nx, ny=ny, nz=nz, c=c, species=fill.species, fields=fields,
+                  meta=dict(workload=f"shock_{dim}d3v", gamma_flow=gamma_flow, theta=theta,
+                            r_p=r_p, ppc=ppc, q_abs=q_abs, filter_passes=filter_passes,
+                            shock=shock))
+
+
+def injected_count(pl: Plasma, steps: int) -> int:
+    """Upper bound on the particles per species that the injector of a
+    shock_tube lets in over `steps` steps: the template density times the
+    distance the injector front moves in template coordinates, plus one
+    template block of slack for the partial blocks at both ends."""
+    sh = pl.meta["shock"]
+    nt = sh["templates"][0].n
+    front = min(sh["x_inj"] + sh["v_inj"] * steps, sh["x_max"]) - sh["x_inj"] + sh["v_up"] * steps
+    return int(math.ceil(front / sh["lt"] * nt)) + nt
+
+
 def weibel_box(dim: int, n: int, ppc: int, gamma_b: float, theta: float, r_p: float = 10.0,
                c: float = 0.45, seed: int = 0) -> Plasma:
     """One Weibel box: 1D (n cells, beams along +-y as in weibel_1d) or 2D
