@@ -44,6 +44,13 @@ def _shock(n):
     return workloads.shock_3d(nx=n, ny=n // 8, nz=n // 8, seed=1236)
 
 
+def _shock_tube(n):
+    import workloads
+    return workloads.shock_tube(dim=3, nx=n, ny=n // 8, nz=n // 8, ppc=8, gamma_flow=10.0,
+                                theta=1e-4, r_p=10.0, wall=1, x_inj=n // 2,
+                                lt=max(8, min(64, n // 16)), filter_passes=4, seed=1238)
+
+
 # The set-ups of Sects. 4.1-4.3 at their benchmark sizes; the turbulence box is
 # the one the headline metric is quoted on, the others are reported on request.
 WORKLOADS = {
@@ -56,6 +63,14 @@ WORKLOADS = {
     "shock_3d3v_periodic": dict(make=_shock, dim=3, grid=1024, sample_grid=64, filter_passes=4,
                                 desc=dict(ppc_per_species=8, species=2, theta=1e-4,
                                           gamma_flow=10.0, r_p=10.0)),
+    # the shock set-up with its boundaries: conducting wall on the node x = 1
+    # (one guard cell for the mirror image), receding injector moving at c
+    # from x = nx/2 (the box starts half full), upstream template of 64 cells
+    "shock_3d3v": dict(make=_shock_tube, dim=3, grid=1024, sample_grid=64, filter_passes=4,
+                       shock=True,
+                       desc=dict(ppc_per_species=8, species=2, theta=1e-4, gamma_flow=10.0,
+                                 r_p=10.0, wall=1, injector_start="nx/2",
+                                 injector_speed="c")),
 }
 
 
@@ -177,19 +192,47 @@ def cpu_baseline(name="turbulence_2d3v", steps=0, sample_grid=None, target_s=12.
     n = sample_grid or w["sample_grid"]
     pl = w["make"](n)
     g, F, sp = oracle.from_plasma(pl)
+    run = _oracle_runner(w, pl, g, F, sp)
     t0 = time.perf_counter()
-    oracle.step(g, F, sp, passes=w["filter_passes"])
+    run(1)
     one = time.perf_counter() - t0
     k = steps if steps > 0 else max(1, int(target_s / max(one, 1e-6)))
     t0 = time.perf_counter()
-    oracle.step(g, F, sp, passes=w["filter_passes"], nsteps=k)
+    done = run(k)
     dt = time.perf_counter() - t0
     box = "x".join(str(v) for v in [pl.nx, pl.ny, pl.nz][: pl.dim])
-    return {"value": pl.nparticles * k / dt, "unit": "particle-steps/s", "cores": 1,
+    return {"value": done / dt, "unit": "particle-steps/s", "cores": 1,
             "kind": "oracle",
-            "sample": f"{name} on a {box} box ({pl.nparticles} particles, same plasma per cell), "
-                      f"{k} steps, FP64, 1 host thread",
+            "sample": f"{name} on a {box} box ({pl.nparticles} particles at the start, same "
+                      f"plasma per cell), {k} steps, FP64, 1 host thread",
             "seconds": dt, "steps": k, "particles": pl.nparticles}
+
+
+def _oracle_runner(w, pl, g, F, sp):
+    """run(k): k oracle steps of the workload (with the wall and injector of a
+    shock set-up); returns the particle-steps done."""
+    import oracle
+
+    state = {"s": 0}
+    if not w.get("shock"):
+        def run(k):
+            oracle.step(g, F, sp, passes=w["filter_passes"], nsteps=k)
+            return sum(x.n for x in sp) * k
+        return run
+    wall, i_zero, inj = oracle.shock_from_plasma(pl)
+
+    def run(k):
+        oracle.set_wall(wall, i_zero)
+        done = 0
+        try:
+            for _ in range(k):
+                done += sum(x.n for x in sp)
+                oracle.step_shock(g, F, sp, inj, state["s"], passes=w["filter_passes"])
+                state["s"] += 1
+        finally:
+            oracle.set_wall(0, 0)
+        return done
+    return run
 
 
 def run_reference(args):
@@ -216,11 +259,12 @@ def run_reference(args):
         parts = max(1, parts // 2 ** w["dim"])
     pl = w["make"](n)
     g, F, sp = oracle.from_plasma(pl)
-    oracle.step(g, F, sp, passes=w["filter_passes"], nsteps=args.warmup)
+    run = _oracle_runner(w, pl, g, F, sp)
+    run(args.warmup)
     t0 = time.perf_counter()
-    oracle.step(g, F, sp, passes=w["filter_passes"], nsteps=args.steps)
+    done = run(args.steps)
     dt = time.perf_counter() - t0
-    value = pl.nparticles * args.steps / dt
+    value = done / dt
     box = "x".join(str(v) for v in [pl.nx, pl.ny, pl.nz][: pl.dim])
     sample = (f"{args.workload} on a {box} box ({pl.nparticles} particles, same plasma per cell) "
               f"per step, FP64, 1 host thread")
@@ -237,12 +281,13 @@ def run_reference(args):
     return 0
 
 
-def push_bytes_per_launch(pl) -> float:
+def push_bytes_per_launch(pl, nparticles=None) -> float:
     """Algorithmic DRAM bytes of one fused particle launch: every particle's SoA
     record (int32 cell, D float offsets, 3 float u) read once and written once,
     the six E and B planes read once and the three J planes written once."""
     rec = 4 + 4 * pl.dim + 12
-    return float(pl.nparticles * 2 * rec + pl.ncells * (6 + 3) * 4)
+    n = pl.nparticles if nparticles is None else nparticles
+    return float(n * 2 * rec + pl.ncells * (6 + 3) * 4)
 
 
 def run_ours(args):
@@ -263,6 +308,7 @@ def run_ours(args):
     # every rank steps its own replica of the box; --grid changes its size for profiling runs
     w = WORKLOADS[args.workload]
     pl = w["make"](args.grid or w["grid"])
+    shock = bool(w.get("shock"))
     tuning = dict(filter_passes=w["filter_passes"])
     if args.sort_every:
         tuning["sort_every"] = args.sort_every
@@ -270,9 +316,16 @@ def run_ours(args):
         tuning["tile"] = [int(v) for v in args.tile.split(",")] + [1] * (3 - len(args.tile.split(",")))
     if args.halo:
         tuning["halo"] = args.halo
-    sim = Simulation.from_plasma(pl, device=f"cuda:{local}", tuning=tuning)
+    cap = None
+    if shock:  # room for every particle the injector lets in during this run
+        total = args.warmup + args.steps + args.e2e_steps + 4
+        cap = [s.n + workloads.injected_count(pl, total) for s in pl.species]
+    sim = Simulation.from_plasma(pl, device=f"cuda:{local}", tuning=tuning, capacity=cap)
+    if shock:
+        sim.set_shock_from_plasma(pl)
     dev = torch.device(f"cuda:{local}")
-    if args.autotune:  # untimed: real steps under candidate tunings, keeps the fastest
+    autotuned = args.autotune and not shock  # its steps would advance the shock: defaults
+    if autotuned:  # untimed: real steps under candidate tunings, keeps the fastest
         sim.autotune(None, steps=20)
     tun = sim.tuning()
     for _ in range(args.warmup):
@@ -291,8 +344,10 @@ def run_ours(args):
     B.pic_timing(sim.ctx, True)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    done = 0  # particle-steps: the count at the start of each step (host state, no sync)
     t0.record(sim.stream)
     for _ in range(args.steps):
+        done += sum(sim.counts())
         sim.step(1)
     t1.record(sim.stream)
     torch.cuda.synchronize(dev)
@@ -308,32 +363,45 @@ def run_ours(args):
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_max = float(t.item())
-    value = world * pl.nparticles * args.steps / (ms_max * 1e-3)
+    value = world * done / (ms_max * 1e-3)
+    avg_n = done / max(args.steps, 1)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     if args.e2e_steps > 0:
         F0, sp0 = sim.download()
         hs, keep = [], []
-        for s in sp0:
-            arrs = [torch.from_numpy(s[k]).pin_memory() for k in ("cell", "off", "u")]
+        for s, d in zip(sp0, sim.species):  # host rows as long as the device rows (cap)
+            arrs = []
+            for k, rows in (("cell", 0), ("off", pl.dim), ("u", 3)):
+                shape = (d["cap"],) if rows == 0 else (rows, d["cap"])
+                a = torch.zeros(shape, dtype=torch.int32 if rows == 0 else torch.float32).pin_memory()
+                a[..., : s[k].shape[-1]] = torch.from_numpy(s[k])
+                arrs.append(a)
             keep.append(arrs)
             hs.append(B.pic_host_species(*[a.data_ptr() for a in arrs]))
         hf = torch.from_numpy(F0).pin_memory()
-        h2d = sum(a.numel() * a.element_size() for arrs in keep for a in arrs) + hf.numel() * 4
+        rec = 4 + 4 * pl.dim + 12
         B.pic_step_host(sim.ctx, hs, hf.data_ptr(), 1)  # warm-up
         if dist is not None:
             dist.barrier()
+        e_done, h2d, d2h = 0, 0, 0
         te = time.perf_counter()
         for _ in range(args.e2e_steps):
+            n_in = sum(sim.counts())
             B.pic_step_host(sim.ctx, hs, hf.data_ptr(), 1)
+            n_out = sum(sim.counts())
+            e_done += n_in
+            h2d += n_in * rec + hf.numel() * 4
+            d2h += n_out * rec + hf.numel() * 4
         e_s = time.perf_counter() - te
         if dist is not None:
             t = torch.tensor([e_s], device=dev, dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e_s = float(t.item())
-        e2e = {"value": world * pl.nparticles * args.e2e_steps / e_s, "unit": "particle-steps/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d),
+        e2e = {"value": world * e_done / e_s, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": int(h2d // args.e2e_steps),
+               "d2h_bytes_per_step": int(d2h // args.e2e_steps),
                "steps": args.e2e_steps,
                "note": "pic_step_host: pinned host particles + fields copied in, one step, copied back"}
 
@@ -346,19 +414,24 @@ def run_ours(args):
     push_ms, push_n = kt["push"]
     avg_push_s = push_ms * 1e-3 / max(push_n, 1)
     peak, peak_kind = hbm_peak()
-    alg = push_bytes_per_launch(pl)
+    alg = push_bytes_per_launch(pl, avg_n)
     achieved = alg / avg_push_s / 1e9
     traffic = profiled_traffic() if args.workload == "turbulence_2d3v" and pl.nx == 1024 else None
     nsorts = -(-args.steps // tun["sort_every"])  # at most one sort per cadence in the loop
     launches = args.steps * (4 + tun["filter_passes"] * pl.dim) + nsorts * 3 * sim.nspecies
+    if shock:  # per step: 3 wall-field passes, the wall kernel, the injection, and the tail
+        # kernel on every step that does not start with a sort
+        launches += args.steps * 5 + (args.steps - nsorts)
     wl = workload_config(args.workload, pl)
     line = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": dict(wl, particles=pl.nparticles, sort_every=tun["sort_every"],
-                       tile=tun["tile"][: pl.dim], halo=tun["halo"], autotuned=bool(args.autotune),
+        "config": dict(wl, particles=pl.nparticles if not shock else
+                       {"start": pl.nparticles, "end": sum(sim.counts()), "mean_timed": avg_n},
+                       sort_every=tun["sort_every"],
+                       tile=tun["tile"][: pl.dim], halo=tun["halo"], autotuned=bool(autotuned),
                        parallelism="replicas" if world > 1 else "single-gpu",
                        l2=("inputs larger than L2 (particle SoA %.2f GB), no flush" if
                            pl.nparticles * (16 + 4 * pl.dim) > 2 * 129e6 else

@@ -3,7 +3,9 @@
  * (Nattila, arXiv:1906.06306, Sect. 2.3, Table 1, Appendices B-D).
  *
  * Units and lattice (Sect. 2.3, Appendix A): dx = dt = 1; the Courant number c
- * is the only constant of the field equations.  All boundaries are periodic.
+ * is the only constant of the field equations.  All boundaries are periodic,
+ * unless pic_set_shock adds the conducting wall and receding injector of the
+ * paper's shock set-up along x (Sect. 4.2).
  *
  * Fields: ONE caller-owned device buffer of 9 float planes, each
  * nz*ny*nx floats, x fastest: Ex Ey Ez Bx By Bz Jx Jy Jz.  Element [i,j,k] of
@@ -14,10 +16,11 @@
  * Time levels: on entry to a step E is at t^n and B at t^(n-1/2); particles
  * hold x^n and u^(n-1/2).
  *
- * Particles, per species, caller-owned device buffers (structure of arrays):
- *   cell  int32[n]       linear cell index i + nx*(j + ny*k)
- *   off   float[dim][n]  in-cell offset of each gridded coordinate, in [0,1)
- *   u     float[3][n]    spatial four-velocity in units of c
+ * Particles, per species, caller-owned device buffers (structure of arrays,
+ * rows of cap elements, of which the first n are particles):
+ *   cell  int32[cap]       linear cell index i + nx*(j + ny*k)
+ *   off   float[dim][cap]  in-cell offset of each gridded coordinate, in [0,1)
+ *   u     float[3][cap]    spatial four-velocity in units of c
  * The library keeps particles sorted by spatial tile and may reorder them
  * (pic_sort, pic_step); after every call returns (on the stream) the caller's
  * buffers hold the current particles.
@@ -64,9 +67,10 @@ typedef struct {
 
 /* One species.  q is the charge of a macro-particle (signed, code units; the
  * ZigZag current of Appendix D is proportional to it) and m its mass, so that
- * q/m is the s-hat of the Boris scheme (Appendix C).  Pointers are device
- * pointers with the layout above; the caller keeps them alive until
- * pic_destroy. */
+ * q/m is the s-hat of the Boris scheme (Appendix C).  n is the particle count
+ * and cap (>= n; 0 means n) the row length of the arrays: the room the
+ * injector of pic_set_shock may fill.  Pointers are device pointers with the
+ * layout above; the caller keeps them alive until pic_destroy. */
 typedef struct {
   float q;
   float m;
@@ -74,10 +78,12 @@ typedef struct {
   int32_t* cell;
   float* off;
   float* u;
+  int64_t cap;
 } pic_species;
 
 /* Host-side particles of one species for pic_step_host (same layout as
- * pic_species, host pointers; pinned memory gives full copy bandwidth). */
+ * pic_species, rows of cap elements, host pointers; pinned memory gives full
+ * copy bandwidth). */
 typedef struct {
   int32_t* cell;
   float* off;
@@ -109,7 +115,8 @@ typedef struct {
 #define PIC_KERNEL_EUPD 2   /* E update with -J */
 #define PIC_KERNEL_FILTER 3 /* one Binomial2 pass */
 #define PIC_KERNEL_SORT 4   /* tile sort: count + scan + scatter + copy back */
-#define PIC_KERNEL_KINDS 5
+#define PIC_KERNEL_BOUNDARY 5 /* wall fields and injection (pic_set_shock) */
+#define PIC_KERNEL_KINDS 6
 
 /* Create a context for `grid`, `nspecies` (1..PIC_MAX_SPECIES) species, Courant
  * number c (0 < c < 1 for the explicit scheme, Sect. 2.3) and time step dt,
@@ -153,7 +160,8 @@ pic_status pic_sort(pic_ctx* ctx);
  * x^n (Sect. 2.3.2), relativistic Boris push u^(n-1/2) -> u^(n+1/2)
  * (Appendix C), position update x^(n+1) = x^n + c u / gamma (Eq. fdX) with
  * periodic wrap.  The pre-move positions are kept in library scratch for
- * pic_deposit. */
+ * pic_deposit.  PIC_ERR_STATE on a context with shock boundaries (the split
+ * path does not model the wall; pic_step does). */
 pic_status pic_gather_push(pic_ctx* ctx);
 
 /* comp_curr of Table 1: adds the ZigZag current (Appendix D) of every particle's
@@ -174,8 +182,58 @@ pic_status pic_field_update(pic_ctx* ctx, int which);
  * Binomial2 passes on J, E update with -J.  Every sort_every steps (counted
  * over the life of the context) the particles are re-sorted by tile before
  * the push.  On return the J planes hold the filtered current of the last
- * step. */
+ * step.  With shock boundaries (pic_set_shock) the wall's field boundary
+ * follows each field update and the injector adds particles at the end of
+ * each step; PIC_ERR_ARG (before any work of that step) if a species would
+ * exceed its cap. */
 pic_status pic_step(pic_ctx* ctx, int nsteps);
+
+/* Shock boundaries along x (Sect. 4.2; the paper states them in words, the
+ * readings below make them precise).
+ *
+ * Conducting wall on the node plane x = wall (1 <= wall, 2 wall < i_zero): a
+ * particle whose move ends below x = wall is reflected specularly
+ * (x -> 2 wall - x, u_x -> -u_x) and its current is deposited along the true
+ * path, a straight ZigZag segment to the wall plane and the mirrored
+ * remainder, so charge is conserved on every node.  After each field update
+ * the tangential E on the wall plane (Ey, Ez at i = wall) is set to zero and
+ * the cells behind it (i < wall) to the mirror image of the plasma side that a
+ * perfect conductor implies (tangential E and normal B odd, normal E and
+ * tangential B even about x = wall: integer-x components at i take the value
+ * at 2 wall - i, half-integer ones, stored at i for x = i + 1/2, the value at
+ * 2 wall - 1 - i).  The Gauss residual of pic_energies then holds on the
+ * nodes i > wall; the wall node carries the conductor's surface charge.
+ *
+ * Receding injector: it starts at x0 and moves at v_inj cells per step (the
+ * paper: the speed of light, c) up to x_max, X(s) = min(x0 + v_inj s, x_max)
+ * with s the steps since this call.  An upstream template per species (host
+ * arrays in the layout of pic_host_species with rows of nt[s] elements; cells
+ * index an lt x ny x nz block, sorted by x = i + off_x; q and m are those of
+ * the species) is repeated along x and moves at -v_up cells per step.  In
+ * template coordinates the injector is at A(s) = (X(s) - x0) + v_up s; during
+ * step s every particle of copy m with A(s) - m lt <= x_t < A(s+1) - m lt is
+ * appended to its species at x = x_t + ((m lt + x0) - v_up (s + 1)) (double
+ * precision; the offset is rounded to float and an offset that rounds to 1
+ * moves to the next cell), in the order m, then template index.  E and B at
+ * i >= i_zero = floor(x_max) + 2 are set to zero after each field update.
+ * The library copies the templates; the species' device arrays must have
+ * room (cap) for what is injected.  Requires x0 > wall, x0 <= x_max <= nx - 3,
+ * v_inj >= 0, v_up >= 0, v_inj + v_up < lt, and every particle at x >= wall
+ * (particles behind the wall are flagged as invalid data by pic_check).
+ * Contexts with shock boundaries cannot join a batch, and pic_gather_push /
+ * pic_deposit refuse them.  PIC_ERR_ARG on invalid arguments. */
+typedef struct {
+  int wall;
+  int lt;
+  double x0, x_max, v_inj, v_up;
+  int64_t nt[PIC_MAX_SPECIES];
+  pic_host_species tmpl[PIC_MAX_SPECIES];
+} pic_shock;
+pic_status pic_set_shock(pic_ctx* ctx, const pic_shock* shock);
+
+/* Current particle count of each species (grows with injection): writes
+ * nout >= nspecies values.  No synchronisation: the counts are host state. */
+pic_status pic_particle_counts(pic_ctx* ctx, int64_t* n, int nout);
 
 /* Diagnostics (synchronising).  out[0] = 0.5 sum E^2, out[1] = 0.5 sum B^2,
  * out[2+s] = sum m c^2 (gamma - 1) of species s, out[2+ns] = max |div E -
@@ -193,7 +251,9 @@ pic_status pic_check(pic_ctx* ctx);
 /* End-to-end step from host memory: copies every species' particles from
  * `hs` and the 9 field planes from `host_fields` into the context's device
  * buffers, runs pic_step(nsteps), copies particles and fields back into the
- * same host buffers and synchronises. */
+ * same host buffers and synchronises.  Host rows have the species' cap
+ * elements; the counts before the steps are copied in and those after them
+ * (pic_particle_counts) copied out. */
 pic_status pic_step_host(pic_ctx* ctx, const pic_host_species* hs, float* host_fields,
                          int nsteps);
 
@@ -262,8 +322,9 @@ pic_status pic_filter_current_static(const pic_grid* grid, float* J, int passes,
  * is launched nsteps / L times on `stream`; the remaining steps run through
  * pic_step.  The graph is rebuilt when a context's tuning or its position in
  * its sort cycle changed since the capture.  Results are those of pic_step
- * on each context.  Contexts must not be destroyed before the batch.  Errors:
- * PIC_ERR_ARG (message in pic_last_error(NULL)), PIC_ERR_CUDA. */
+ * on each context.  Contexts must not be destroyed before the batch, and a
+ * context with shock boundaries cannot join one.  Errors: PIC_ERR_ARG
+ * (message in pic_last_error(NULL)), PIC_ERR_CUDA. */
 typedef struct pic_batch pic_batch;
 pic_status pic_batch_create(pic_batch** out, pic_ctx* const* ctxs, int nctx);
 pic_status pic_batch_step(pic_batch* batch, int nsteps, void* stream);

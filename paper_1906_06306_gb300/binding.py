@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_CUDA", 3: "PIC_ERR_OO
                 4: "PIC_ERR_TIMEOUT", 5: "PIC_ERR_STATE"}
 PIC_MAX_SPECIES = 4
 PIC_FIELD_B_HALF, PIC_FIELD_E = 0, 1
-KERNEL_KINDS = ["push", "b_half", "e_update", "filter", "sort"]
+KERNEL_KINDS = ["push", "b_half", "e_update", "filter", "sort", "boundary"]
 
 
 class pic_grid(ctypes.Structure):
@@ -27,11 +27,17 @@ class pic_grid(ctypes.Structure):
 
 class pic_species(ctypes.Structure):
     _fields_ = [("q", c_float), ("m", c_float), ("n", c_int64), ("cell", c_void_p),
-                ("off", c_void_p), ("u", c_void_p)]
+                ("off", c_void_p), ("u", c_void_p), ("cap", c_int64)]
 
 
 class pic_host_species(ctypes.Structure):
     _fields_ = [("cell", c_void_p), ("off", c_void_p), ("u", c_void_p)]
+
+
+class pic_shock(ctypes.Structure):
+    _fields_ = [("wall", c_int), ("lt", c_int), ("x0", c_double), ("x_max", c_double),
+                ("v_inj", c_double), ("v_up", c_double), ("nt", c_int64 * PIC_MAX_SPECIES),
+                ("tmpl", pic_host_species * PIC_MAX_SPECIES)]
 
 
 class pic_tuning(ctypes.Structure):
@@ -47,6 +53,8 @@ SIGNATURES = {
     "pic_set_tuning": (c_int, [_P, ctypes.POINTER(pic_tuning)]),
     "pic_set_pusher": (c_int, [_P, c_int]),
     "pic_set_field_solver": (c_int, [_P, c_int]),
+    "pic_set_shock": (c_int, [_P, ctypes.POINTER(pic_shock)]),
+    "pic_particle_counts": (c_int, [_P, ctypes.POINTER(c_int64), c_int]),
     "pic_sort": (c_int, [_P]),
     "pic_gather_push": (c_int, [_P]),
     "pic_deposit": (c_int, [_P]),
@@ -130,6 +138,18 @@ def pic_set_field_solver(ctx, order: int) -> None:
 
 def pic_set_pusher(ctx, pusher: int) -> None:
     _check(_lib.pic_set_pusher(ctx, pusher), ctx)
+
+
+def pic_set_shock(ctx, shock: pic_shock) -> None:
+    """Conducting wall and receding injector along x (Sect. 4.2); the template
+    host arrays referenced by `shock` are copied by the library."""
+    _check(_lib.pic_set_shock(ctx, ctypes.byref(shock)), ctx)
+
+
+def pic_particle_counts(ctx, nspecies: int):
+    out = (c_int64 * nspecies)()
+    _check(_lib.pic_particle_counts(ctx, out, nspecies), ctx)
+    return [int(v) for v in out]
 
 
 def pic_sort(ctx) -> None:

@@ -19,8 +19,10 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpic.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code is compiled without floating-point contraction: the injector's
+# double-precision position arithmetic must round the same way on every host
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              f"-I{INCLUDE}", f"-I{CSRC}"]
+              "-Xcompiler", "-ffp-contract=off", f"-I{INCLUDE}", f"-I{CSRC}"]
 
 
 def _nvcc() -> str:

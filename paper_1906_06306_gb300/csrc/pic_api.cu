@@ -55,6 +55,18 @@ struct pic_ctx {
   int* d_status = nullptr;
   unsigned long long* d_strays = nullptr;  // particles that took the global path
   int pusher = 0;                          // PIC_PUSHER_*
+  long long cap[PIC_MAX_SPECIES] = {};     // row length of each species' arrays
+  long long sorted_n[PIC_MAX_SPECIES] = {};  // count at the last sort (start of the tail)
+  // shock boundaries (pic_set_shock)
+  bool shock = false;
+  int wall = 0, i_zero = 0, lt = 0;
+  double x0 = 0.0, x_max = 0.0, v_inj = 0.0, v_up = 0.0;
+  long long shock_steps = 0;                 // steps since pic_set_shock
+  long long tn[PIC_MAX_SPECIES] = {};        // template particles per species
+  std::vector<double> txs[PIC_MAX_SPECIES];  // template x = i + off_x (host, sorted)
+  void* d_tmpl = nullptr;                    // template records of every species
+  int* d_wlist = nullptr;                    // wall crossers, room for cap[s] per species
+  int* d_wcount = nullptr;                   // entries per species
   long long steps = 0;
   bool timing = false;
   std::vector<TimedLaunch> pending;
@@ -111,6 +123,9 @@ void free_all(pic_ctx* ctx) {
   dfree(ctx->d_acc);
   dfree(ctx->d_status);
   dfree(ctx->d_strays);
+  dfree(ctx->d_tmpl);
+  dfree(ctx->d_wlist);
+  dfree(ctx->d_wcount);
   for (auto& t : ctx->pending) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
@@ -200,8 +215,32 @@ cudaError_t timed(pic_ctx* ctx, int kind, Fn fn) {
 // offset (in 4-byte words) of species s in the sorted buffer
 long long sortbuf_offset(const pic_ctx* ctx, int s) {
   long long o = 0;
-  for (int r = 0; r < s; ++r) o += ctx->sp[r].n * (1 + ctx->grid.dim + 3);
+  for (int r = 0; r < s; ++r) o += ctx->cap[r] * (1 + ctx->grid.dim + 3);
   return o;
+}
+
+long long total_cap(const pic_ctx* ctx) {
+  long long t = 0;
+  for (int s = 0; s < ctx->ns; ++s) t += ctx->cap[s];
+  return t;
+}
+
+// Copy `rows` rows of n elements of `elem` bytes between arrays whose rows
+// are ld elements long.
+cudaError_t copy_rows(void* dst, const void* src, size_t elem, long long n, long long ld, int rows,
+                      cudaMemcpyKind kind, cudaStream_t st) {
+  if (n == 0 || rows == 0) return cudaSuccess;
+  if (ld == n) return cudaMemcpyAsync(dst, src, elem * (size_t)n * rows, kind, st);
+  return cudaMemcpy2DAsync(dst, elem * (size_t)ld, src, elem * (size_t)ld, elem * (size_t)n,
+                           (size_t)rows, kind, st);
+}
+
+// Thread blocks for the particles appended since the last sort.
+int tail_blocks(const pic_ctx* ctx) {
+  long long mx = 0;
+  for (int s = 0; s < ctx->ns; ++s) mx = std::max(mx, ctx->sp[s].n - ctx->sorted_n[s]);
+  const long long b = (mx + kPushThreads - 1) / kPushThreads;
+  return (int)std::min<long long>(b, 8 * 152);
 }
 
 PushParams make_params(pic_ctx* ctx) {
@@ -231,6 +270,8 @@ PushParams make_params(pic_ctx* ctx) {
     S.q = ctx->sp[s].q;
     S.qm = ctx->sp[s].q / ctx->sp[s].m;
     S.n = ctx->sp[s].n;
+    S.ld = ctx->cap[s];
+    S.tail = ctx->sorted_n[s];
     S.cell = ctx->sp[s].cell;
     S.off = ctx->sp[s].off;
     S.u = ctx->sp[s].u;
@@ -240,14 +281,18 @@ PushParams make_params(pic_ctx* ctx) {
     if (ctx->sorted_pending) {
       int* c = (int*)ctx->d_sortbuf + sortbuf_offset(ctx, s);
       S.rcell = c;
-      S.roff = (const float*)(c + S.n);
-      S.ru = (const float*)(c + S.n) + (long long)ctx->grid.dim * S.n;
+      S.roff = (const float*)(c + S.ld);
+      S.ru = (const float*)(c + S.ld) + (long long)ctx->grid.dim * S.ld;
     }
     S.tstart = ctx->d_tstart[s];
     S.cell_old = ctx->d_cell_old ? ctx->d_cell_old + o : nullptr;
     S.off_old = ctx->d_off_old ? ctx->d_off_old + (long long)ctx->grid.dim * o : nullptr;
-    o += ctx->sp[s].n;
+    S.wlist = ctx->d_wlist ? ctx->d_wlist + o : nullptr;
+    S.wcount = ctx->d_wcount ? ctx->d_wcount + s : nullptr;
+    o += ctx->cap[s];
   }
+  P.wall = ctx->shock ? ctx->wall : 0;
+  P.tail_blocks = tail_blocks(ctx);
   return P;
 }
 
@@ -259,7 +304,7 @@ pic_status do_sort(pic_ctx* ctx, bool copy_back) {
   const int D = ctx->grid.dim;
   const cudaError_t e = timed(ctx, PIC_KERNEL_SORT, [&]() -> cudaError_t {
     for (int s = 0; s < ctx->ns; ++s) {
-      const long long n = ctx->sp[s].n;
+      const long long n = ctx->sp[s].n, ld = ctx->cap[s];
       cudaError_t r = cudaMemsetAsync(ctx->d_count, 0, sizeof(int) * ctx->tile.ntiles, ctx->st);
       if (r != cudaSuccess) return r;
       r = launch_tile_count(P, ctx->sp[s].cell, n, ctx->d_count, ctx->st);
@@ -268,26 +313,94 @@ pic_status do_sort(pic_ctx* ctx, bool copy_back) {
       if (r != cudaSuccess) return r;
       if (n == 0) continue;
       int* cell_out = (int*)ctx->d_sortbuf + sortbuf_offset(ctx, s);
-      float* off_out = (float*)(cell_out + n);
-      float* u_out = off_out + (long long)D * n;
-      r = launch_tile_scatter(P, ctx->sp[s].cell, ctx->sp[s].off, ctx->sp[s].u, n, ctx->d_cursor,
-                              cell_out, off_out, u_out, ctx->st);
+      float* off_out = (float*)(cell_out + ld);
+      float* u_out = off_out + (long long)D * ld;
+      r = launch_tile_scatter(P, ctx->sp[s].cell, ctx->sp[s].off, ctx->sp[s].u, n, ld,
+                              ctx->d_cursor, cell_out, off_out, u_out, ctx->st);
       if (r != cudaSuccess) return r;
       if (!copy_back) continue;
-      r = cudaMemcpyAsync(ctx->sp[s].cell, cell_out, sizeof(int) * n, cudaMemcpyDeviceToDevice, ctx->st);
+      const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+      r = copy_rows(ctx->sp[s].cell, cell_out, sizeof(int), n, ld, 1, k, ctx->st);
       if (r != cudaSuccess) return r;
-      r = cudaMemcpyAsync(ctx->sp[s].off, off_out, sizeof(float) * D * n, cudaMemcpyDeviceToDevice,
-                          ctx->st);
+      r = copy_rows(ctx->sp[s].off, off_out, sizeof(float), n, ld, D, k, ctx->st);
       if (r != cudaSuccess) return r;
-      r = cudaMemcpyAsync(ctx->sp[s].u, u_out, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, ctx->st);
+      r = copy_rows(ctx->sp[s].u, u_out, sizeof(float), n, ld, 3, k, ctx->st);
       if (r != cudaSuccess) return r;
     }
     return cudaSuccess;
   });
   if (e != cudaSuccess) return cuda_fail(ctx, "tile sort", e);
+  long long ntot = 0;
+  for (int s = 0; s < ctx->ns; ++s) {
+    ctx->sorted_n[s] = ctx->sp[s].n;
+    ntot += ctx->sp[s].n;
+  }
+  if (ntot != ctx->ntot) {  // injection changed the count: re-derive the splits per tile
+    TileDev td{};
+    int splits = 1;
+    if (derive_tiles(ctx->grid, ctx->tun, ntot, &td, &splits).empty()) ctx->splits = splits;
+    ctx->ntot = ntot;
+  }
   ctx->snapshot_valid = false;
   ctx->sorted_pending = !copy_back;
   return PIC_OK;
+}
+
+// Template coordinate of the receding injector after s steps:
+// A(s) = (X(s) - x0) + v_up s with X(s) = min(x0 + v_inj s, x_max).
+double inj_front(const pic_ctx* ctx, long long s) {
+  const double X = std::fmin(ctx->x0 + ctx->v_inj * (double)s, ctx->x_max);
+  return (X - ctx->x0) + ctx->v_up * (double)s;
+}
+
+// The injection of step s (the particles of template copy m with
+// A(s) - m lt <= x_t < A(s+1) - m lt), as runs of template indices per
+// species, appended after each species' current particles; add[s] receives
+// each species' count.  The template is sorted by x_t, so each (species, m)
+// is one contiguous run, found by binary search with the same comparisons.
+void plan_injection(const pic_ctx* ctx, long long s, InjectParams* P, long long* add) {
+  *P = InjectParams{};
+  P->g = ctx->g;
+  P->lt = ctx->lt;
+  const double a = inj_front(ctx, s), b = inj_front(ctx, s + 1);
+  const double lt = (double)ctx->lt;
+  long long total = 0;
+  for (int sp = 0; sp < ctx->ns; ++sp) {
+    const std::vector<double>& xs = ctx->txs[sp];
+    long long out = ctx->sp[sp].n;
+    for (long long m = (long long)std::floor(a / lt); m <= (long long)std::floor(b / lt); ++m) {
+      const double am = a - (double)m * lt, bm = b - (double)m * lt;
+      const long long k0 = std::lower_bound(xs.begin(), xs.end(), am) - xs.begin();
+      const long long k1 = std::lower_bound(xs.begin(), xs.end(), bm) - xs.begin();
+      if (k1 <= k0 || P->nruns >= kMaxInjectRuns) continue;
+      InjectRun& R = P->run[P->nruns];
+      R.s = sp;
+      R.k0 = k0;
+      R.k1 = k1;
+      R.out = out;
+      R.shift = ((double)m * lt + ctx->x0) - ctx->v_up * (double)(s + 1);
+      P->first[P->nruns] = total;
+      total += k1 - k0;
+      out += k1 - k0;
+      ++P->nruns;
+    }
+    add[sp] = out - ctx->sp[sp].n;
+  }
+  P->first[P->nruns] = total;
+  const int D = ctx->grid.dim;
+  long long o = 0;
+  for (int sp = 0; sp < ctx->ns; ++sp) {
+    const int* tc = (const int*)ctx->d_tmpl + o;
+    P->tcell[sp] = tc;
+    P->toff[sp] = (const float*)(tc + ctx->tn[sp]);
+    P->tu[sp] = (const float*)(tc + ctx->tn[sp]) + (long long)D * ctx->tn[sp];
+    P->tn[sp] = ctx->tn[sp];
+    P->cell[sp] = ctx->sp[sp].cell;
+    P->off[sp] = ctx->sp[sp].off;
+    P->u[sp] = ctx->sp[sp].u;
+    P->ld[sp] = ctx->cap[sp];
+    o += ctx->tn[sp] * (1 + D + 3);
+  }
 }
 
 pic_status do_filter(pic_ctx* ctx, int passes) {
@@ -343,6 +456,8 @@ pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* spec
     const pic_species& S = species[s];
     if (S.n < 0 || S.n > 0x7fffffffLL)
       return set_err(nullptr, PIC_ERR_ARG, "species n must be in [0, 2^31)");
+    if (S.cap != 0 && (S.cap < S.n || S.cap > 0x7fffffffLL))
+      return set_err(nullptr, PIC_ERR_ARG, "species cap must be 0 or in [n, 2^31)");
     if (S.n > 0 && (!S.cell || !S.off || !S.u))
       return set_err(nullptr, PIC_ERR_ARG, "species buffers are NULL");
     if (!(S.m > 0.f) || !std::isfinite(S.m) || !std::isfinite(S.q))
@@ -354,7 +469,13 @@ pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* spec
   pic_ctx* ctx = new pic_ctx();
   ctx->grid = *grid;
   ctx->ns = nspecies;
-  for (int s = 0; s < nspecies; ++s) ctx->sp[s] = species[s];
+  long long totcap = 0;
+  for (int s = 0; s < nspecies; ++s) {
+    ctx->sp[s] = species[s];
+    ctx->cap[s] = species[s].cap ? species[s].cap : species[s].n;
+    ctx->sp[s].cap = ctx->cap[s];
+    totcap += ctx->cap[s];
+  }
   ctx->c = c;
   ctx->F = fields;
   ctx->st = (cudaStream_t)stream;
@@ -391,7 +512,7 @@ pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* spec
              (e = cudaMemsetAsync(ctx->d_strays, 0, sizeof(unsigned long long), ctx->st)) !=
                  cudaSuccess) {
     s = cuda_fail(nullptr, "status word", e);
-  } else if ((e = dalloc((char**)&ctx->d_sortbuf, (size_t)ntot * (4 + 4 * grid->dim + 12))) !=
+  } else if ((e = dalloc((char**)&ctx->d_sortbuf, (size_t)totcap * (4 + 4 * grid->dim + 12))) !=
              cudaSuccess) {
     s = cuda_fail(nullptr, "sort buffer", e);
   } else if ((s = alloc_tiles(ctx)) != PIC_OK || (s = do_sort(ctx, true)) != PIC_OK) {
@@ -460,6 +581,92 @@ pic_status pic_set_pusher(pic_ctx* ctx, int pusher) {
   return PIC_OK;
 }
 
+pic_status pic_set_shock(pic_ctx* ctx, const pic_shock* sh) {
+  if (!ctx) return PIC_ERR_ARG;
+  if (!sh) return set_err(ctx, PIC_ERR_ARG, "shock is NULL");
+  const int nx = ctx->grid.nx, D = ctx->grid.dim;
+  const double vals[4] = {sh->x0, sh->x_max, sh->v_inj, sh->v_up};
+  for (double v : vals)
+    if (!std::isfinite(v)) return set_err(ctx, PIC_ERR_ARG, "shock parameters must be finite");
+  if (sh->wall < 1) return set_err(ctx, PIC_ERR_ARG, "wall must be >= 1");
+  if (sh->lt < 1) return set_err(ctx, PIC_ERR_ARG, "lt must be >= 1");
+  if (!(sh->x_max <= nx - 3)) return set_err(ctx, PIC_ERR_ARG, "x_max must be <= nx - 3");
+  if (!(sh->x0 <= sh->x_max)) return set_err(ctx, PIC_ERR_ARG, "x0 must be <= x_max");
+  if (!(sh->v_inj >= 0.0 && sh->v_up >= 0.0))
+    return set_err(ctx, PIC_ERR_ARG, "v_inj and v_up must be >= 0");
+  if (!(sh->v_inj + sh->v_up < sh->lt))
+    return set_err(ctx, PIC_ERR_ARG, "v_inj + v_up must be < lt");
+  if (!(sh->x0 - sh->v_up >= sh->wall + 1))
+    return set_err(ctx, PIC_ERR_ARG, "x0 - v_up must be >= wall + 1");
+  const int i_zero = (int)std::floor(sh->x_max) + 2;
+  if (2 * sh->wall >= i_zero) return set_err(ctx, PIC_ERR_ARG, "2 wall must be < floor(x_max) + 2");
+  const long long block = (long long)sh->lt * ctx->grid.ny * ctx->grid.nz;
+  long long words = 0;
+  std::vector<double> xs[PIC_MAX_SPECIES];
+  for (int s = 0; s < ctx->ns; ++s) {
+    const long long nt = sh->nt[s];
+    if (nt < 0 || nt > 0x7fffffffLL) return set_err(ctx, PIC_ERR_ARG, "template nt must be in [0, 2^31)");
+    const pic_host_species& T = sh->tmpl[s];
+    if (nt > 0 && (!T.cell || !T.off || !T.u))
+      return set_err(ctx, PIC_ERR_ARG, "template buffers are NULL");
+    xs[s].resize((size_t)nt);
+    for (long long k = 0; k < nt; ++k) {
+      const int c = T.cell[k];
+      if (c < 0 || c >= block) return set_err(ctx, PIC_ERR_ARG, "template cell outside lt x ny x nz");
+      for (int d = 0; d < D; ++d)
+        if (!(T.off[d * nt + k] >= 0.0f && T.off[d * nt + k] < 1.0f))
+          return set_err(ctx, PIC_ERR_ARG, "template offset outside [0,1)");
+      for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(T.u[a * nt + k]))
+          return set_err(ctx, PIC_ERR_ARG, "template four-velocity not finite");
+      xs[s][k] = (double)(c % sh->lt) + (double)T.off[k];
+      if (k > 0 && xs[s][k] < xs[s][k - 1])
+        return set_err(ctx, PIC_ERR_ARG, "template not sorted by x");
+    }
+    words += nt * (1 + D + 3);
+  }
+  // copy the templates (cell, off rows, u rows per species) to the device
+  PIC_CK(ctx, cudaStreamSynchronize(ctx->st));
+  dfree(ctx->d_tmpl);
+  PIC_CK(ctx, dalloc((char**)&ctx->d_tmpl, (size_t)words * 4));
+  if (!ctx->d_wlist) {
+    PIC_CK(ctx, dalloc(&ctx->d_wlist, (size_t)total_cap(ctx)));
+    PIC_CK(ctx, dalloc(&ctx->d_wcount, (size_t)PIC_MAX_SPECIES));
+  }
+  long long o = 0;
+  for (int s = 0; s < ctx->ns; ++s) {
+    const long long nt = sh->nt[s];
+    int* tc = (int*)ctx->d_tmpl + o;
+    if (nt > 0) {
+      PIC_CK(ctx, cudaMemcpy(tc, sh->tmpl[s].cell, 4 * nt, cudaMemcpyHostToDevice));
+      PIC_CK(ctx, cudaMemcpy(tc + nt, sh->tmpl[s].off, 4 * D * nt, cudaMemcpyHostToDevice));
+      PIC_CK(ctx, cudaMemcpy(tc + nt + D * nt, sh->tmpl[s].u, 12 * nt, cudaMemcpyHostToDevice));
+    }
+    ctx->tn[s] = nt;
+    ctx->txs[s].swap(xs[s]);
+    o += nt * (1 + D + 3);
+  }
+  ctx->shock = true;
+  ctx->wall = sh->wall;
+  ctx->i_zero = i_zero;
+  ctx->lt = sh->lt;
+  ctx->x0 = sh->x0;
+  ctx->x_max = sh->x_max;
+  ctx->v_inj = sh->v_inj;
+  ctx->v_up = sh->v_up;
+  ctx->shock_steps = 0;
+  // the fields entering the first step satisfy the wall's boundary
+  PIC_CK(ctx, launch_wall_fields(ctx->g, ctx->F, ctx->wall, ctx->i_zero, ctx->st));
+  return PIC_OK;
+}
+
+pic_status pic_particle_counts(pic_ctx* ctx, int64_t* n, int nout) {
+  if (!ctx || !n) return set_err(ctx, PIC_ERR_ARG, "NULL argument");
+  if (nout < ctx->ns) return set_err(ctx, PIC_ERR_ARG, "nout must be >= nspecies");
+  for (int s = 0; s < ctx->ns; ++s) n[s] = ctx->sp[s].n;
+  return PIC_OK;
+}
+
 pic_status pic_sort(pic_ctx* ctx) {
   if (!ctx) return PIC_ERR_ARG;
   return do_sort(ctx, true);
@@ -467,9 +674,11 @@ pic_status pic_sort(pic_ctx* ctx) {
 
 pic_status pic_gather_push(pic_ctx* ctx) {
   if (!ctx) return PIC_ERR_ARG;
+  if (ctx->shock)
+    return set_err(ctx, PIC_ERR_STATE, "the split gather/deposit path does not model the wall");
   if (!ctx->d_cell_old) {
-    PIC_CK(ctx, dalloc(&ctx->d_cell_old, (size_t)ctx->ntot));
-    PIC_CK(ctx, dalloc(&ctx->d_off_old, (size_t)ctx->ntot * ctx->grid.dim));
+    PIC_CK(ctx, dalloc(&ctx->d_cell_old, (size_t)total_cap(ctx)));
+    PIC_CK(ctx, dalloc(&ctx->d_off_old, (size_t)total_cap(ctx) * ctx->grid.dim));
   }
   const PushParams P = make_params(ctx);
   const cudaError_t e = timed(ctx, PIC_KERNEL_PUSH,
@@ -481,6 +690,8 @@ pic_status pic_gather_push(pic_ctx* ctx) {
 
 pic_status pic_deposit(pic_ctx* ctx) {
   if (!ctx) return PIC_ERR_ARG;
+  if (ctx->shock)
+    return set_err(ctx, PIC_ERR_STATE, "the split gather/deposit path does not model the wall");
   if (!ctx->snapshot_valid)
     return set_err(ctx, PIC_ERR_STATE, "pic_deposit needs a preceding pic_gather_push");
   const PushParams P = make_params(ctx);
@@ -512,7 +723,21 @@ pic_status pic_field_update(pic_ctx* ctx, int which) {
 pic_status pic_step(pic_ctx* ctx, int nsteps) {
   if (!ctx) return PIC_ERR_ARG;
   if (nsteps < 0) return set_err(ctx, PIC_ERR_ARG, "nsteps must be >= 0");
+  const auto wall_bc = [&]() {
+    if (!ctx->shock) return cudaSuccess;
+    return timed(ctx, PIC_KERNEL_BOUNDARY, [&]() {
+      return launch_wall_fields(ctx->g, ctx->F, ctx->wall, ctx->i_zero, ctx->st);
+    });
+  };
   for (int it = 0; it < nsteps; ++it) {
+    InjectParams IP{};
+    long long add[PIC_MAX_SPECIES] = {};
+    if (ctx->shock) {  // plan this step's injection first: refuse it whole if it does not fit
+      plan_injection(ctx, ctx->shock_steps, &IP, add);
+      for (int s = 0; s < ctx->ns; ++s)
+        if (ctx->sp[s].n + add[s] > ctx->cap[s])
+          return set_err(ctx, PIC_ERR_ARG, "injection would exceed a species' cap");
+    }
     if (ctx->steps > 0 && ctx->steps % ctx->tun.sort_every == 0) {
       const pic_status s = do_sort(ctx, false);
       if (s != PIC_OK) return s;
@@ -520,15 +745,32 @@ pic_status pic_step(pic_ctx* ctx, int nsteps) {
     const PushParams P = make_params(ctx);
     ctx->sorted_pending = false;
     cudaError_t e = timed(ctx, PIC_KERNEL_BHALF, [&]() { return launch_b_half(ctx->g, ctx->F, 1, ctx->st); });
+    if (e == cudaSuccess) e = wall_bc();
     if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
-    e = timed(ctx, PIC_KERNEL_PUSH, [&]() { return launch_particles(ctx->grid.dim, 0, P, ctx->st); });
+    e = timed(ctx, PIC_KERNEL_PUSH, [&]() {
+      if (ctx->shock) {
+        const cudaError_t m = cudaMemsetAsync(ctx->d_wcount, 0, sizeof(int) * ctx->ns, ctx->st);
+        if (m != cudaSuccess) return m;
+      }
+      return launch_particles(ctx->grid.dim, 0, P, ctx->st);
+    });
     if (e != cudaSuccess) return cuda_fail(ctx, "gather/push/deposit kernel", e);
     e = timed(ctx, PIC_KERNEL_BHALF, [&]() { return launch_b_half(ctx->g, ctx->F, 0, ctx->st); });
+    if (e == cudaSuccess) e = wall_bc();
     if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
     const pic_status s = do_filter(ctx, ctx->tun.filter_passes);
     if (s != PIC_OK) return s;
     e = timed(ctx, PIC_KERNEL_EUPD, [&]() { return launch_e_update(ctx->g, ctx->F, ctx->st); });
+    if (e == cudaSuccess) e = wall_bc();
     if (e != cudaSuccess) return cuda_fail(ctx, "E update", e);
+    if (ctx->shock) {
+      if (IP.nruns > 0) {
+        e = timed(ctx, PIC_KERNEL_BOUNDARY, [&]() { return launch_inject(IP, ctx->st); });
+        if (e != cudaSuccess) return cuda_fail(ctx, "injection", e);
+      }
+      for (int s2 = 0; s2 < ctx->ns; ++s2) ctx->sp[s2].n += add[s2];
+      ++ctx->shock_steps;
+    }
     ++ctx->steps;
   }
   ctx->snapshot_valid = false;
@@ -550,9 +792,9 @@ pic_status pic_energies(pic_ctx* ctx, double* out, int nout) {
   PIC_CK(ctx, launch_field_energy(ctx->g, ctx->F, ctx->d_acc, ctx->st));
   const double c2 = (double)ctx->c * (double)ctx->c;
   for (int s = 0; s < ns; ++s) {
-    PIC_CK(ctx, launch_kinetic(ctx->sp[s].u, ctx->sp[s].n, (double)ctx->sp[s].m * c2,
+    PIC_CK(ctx, launch_kinetic(ctx->sp[s].u, ctx->sp[s].n, ctx->cap[s], (double)ctx->sp[s].m * c2,
                                ctx->d_acc + 2 + s, ctx->st));
-    PIC_CK(ctx, launch_rho(ctx->g, ctx->sp[s].cell, ctx->sp[s].off, ctx->sp[s].n,
+    PIC_CK(ctx, launch_rho(ctx->g, ctx->sp[s].cell, ctx->sp[s].off, ctx->sp[s].n, ctx->cap[s],
                            (double)ctx->sp[s].q, ctx->d_rho, ctx->st));
   }
   double* a = ctx->d_rho;
@@ -565,13 +807,16 @@ pic_status pic_energies(pic_ctx* ctx, double* out, int nout) {
       b = t;
     }
   }
-  PIC_CK(ctx, launch_gauss(ctx->g, ctx->F, a, (unsigned long long*)(ctx->d_acc + 2 + ns),
-                           ctx->d_acc + 3 + ns, ctx->st));
+  // with the wall, the residual covers the plasma side: wall < i < i_zero
+  const int i_lo = ctx->shock ? ctx->wall + 1 : 0;
+  const int i_hi = ctx->shock ? ctx->i_zero : ctx->grid.nx;
+  PIC_CK(ctx, launch_gauss(ctx->g, ctx->F, a, i_lo, i_hi,
+                           (unsigned long long*)(ctx->d_acc + 2 + ns), ctx->d_acc + 3 + ns, ctx->st));
   double h[4 + PIC_MAX_SPECIES];
   PIC_CK(ctx, cudaMemcpyAsync(h, ctx->d_acc, sizeof(double) * (4 + ns), cudaMemcpyDeviceToHost, ctx->st));
   PIC_CK(ctx, cudaStreamSynchronize(ctx->st));
   for (int i = 0; i < 3 + ns; ++i) out[i] = h[i];
-  out[3 + ns] = std::sqrt(h[3 + ns] / (double)P);
+  out[3 + ns] = std::sqrt(h[3 + ns] / ((double)(i_hi - i_lo) * (double)(P / ctx->grid.nx)));
   return PIC_OK;
 }
 
@@ -598,21 +843,21 @@ pic_status pic_step_host(pic_ctx* ctx, const pic_host_species* hs, float* host_f
       return set_err(ctx, PIC_ERR_ARG, "host species buffers are NULL");
   const cudaMemcpyKind h2d = cudaMemcpyHostToDevice, d2h = cudaMemcpyDeviceToHost;
   for (int s = 0; s < ctx->ns; ++s) {
-    const long long n = ctx->sp[s].n;
+    const long long n = ctx->sp[s].n, ld = ctx->cap[s];
     if (n == 0) continue;
-    PIC_CK(ctx, cudaMemcpyAsync(ctx->sp[s].cell, hs[s].cell, 4 * n, h2d, ctx->st));
-    PIC_CK(ctx, cudaMemcpyAsync(ctx->sp[s].off, hs[s].off, 4 * D * n, h2d, ctx->st));
-    PIC_CK(ctx, cudaMemcpyAsync(ctx->sp[s].u, hs[s].u, 12 * n, h2d, ctx->st));
+    PIC_CK(ctx, copy_rows(ctx->sp[s].cell, hs[s].cell, 4, n, ld, 1, h2d, ctx->st));
+    PIC_CK(ctx, copy_rows(ctx->sp[s].off, hs[s].off, 4, n, ld, D, h2d, ctx->st));
+    PIC_CK(ctx, copy_rows(ctx->sp[s].u, hs[s].u, 4, n, ld, 3, h2d, ctx->st));
   }
   PIC_CK(ctx, cudaMemcpyAsync(ctx->F, host_fields, 36 * ctx->g.plane, h2d, ctx->st));
   const pic_status s = pic_step(ctx, nsteps);
   if (s != PIC_OK) return s;
   for (int sp = 0; sp < ctx->ns; ++sp) {
-    const long long n = ctx->sp[sp].n;
+    const long long n = ctx->sp[sp].n, ld = ctx->cap[sp];
     if (n == 0) continue;
-    PIC_CK(ctx, cudaMemcpyAsync(hs[sp].cell, ctx->sp[sp].cell, 4 * n, d2h, ctx->st));
-    PIC_CK(ctx, cudaMemcpyAsync(hs[sp].off, ctx->sp[sp].off, 4 * D * n, d2h, ctx->st));
-    PIC_CK(ctx, cudaMemcpyAsync(hs[sp].u, ctx->sp[sp].u, 12 * n, d2h, ctx->st));
+    PIC_CK(ctx, copy_rows(hs[sp].cell, ctx->sp[sp].cell, 4, n, ld, 1, d2h, ctx->st));
+    PIC_CK(ctx, copy_rows(hs[sp].off, ctx->sp[sp].off, 4, n, ld, D, d2h, ctx->st));
+    PIC_CK(ctx, copy_rows(hs[sp].u, ctx->sp[sp].u, 4, n, ld, 3, d2h, ctx->st));
   }
   PIC_CK(ctx, cudaMemcpyAsync(host_fields, ctx->F, 36 * ctx->g.plane, d2h, ctx->st));
   PIC_CK(ctx, cudaStreamSynchronize(ctx->st));
@@ -855,6 +1100,8 @@ pic_status pic_batch_create(pic_batch** out, pic_ctx* const* ctxs, int nctx) {
   if (!ctxs || nctx < 1) return set_err(nullptr, PIC_ERR_ARG, "need at least one context");
   for (int i = 0; i < nctx; ++i) {
     if (!ctxs[i]) return set_err(nullptr, PIC_ERR_ARG, "NULL context");
+    if (ctxs[i]->shock)
+      return set_err(nullptr, PIC_ERR_ARG, "a context with shock boundaries cannot join a batch");
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return set_err(nullptr, PIC_ERR_ARG, "a context appears twice");
   }
@@ -893,6 +1140,8 @@ pic_status pic_batch_step(pic_batch* b, int nsteps, void* stream) {
   long long cycle = 1;
   for (pic_ctx* c : b->ctxs) {
     if (c->st != st) return set_err(nullptr, PIC_ERR_ARG, "every context must use the batch's stream");
+    if (c->shock)
+      return set_err(nullptr, PIC_ERR_ARG, "a context with shock boundaries cannot join a batch");
     cycle = cycle / gcd_ll(cycle, c->tun.sort_every) * c->tun.sort_every;
     if (cycle > kMaxCycle) return set_err(nullptr, PIC_ERR_ARG, "lcm of the sort cadences exceeds 240");
   }

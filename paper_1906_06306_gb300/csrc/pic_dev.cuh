@@ -13,7 +13,7 @@ namespace pic {
 enum { EX = 0, EY, EZ, BX, BY, BZ, JX, JY, JZ };
 
 // device status word bits (pic_check)
-enum : int { ST_BAD_CELL = 1, ST_BAD_OFF = 2, ST_BAD_U = 4 };
+enum : int { ST_BAD_CELL = 1, ST_BAD_OFF = 2, ST_BAD_U = 4, ST_BEHIND_WALL = 8 };
 
 struct GridDev {
   int dim;
@@ -36,16 +36,20 @@ struct TileDev {
 struct SpeciesDev {
   float q;            // macro-particle charge
   float qm;           // q/m, the s-hat of Appendix C
-  long long n;
+  long long n;        // particles
+  long long ld;       // row length of the SoA arrays (capacity, >= n)
+  long long tail;     // particles [tail, n) were appended since the last sort
   int* cell;          // particle arrays written by the push
-  float* off;         // [D][n]
-  float* u;           // [3][n]
+  float* off;         // [D][ld]
+  float* u;           // [3][ld]
   const int* rcell;   // particle arrays read by the push (the sorted buffer right
   const float* roff;  // after a sort inside the step, else the same as cell/off/u)
   const float* ru;
   const int* tstart;  // [ntiles+1] tile bucket offsets
   int* cell_old;      // pre-move snapshot (split gather/deposit path)
-  float* off_old;     // [D][n]
+  float* off_old;     // [D][ld]
+  int* wlist;         // particles whose move crossed the conducting wall (room for ld)
+  int* wcount;        // entries in wlist
 };
 
 // Exact division of 0 <= x < 2^31 by a fixed divisor d >= 1 by multiply and

@@ -48,12 +48,13 @@ __global__ void k_field_energy(const float* __restrict__ F, long long P, double*
 }
 
 // m c^2 (gamma - 1) with gamma - 1 = u^2 / (gamma + 1)
-__global__ void k_kinetic(const float* __restrict__ u, long long n, double mc2, double* acc) {
+__global__ void k_kinetic(const float* __restrict__ u, long long n, long long ld, double mc2,
+                          double* acc) {
   __shared__ double sh[32];
   double s = 0.0;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
-    const double a = u[p], b = u[n + p], c = u[2 * n + p];
+    const double a = u[p], b = u[ld + p], c = u[2 * ld + p];
     const double u2 = a * a + b * b + c * c;
     s += u2 / (sqrt(1.0 + u2) + 1.0);
   }
@@ -64,7 +65,7 @@ __global__ void k_kinetic(const float* __restrict__ u, long long n, double mc2, 
 // charge q with weights (1 - w, w) per gridded axis onto the 2^D nodes
 template <int D>
 __global__ void k_rho(const GridDev g, const int* __restrict__ cell, const float* __restrict__ off,
-                      long long n, double q, double* rho) {
+                      long long n, long long ld, double q, double* rho) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
        p += (long long)gridDim.x * blockDim.x) {
     const int c = cell[p];
@@ -76,7 +77,7 @@ __global__ void k_rho(const GridDev g, const int* __restrict__ cell, const float
     ijk[2] = r / g.n[1];
     double w[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-    for (int d = 0; d < D; ++d) w[d] = off[d * n + p];
+    for (int d = 0; d < D; ++d) w[d] = off[d * ld + p];
 #pragma unroll
     for (int corner = 0; corner < (1 << D); ++corner) {
       double wt = q;
@@ -92,11 +93,11 @@ __global__ void k_rho(const GridDev g, const int* __restrict__ cell, const float
   }
 }
 
-// res = div- E - rho on the nodes; max |res| (bit pattern of a non-negative
-// double, which orders like the value) and sum res^2
+// res = div- E - rho on the nodes with i_lo <= i < i_hi; max |res| (bit
+// pattern of a non-negative double, which orders like the value) and sum res^2
 template <int D>
 __global__ void k_gauss(const GridDev g, const float* __restrict__ F, const double* __restrict__ rho,
-                        unsigned long long* acc_max, double* acc_sq) {
+                        int i_lo, int i_hi, unsigned long long* acc_max, double* acc_sq) {
   __shared__ double sh[32];
   __shared__ unsigned long long shm;
   if (threadIdx.x == 0) shm = 0ull;
@@ -108,6 +109,7 @@ __global__ void k_gauss(const GridDev g, const float* __restrict__ F, const doub
     const int i = (int)(idx % n0);
     const long long r = idx / n0;
     const int j = (int)(r % n1), k = (int)(r / n1);
+    if (i < i_lo || i >= i_hi) continue;
     double div = (double)F[EX * P + idx] - (double)F[EX * P + idx - ((i > 0) ? 1 : 1 - n0)];
     if (D >= 2)
       div += (double)F[EY * P + idx] -
@@ -134,32 +136,33 @@ cudaError_t launch_field_energy(const GridDev& g, const float* F, double* acc, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_kinetic(const float* u, long long n, double mc2, double* acc, cudaStream_t st) {
+cudaError_t launch_kinetic(const float* u, long long n, long long ld, double mc2, double* acc,
+                           cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_kinetic<<<blocks_for(n), 256, 0, st>>>(u, n, mc2, acc);
+  k_kinetic<<<blocks_for(n), 256, 0, st>>>(u, n, ld, mc2, acc);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rho(const GridDev& g, const int* cell, const float* off, long long n, double q,
-                       double* rho, cudaStream_t st) {
+cudaError_t launch_rho(const GridDev& g, const int* cell, const float* off, long long n,
+                       long long ld, double q, double* rho, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const unsigned nb = blocks_for(n);
   switch (g.dim) {
-    case 1: k_rho<1><<<nb, 256, 0, st>>>(g, cell, off, n, q, rho); break;
-    case 2: k_rho<2><<<nb, 256, 0, st>>>(g, cell, off, n, q, rho); break;
-    case 3: k_rho<3><<<nb, 256, 0, st>>>(g, cell, off, n, q, rho); break;
+    case 1: k_rho<1><<<nb, 256, 0, st>>>(g, cell, off, n, ld, q, rho); break;
+    case 2: k_rho<2><<<nb, 256, 0, st>>>(g, cell, off, n, ld, q, rho); break;
+    case 3: k_rho<3><<<nb, 256, 0, st>>>(g, cell, off, n, ld, q, rho); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_gauss(const GridDev& g, const float* F, const double* rho,
+cudaError_t launch_gauss(const GridDev& g, const float* F, const double* rho, int i_lo, int i_hi,
                          unsigned long long* acc_max, double* acc_sq, cudaStream_t st) {
   const unsigned nb = blocks_for(g.plane);
   switch (g.dim) {
-    case 1: k_gauss<1><<<nb, 256, 0, st>>>(g, F, rho, acc_max, acc_sq); break;
-    case 2: k_gauss<2><<<nb, 256, 0, st>>>(g, F, rho, acc_max, acc_sq); break;
-    case 3: k_gauss<3><<<nb, 256, 0, st>>>(g, F, rho, acc_max, acc_sq); break;
+    case 1: k_gauss<1><<<nb, 256, 0, st>>>(g, F, rho, i_lo, i_hi, acc_max, acc_sq); break;
+    case 2: k_gauss<2><<<nb, 256, 0, st>>>(g, F, rho, i_lo, i_hi, acc_max, acc_sq); break;
+    case 3: k_gauss<3><<<nb, 256, 0, st>>>(g, F, rho, i_lo, i_hi, acc_max, acc_sq); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

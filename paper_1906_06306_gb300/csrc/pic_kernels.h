@@ -39,6 +39,8 @@ struct PushParams {
   float jq_inv;        // 1 / jq
   unsigned long long* strays;  // running count of particles that took the global path
   int pusher;                  // 0 Boris (Appendix C), 1 Higuera-Cary
+  int wall;                    // conducting wall on the node plane x = wall (0: none)
+  int tail_blocks;             // extra blocks for the unsorted tails [tail, n)
 };
 
 // Quantum of the fixed-point shared-memory current (a power of 2) for charges
@@ -54,7 +56,10 @@ FastDiv make_fastdiv(int d);
 void set_global_error(const char* msg);
 
 // mode 0: fused gather + push + move + deposit; 1: gather + push + move and
-// pre-move snapshot; 2: deposit from the snapshot and the stored new u.
+// pre-move snapshot; 2: deposit from the snapshot and the stored new u.  Mode
+// 0 with P.wall > 0 runs the fused kernel's wall variant (mode 3), which also
+// reflects at the conducting wall; then the unsorted tail and the wall
+// crossers are processed by two small kernels after it.
 cudaError_t launch_particles(int dim, int mode, const PushParams& P, cudaStream_t st);
 cudaError_t set_particle_smem_limit(int bytes);
 size_t particle_smem_bytes(int dim, const TileDev& t);
@@ -77,17 +82,51 @@ cudaError_t launch_tile_count(const SortParams& P, const int* cell, long long n,
                               cudaStream_t st);
 cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* cursor,
                              cudaStream_t st);
+// arrays with rows of ld elements, the first n of which are particles
 cudaError_t launch_tile_scatter(const SortParams& P, const int* cell, const float* off,
-                                const float* u, long long n, int* cursor, int* cell_out,
-                                float* off_out, float* u_out, cudaStream_t st);
+                                const float* u, long long n, long long ld, int* cursor,
+                                int* cell_out, float* off_out, float* u_out, cudaStream_t st);
 
 // diagnostics: acc[0] += 0.5 sum E^2, acc[1] += 0.5 sum B^2
 cudaError_t launch_field_energy(const GridDev& g, const float* F, double* acc, cudaStream_t st);
-cudaError_t launch_kinetic(const float* u, long long n, double mc2, double* acc, cudaStream_t st);
-cudaError_t launch_rho(const GridDev& g, const int* cell, const float* off, long long n, double q,
-                       double* rho, cudaStream_t st);
-// acc_max (as the bit pattern of a non-negative double), acc_sq += sum res^2
-cudaError_t launch_gauss(const GridDev& g, const float* F, const double* rho,
+cudaError_t launch_kinetic(const float* u, long long n, long long ld, double mc2, double* acc,
+                           cudaStream_t st);
+cudaError_t launch_rho(const GridDev& g, const int* cell, const float* off, long long n,
+                       long long ld, double q, double* rho, cudaStream_t st);
+// over the nodes with i_lo <= i < i_hi: acc_max (as the bit pattern of a
+// non-negative double), acc_sq += sum res^2
+cudaError_t launch_gauss(const GridDev& g, const float* F, const double* rho, int i_lo, int i_hi,
                          unsigned long long* acc_max, double* acc_sq, cudaStream_t st);
+
+// Shock boundaries (Sect. 4.2): the conducting wall's field boundary (zero
+// tangential E on the node plane x = wall, mirror image behind it) and zero E
+// and B at i >= i_zero, applied after each field update.
+cudaError_t launch_wall_fields(const GridDev& g, float* F, int wall, int i_zero, cudaStream_t st);
+
+// One contiguous run of injected particles: template indices [k0, k1) of copy
+// m of species s, written from output index `out` on, x = x_t + shift.
+struct InjectRun {
+  int s;
+  long long k0, k1;
+  long long out;
+  double shift;
+};
+constexpr int kMaxInjectRuns = 3 * kMaxSpecies;
+struct InjectParams {
+  GridDev g;
+  int lt;                      // template block length along x
+  int nruns;
+  long long first[kMaxInjectRuns + 1];  // prefix of run lengths (first[nruns] = total)
+  InjectRun run[kMaxInjectRuns];
+  const int* tcell[kMaxSpecies];  // template arrays of each species, rows of tn[s]
+  const float* toff[kMaxSpecies];
+  const float* tu[kMaxSpecies];
+  long long tn[kMaxSpecies];
+  int* cell[kMaxSpecies];         // species arrays, rows of ld[s]
+  float* off[kMaxSpecies];
+  float* u[kMaxSpecies];
+  long long ld[kMaxSpecies];
+};
+cudaError_t launch_inject(const InjectParams& P, cudaStream_t st);
 
 }  // namespace pic

@@ -97,7 +97,7 @@ struct PRec {
 
 template <int D, int MODE>
 __device__ __forceinline__ void load_rec(const SpeciesDev& S, int p, PRec& r) {
-  const long long n = S.n;
+  const long long n = S.ld;
   if (MODE == 2) {
     r.cell = S.cell_old[p];
 #pragma unroll
@@ -115,15 +115,54 @@ __device__ __forceinline__ void load_rec(const SpeciesDev& S, int p, PRec& r) {
   for (int d = D; d < 3; ++d) r.o[d] = 0.f;
 }
 
-// One particle through gather -> Boris -> move -> ZigZag.  GLOBAL = false:
-// the shared-memory window is used and a particle whose stencil leaves the
-// window is not touched (returns false, the caller queues it).  GLOBAL = true:
-// everything goes through global memory (the deferred pass over the queue).
-template <int D, int MODE, bool GLOBAL>
+// First segment of a reflection at the conducting wall (the shock set-up of
+// Sect. 4.2): the particle moved from the wall's cell (offsets o1) to below
+// the wall plane (cell offset dc with dc[0] = -1, offsets o2; displacement
+// dn).  Its current follows the true path: a straight segment to the point
+// where it meets the wall plane, a fraction s = o1x / (o1x + 1 - o2x) of the
+// move, then the mirrored remainder.  Writes the crossing point (cell offset
+// e, offsets z) and the first segment's share w of dn on non-gridded axes.
+template <int D>
+__device__ __forceinline__ float wall_crossing(const int* dc, const float* o1, const float* o2,
+                                               const float* dn, int* e, float* z, float* w) {
+  const float s = o1[0] / (o1[0] + (1.0f - o2[0]));  // 1 - o2x is exact: o2x > 1/2
+  e[0] = 0;
+  z[0] = 0.f;
+  w[0] = 0.f;
+#pragma unroll
+  for (int d = 1; d < 3; ++d) {
+    if (d < D) {
+      // crossing point relative to the old cell, kept between the two cells
+      const float y = fmaf(s, (float)dc[d] + o2[d] - o1[d], o1[d]);
+      const int lo = dc[d] < 0 ? dc[d] : 0, hi = dc[d] > 0 ? dc[d] : 0;
+      int f = (int)floorf(y);
+      f = f < lo ? lo : (f > hi ? hi : f);
+      const float r = y - (float)f;
+      e[d] = f;
+      z[d] = r < 0.f ? 0.f : (r < 1.f ? r : 0.99999994f);
+      w[d] = 0.f;
+    } else {
+      e[d] = 0;
+      z[d] = 0.f;
+      w[d] = s * dn[d];
+    }
+  }
+  return s;
+}
+
+// One particle through gather -> Boris -> move -> ZigZag.  PATH 0: the
+// shared-memory window is used and a particle whose stencil leaves the window
+// is not touched (returns false, the caller queues it).  PATH 1: everything
+// goes through global memory (the deferred pass over the queue).  In both, a
+// move that crosses the conducting wall is not applied: the particle goes on
+// its species' wall list (k_particles_wall reflects it).  PATH 2: global
+// memory with the reflection applied here (tail and wall kernels).
+template <int D, int MODE, int PATH>
 __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesDev& S, int p,
                                              PRec r, const float* sm, const SmemJ& SJ,
                                              const GlobAcc& GA, const int* w0, float qs) {
-  const long long n = S.n;
+  constexpr bool GLOBAL = PATH != 0;
+  const long long n = S.ld;
   // invalid data: cell outside the lattice, offset outside [0,1), non-finite u
   bool bad_off = false;
 #pragma unroll
@@ -144,6 +183,10 @@ __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesD
       ijk[2] = fdiv(q, P.div1);
       ijk[1] = q - ijk[2] * P.g.n[1];
     }
+  }
+  if (MODE == 3 && ijk[0] < P.wall) {  // behind the conducting wall
+    atomicOr(P.status, ST_BEHIND_WALL);
+    return true;
   }
   int l[3] = {0, 0, 0};
   if (!GLOBAL) {
@@ -180,15 +223,28 @@ __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesD
   int dc[3] = {0, 0, 0};
   move<D>(u, o1, P.g.c, o2, dc, dn);
 
+  // A move that ends below the wall plane (only from the wall's own cell: a
+  // step is shorter than one cell) is reflected: x -> 2 wall - x, u_x -> -u_x.
+  // Paths 0 and 1 leave it to k_particles_wall (keeping the reflection out of
+  // the tile kernel keeps its registers); the record is not written.
+  const bool refl = MODE == 3 && ijk[0] + dc[0] < P.wall;
+  if (PATH != 2 && refl) {
+    S.wlist[atomicAdd(S.wcount, 1)] = p;
+    return true;
+  }
+
   if (MODE != 2) {
     int nc[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < D; ++d) nc[d] = wrap1(ijk[d] + dc[d], P.g.n[d]);
+    if (refl) nc[0] = ijk[0];
     const int cell2 = nc[0] + P.g.n[0] * (nc[1] + P.g.n[1] * nc[2]);
+    S.u[p] = refl ? -u[0] : u[0];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) S.u[a * n + p] = u[a];
+    for (int a = 1; a < 3; ++a) S.u[a * n + p] = u[a];
+    S.off[p] = refl ? 1.0f - o2[0] : o2[0];
 #pragma unroll
-    for (int d = 0; d < D; ++d) S.off[d * n + p] = o2[d];
+    for (int d = 1; d < D; ++d) S.off[d * n + p] = o2[d];
     S.cell[p] = cell2;
     if (MODE == 1) {
       S.cell_old[p] = r.cell;
@@ -197,10 +253,32 @@ __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesD
     }
   }
   if (MODE != 1) {
-    if (GLOBAL)
-      zigzag<D>(GA, ijk, dc, o1, o2, dn, S.q);
-    else
+    if (GLOBAL) {
+      // one straight ZigZag move, or the two segments of a reflected one
+      // (a single call site keeps the global pass small)
+      int b[3] = {ijk[0], ijk[1], ijk[2]}, e[3] = {dc[0], dc[1], dc[2]};
+      float a[3] = {o1[0], o1[1], o1[2]}, z[3] = {o2[0], o2[1], o2[2]};
+      float w[3] = {dn[0], dn[1], dn[2]};
+      if (refl) wall_crossing<D>(dc, o1, o2, dn, e, z, w);
+#pragma unroll 1
+      for (int seg = 0; seg < (refl ? 2 : 1); ++seg) {
+        if (seg == 1) {
+          // from the crossing point (cell b + e, offsets z) to the mirror
+          // image of the end point (x offset 1 - o2x in the wall's cell)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            b[d] = d < D ? wrap1(b[d] + e[d], P.g.n[d]) : 0;
+            a[d] = z[d];
+            w[d] = d < D ? 0.f : dn[d] - w[d];
+            e[d] = d == 0 || d >= D ? 0 : dc[d] - e[d];
+            z[d] = d == 0 ? 1.0f - o2[0] : o2[d];
+          }
+        }
+        zigzag<D>(GA, b, e, a, z, w, S.q);
+      }
+    } else {
       zigzag<D>(SJ, l, dc, o1, o2, dn, qs);
+    }
   }
   return true;
 }
@@ -210,6 +288,7 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? 2 : PIC_PUSH_MIN_BLOCKS
     k_particles(const PushParams P) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int q_n;  // entries in the stray queue
+  const GlobAcc GA{P.F, P.g.plane, P.g.n[0], P.g.n[1], P.g.n[2]};
   const int tile = blockIdx.x / P.splits;
   const int split = blockIdx.x - tile * P.splits;
   const int tc[3] = {tile % P.t.nt[0], (tile / P.t.nt[0]) % P.t.nt[1],
@@ -225,7 +304,6 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? 2 : PIC_PUSH_MIN_BLOCKS
   int* ji = reinterpret_cast<int*>(sm + fw);
   float* jf = sm + fw + 3 * ws;
   int* queue = reinterpret_cast<int*>(sm + fw + 6 * ws);
-  const GlobAcc GA{P.F, P.g.plane, P.g.n[0], P.g.n[1], P.g.n[2]};
   const SmemJ SJ{ji, W0, W0 * W1, ws};
 
   if (threadIdx.x == 0) q_n = 0;
@@ -282,7 +360,7 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? 2 : PIC_PUSH_MIN_BLOCKS
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
       PRec r;
       load_rec<D, MODE>(S, queue[i], r);
-      one_particle<D, MODE, true>(P, S, queue[i], r, sm, SJ, GA, w0, 0.f);
+      one_particle<D, MODE, 1>(P, S, queue[i], r, sm, SJ, GA, w0, 0.f);
     }
     if (threadIdx.x == 0) atomicAdd(P.strays, (unsigned long long)cnt);
     __syncthreads();
@@ -311,7 +389,7 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? 2 : PIC_PUSH_MIN_BLOCKS
       } else if (p < b) {
         load_rec<D, MODE>(S, p, cur);
       }
-      if (p < b && !one_particle<D, MODE, false>(P, S, p, cur, sm, SJ, GA, w0, qs))
+      if (p < b && !one_particle<D, MODE, 0>(P, S, p, cur, sm, SJ, GA, w0, qs))
         queue[atomicAdd(&q_n, 1)] = p;
       if (PIC_PREFETCH) cur = nxt;
       if (++batches == kSpillEvery) {
@@ -341,6 +419,40 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? 2 : PIC_PUSH_MIN_BLOCKS
         const float v = jf[c * ws + w];
         if (v != 0.0f) atomicAdd(&P.F[(JX + c) * P.g.plane + gi], v);
       }
+    }
+  }
+}
+
+// Particles appended (injected) since the last sort belong to no tile bucket
+// yet: they take the global-memory path, grid-strided over [tail, n).
+template <int D>
+__global__ void __launch_bounds__(kPushThreads) k_particles_tail(const PushParams P) {
+  const GlobAcc GA{P.F, P.g.plane, P.g.n[0], P.g.n[1], P.g.n[2]};
+  for (int s = 0; s < P.nspecies; ++s) {
+    const SpeciesDev& S = P.sp[s];
+    for (long long p = S.tail + (long long)blockIdx.x * blockDim.x + threadIdx.x; p < S.n;
+         p += (long long)gridDim.x * blockDim.x) {
+      PRec r;
+      load_rec<D, 3>(S, (int)p, r);
+      one_particle<D, 3, 2>(P, S, (int)p, r, nullptr, SmemJ{nullptr, 0, 0, 0}, GA, nullptr, 0.f);
+    }
+  }
+}
+
+// Particles whose move crossed the conducting wall (listed by k_particles):
+// the whole update again through global memory, with the reflection.  The
+// records were not written, so they are read where k_particles read them.
+template <int D>
+__global__ void __launch_bounds__(kPushThreads) k_particles_wall(const PushParams P) {
+  const GlobAcc GA{P.F, P.g.plane, P.g.n[0], P.g.n[1], P.g.n[2]};
+  for (int s = 0; s < P.nspecies; ++s) {
+    const SpeciesDev& S = P.sp[s];
+    const int cnt = *S.wcount;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+      const int p = S.wlist[i];
+      PRec r;
+      load_rec<D, 3>(S, p, r);
+      one_particle<D, 3, 2>(P, S, p, r, nullptr, SmemJ{nullptr, 0, 0, 0}, GA, nullptr, 0.f);
     }
   }
 }
@@ -380,7 +492,8 @@ cudaError_t set_particle_smem_limit(int bytes) {
 #define PIC_SET(D)                                  \
   if (e == cudaSuccess) e = set_limit<D, 0>(bytes); \
   if (e == cudaSuccess) e = set_limit<D, 1>(bytes); \
-  if (e == cudaSuccess) e = set_limit<D, 2>(bytes);
+  if (e == cudaSuccess) e = set_limit<D, 2>(bytes); \
+  if (e == cudaSuccess) e = set_limit<D, 3>(bytes);
   PIC_SET(1)
   PIC_SET(2)
   PIC_SET(3)
@@ -392,20 +505,27 @@ template <int D, int MODE>
 static void launch(const PushParams& P, cudaStream_t st) {
   const unsigned nblocks = (unsigned)P.t.ntiles * (unsigned)P.splits;
   k_particles<D, MODE><<<nblocks, kPushThreads, particle_smem_bytes(D, P.t), st>>>(P);
+  if ((MODE == 0 || MODE == 3) && P.tail_blocks > 0)
+    k_particles_tail<D><<<(unsigned)P.tail_blocks, kPushThreads, 0, st>>>(P);
+  if (MODE == 3) k_particles_wall<D><<<4 * 152, kPushThreads, 0, st>>>(P);
 }
 
 cudaError_t launch_particles(int dim, int mode, const PushParams& P, cudaStream_t st) {
   if ((long long)P.t.ntiles * P.splits == 0) return cudaSuccess;
-  switch (dim * 3 + mode) {
-    case 3: launch<1, 0>(P, st); break;
-    case 4: launch<1, 1>(P, st); break;
-    case 5: launch<1, 2>(P, st); break;
-    case 6: launch<2, 0>(P, st); break;
-    case 7: launch<2, 1>(P, st); break;
-    case 8: launch<2, 2>(P, st); break;
-    case 9: launch<3, 0>(P, st); break;
-    case 10: launch<3, 1>(P, st); break;
-    case 11: launch<3, 2>(P, st); break;
+  if (mode == 0 && P.wall > 0) mode = 3;  // the fused kernel with the conducting wall
+  switch (dim * 4 + mode) {
+    case 4: launch<1, 0>(P, st); break;
+    case 5: launch<1, 1>(P, st); break;
+    case 6: launch<1, 2>(P, st); break;
+    case 7: launch<1, 3>(P, st); break;
+    case 8: launch<2, 0>(P, st); break;
+    case 9: launch<2, 1>(P, st); break;
+    case 10: launch<2, 2>(P, st); break;
+    case 11: launch<2, 3>(P, st); break;
+    case 12: launch<3, 0>(P, st); break;
+    case 13: launch<3, 1>(P, st); break;
+    case 14: launch<3, 2>(P, st); break;
+    case 15: launch<3, 3>(P, st); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int* __restrict__ coun
 template <int D>
 __global__ void k_tile_scatter(const SortParams P, const int* __restrict__ cell,
                                const float* __restrict__ off, const float* __restrict__ u,
-                               long long n, int* cursor, int* __restrict__ cell_out,
+                               long long n, long long ld, int* cursor, int* __restrict__ cell_out,
                                float* __restrict__ off_out, float* __restrict__ u_out) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -104,9 +104,9 @@ __global__ void k_tile_scatter(const SortParams P, const int* __restrict__ cell,
       const long long q = warp_reserve(cursor, tile_key(P, c), active);
       cell_out[q] = c;
 #pragma unroll
-      for (int d = 0; d < D; ++d) off_out[d * n + q] = off[d * n + p];
+      for (int d = 0; d < D; ++d) off_out[d * ld + q] = off[d * ld + p];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) u_out[a * n + q] = u[a * n + p];
+      for (int a = 0; a < 3; ++a) u_out[a * ld + q] = u[a * ld + p];
     }
   }
 }
@@ -131,14 +131,14 @@ cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* curs
 }
 
 cudaError_t launch_tile_scatter(const SortParams& P, const int* cell, const float* off,
-                                const float* u, long long n, int* cursor, int* cell_out,
-                                float* off_out, float* u_out, cudaStream_t st) {
+                                const float* u, long long n, long long ld, int* cursor,
+                                int* cell_out, float* off_out, float* u_out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const unsigned nb = blocks_for(n);
   switch (P.g.dim) {
-    case 1: k_tile_scatter<1><<<nb, 256, 0, st>>>(P, cell, off, u, n, cursor, cell_out, off_out, u_out); break;
-    case 2: k_tile_scatter<2><<<nb, 256, 0, st>>>(P, cell, off, u, n, cursor, cell_out, off_out, u_out); break;
-    case 3: k_tile_scatter<3><<<nb, 256, 0, st>>>(P, cell, off, u, n, cursor, cell_out, off_out, u_out); break;
+    case 1: k_tile_scatter<1><<<nb, 256, 0, st>>>(P, cell, off, u, n, ld, cursor, cell_out, off_out, u_out); break;
+    case 2: k_tile_scatter<2><<<nb, 256, 0, st>>>(P, cell, off, u, n, ld, cursor, cell_out, off_out, u_out); break;
+    case 3: k_tile_scatter<3><<<nb, 256, 0, st>>>(P, cell, off, u, n, ld, cursor, cell_out, off_out, u_out); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -16,10 +16,11 @@ class Simulation:
 
     fields: float32[9, nz, ny, nx] (Ex Ey Ez Bx By Bz Jx Jy Jz);
     species: list of dicts with q, m, cell int32[n], off float32[D, n],
-    u float32[3, n]."""
+    u float32[3, n].  capacity (one per species, or None): row length of the
+    device arrays, the room an injector (set_shock) may fill."""
 
     def __init__(self, dim, nx, ny, nz, c, fields, species, device="cuda:0", stream=None,
-                 tuning=None):
+                 tuning=None, capacity=None):
         import torch
 
         self.torch = torch
@@ -29,15 +30,27 @@ class Simulation:
         self.fields = torch.from_numpy(np.ascontiguousarray(fields, dtype=np.float32)).to(self.device)
         self.species = []
         sps = []
-        for s in species:
-            d = dict(q=float(s["q"]), m=float(s["m"]),
-                     cell=torch.from_numpy(np.ascontiguousarray(s["cell"], dtype=np.int32)).to(self.device),
-                     off=torch.from_numpy(np.ascontiguousarray(s["off"], dtype=np.float32)).to(self.device),
-                     u=torch.from_numpy(np.ascontiguousarray(s["u"], dtype=np.float32)).to(self.device))
-            d["n"] = int(d["cell"].shape[0])
+        for i, s in enumerate(species):
+            n = int(np.asarray(s["cell"]).shape[0])
+            cap = max(n, int(capacity[i])) if capacity is not None else n
+            if cap == n:
+                cell = np.ascontiguousarray(s["cell"], dtype=np.int32)
+                off = np.ascontiguousarray(s["off"], dtype=np.float32).reshape(dim, n)
+                u = np.ascontiguousarray(s["u"], dtype=np.float32)
+            else:
+                cell = np.zeros(cap, dtype=np.int32)
+                off = np.zeros((dim, cap), dtype=np.float32)
+                u = np.zeros((3, cap), dtype=np.float32)
+                cell[:n] = s["cell"]
+                off[:, :n] = s["off"]
+                u[:, :n] = s["u"]
+            d = dict(q=float(s["q"]), m=float(s["m"]), n=n, cap=cap,
+                     cell=torch.from_numpy(cell).to(self.device),
+                     off=torch.from_numpy(off).to(self.device),
+                     u=torch.from_numpy(u).to(self.device))
             self.species.append(d)
-            sps.append(B.pic_species(d["q"], d["m"], d["n"], d["cell"].data_ptr(),
-                                     d["off"].data_ptr(), d["u"].data_ptr()))
+            sps.append(B.pic_species(d["q"], d["m"], n, d["cell"].data_ptr(),
+                                     d["off"].data_ptr(), d["u"].data_ptr(), cap))
         grid = B.pic_grid(dim, nx, ny, nz)
         torch.cuda.synchronize(self.device)
         self.ctx = B.pic_init(grid, sps, self.c, 1.0, self.fields.data_ptr(), self.stream.cuda_stream)
@@ -53,9 +66,36 @@ class Simulation:
     def nspecies(self):
         return len(self.species)
 
+    def counts(self):
+        """Current particle count of each species (grows with injection)."""
+        return B.pic_particle_counts(self.ctx, self.nspecies)
+
     @property
     def nparticles(self):
-        return sum(s["n"] for s in self.species)
+        return sum(self.counts())
+
+    def set_shock(self, wall, lt, x0, x_max, v_inj, v_up, templates):
+        """Conducting wall and receding injector along x (Sect. 4.2).
+        templates: one (cell int32[nt], off float32[D, nt], u float32[3, nt])
+        per species, cells of an lt x ny x nz block, sorted by x."""
+        sh = B.pic_shock()
+        sh.wall, sh.lt = int(wall), int(lt)
+        sh.x0, sh.x_max, sh.v_inj, sh.v_up = float(x0), float(x_max), float(v_inj), float(v_up)
+        keep = []
+        for i, (cell, off, u) in enumerate(templates):
+            arrs = [np.ascontiguousarray(cell, dtype=np.int32),
+                    np.ascontiguousarray(off, dtype=np.float32),
+                    np.ascontiguousarray(u, dtype=np.float32)]
+            keep.append(arrs)
+            sh.nt[i] = arrs[0].shape[0]
+            sh.tmpl[i] = B.pic_host_species(*[a.ctypes.data for a in arrs])
+        B.pic_set_shock(self.ctx, sh)
+
+    def set_shock_from_plasma(self, pl):
+        """The wall and injector of a workloads.shock_tube plasma."""
+        sh = pl.meta["shock"]
+        self.set_shock(sh["wall"], sh["lt"], sh["x_inj"], sh["x_max"], sh["v_inj"], sh["v_up"],
+                       [(t.cell, t.off, t.u) for t in sh["templates"]])
 
     def set_tuning(self, tile=None, halo=0, sort_every=0, filter_passes=0, chunk=0):
         t = B.pic_tuning()
@@ -120,10 +160,13 @@ class Simulation:
         B.pic_check(self.ctx)
 
     def download(self):
-        """Host copies: (fields, [dict(cell, off, u) per species])."""
+        """Host copies: (fields, [dict(cell, off, u) per species]) of the current
+        particles."""
         self.stream.synchronize()
-        sp = [dict(q=s["q"], m=s["m"], cell=s["cell"].cpu().numpy(), off=s["off"].cpu().numpy(),
-                   u=s["u"].cpu().numpy()) for s in self.species]
+        ns = self.counts()
+        sp = [dict(q=s["q"], m=s["m"], cell=s["cell"][:n].cpu().numpy(),
+                   off=s["off"][:, :n].cpu().numpy(), u=s["u"][:, :n].cpu().numpy())
+              for s, n in zip(self.species, ns)]
         return self.fields.cpu().numpy(), sp
 
     def close(self):

@@ -44,8 +44,8 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(_declared()) == set(lib.SIGNATURES), "binding covers exactly the header"
 
 
-def _species(lib, n=4, q=-1.0, m=1.0, ptr=0x1000):
-    return lib.pic_species(q, m, n, ptr, ptr, ptr)
+def _species(lib, n=4, q=-1.0, m=1.0, ptr=0x1000, cap=0):
+    return lib.pic_species(q, m, n, ptr, ptr, ptr, cap)
 
 
 @pytest.mark.parametrize("case,msg", [
@@ -65,6 +65,7 @@ def _species(lib, n=4, q=-1.0, m=1.0, ptr=0x1000):
     (dict(null_fields=True), "NULL"),
     (dict(dim=3, nx=2048, ny=2048, nz=1024), "int32"),
     (dict(dim=2, nx=4, ny=70000), "65535"),
+    (dict(cap=2), "cap"),
 ])
 def test_pic_init_rejects_bad_arguments(lib, case, msg):
     dim = case.get("dim", 2)
@@ -75,8 +76,8 @@ def test_pic_init_rejects_bad_arguments(lib, case, msg):
     if "ny" in case:
         g.ny = case["ny"]
     ns = case.get("nspecies", 2)
-    sp = (lib.pic_species * 5)(*[_species(lib, n=case.get("n", 4), m=case.get("m", 1.0))
-                                 for _ in range(5)])
+    sp = (lib.pic_species * 5)(*[_species(lib, n=case.get("n", 4), m=case.get("m", 1.0),
+                                          cap=case.get("cap", 0)) for _ in range(5)])
     if case.get("null_cell"):
         sp[0].cell = None
     out = ctypes.c_void_p(123)
@@ -93,3 +94,5 @@ def test_null_context_is_an_argument_error(lib):
         assert getattr(lib._lib, name)(None) == lib.PIC_ERR_ARG
     assert lib._lib.pic_step(None, 1) == lib.PIC_ERR_ARG
     assert lib._lib.pic_field_update(None, 0) == lib.PIC_ERR_ARG
+    assert lib._lib.pic_set_shock(None, None) == lib.PIC_ERR_ARG
+    assert lib._lib.pic_particle_counts(None, None, 0) == lib.PIC_ERR_ARG
