@@ -410,14 +410,12 @@ pic_status do_filter(pic_ctx* ctx, int passes) {
   float* a = J;
   float* b = ctx->d_jtmp;
   for (int p = 0; p < passes; ++p) {
-    for (int axis = 0; axis < ctx->grid.dim; ++axis) {
-      const cudaError_t e = timed(
-          ctx, PIC_KERNEL_FILTER, [&]() { return launch_filter_f32(ctx->g, a, b, 3, axis, ctx->st); });
-      if (e != cudaSuccess) return cuda_fail(ctx, "binomial filter", e);
-      float* t = a;
-      a = b;
-      b = t;
-    }
+    const cudaError_t e = timed(
+        ctx, PIC_KERNEL_FILTER, [&]() { return launch_filter_pass_f32(ctx->g, a, b, 3, ctx->st); });
+    if (e != cudaSuccess) return cuda_fail(ctx, "binomial filter", e);
+    float* t = a;
+    a = b;
+    b = t;
   }
   if (a != J)
     PIC_CK(ctx, cudaMemcpyAsync(J, a, sizeof(float) * 3 * ctx->g.plane, cudaMemcpyDeviceToDevice,

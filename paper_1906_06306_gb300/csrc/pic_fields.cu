@@ -110,6 +110,78 @@ __global__ void k_filter_axis(const T* __restrict__ src, T* __restrict__ dst, co
   dst[comp * P + idx] = T(0.25) * s[lo] + T(0.5) * s[idx] + T(0.25) * s[hi];
 }
 
+// One full Binomial2 pass (the x, y and z sub-passes in that order) on each
+// of the consecutive planes src -> dst, fused through shared memory: a block
+// loads a TX x TY x TZ tile of one plane plus a one-cell periodic halo, runs
+// the sub-passes on it in shared memory and writes the tile.  Every output
+// goes through the same arithmetic, in the same order, as three
+// k_filter_axis sub-passes, but a pass moves 24 B per cell instead of 72.
+// Grid: x = tile index, y = plane.
+template <int D, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(256) k_filter_pass(const float* __restrict__ src,
+                                                     float* __restrict__ dst, const GridDev g,
+                                                     int ntx, int nty) {
+  constexpr int HX = TX + 2, HY = D >= 2 ? TY + 2 : 1, HZ = D >= 3 ? TZ + 2 : 1;
+  constexpr int OY = D >= 2 ? TY : 1, OZ = D >= 3 ? TZ : 1;
+  __shared__ float a[HX * HY * HZ];
+  __shared__ float b[TX * HY * HZ];
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const int tile = blockIdx.x;
+  const int x0 = (tile % ntx) * TX;
+  const int y0 = ((tile / ntx) % nty) * OY;
+  const int z0 = (tile / (ntx * nty)) * OZ;
+  const long long P = g.plane;
+  const float* s = src + (long long)blockIdx.y * P;
+  float* d = dst + (long long)blockIdx.y * P;
+  // tile coordinates run from -1 to n + T - 1: one conditional wrap suffices
+  // when the extent is larger than the tile (else, tiny grids, a modulo)
+  const bool fast = n0 > TX && (D < 2 || n1 > TY) && (D < 3 || n2 > TZ);
+  for (int t = threadIdx.x; t < HX * HY * HZ; t += blockDim.x) {
+    const int lx = t % HX, r = t / HX, ly = r % HY, lz = r / HY;
+    int gx = x0 + lx - 1, gy = D >= 2 ? y0 + ly - 1 : 0, gz = D >= 3 ? z0 + lz - 1 : 0;
+    if (fast) {
+      gx = wrap1(gx, n0);
+      if (D >= 2) gy = wrap1(gy, n1);
+      if (D >= 3) gz = wrap1(gz, n2);
+    } else {
+      gx = wrapi(gx, n0);
+      if (D >= 2) gy = wrapi(gy, n1);
+      if (D >= 3) gz = wrapi(gz, n2);
+    }
+    a[t] = s[(long long)gx + (long long)n0 * (gy + (long long)n1 * gz)];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < TX * HY * HZ; t += blockDim.x) {  // x sub-pass: a -> b
+    const int lx = t % TX, r = t / TX;
+    const float* q = a + lx + HX * r;
+    b[t] = 0.25f * q[0] + 0.5f * q[1] + 0.25f * q[2];
+  }
+  __syncthreads();
+  const float* res = b;  // result tile, rows of TX
+  if (D >= 2) {
+    for (int t = threadIdx.x; t < TX * TY * HZ; t += blockDim.x) {  // y sub-pass: b -> a
+      const int lx = t % TX, r = t / TX, ly = r % TY, lz = r / TY;
+      const float* q = b + lx + TX * (ly + HY * lz);
+      a[t] = 0.25f * q[0] + 0.5f * q[TX] + 0.25f * q[2 * TX];
+    }
+    __syncthreads();
+    res = a;
+  }
+  for (int t = threadIdx.x; t < TX * OY * OZ; t += blockDim.x) {
+    const int lx = t % TX, r = t / TX, ly = r % OY, lz = r / OY;
+    const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+    if (gx >= n0 || gy >= n1 || gz >= n2) continue;
+    float v;
+    if (D >= 3) {  // z sub-pass straight from the y result
+      const float* q = res + lx + TX * (ly + TY * lz);
+      v = 0.25f * q[0] + 0.5f * q[TX * TY] + 0.25f * q[2 * TX * TY];
+    } else {
+      v = res[t];
+    }
+    d[(long long)gx + (long long)n0 * (gy + (long long)n1 * gz)] = v;
+  }
+}
+
 // Offsets (elements) of the lattice points a-2, a-1, a+1, a+2 along an axis of
 // n points with stride s, periodic.
 struct Nb {
@@ -242,6 +314,29 @@ static cudaError_t launch_filter(const GridDev& g, const T* src, T* dst, int nco
 cudaError_t launch_filter_f32(const GridDev& g, const float* src, float* dst, int ncomp, int axis,
                               cudaStream_t st) {
   return launch_filter<float>(g, src, dst, ncomp, axis, st);
+}
+
+template <int D, int TX, int TY, int TZ>
+static cudaError_t launch_pass(const GridDev& g, const float* src, float* dst, int ncomp,
+                               cudaStream_t st) {
+  const int ntx = (g.n[0] + TX - 1) / TX;
+  const int nty = D >= 2 ? (g.n[1] + TY - 1) / TY : 1;
+  const int ntz = D >= 3 ? (g.n[2] + TZ - 1) / TZ : 1;
+  const long long tiles = (long long)ntx * nty * ntz;
+  if (tiles > 0x7fffffffLL || ncomp > 65535) return cudaErrorInvalidValue;
+  k_filter_pass<D, TX, TY, TZ><<<dim3((unsigned)tiles, (unsigned)ncomp), 256, 0, st>>>(
+      src, dst, g, ntx, nty);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_filter_pass_f32(const GridDev& g, const float* src, float* dst, int ncomp,
+                                   cudaStream_t st) {
+  switch (g.dim) {
+    case 1: return launch_pass<1, 1024, 1, 1>(g, src, dst, ncomp, st);
+    case 2: return launch_pass<2, 32, 32, 1>(g, src, dst, ncomp, st);
+    case 3: return launch_pass<3, 32, 8, 8>(g, src, dst, ncomp, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_filter_f64(const GridDev& g, const double* src, double* dst, int ncomp,

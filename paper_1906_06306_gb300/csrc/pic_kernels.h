@@ -17,6 +17,9 @@ constexpr int kMaxSpecies = 4;
 #ifndef PIC_PUSH_MIN_BLOCKS
 #define PIC_PUSH_MIN_BLOCKS 5
 #endif
+#ifndef PIC_PUSH_MIN_BLOCKS_3D
+#define PIC_PUSH_MIN_BLOCKS_3D 2
+#endif
 #ifndef PIC_PREFETCH
 #define PIC_PREFETCH 0
 #endif
@@ -72,6 +75,10 @@ cudaError_t launch_filter_f32(const GridDev& g, const float* src, float* dst, in
                               cudaStream_t st);
 cudaError_t launch_filter_f64(const GridDev& g, const double* src, double* dst, int ncomp,
                               int axis, cudaStream_t st);
+// one full Binomial2 pass (every gridded axis, x first) over ncomp consecutive
+// planes, src -> dst, the sub-passes fused through shared memory
+cudaError_t launch_filter_pass_f32(const GridDev& g, const float* src, float* dst, int ncomp,
+                                   cudaStream_t st);
 
 struct SortParams {
   GridDev g;
