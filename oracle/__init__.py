@@ -26,6 +26,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pic_oracle.c")
+_SRC_ADJ = os.path.join(_HERE, "pic_oracle_adj.c")
 _HDR = os.path.join(_HERE, "pic_oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
@@ -40,11 +41,11 @@ class _Grid(ctypes.Structure):
 
 def build(force: bool = False) -> str:
     """Compile pic_oracle.c into liboracle.so (no fast-math, no FMA contraction)."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_ADJ, _HDR))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"])
+                               "-shared", "-fPIC", _SRC, _SRC_ADJ, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -265,6 +266,41 @@ def step_shock(g: Grid, F, species, injector, s0: int, passes: int = 0, nsteps: 
         step(g, F, species, passes=passes, nsteps=1)
         if injector is not None:
             injector.inject(s0 + t, species)
+
+
+def adj_step(g: Grid, F, species, xbar, ubar, A, passes: int = 0):
+    """Reverse of one `step` (FDTD2, Boris): F and species are the forward
+    state at the start of the step; A (adjoint field planes), xbar[s]
+    (float64[3, n]) and ubar[s] (float64[3, n]) go in as the gradient with
+    respect to the state after the step and come out with respect to the
+    state before it."""
+    ns = len(species)
+    xs = (_D * ns)(*[_p(s.x) for s in species])
+    us = (_D * ns)(*[_p(s.u) for s in species])
+    n = (ctypes.c_long * ns)(*[s.n for s in species])
+    q = (ctypes.c_double * ns)(*[s.q for s in species])
+    m = (ctypes.c_double * ns)(*[s.m for s in species])
+    xb = (_D * ns)(*[_p(a) for a in xbar])
+    ub = (_D * ns)(*[_p(a) for a in ubar])
+    work = np.zeros(9 * g.ncells)
+    lib().orc_adj_step(g.c_struct(), _p(F), xs, us, n, q, m, ctypes.c_int(ns), ctypes.c_int(passes),
+                       xb, ub, _p(A), _p(work))
+
+
+def gradient(g: Grid, F, species, nsteps: int, loss_grad, passes: int = 0):
+    """Gradient of a loss of the state after `nsteps` steps with respect to
+    the initial state, by the discrete adjoint: the forward states are kept
+    (small cases), then adj_step runs backwards.  loss_grad(F, species) returns
+    (A, xbar, ubar) for the final state.  Returns (A, xbar, ubar) at t = 0;
+    F and species are left at the final state."""
+    states = []
+    for _ in range(nsteps):
+        states.append((F.copy(), [Species(s.q, s.m, s.x.copy(), s.u.copy()) for s in species]))
+        step(g, F, species, passes=passes)
+    A, xbar, ubar = loss_grad(F, species)
+    for Fs, sps in reversed(states):
+        adj_step(g, Fs, sps, xbar, ubar, A, passes=passes)
+    return A, xbar, ubar
 
 
 def charge_density(g: Grid, species):

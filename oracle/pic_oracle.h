@@ -101,6 +101,24 @@ long orc_inject(const double* xt, const double* ut, long nt, long lt, double x0,
 void orc_step(const orc_grid* g, double* F, double** x, double** u, const long* n,
               const double* q, const double* m, int ns, int passes, double* work);
 
+/* Reverse mode (discrete adjoint) of orc_step, FDTD2 and Boris only
+ * (pic_oracle_adj.c).  A holds adjoint field planes in the field layout
+ * (Ebar, Bbar; the J planes are scratch): on entry the gradient of a loss
+ * with respect to E and B after the step, on exit with respect to E and B
+ * before it.  xbar[s] (gridded rows of float[3][n]) and ubar[s] likewise for
+ * the particles.  F, x, u: the forward state at the start of the step.  work
+ * must hold 9 * ncells doubles. */
+void orc_adj_step(const orc_grid* g, const double* F, double** x, double** u, const long* n,
+                  const double* q, const double* m, int ns, int passes, double** xbar,
+                  double** ubar, double* A, double* work);
+/* Pieces of orc_adj_step: adjoints of orc_push_half_b, of orc_push_e with
+ * orc_add_cur (Jbar = -Ebar), and of the particle part (F1 = E and the B of
+ * the first half step). */
+void orc_adj_push_half_b(const orc_grid* g, double* A);
+void orc_adj_push_e(const orc_grid* g, double* A);
+void orc_adj_particles(const orc_grid* g, const double* F1, const double* x, const double* u,
+                       long n, double q, double qm, double* xbar, double* ubar, double* A);
+
 /* Charge density on the nodes, first-order (cloud-in-cell) shape, added into
  * rho[nz][ny][nx]. */
 void orc_charge_density(const orc_grid* g, const double* x, long n, double q, double* rho);
