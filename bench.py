@@ -534,6 +534,144 @@ def run_batched(args):
     return 0
 
 
+def run_adjoint(args):
+    """Gradient of the magnetic energy after --steps steps (200 for the 256^2
+    box of the differentiable set-up: 32 particles per cell per species,
+    theta 0.1, sigma 1, 64 seeded modes of dB ~ 0.1 B0) with respect to the 64
+    mode amplitudes and every initial four-velocity: forward run with
+    checkpoints every 20 steps, then the reverse sweep (recompute + adjoint
+    steps).  value = particle-steps of the forward run per second of forward +
+    reverse.  Replicas only for N > 1."""
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import workloads
+    from paper_1906_06306_gb300 import Simulation
+    from paper_1906_06306_gb300 import binding as B
+    from paper_1906_06306_gb300.adjoint import MagneticEnergy, MagneticEnergyProblem
+
+    n = args.grid or 256
+    pl, mf, amps = workloads.adjoint_box(n=n, ppc=32, theta=0.1, sigma=1.0, modes=8, seed=1239)
+    dev = torch.device(f"cuda:{local}")
+    sim = Simulation.from_plasma(pl, device=f"cuda:{local}")
+    prob = MagneticEnergyProblem(sim, mf, nsteps=args.warmup, checkpoint_every=20)
+    a = torch.tensor(amps, device=dev)
+    u0 = prob.u0()
+    prob.run(a, u0)  # warm-up: a short gradient
+    prob.gradient()
+    prob.nsteps = args.steps
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    B.pic_kernel_times(sim.ctx)
+    B.pic_timing(sim.ctx, True)
+    t0, t1, t2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    t0.record(sim.stream)
+    loss = prob.run(a, u0)
+    t1.record(sim.stream)
+    g_a, g_u = prob.gradient()
+    t2.record(sim.stream)
+    torch.cuda.synchronize(dev)
+    ms_f, ms_b = t0.elapsed_time(t1), t1.elapsed_time(t2)
+    kt = B.pic_kernel_times(sim.ctx)
+    B.pic_timing(sim.ctx, False)
+    clocks = sampler.stop()
+    ms = ms_f + ms_b
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    npart = pl.nparticles
+    value = world * npart * args.steps / (ms * 1e-3)
+    # end to end through the autograd function: parameters from pinned host
+    # memory, gradients back to the host
+    ha = torch.from_numpy(amps).pin_memory()
+    hu = u0.cpu().pin_memory()
+    te = time.perf_counter()
+    ad = ha.to(dev, non_blocking=True).requires_grad_()
+    ud = hu.to(dev, non_blocking=True).requires_grad_()
+    lo = MagneticEnergy.apply(ad, ud, prob)
+    lo.backward()
+    ga_h, gu_h = ad.grad.cpu(), ud.grad.cpu()
+    e_s = time.perf_counter() - te
+    adj_ms, adj_n = kt["adjoint"]
+    avg_adj = adj_ms * 1e-3 / max(adj_n, 1)
+    # per adjoint step: particle state read (4 + 8 + 12 B) and gradients read and
+    # written (2 x (8 + 12) B); E, B read and their gradients added once per cell
+    alg = npart * (24 + 40) + pl.ncells * 4 * (6 + 9 + 12)
+    peak, peak_kind = hbm_peak()
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": dict(workload="adjoint_2d3v", grid=[n, n], ppc_per_species=32, species=2,
+                       theta=0.1, sigma=1.0, modes=int(mf.shape[0]), checkpoint_every=20,
+                       particles=npart, loss=float(loss),
+                       grad_norm_amps=float(g_a.norm()), grad_norm_u0=float(g_u.norm()),
+                       forward_ms=ms_f, reverse_ms=ms_b,
+                       l2=("each adjoint step reads its own stored forward state (%.2f GB) and"
+                           " the gradients (%.2f GB): %.2f GB per step, larger than L2; no flush")
+                       % (npart * 24 / 1e9, npart * 20 / 1e9, npart * 44 / 1e9),
+                       parallelism="replicas" if world > 1 else "single-gpu"),
+        "roofline": {"bound": "hbm", "achieved": alg / avg_adj / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": alg / avg_adj / 1e9 / peak, "traffic": None,
+                     "kernel": "pic_adjoint_step (field adjoints + k_adj_particles)",
+                     "peak_source": peak_kind, "avg_launch_us": avg_adj * 1e6,
+                     "alg_bytes_per_launch": alg},
+        "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in kt.items()},
+        "clocks": clocks,
+        "e2e": {"value": world * npart * args.steps / e_s, "unit": "particle-steps/s",
+                "h2d_bytes_per_step": int((ha.numel() + hu.numel()) * 4 / args.steps),
+                "d2h_bytes_per_step": int((ga_h.numel() + gu_h.numel()) * 4 / args.steps),
+                "note": "MagneticEnergy.apply + backward from pinned host parameters"},
+    }
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = adjoint_cpu_baseline()
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def adjoint_cpu_baseline(n=32, nsteps=40):
+    """The oracle's gradient (forward states kept, adjoint sweep) of the same
+    loss on a small box of the same plasma (one host thread)."""
+    import numpy as np
+
+    import oracle
+    import workloads
+
+    oracle.build()
+    pl, mf, amps = workloads.adjoint_box(n=n, ppc=32, theta=0.1, sigma=1.0, modes=8, seed=1239)
+    g, F, sp = oracle.from_plasma(pl)
+    F[3:6] += np.tensordot(amps.astype(np.float64), mf.astype(np.float64), axes=1)
+
+    def loss_grad(Ff, spf):
+        A = g.zeros()
+        A[3:6] = Ff[3:6]
+        return A, [np.zeros((3, s.n)) for s in spf], [np.zeros((3, s.n)) for s in spf]
+
+    t0 = time.perf_counter()
+    oracle.gradient(g, F, sp, nsteps, loss_grad)
+    dt = time.perf_counter() - t0
+    return {"value": pl.nparticles * nsteps / dt, "unit": "particle-steps/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"adjoint_2d3v gradient on a {n}x{n} box ({pl.nparticles} particles), "
+                      f"{nsteps} steps forward + adjoint, FP64, 1 host thread"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -552,13 +690,27 @@ def main():
     ap.add_argument("--grid", type=int, default=0,
                     help="box size (2D side, 1D length, 3D x-length with y = z = x/8); "
                          "0 = the workload's benchmark size")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched_weibel"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched_weibel", "adjoint_2d3v"],
                     default="turbulence_2d3v")
     ap.add_argument("--boxes", type=int, default=256, help="boxes of the batched_weibel ensemble")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
+        if args.workload == "adjoint_2d3v":
+            rank, _, _ = dist_env()
+            if rank == 0:
+                cb = adjoint_cpu_baseline()
+                print(json.dumps({"impl": "reference", "metric": METRIC, "value": cb["value"],
+                                  "unit": cb["unit"], "n_gpus": args.gpus, "steps": args.steps,
+                                  "warmup": args.warmup, "higher_is_better": True,
+                                  "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                                  "data": "synthetic",
+                                  "config": {"workload": "adjoint_2d3v", "sample": cb["sample"]},
+                                  "cpu_baseline": cb,
+                                  "e2e": {"value": cb["value"], "unit": cb["unit"],
+                                          "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+            return 0
         if args.workload == "batched_weibel":
             print(json.dumps({"impl": "reference", "unavailable":
                               "the oracle steps one box at a time; time it with "
@@ -567,6 +719,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched_weibel":
         return run_batched(args)
+    if args.workload == "adjoint_2d3v":
+        return run_adjoint(args)
     return run_ours(args)
 
 

@@ -116,7 +116,8 @@ typedef struct {
 #define PIC_KERNEL_FILTER 3 /* one Binomial2 pass */
 #define PIC_KERNEL_SORT 4   /* tile sort: count + scan + scatter + copy back */
 #define PIC_KERNEL_BOUNDARY 5 /* wall fields and injection (pic_set_shock) */
-#define PIC_KERNEL_KINDS 6
+#define PIC_KERNEL_ADJOINT 6  /* pic_adjoint_step */
+#define PIC_KERNEL_KINDS 7
 
 /* Create a context for `grid`, `nspecies` (1..PIC_MAX_SPECIES) species, Courant
  * number c (0 < c < 1 for the explicit scheme, Sect. 2.3) and time step dt,
@@ -230,6 +231,40 @@ typedef struct {
   pic_host_species tmpl[PIC_MAX_SPECIES];
 } pic_shock;
 pic_status pic_set_shock(pic_ctx* ctx, const pic_shock* shock);
+
+/* Discrete adjoint (reverse mode) of one pic_step, for gradients of a loss
+ * of the state after many steps with respect to an earlier state (the
+ * paper's method has no adjoint; this differentiates its time step).  The
+ * step is read as the composition
+ *   B1 = B - (c/2) curl+ E;  e, b = gather(E, B1; x);  u' = Boris(u, e, b);
+ *   x' = x + c u'/gamma(u');  J = sum ZigZag(x, x');  B2 = B1 - (c/2) curl+ E;
+ *   E' = E + c curl- B2 - F^p J      (Eqs. fdB, fdX, fdE; Apps. C, D; Table 1)
+ * and reversed exactly: (curl+)^T = curl- on the periodic lattice, the
+ * Binomial2 filter F is symmetric, and each particle goes back through the
+ * chain rule of ZigZag, move, Boris and gather (its cell and the branch of
+ * the ZigZag relay point are those of the forward step, where the step is
+ * differentiable).
+ *
+ * fwd_fields: the caller's device copy of the 9 field planes at the start of
+ * the step (E^n, B^(n-1/2)); sp[s].cell/off/u: the species' particles at the
+ * start of the step, in the slots the adjoint arrays use (rows of the
+ * species' cap, count from pic_particle_counts); sp[s].xbar (float[dim][cap])
+ * and sp[s].ubar (float[3][cap]): on entry the gradient with respect to the
+ * particles after the step, on exit before it.  adj_fields (9 planes): on
+ * entry the gradient with respect to E and B after the step (the J planes
+ * are scratch), on exit with respect to E and B before it (J planes zero).
+ * Uses the context's grid, Courant number, species q/m and filter passes;
+ * PIC_ERR_STATE unless the field solver is FDTD2, the pusher Boris and there
+ * are no shock boundaries.  Enqueued on the context's stream. */
+typedef struct {
+  const int32_t* cell;
+  const float* off;
+  const float* u;
+  float* xbar;
+  float* ubar;
+} pic_adjoint_species;
+pic_status pic_adjoint_step(pic_ctx* ctx, const float* fwd_fields, const pic_adjoint_species* sp,
+                            float* adj_fields);
 
 /* Current particle count of each species (grows with injection): writes
  * nout >= nspecies values.  No synchronisation: the counts are host state. */

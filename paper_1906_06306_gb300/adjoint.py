@@ -1,0 +1,169 @@
+"""Gradients through many PIC steps by the discrete adjoint.
+
+`Adjoint` runs a Simulation forward with a checkpoint of the state every K
+steps; the reverse sweep recomputes each segment of K steps from its
+checkpoint (keeping those K states) and runs pic_adjoint_step backwards over
+them.  `MagneticEnergy` wraps it in a torch.autograd.Function: the magnetic
+energy 0.5 sum B^2 after n steps as a function of the amplitudes of the
+initial magnetic perturbation modes and of the initial four-velocities.
+
+Every step, forward and adjoint, runs in libpic's kernels; PyTorch holds the
+checkpoints and does the bookkeeping of the parametrisation (the initial
+field as amplitudes times mode fields, and its transpose).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import binding as B
+
+NO_SORT = 1 << 30  # sort cadence for adjoint runs: particle slots stay fixed
+
+
+class Adjoint:
+    """Forward run of `sim` with checkpoints every `checkpoint_every` steps and
+    the reverse sweep.  Tile sorting is switched off on `sim` (the adjoint
+    arrays follow the particle slots, which a sort would permute); particles
+    that leave their tile take the global-memory path instead."""
+
+    def __init__(self, sim, checkpoint_every: int = 20):
+        if checkpoint_every < 1:
+            raise ValueError("checkpoint_every must be >= 1")
+        self.sim = sim
+        self.K = int(checkpoint_every)
+        self.nsteps = 0
+        self.ckpt = []
+        sim.set_tuning(sort_every=NO_SORT)
+
+    def _state(self):
+        s = self.sim
+        return (s.fields.clone(),
+                [(d["cell"].clone(), d["off"].clone(), d["u"].clone()) for d in s.species])
+
+    def _restore(self, st):
+        F, sp = st
+        self.sim.fields.copy_(F)
+        for d, (c, o, u) in zip(self.sim.species, sp):
+            d["cell"].copy_(c)
+            d["off"].copy_(o)
+            d["u"].copy_(u)
+
+    def forward(self, nsteps: int):
+        """nsteps steps of the simulation, keeping a checkpoint every K."""
+        self.nsteps = int(nsteps)
+        self.ckpt = []
+        for t in range(self.nsteps):
+            if t % self.K == 0:
+                self.ckpt.append(self._state())
+            self.sim.step(1)
+
+    def zeros(self):
+        """Adjoint buffers for the current simulation: (fields [9, ...],
+        xbar per species [D, cap], ubar per species [3, cap]), zero."""
+        torch = self.sim.torch
+        A = torch.zeros_like(self.sim.fields)
+        xb = [torch.zeros((self.sim.dim, d["cap"]), dtype=torch.float32, device=self.sim.device)
+              for d in self.sim.species]
+        ub = [torch.zeros((3, d["cap"]), dtype=torch.float32, device=self.sim.device)
+              for d in self.sim.species]
+        return A, xb, ub
+
+    def backward(self, A, xbar, ubar):
+        """Reverse sweep: A, xbar, ubar hold the gradient with respect to the
+        final state and are turned, in place, into the gradient with respect
+        to the state at the start of the forward run.  The simulation is left
+        at the final state."""
+        sim = self.sim
+        final = self._state()
+        for seg in reversed(range(len(self.ckpt))):
+            t0 = seg * self.K
+            t1 = min(self.nsteps, t0 + self.K)
+            self._restore(self.ckpt[seg])
+            states = []
+            for _ in range(t0, t1):
+                states.append(self._state())
+                sim.step(1)
+            for F, sp in reversed(states):
+                asp = [B.pic_adjoint_species(c.data_ptr(), o.data_ptr(), u.data_ptr(),
+                                             xb.data_ptr(), ub.data_ptr())
+                       for (c, o, u), xb, ub in zip(sp, xbar, ubar)]
+                B.pic_adjoint_step(sim.ctx, F.data_ptr(), asp, A.data_ptr())
+        self._restore(final)
+        return A, xbar, ubar
+
+
+class MagneticEnergyProblem:
+    """The differentiable set-up: a Simulation whose initial B is
+    base B + sum_m amps[m] modes[m] and whose initial four-velocities are
+    given, run for nsteps with checkpoints every K.  modes: float32 array
+    [M, 3, nz, ny, nx] of B perturbation fields (planes Bx, By, Bz)."""
+
+    def __init__(self, sim, modes, nsteps: int, checkpoint_every: int = 20):
+        torch = sim.torch
+        self.sim = sim
+        self.adj = Adjoint(sim, checkpoint_every)
+        self.nsteps = int(nsteps)
+        self.modes = torch.as_tensor(np.asarray(modes, dtype=np.float32), device=sim.device)
+        self.base_fields = sim.fields.clone()
+        self.base = [(d["cell"].clone(), d["off"].clone()) for d in sim.species]
+        self.counts = sim.counts()
+
+    def u0(self):
+        """Initial four-velocities of every species, concatenated: [3, N]."""
+        return self.sim.torch.cat([d["u"][:, :n].clone() for d, n in zip(self.sim.species,
+                                                                         self.counts)], dim=1)
+
+    def run(self, amps, u0):
+        """Set the initial state from (amps, u0), run forward, return the
+        magnetic energy 0.5 sum B^2 (FP64 reduction on the GPU)."""
+        sim = self.sim
+        F = self.base_fields.clone()
+        F[3:6] += (amps.to(F.dtype)[:, None, None, None, None] * self.modes).sum(0)
+        sim.fields.copy_(F)
+        off = 0
+        for d, (c, o), n in zip(sim.species, self.base, self.counts):
+            d["cell"].copy_(c)
+            d["off"].copy_(o)
+            d["u"][:, :n].copy_(u0[:, off:off + n].to(d["u"].dtype))
+            off += n
+        self.adj.forward(self.nsteps)
+        return sim.energies()[1]
+
+    def gradient(self, g=1.0):
+        """Gradient of g * loss with respect to (amps, u0) after run()."""
+        A, xb, ub = self.adj.zeros()
+        A[3:6] = g * self.sim.fields[3:6]
+        self.adj.backward(A, xb, ub)
+        torch = self.sim.torch
+        g_amps = (self.modes * A[3:6][None]).flatten(1).sum(1)
+        g_u0 = torch.cat([u[:, :n] for u, n in zip(ub, self.counts)], dim=1)
+        return g_amps, g_u0
+
+
+def _make_function():
+    import torch
+
+    class MagneticEnergy(torch.autograd.Function):
+        """loss = MagneticEnergy.apply(amps, u0, problem): the magnetic energy
+        after problem.nsteps steps; backward by the discrete adjoint."""
+
+        @staticmethod
+        def forward(ctx, amps, u0, problem):
+            ctx.problem = problem
+            loss = problem.run(amps.detach(), u0.detach())
+            return torch.tensor(loss, dtype=torch.float64, device=amps.device)
+
+        @staticmethod
+        def backward(ctx, grad):
+            g_amps, g_u0 = ctx.problem.gradient(float(grad))
+            return g_amps.to(torch.float32), g_u0.to(torch.float32), None
+
+    return MagneticEnergy
+
+
+def __getattr__(name):
+    if name == "MagneticEnergy":
+        fn = _make_function()
+        globals()["MagneticEnergy"] = fn
+        return fn
+    raise AttributeError(name)

@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_CUDA", 3: "PIC_ERR_OO
                 4: "PIC_ERR_TIMEOUT", 5: "PIC_ERR_STATE"}
 PIC_MAX_SPECIES = 4
 PIC_FIELD_B_HALF, PIC_FIELD_E = 0, 1
-KERNEL_KINDS = ["push", "b_half", "e_update", "filter", "sort", "boundary"]
+KERNEL_KINDS = ["push", "b_half", "e_update", "filter", "sort", "boundary", "adjoint"]
 
 
 class pic_grid(ctypes.Structure):
@@ -40,6 +40,11 @@ class pic_shock(ctypes.Structure):
                 ("tmpl", pic_host_species * PIC_MAX_SPECIES)]
 
 
+class pic_adjoint_species(ctypes.Structure):
+    _fields_ = [("cell", c_void_p), ("off", c_void_p), ("u", c_void_p), ("xbar", c_void_p),
+                ("ubar", c_void_p)]
+
+
 class pic_tuning(ctypes.Structure):
     _fields_ = [("tile", c_int * 3), ("halo", c_int), ("sort_every", c_int),
                 ("filter_passes", c_int), ("chunk", c_int)]
@@ -55,6 +60,7 @@ SIGNATURES = {
     "pic_set_field_solver": (c_int, [_P, c_int]),
     "pic_set_shock": (c_int, [_P, ctypes.POINTER(pic_shock)]),
     "pic_particle_counts": (c_int, [_P, ctypes.POINTER(c_int64), c_int]),
+    "pic_adjoint_step": (c_int, [_P, c_void_p, ctypes.POINTER(pic_adjoint_species), c_void_p]),
     "pic_sort": (c_int, [_P]),
     "pic_gather_push": (c_int, [_P]),
     "pic_deposit": (c_int, [_P]),
@@ -144,6 +150,13 @@ def pic_set_shock(ctx, shock: pic_shock) -> None:
     """Conducting wall and receding injector along x (Sect. 4.2); the template
     host arrays referenced by `shock` are copied by the library."""
     _check(_lib.pic_set_shock(ctx, ctypes.byref(shock)), ctx)
+
+
+def pic_adjoint_step(ctx, fwd_fields_ptr: int, species, adj_fields_ptr: int) -> None:
+    """Reverse of one pic_step: species is a sequence of pic_adjoint_species
+    (forward particles at the start of the step, gradients xbar/ubar in place)."""
+    arr = (pic_adjoint_species * len(species))(*species)
+    _check(_lib.pic_adjoint_step(ctx, c_void_p(fwd_fields_ptr), arr, c_void_p(adj_fields_ptr)), ctx)
 
 
 def pic_particle_counts(ctx, nspecies: int):

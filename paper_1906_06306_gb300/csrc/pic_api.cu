@@ -67,6 +67,7 @@ struct pic_ctx {
   void* d_tmpl = nullptr;                    // template records of every species
   int* d_wlist = nullptr;                    // wall crossers, room for cap[s] per species
   int* d_wcount = nullptr;                   // entries per species
+  float* d_adjF = nullptr;                   // forward fields of an adjoint step (9 planes)
   long long steps = 0;
   bool timing = false;
   std::vector<TimedLaunch> pending;
@@ -126,6 +127,7 @@ void free_all(pic_ctx* ctx) {
   dfree(ctx->d_tmpl);
   dfree(ctx->d_wlist);
   dfree(ctx->d_wcount);
+  dfree(ctx->d_adjF);
   for (auto& t : ctx->pending) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
@@ -655,6 +657,64 @@ pic_status pic_set_shock(pic_ctx* ctx, const pic_shock* sh) {
   ctx->shock_steps = 0;
   // the fields entering the first step satisfy the wall's boundary
   PIC_CK(ctx, launch_wall_fields(ctx->g, ctx->F, ctx->wall, ctx->i_zero, ctx->st));
+  return PIC_OK;
+}
+
+pic_status pic_adjoint_step(pic_ctx* ctx, const float* fwd_fields, const pic_adjoint_species* sp,
+                            float* adj_fields) {
+  if (!ctx) return PIC_ERR_ARG;
+  if (!fwd_fields || !sp || !adj_fields) return set_err(ctx, PIC_ERR_ARG, "NULL argument");
+  if (ctx->g.order != 2 || ctx->pusher != PIC_PUSHER_BORIS || ctx->shock)
+    return set_err(ctx, PIC_ERR_STATE, "the adjoint covers FDTD2, Boris and periodic boxes");
+  const int D = ctx->grid.dim;
+  for (int s = 0; s < ctx->ns; ++s)
+    if (ctx->sp[s].n > 0 && (!sp[s].cell || !sp[s].off || !sp[s].u || !sp[s].xbar || !sp[s].ubar))
+      return set_err(ctx, PIC_ERR_ARG, "adjoint species buffers are NULL");
+  const long long P = ctx->g.plane;
+  if (!ctx->d_adjF) PIC_CK(ctx, dalloc(&ctx->d_adjF, 9 * (size_t)P));
+  if (!ctx->d_jtmp) PIC_CK(ctx, dalloc(&ctx->d_jtmp, 3 * (size_t)P));
+  AdjParams AP{};
+  AP.g = ctx->g;
+  AP.F1 = ctx->d_adjF;
+  AP.A = adj_fields;
+  AP.nspecies = ctx->ns;
+  for (int s = 0; s < ctx->ns; ++s) {
+    AdjSpecies& S = AP.sp[s];
+    S.q = ctx->sp[s].q;
+    S.qm = ctx->sp[s].q / ctx->sp[s].m;
+    S.n = ctx->sp[s].n;
+    S.ld = ctx->cap[s];
+    S.cell = sp[s].cell;
+    S.off = sp[s].off;
+    S.u = sp[s].u;
+    S.xbar = sp[s].xbar;
+    S.ubar = sp[s].ubar;
+  }
+  (void)D;
+  const cudaError_t e = timed(ctx, PIC_KERNEL_ADJOINT, [&]() -> cudaError_t {
+    // forward fields seen by the particles: E and B1 = B - (c/2) curl+ E
+    cudaError_t r = cudaMemcpyAsync(ctx->d_adjF, fwd_fields, sizeof(float) * 6 * P,
+                                    cudaMemcpyDeviceToDevice, ctx->st);
+    if (r == cudaSuccess) r = launch_b_half(ctx->g, ctx->d_adjF, 0, ctx->st);
+    if (r == cudaSuccess) r = launch_adj_e(ctx->g, adj_fields, ctx->st);  // E' = E + c curl- B2 - Jf
+    float* J = adj_fields + JX * P;
+    float* a = J;
+    float* b = ctx->d_jtmp;
+    for (int p = 0; p < ctx->tun.filter_passes && r == cudaSuccess; ++p) {  // Jf = F^p J
+      r = launch_filter_pass_f32(ctx->g, a, b, 3, ctx->st);
+      float* t = a;
+      a = b;
+      b = t;
+    }
+    if (r == cudaSuccess && a != J)
+      r = cudaMemcpyAsync(J, a, sizeof(float) * 3 * P, cudaMemcpyDeviceToDevice, ctx->st);
+    if (r == cudaSuccess) r = launch_adj_b_half(ctx->g, adj_fields, ctx->st);  // B2 = B1 - ...
+    if (r == cudaSuccess) r = launch_adj_particles(AP, ctx->st);             // particles
+    if (r == cudaSuccess) r = launch_adj_b_half(ctx->g, adj_fields, ctx->st);  // B1 = B - ...
+    if (r == cudaSuccess) r = cudaMemsetAsync(J, 0, sizeof(float) * 3 * P, ctx->st);
+    return r;
+  });
+  if (e != cudaSuccess) return cuda_fail(ctx, "adjoint step", e);
   return PIC_OK;
 }
 

@@ -136,4 +136,28 @@ struct InjectParams {
 };
 cudaError_t launch_inject(const InjectParams& P, cudaStream_t st);
 
+// Discrete adjoint of the step (FDTD2, Boris, periodic; pic_adjoint.cu).
+struct AdjSpecies {
+  float q, qm;
+  long long n, ld;        // particles, row length of the arrays
+  const int* cell;        // forward particles at the start of the step
+  const float* off;       // [D][ld]
+  const float* u;         // [3][ld]
+  float* xbar;            // [D][ld] gradient of the position (in: after, out: before)
+  float* ubar;            // [3][ld] gradient of u
+};
+struct AdjParams {
+  GridDev g;
+  const float* F1;  // forward E and the B of the first half step (9-plane layout)
+  float* A;         // adjoint planes: Ebar, Bbar, Jbar
+  int nspecies;
+  AdjSpecies sp[kMaxSpecies];
+};
+// Bbar += c curl+ Ebar, Jbar = -Ebar (adjoint of the E update with -J)
+cudaError_t launch_adj_e(const GridDev& g, float* A, cudaStream_t st);
+// Ebar -= (c/2) curl- Bbar (adjoint of a B half step)
+cudaError_t launch_adj_b_half(const GridDev& g, float* A, cudaStream_t st);
+// adjoint of gather + Boris + move + ZigZag for every particle
+cudaError_t launch_adj_particles(const AdjParams& P, cudaStream_t st);
+
 }  // namespace pic

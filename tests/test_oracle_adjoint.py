@@ -147,3 +147,17 @@ def test_magnetic_energy_gradient_of_a_weibel_run(orc):
             return loss(Fs, sps)
         fd = (atf(1) - atf(-1)) / (2 * h)
         assert A[comp, 0, 0, i] == pytest.approx(fd, rel=1e-5, abs=1e-12)
+
+
+def test_adjoint_box_modes_are_solenoidal_and_scaled():
+    """The perturbation modes of the differentiable set-up are lattice curls
+    (div+ B = 0 at the cell centres) and the seeded amplitudes give the
+    requested rms dB / B0."""
+    import workloads
+
+    pl, mf, amps = workloads.adjoint_box(n=32, ppc=2, modes=4, db_over_b0=0.1, seed=3)
+    bx, by = mf[:, 0, 0].astype(np.float64), mf[:, 1, 0].astype(np.float64)
+    div = (np.roll(bx, -1, axis=2) - bx) + (np.roll(by, -1, axis=1) - by)
+    assert np.abs(div).max() < 1e-6
+    db = np.tensordot(amps.astype(np.float64), mf.astype(np.float64), axes=1)
+    assert np.sqrt((db ** 2).sum(0).mean()) == pytest.approx(0.1 * pl.meta["b0"], rel=1e-5)

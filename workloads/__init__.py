@@ -19,6 +19,8 @@ from .plasma import (  # noqa: F401
     shock_tube,
     injected_count,
     weibel_box,
+    magnetic_modes,
+    adjoint_box,
     weibel_ensemble,
     CONFIGS,
 )

@@ -305,6 +305,53 @@ def injected_count(pl: Plasma, steps: int) -> int:
     return int(math.ceil(front / sh["lt"] * nt)) + nt
 
 
+def magnetic_modes(n: int, modes: int, seed: int) -> np.ndarray:
+    """Perturbation fields of an n x n periodic box: for every wavenumber pair
+    (m, k) in 1..modes, the lattice curl of
+    A_z = (L / (2 pi |K|)) sin(2 pi m x / L + phi) sin(2 pi k y / L + psi)
+    (|K| = sqrt(m^2 + k^2), seeded phases), so each field is discretely
+    solenoidal with an amplitude of order 1.  float32 [modes^2, 3, 1, n, n],
+    planes Bx (at (i, j+1/2)), By (at (i+1/2, j)), Bz (zero)."""
+    gen = rng(seed)
+    L = float(n)
+    x = np.arange(n, dtype=np.float64)
+    out = np.zeros((modes * modes, 3, 1, n, n), dtype=np.float32)
+    for m in range(1, modes + 1):
+        for k in range(1, modes + 1):
+            phi, psi = 2.0 * math.pi * gen.random(2)
+            K = math.sqrt(m * m + k * k)
+            az = (L / (2.0 * math.pi * K)) * np.outer(np.sin(2.0 * math.pi * k * x / L + psi),
+                                                      np.sin(2.0 * math.pi * m * x / L + phi))
+            idx = (m - 1) * modes + (k - 1)
+            out[idx, 0, 0] = np.roll(az, -1, axis=0) - az
+            out[idx, 1, 0] = -(np.roll(az, -1, axis=1) - az)
+    return out
+
+
+def adjoint_box(n: int = 256, ppc: int = 32, theta: float = 0.1, sigma: float = 1.0,
+                r_p: float = 4.0, modes: int = 8, db_over_b0: float = 0.1, c: float = 0.45,
+                seed: int = 1239):
+    """Differentiable turbulence-like set-up: a 2D3V periodic pair plasma at
+    rest (Maxwell-Juettner theta) with the guide field B0 z-hat of
+    magnetisation sigma (as in turbulence_2d) and an initial perturbation
+    sum_m amps[m] * mode_m over modes^2 fields of magnetic_modes, with seeded
+    amplitudes scaled so that the rms of dB is db_over_b0 * B0.  Returns
+    (plasma without the perturbation, mode fields, amplitudes)."""
+    mean_g = mj_mean_gamma(theta)
+    q_abs = charge_from_skin_depth(c, r_p, ppc, mean_g)
+    b0 = math.sqrt(sigma * ppc * q_abs * c * c * mean_g * 2.0)
+    pl = uniform_plasma(2, n, n, 1, c, ppc, q_abs, theta, seed,
+                        meta=dict(workload="adjoint_2d3v", theta=theta, sigma=sigma, r_p=r_p,
+                                  ppc=ppc, q_abs=q_abs, b0=b0, mean_gamma=mean_g,
+                                  filter_passes=0))
+    pl.fields[5, 0] = np.float32(b0)
+    mf = magnetic_modes(n, modes, seed + 100000)
+    amps = rng(seed + 200000).normal(size=modes * modes)
+    db = np.tensordot(amps, mf.astype(np.float64), axes=1)
+    amps *= db_over_b0 * b0 / math.sqrt(float((db ** 2).sum(0).mean()))
+    return pl, mf, amps.astype(np.float32)
+
+
 def weibel_box(dim: int, n: int, ppc: int, gamma_b: float, theta: float, r_p: float = 10.0,
                c: float = 0.45, seed: int = 0) -> Plasma:
     """One Weibel box: 1D (n cells, beams along +-y as in weibel_1d) or 2D
