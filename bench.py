@@ -174,6 +174,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def job_value(seconds, units, dist=None, device=None):
+    """Whole-job throughput of replicas: every rank processed `units` in
+    `seconds`; the job took as long as its slowest rank (max over ranks) and
+    processed the units of all ranks (sum).  Returns (max seconds, units/s)."""
+    if dist is None:
+        return seconds, units / seconds
+    import torch
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item()) / float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -358,12 +373,8 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     sim.check()
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * done / (ms_max * 1e-3)
+    s_max, value = job_value(ms * 1e-3, done, dist, dev)
+    ms_max = s_max * 1e3
     avg_n = done / max(args.steps, 1)
 
     # ---- end to end through the C ABI with host buffers ----
@@ -394,12 +405,8 @@ def run_ours(args):
             e_done += n_in
             h2d += n_in * rec + hf.numel() * 4
             d2h += n_out * rec + hf.numel() * 4
-        e_s = time.perf_counter() - te
-        if dist is not None:
-            t = torch.tensor([e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_s = float(t.item())
-        e2e = {"value": world * e_done / e_s, "unit": "particle-steps/s",
+        e_s, e_value = job_value(time.perf_counter() - te, e_done, dist, dev)
+        e2e = {"value": e_value, "unit": "particle-steps/s",
                "h2d_bytes_per_step": int(h2d // args.e2e_steps),
                "d2h_bytes_per_step": int(d2h // args.e2e_steps),
                "steps": args.e2e_steps,
@@ -467,6 +474,11 @@ def run_batched(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
     import workloads
     from paper_1906_06306_gb300 import Batch, Simulation
 
@@ -483,6 +495,8 @@ def run_batched(args):
     stream = sims[0].stream
     batch.step(args.warmup)
     torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -503,7 +517,8 @@ def run_batched(args):
     ms_seq = s0.elapsed_time(s1)
     for sm in sims:
         sm.check()
-    value = npart * args.steps / (ms * 1e-3)
+    s_max, value = job_value(ms * 1e-3, npart * args.steps, dist, dev)
+    ms = s_max * 1e3
     alg = sum(float(p.nparticles * 2 * (4 + 4 * p.dim + 12) + p.ncells * 48) for p in plasmas)
     achieved = alg * args.steps / (ms * 1e-3) / 1e9
     peak, peak_kind = hbm_peak()
@@ -531,6 +546,8 @@ def run_batched(args):
     batch.close()
     for sm in sims:
         sm.close()
+    if dist is not None:
+        dist.destroy_process_group()
     return 0
 
 
@@ -585,13 +602,9 @@ def run_adjoint(args):
     kt = B.pic_kernel_times(sim.ctx)
     B.pic_timing(sim.ctx, False)
     clocks = sampler.stop()
-    ms = ms_f + ms_b
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     npart = pl.nparticles
-    value = world * npart * args.steps / (ms * 1e-3)
+    s_max, value = job_value((ms_f + ms_b) * 1e-3, npart * args.steps, dist, dev)
+    ms = s_max * 1e3
     # end to end through the autograd function: parameters from pinned host
     # memory, gradients back to the host
     ha = torch.from_numpy(amps).pin_memory()
@@ -602,7 +615,7 @@ def run_adjoint(args):
     lo = MagneticEnergy.apply(ad, ud, prob)
     lo.backward()
     ga_h, gu_h = ad.grad.cpu(), ud.grad.cpu()
-    e_s = time.perf_counter() - te
+    e_s, e_value = job_value(time.perf_counter() - te, npart * args.steps, dist, dev)
     adj_ms, adj_n = kt["adjoint"]
     avg_adj = adj_ms * 1e-3 / max(adj_n, 1)
     # per adjoint step: particle state read (4 + 8 + 12 B) and gradients read and
@@ -630,7 +643,7 @@ def run_adjoint(args):
                      "alg_bytes_per_launch": alg},
         "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in kt.items()},
         "clocks": clocks,
-        "e2e": {"value": world * npart * args.steps / e_s, "unit": "particle-steps/s",
+        "e2e": {"value": e_value, "unit": "particle-steps/s",
                 "h2d_bytes_per_step": int((ha.numel() + hu.numel()) * 4 / args.steps),
                 "d2h_bytes_per_step": int((ga_h.numel() + gu_h.numel()) * 4 / args.steps),
                 "note": "MagneticEnergy.apply + backward from pinned host parameters"},
