@@ -446,7 +446,8 @@ def run_ours(args):
                            " no flush") % (pl.nparticles * (16 + 4 * pl.dim) / 1e9)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": f"k_particles<{pl.dim},0> (gather+push+move+deposit)",
+                     "kernel": f"k_particles<{pl.dim},{3 if shock else 0}> (gather+push+move+deposit"
+                               + (", conducting-wall variant)" if shock else ")"),
                      "peak_source": peak_kind, "avg_launch_us": avg_push_s * 1e6,
                      "alg_bytes_per_launch": alg},
         "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in kt.items()},

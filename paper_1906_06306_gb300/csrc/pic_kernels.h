@@ -12,7 +12,7 @@ constexpr int kMaxSpecies = 4;
 #define PIC_PUSH_THREADS 256
 #endif
 #ifndef PIC_SPILL_EVERY
-#define PIC_SPILL_EVERY 8
+#define PIC_SPILL_EVERY 16
 #endif
 #ifndef PIC_PUSH_MIN_BLOCKS
 #define PIC_PUSH_MIN_BLOCKS 5
@@ -25,7 +25,11 @@ constexpr int kMaxSpecies = 4;
 #endif
 constexpr int kPushThreads = PIC_PUSH_THREADS;
 constexpr int kSpillEvery = PIC_SPILL_EVERY;  // batches of kPushThreads particles between spills
-constexpr int kQueueCap = 2048;  // shared-memory queue of particles outside the tile window
+// Shared-memory queue of particles outside the tile window.  It is drained at
+// every spill point where it holds anything, and between two spill points at
+// most kSpillEvery batches of kPushThreads particles can be queued, so this
+// capacity can never be exceeded.
+constexpr int kQueueCap = kPushThreads * kSpillEvery;
 
 struct PushParams {
   GridDev g;
