@@ -7,7 +7,8 @@ import pytest
 import oracle
 import workloads
 
-from gpu_helpers import compare_fields, compare_particles, oracle_from_sim, step_floor
+from gpu_helpers import (compare_fields, compare_particles, current_scale, oracle_from_sim,
+                         step_floor)
 
 pytestmark = pytest.mark.gpu
 
@@ -221,4 +222,62 @@ def test_set_shock_rejects_bad_arguments(bad, msg):
     with pytest.raises(B.PicError) as ei:
         sim.set_shock(templates=temps, **args)
     assert ei.value.status == B.PIC_ERR_ARG and msg in str(ei.value)
+    sim.close()
+
+
+def test_full_size_shock_step_sampled_against_oracle(oracle_wall):
+    """The 1024x128x128 shock set-up of the benchmark (wall on x = 1, injector
+    from x = 512, 8 particles per cell per species, 4 filter passes, default
+    3D launch configuration): one pic_step; sampled particles, including ones
+    in the wall's cell that reflect, against the oracle's gather + Boris + move
+    from the same state; every injected particle bit for bit against the
+    oracle's injector; the Gauss residual on the plasma side."""
+    from paper_1906_06306_gb300 import Simulation
+
+    pl = workloads.shock_tube(dim=3, nx=1024, ny=128, nz=128, ppc=8, gamma_flow=10.0,
+                              theta=1e-4, r_p=10.0, wall=1, x_inj=512, lt=64,
+                              filter_passes=4, seed=1238)
+    cap = [s.n + workloads.injected_count(pl, 3) for s in pl.species]
+    sim = Simulation.from_plasma(pl, capacity=cap, tuning=dict(filter_passes=4))
+    sim.set_shock_from_plasma(pl)
+    F0, sp0 = sim.download()
+    n0 = [s["cell"].shape[0] for s in sp0]
+    sim.step(1)
+    sim.check()
+    F1, sp1 = sim.download()
+    g = oracle.Grid(3, pl.nx, pl.ny, pl.nz, pl.c)
+    w, i_zero, inj = oracle.shock_from_plasma(pl)
+    oracle_wall(w, i_zero)
+    Fb = F0.astype(np.float64)
+    oracle.push_half_b(g, Fb)
+    oracle.wall_fields(g, Fb, w, i_zero)
+    rs = np.random.default_rng(31)
+    reflected = 0
+    for s0, s1, n in zip(sp0, sp1, n0):
+        at_wall = np.flatnonzero(s0["cell"] % pl.nx == w)
+        pick = np.concatenate([rs.choice(n, size=20000, replace=False),
+                               rs.choice(at_wall, size=5000, replace=False)])
+        sub = oracle.Species(s0["q"], s0["m"], oracle.positions(g, s0["cell"][pick], s0["off"][:, pick]),
+                             s0["u"][:, pick].astype(np.float64))
+        oracle.push_particles(g, Fb, sub)
+        u1 = s1["u"][:, pick].astype(np.float64)
+        assert (np.abs(u1 - sub.u) <= 1e-5 * np.maximum(1.0, np.abs(sub.u))).all()
+        x1 = oracle.positions(g, s1["cell"][pick], s1["off"][:, pick])
+        assert np.abs(x1 - sub.x).max() < 2e-5
+        reflected += int((sub.u[0] > 0).sum())
+    assert reflected > 1000  # the wall's cell holds particles that bounced
+    # injection of step 0, bit for bit (same double-precision decisions)
+    osp = [oracle.Species(s["q"], s["m"], np.zeros((3, 0)), np.zeros((3, 0))) for s in sp0]
+    counts = inj.inject(0, osp)
+    for s1, n, k, o in zip(sp1, n0, counts, osp):
+        assert s1["cell"].shape[0] == n + k and k > 100000
+        xg = oracle.positions(g, s1["cell"][n:], s1["off"][:, n:])
+        assert np.array_equal(xg, o.x)
+        assert np.array_equal(s1["u"][:, n:].astype(np.float64), o.u)
+    # the pairs' currents cancel almost exactly, so FP32 rounding scales with
+    # the per-species current c sum |q| n / ncells, not with the net field
+    en = sim.energies()
+    jscale = current_scale(g, [oracle.Species(s["q"], s["m"], np.zeros((3, n + k)), np.zeros((3, 1)))
+                               for s, n, k in zip(sp1, n0, counts)])
+    assert en[2 + sim.nspecies] < 1e-5 * jscale
     sim.close()
