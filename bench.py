@@ -83,10 +83,17 @@ PROFILE = os.path.join(ROOT, "profiles", "push_turbulence_2d3v.md")
 
 
 def kernel_source_hash() -> str:
+    """Hash of the particle kernel's sources with comments and whitespace
+    removed: it changes when the code changes, not when a comment does."""
+    import re
+
     h = hashlib.sha256()
     for f in ("pic_particles.cu", "pic_dev.cuh", "pic_kernels.h"):
-        with open(os.path.join(ROOT, "paper_1906_06306_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1906_06306_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

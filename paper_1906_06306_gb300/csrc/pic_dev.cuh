@@ -89,9 +89,8 @@ struct SmemAcc {
 };
 
 // Shared-memory current window in int32 fixed point: the caller passes values
-// already divided by the quantum; integer shared atomics are native and
-// unaffected by lanes that hit the same word.  Planes Jx, Jy, Jz of
-// W0 x W1 x W2 ints.
+// already divided by the quantum; integer shared atomics are native (FP32 ones
+// retry in a loop when lanes collide).  Planes Jx, Jy, Jz of W0 x W1 x W2 ints.
 #ifndef PIC_MAGIC_F2I
 #define PIC_MAGIC_F2I 1
 #endif
