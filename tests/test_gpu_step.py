@@ -50,6 +50,27 @@ def test_step_matches_oracle_over_short_run(name):
     sim.close()
 
 
+@pytest.mark.parametrize("tile,halo", [((16, 8), 3), ((16, 16), 3), ((16, 8), 2)])
+def test_fixed_and_generic_window_kernels_match_oracle(tile, halo):
+    """The 2D particle kernel has compile-time window instantiations for the
+    windows of 16x8 and 16x16 tiles with halo 3; each of them and the generic
+    kernel (halo 2) against the oracle on a box that spans several tiles with
+    ragged edges, with sorts and strays."""
+    from paper_1906_06306_gb300 import Simulation
+
+    pl = workloads.turbulence_2d(n=52, ppc=4, r_p=4.0, theta=0.3, sigma=10.0, modes=4, seed=26)
+    sim = Simulation.from_plasma(pl, tuning=dict(tile=[tile[0], tile[1], 1], halo=halo,
+                                                 sort_every=1000))
+    g, F, osp, _ = oracle_from_sim(sim)
+    for k in range(1, 7):
+        sim.step(1)
+        oracle.step(g, F, osp)
+    Fg, spg = sim.download()
+    compare_fields(Fg, F, floor=step_floor(g, osp, 6))
+    compare_particles(g, spg, osp)
+    sim.close()
+
+
 def test_step_with_frequent_sorts_and_strays_matches_oracle_fields():
     """A hot plasma, halo 1 and a sort every 5 steps: many particles leave
     their tile window between sorts and take the global-memory path; the
