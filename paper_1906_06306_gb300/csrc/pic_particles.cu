@@ -28,21 +28,21 @@
 namespace pic {
 
 // Window extents of a block: from the tuning at run time (FW0 = 0), or fixed
-// at compile time for the common 2D windows (FW0 x FW1), which turns every
+// at compile time for the common windows (FW0 x FW1 x FW2), which turns every
 // shared-memory offset of the stencils and current words into a constant
-// (measured 4.5 % faster on the 16x8-tile window).  The launcher picks a fixed
-// instantiation only when the tuning's window has exactly those extents.
-template <int FW0, int FW1>
+// (measured 4.5 % faster on the 2D 16x8-tile window).  The launcher picks a
+// fixed instantiation only when the tuning's window has exactly those extents.
+template <int FW0, int FW1, int FW2>
 struct Win {
   static __device__ __forceinline__ int w(const PushParams& P, int d) {
-    if (FW0 > 0) return d == 0 ? FW0 : d == 1 ? FW1 : 1;
+    if (FW0 > 0) return d == 0 ? FW0 : d == 1 ? FW1 : FW2;
     return P.t.W[d];
   }
   static __device__ __forceinline__ int wc(const PushParams& P) {
-    return FW0 > 0 ? FW0 * FW1 : P.t.wcells;
+    return FW0 > 0 ? FW0 * FW1 * FW2 : P.t.wcells;
   }
   static __device__ __forceinline__ int ws(const PushParams& P) {
-    return FW0 > 0 ? (FW0 * FW1 + 3) / 4 * 4 : P.t.wstride;
+    return FW0 > 0 ? (FW0 * FW1 * FW2 + 3) / 4 * 4 : P.t.wstride;
   }
 };
 
@@ -194,7 +194,7 @@ __device__ __forceinline__ float wall_crossing(const int* dc, const float* o1, c
 // move that crosses the conducting wall is not applied: the particle goes on
 // its species' wall list (k_particles_wall reflects it).  PATH 2: global
 // memory with the reflection applied here (tail and wall kernels).
-template <int D, int MODE, int PATH, int FW0 = 0, int FW1 = 0>
+template <int D, int MODE, int PATH, int FW0 = 0, int FW1 = 0, int FW2 = 1>
 __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesDev& S, int p,
                                              PRec r, const float* sm, const SmemJ& SJ,
                                              const GlobAcc& GA, const int* w0, float qs) {
@@ -238,7 +238,7 @@ __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesD
         v = wrapi(v, P.g.n[d]);
       }
       l[d] = v;
-      inwin &= (unsigned)(v - 1) <= (unsigned)(Win<FW0, FW1>::w(P, d) - 4);
+      inwin &= (unsigned)(v - 1) <= (unsigned)(Win<FW0, FW1, FW2>::w(P, d) - 4);
     }
     if (!inwin) return false;
   }
@@ -250,8 +250,8 @@ __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesD
     if (GLOBAL)
       gather<D>(GA, ijk, o1, e, b);
     else
-      gather_smem<D>(sm, Win<FW0, FW1>::wc(P), Win<FW0, FW1>::w(P, 0),
-                     Win<FW0, FW1>::w(P, 0) * Win<FW0, FW1>::w(P, 1), l, o1, e, b);
+      gather_smem<D>(sm, Win<FW0, FW1, FW2>::wc(P), Win<FW0, FW1, FW2>::w(P, 0),
+                     Win<FW0, FW1, FW2>::w(P, 0) * Win<FW0, FW1, FW2>::w(P, 1), l, o1, e, b);
     if (P.pusher == 1)
       higuera_cary(u, e, b, S.qm, P.g.c, P.inv_c, P.inv_c2);
     else
@@ -321,7 +321,7 @@ __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesD
   return true;
 }
 
-template <int D, int MODE, int FW0 = 0, int FW1 = 0>
+template <int D, int MODE, int FW0 = 0, int FW1 = 0, int FW2 = 1>
 __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D : PIC_PUSH_MIN_BLOCKS)
     k_particles(const PushParams P) {
   extern __shared__ __align__(16) float sm[];
@@ -334,9 +334,9 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
   int w0[3] = {0, 0, 0};
 #pragma unroll
   for (int d = 0; d < D; ++d) w0[d] = tc[d] * P.t.T[d] - P.t.H;
-  const int wc = Win<FW0, FW1>::wc(P);
-  const int ws = Win<FW0, FW1>::ws(P);  // plane stride of the current windows (wc rounded up to 4)
-  const int W0 = Win<FW0, FW1>::w(P, 0), W1 = Win<FW0, FW1>::w(P, 1);
+  const int wc = Win<FW0, FW1, FW2>::wc(P);
+  const int ws = Win<FW0, FW1, FW2>::ws(P);  // plane stride of the current windows (wc rounded up to 4)
+  const int W0 = Win<FW0, FW1, FW2>::w(P, 0), W1 = Win<FW0, FW1, FW2>::w(P, 1);
   constexpr int NF = field_floats<D>();
   const int fw = field_words(NF, wc);
   int* ji = reinterpret_cast<int*>(sm + fw);
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
       PRec r;
       load_rec<D, MODE>(S, queue[i], r);
-      one_particle<D, MODE, 1, FW0, FW1>(P, S, queue[i], r, sm, SJ, GA, w0, 0.f);
+      one_particle<D, MODE, 1, FW0, FW1, FW2>(P, S, queue[i], r, sm, SJ, GA, w0, 0.f);
     }
     if (threadIdx.x == 0) atomicAdd(P.strays, (unsigned long long)cnt);
     __syncthreads();
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
       } else if (p < b) {
         load_rec<D, MODE>(S, p, cur);
       }
-      if (p < b && !one_particle<D, MODE, 0, FW0, FW1>(P, S, p, cur, sm, SJ, GA, w0, qs))
+      if (p < b && !one_particle<D, MODE, 0, FW0, FW1, FW2>(P, S, p, cur, sm, SJ, GA, w0, qs))
         queue[atomicAdd(&q_n, 1)] = p;
       if (PIC_PREFETCH) cur = nxt;
       if (++batches == kSpillEvery) {
@@ -519,9 +519,9 @@ FastDiv make_fastdiv(int d) {
   return f;
 }
 
-template <int D, int MODE, int FW0 = 0, int FW1 = 0>
+template <int D, int MODE, int FW0 = 0, int FW1 = 0, int FW2 = 1>
 static cudaError_t set_limit(int bytes) {
-  return cudaFuncSetAttribute(k_particles<D, MODE, FW0, FW1>,
+  return cudaFuncSetAttribute(k_particles<D, MODE, FW0, FW1, FW2>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
@@ -538,6 +538,8 @@ cudaError_t set_particle_smem_limit(int bytes) {
 #undef PIC_SET
   if (e == cudaSuccess) e = set_limit<2, 0, 23, 15>(bytes);
   if (e == cudaSuccess) e = set_limit<2, 0, 23, 23>(bytes);
+  if (e == cudaSuccess) e = set_limit<3, 0, 13, 13, 9>(bytes);
+  if (e == cudaSuccess) e = set_limit<3, 3, 13, 13, 9>(bytes);
   return e;
 }
 
@@ -545,12 +547,18 @@ template <int D, int MODE>
 static void launch(const PushParams& P, cudaStream_t st) {
   const unsigned nblocks = (unsigned)P.t.ntiles * (unsigned)P.splits;
   const size_t smem = particle_smem_bytes(D, P.t);
-  // fixed-window instantiations for the 2D windows of 16x8 and 16x16 tiles
-  // with halo 3 (23 x 15, 23 x 23); any other window takes the generic kernel
+  // fixed-window instantiations: 2D windows of 16x8 and 16x16 tiles with
+  // halo 3 (23 x 15, 23 x 23), the 3D window of 8x8x4 tiles with halo 2
+  // (13 x 13 x 9); any other window takes the generic kernel
+  const bool w3 = P.t.W[0] == 13 && P.t.W[1] == 13 && P.t.W[2] == 9;
   if (D == 2 && MODE == 0 && P.t.W[0] == 23 && P.t.W[1] == 15)
     k_particles<2, 0, 23, 15><<<nblocks, kPushThreads, smem, st>>>(P);
   else if (D == 2 && MODE == 0 && P.t.W[0] == 23 && P.t.W[1] == 23)
     k_particles<2, 0, 23, 23><<<nblocks, kPushThreads, smem, st>>>(P);
+  else if (D == 3 && MODE == 0 && w3)
+    k_particles<3, 0, 13, 13, 9><<<nblocks, kPushThreads, smem, st>>>(P);
+  else if (D == 3 && MODE == 3 && w3)
+    k_particles<3, 3, 13, 13, 9><<<nblocks, kPushThreads, smem, st>>>(P);
   else
     k_particles<D, MODE><<<nblocks, kPushThreads, smem, st>>>(P);
   if ((MODE == 0 || MODE == 3) && P.tail_blocks > 0)
