@@ -277,9 +277,10 @@ __global__ void __launch_bounds__(256) k_adj_particles(const AdjParams P) {
       const int cell = S.cell[p];
       if (cell < 0 || (long long)cell >= P.g.plane) continue;
       int b[3] = {0, 0, 0};
-      b[0] = cell % P.g.n[0];
-      b[1] = (cell / P.g.n[0]) % P.g.n[1];
-      b[2] = cell / (P.g.n[0] * P.g.n[1]);
+      const int r = fdiv(cell, P.div0);
+      b[0] = cell - r * P.g.n[0];
+      b[2] = fdiv(r, P.div1);
+      b[1] = r - b[2] * P.g.n[1];
       float o1[3] = {0.f, 0.f, 0.f}, u[3];
 #pragma unroll
       for (int d = 0; d < D; ++d) o1[d] = S.off[d * ld + p];

@@ -302,7 +302,7 @@ PushParams make_params(pic_ctx* ctx) {
 // sorted particles are copied into the caller's arrays; without, the next push
 // reads them from the buffer and writes the caller's arrays (pic_step).
 pic_status do_sort(pic_ctx* ctx, bool copy_back) {
-  SortParams P{ctx->g, ctx->tile, ctx->d_status};
+  const SortParams P = make_sort_params(ctx->g, ctx->tile, ctx->d_status);
   const int D = ctx->grid.dim;
   const cudaError_t e = timed(ctx, PIC_KERNEL_SORT, [&]() -> cudaError_t {
     for (int s = 0; s < ctx->ns; ++s) {
@@ -677,6 +677,8 @@ pic_status pic_adjoint_step(pic_ctx* ctx, const float* fwd_fields, const pic_adj
   AP.g = ctx->g;
   AP.F1 = ctx->d_adjF;
   AP.A = adj_fields;
+  AP.div0 = make_fastdiv(ctx->g.n[0]);
+  AP.div1 = make_fastdiv(ctx->g.n[1]);
   AP.nspecies = ctx->ns;
   for (int s = 0; s < ctx->ns; ++s) {
     AdjSpecies& S = AP.sp[s];

@@ -88,7 +88,10 @@ struct SortParams {
   GridDev g;
   TileDev t;
   int* status;
+  FastDiv dn0, dn1;          // by the grid extents n0, n1: cell -> (i, j, k)
+  FastDiv dt0, dt1, dt2;     // by the tile extents: lattice point -> tile
 };
+SortParams make_sort_params(const GridDev& g, const TileDev& t, int* status);
 cudaError_t launch_tile_count(const SortParams& P, const int* cell, long long n, int* count,
                               cudaStream_t st);
 cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* cursor,
@@ -154,6 +157,7 @@ struct AdjParams {
   GridDev g;
   const float* F1;  // forward E and the B of the first half step (9-plane layout)
   float* A;         // adjoint planes: Ebar, Bbar, Jbar
+  FastDiv div0, div1;  // by n0 and n1: cell -> (i, j, k)
   int nspecies;
   AdjSpecies sp[kMaxSpecies];
 };

@@ -7,15 +7,17 @@
 
 namespace pic {
 
+// Tile of a cell; every division is an exact multiply-shift (FastDiv).
 __device__ __forceinline__ int tile_key(const SortParams& P, int cell) {
   if (cell < 0 || (long long)cell >= P.g.plane) {
     atomicOr(P.status, ST_BAD_CELL);
     return 0;  // kept (in tile 0) so that no particle is lost
   }
-  const int i = cell % P.g.n[0];
-  const int r = cell / P.g.n[0];
-  const int j = r % P.g.n[1], k = r / P.g.n[1];
-  return i / P.t.T[0] + P.t.nt[0] * (j / P.t.T[1] + P.t.nt[1] * (k / P.t.T[2]));
+  const int r = fdiv(cell, P.dn0);
+  const int i = cell - r * P.g.n[0];
+  const int k = fdiv(r, P.dn1);
+  const int j = r - k * P.g.n[1];
+  return fdiv(i, P.dt0) + P.t.nt[0] * (fdiv(j, P.dt1) + P.t.nt[1] * fdiv(k, P.dt2));
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -109,6 +111,19 @@ __global__ void k_tile_scatter(const SortParams P, const int* __restrict__ cell,
       for (int a = 0; a < 3; ++a) u_out[a * ld + q] = u[a * ld + p];
     }
   }
+}
+
+SortParams make_sort_params(const GridDev& g, const TileDev& t, int* status) {
+  SortParams P{};
+  P.g = g;
+  P.t = t;
+  P.status = status;
+  P.dn0 = make_fastdiv(g.n[0]);
+  P.dn1 = make_fastdiv(g.n[1]);
+  P.dt0 = make_fastdiv(t.T[0]);
+  P.dt1 = make_fastdiv(t.T[1]);
+  P.dt2 = make_fastdiv(t.T[2]);
+  return P;
 }
 
 static unsigned blocks_for(long long n) {
