@@ -22,15 +22,18 @@
  *   off   float[dim][cap]  in-cell offset of each gridded coordinate, in [0,1)
  *   u     float[3][cap]    spatial four-velocity in units of c
  * The library keeps particles sorted by spatial tile and may reorder them
- * (pic_sort, pic_step); after every call returns (on the stream) the caller's
- * buffers hold the current particles.
+ * (pic_sort, pic_step; particles injected since the last sort follow the
+ * sorted ones); after every call returns (on the stream) the caller's
+ * buffers hold the current particles, whose count pic_particle_counts gives.
  *
  * Ownership: the caller owns the field and particle buffers and the stream;
  * the library owns the context, its scratch (sort buffers, tile tables,
- * pre-move snapshot, filter buffer, diagnostics, status word) and frees them
- * in pic_destroy.  All calls enqueue work on the context's stream and return
- * without synchronising, except pic_energies, pic_check, pic_step_host and
- * pic_kernel_times, which synchronise the stream.  No exception crosses the
+ * pre-move snapshot, filter buffer, diagnostics, status word, injector
+ * templates and wall list) and frees them in pic_destroy.  All calls enqueue
+ * work on the context's stream and return without synchronising, except
+ * pic_energies, pic_check, pic_step_host, pic_stats, pic_autotune,
+ * pic_kernel_times and pic_set_shock (which copies the templates), which
+ * synchronise the stream.  No exception crosses the
  * ABI: every call returns a pic_status; pic_last_error gives the message of
  * the last failure on a context.  A context is not thread-safe.
  */

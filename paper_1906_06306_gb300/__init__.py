@@ -4,6 +4,23 @@ The API names below resolve on first use by loading libpic.so (the CUDA
 kernels behind the C ABI of include/pic.h); if the library is missing that
 access raises -- there is no CPU fallback.  The `build` submodule imports
 without the library so that it can compile it.
+
+Use (device memory and the stream come from PyTorch):
+
+    import workloads
+    from paper_1906_06306_gb300 import Simulation, Batch
+    sim = Simulation.from_plasma(workloads.turbulence_2d(n=256))  # periodic box
+    sim.autotune()          # tile size, halo and sort cadence, by real steps
+    sim.step(100)           # B half, gather+Boris+move+ZigZag, B half, filter, E
+    print(sim.energies())   # 0.5 sum E^2, 0.5 sum B^2, kinetic, Gauss residual
+    fields, particles = sim.download()
+
+    sim.set_field_solver(4); sim.set_pusher("higuera_cary")   # Table 2 variants
+    sim.set_shock_from_plasma(workloads.shock_tube(...))      # wall + injector
+    Batch([sim_a, sim_b, ...]).step(500)                      # ensembles, one graph
+
+    from paper_1906_06306_gb300.adjoint import MagneticEnergy, MagneticEnergyProblem
+    loss = MagneticEnergy.apply(amps, u0, problem); loss.backward()  # discrete adjoint
 """
 _API = {
     "PicError", "pic_init", "pic_set_pusher", "pic_set_field_solver", "pic_get_tuning",
