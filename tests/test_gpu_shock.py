@@ -281,3 +281,32 @@ def test_full_size_shock_step_sampled_against_oracle(oracle_wall):
                                for s, n, k in zip(sp1, n0, counts)])
     assert en[2 + sim.nspecies] < 1e-5 * jscale
     sim.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_shock_tube_with_fdtd4_and_higuera_cary_matches_oracle(oracle_wall, dim):
+    """The solver combination of the paper's shock run (FDTD4, Higuera-Cary,
+    Binomial2) with the wall and the injector: FDTD4's wider stencil reads the
+    conductor's mirror images two cells deep (wall at x = 3)."""
+    pl = _tube(dim, filter_passes=2)
+    nsteps = 8
+    sim = _sim(pl, nsteps, sort_every=1000)
+    sim.set_field_solver(4)
+    sim.set_pusher("higuera_cary")
+    g, F, osp, _ = oracle_from_sim(sim)
+    w, i_zero, inj = oracle.shock_from_plasma(pl)
+    oracle_wall(w, i_zero)
+    oracle.set_field_order(4)
+    oracle.set_pusher("higuera_cary")
+    try:
+        sim.step(nsteps)
+        oracle.step_shock(g, F, osp, inj, 0, passes=2, nsteps=nsteps)
+    finally:
+        oracle.set_field_order(2)
+        oracle.set_pusher("boris")
+    sim.check()
+    assert sim.counts() == [s.n for s in osp]
+    Fg, spg = sim.download()
+    compare_fields(Fg, F, floor=step_floor(g, osp, nsteps))
+    compare_particles(g, spg, osp)
+    sim.close()
