@@ -182,6 +182,162 @@ __global__ void __launch_bounds__(256) k_filter_pass(const float* __restrict__ s
   }
 }
 
+// One full 3D Binomial2 pass (x, y, then z sub-pass) of one plane src -> dst,
+// marching along z.  A block of 256 threads owns a ZX x ZY = 128 x 16 column
+// of (x, y) points over a run of `zrun` z-planes; a thread owns a 4 (x) x 2
+// (y) patch of it.  Each z-plane of the column plus its one-point periodic
+// (x, y) halo is copied into a ring of ZS shared-memory stages with cp.async
+// (16-byte copies for the aligned interior, 4-byte ones for the halo and for
+// ragged or wrapped rows), ZS - 1 planes ahead of the one being filtered.  A
+// thread reads its four rows (y - 1 .. y + 2) with one 16-byte and two 4-byte
+// shared loads each, runs the x and y sub-passes in registers and keeps the
+// last three y results for the z sub-pass.  Reads: the column, its (x, y)
+// halo (rows of neighbouring columns, mostly from L2) and two extra planes
+// per run; writes: the column, 16 bytes per store.  Every output goes through
+// the same arithmetic, in the same order, as three k_filter_axis sub-passes.
+// Grid: x = column index + columns x run, y = plane.
+constexpr int ZX = 128, ZY = 16, ZS = 4;
+constexpr int ZROW = ZX + 8;  // stage row: [3] left halo, [4, 4 + ZX) interior, [4 + ZX] right
+constexpr int ZPLANE = (ZY + 2) * ZROW;
+constexpr int ZCH = ZX / 4 + 2;         // copy operations per stage row
+constexpr int ZOPS = (ZY + 2) * ZCH;    // copy operations per stage (612)
+constexpr int ZOPT = (ZOPS + 255) / 256;  // per thread (3)
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ float b3(float l, float c, float r) {
+  return 0.25f * l + 0.5f * c + 0.25f * r;
+}
+
+__global__ void __launch_bounds__(256, 4) k_filter_z3(const float* __restrict__ src,
+                                                     float* __restrict__ dst, const GridDev g,
+                                                     int ncx, int ncy, int zrun, int vec) {
+  __shared__ __align__(16) float stage[ZS][ZPLANE];
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const long long nxy = (long long)n0 * n1;
+  const int col = blockIdx.x % (ncx * ncy), run = blockIdx.x / (ncx * ncy);
+  const int x0 = (col % ncx) * ZX, y0 = (col / ncx) * ZY, z0 = run * zrun;
+  const int zc = min(zrun, n2 - z0);  // planes z0 .. z0 + zc - 1 are written
+  const long long P = g.plane;
+  const float* s = src + (long long)blockIdx.y * P;
+  float* d = dst + (long long)blockIdx.y * P;
+
+  // This thread's copy operations op = threadIdx.x + 256 j, the same for every
+  // z-plane: stage row op / ZCH (y = y0 - 1 + row) and either a 4-point
+  // interior chunk (c < ZX / 4), the left halo point (c = ZX / 4) or the right.
+  long long yoff[ZOPT];
+  int xs[ZOPT], dofs[ZOPT], kind[ZOPT];  // kind: 0 none, 1 16-byte, 2 four 4-byte, 3 one 4-byte
+#pragma unroll
+  for (int j = 0; j < ZOPT; ++j) {
+    const int op = threadIdx.x + 256 * j;
+    const int row = op / ZCH, c = op % ZCH;
+    kind[j] = 0;
+    yoff[j] = 0;
+    xs[j] = 0;
+    dofs[j] = 0;
+    if (op < ZOPS) {
+      yoff[j] = (long long)n0 * wrapi(y0 - 1 + row, n1);
+      if (c < ZX / 4) {
+        xs[j] = x0 + 4 * c;
+        dofs[j] = row * ZROW + 4 + 4 * c;
+        kind[j] = vec && xs[j] + 3 < n0 ? 1 : 2;
+      } else {
+        xs[j] = wrapi(c == ZX / 4 ? x0 - 1 : x0 + ZX, n0);
+        dofs[j] = row * ZROW + (c == ZX / 4 ? 3 : 4 + ZX);
+        kind[j] = 3;
+      }
+    }
+  }
+  auto issue = [&](int k) {  // copy halo plane k (z = z0 - 1 + k) into stage k % ZS
+    if (k < zc + 2) {
+      int z = z0 - 1 + k;  // -1 <= z <= n2
+      z = z < 0 ? z + n2 : (z >= n2 ? z - n2 : z);
+      const float* base = s + nxy * z;
+      float* st = stage[k % ZS];
+#pragma unroll
+      for (int j = 0; j < ZOPT; ++j) {
+        const float* sr = base + yoff[j];
+        if (kind[j] == 1) {
+          cp_async16(st + dofs[j], sr + xs[j]);
+        } else if (kind[j] == 3) {
+          cp_async4(st + dofs[j], sr + xs[j]);
+        } else if (kind[j] == 2) {
+          for (int e = 0; e < 4; ++e) cp_async4(st + dofs[j] + e, sr + wrapi(xs[j] + e, n0));
+        }
+      }
+    }
+    cp_async_commit();  // an empty group keeps the group count uniform
+  };
+#pragma unroll
+  for (int k = 0; k < ZS - 1; ++k) issue(k);
+
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int gx = x0 + 4 * tx, gy = y0 + 2 * ty;
+  float pm[8], p0[8];  // y results of the two previous planes: [row * 4 + x]
+#pragma unroll
+  for (int i = 0; i < 8; ++i) pm[i] = p0[i] = 0.f;
+  for (int k = 0; k < zc + 2; ++k) {
+    cp_async_wait<ZS - 2>();  // this thread's copies of plane k have landed
+    __syncthreads();          // everyone's have; stage (k - 1) % ZS is no longer read
+    issue(k + ZS - 1);
+    const float* a = stage[k % ZS] + 2 * ty * ZROW + 4 * tx + 3;  // row y - 1, column x - 1
+    float xf[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {  // x sub-pass of rows y - 1 .. y + 2
+      const float l = a[r * ZROW];
+      const float4 m = *reinterpret_cast<const float4*>(a + r * ZROW + 1);
+      const float rr = a[r * ZROW + 5];
+      xf[r][0] = b3(l, m.x, m.y);
+      xf[r][1] = b3(m.x, m.y, m.z);
+      xf[r][2] = b3(m.y, m.z, m.w);
+      xf[r][3] = b3(m.z, m.w, rr);
+    }
+    float p1[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {  // y sub-pass of rows y, y + 1
+      p1[i] = b3(xf[0][i], xf[1][i], xf[2][i]);
+      p1[4 + i] = b3(xf[1][i], xf[2][i], xf[3][i]);
+    }
+    if (k >= 2) {  // z sub-pass of plane z0 + k - 2
+      const int z = z0 + k - 2;
+#pragma unroll
+      for (int rw = 0; rw < 2; ++rw) {
+        if (gy + rw >= n1) continue;
+        float o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = b3(pm[4 * rw + i], p0[4 * rw + i], p1[4 * rw + i]);
+        float* q = d + gx + (long long)n0 * (gy + rw) + nxy * z;
+        if (vec && gx + 3 < n0) {
+          *reinterpret_cast<float4*>(q) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (gx + i < n0) q[i] = o[i];
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      pm[i] = p0[i];
+      p0[i] = p1[i];
+    }
+  }
+  cp_async_wait<0>();
+}
+
 // Offsets (elements) of the lattice points a-2, a-1, a+1, a+2 along an axis of
 // n points with stride s, periodic.
 struct Nb {
@@ -329,12 +485,43 @@ static cudaError_t launch_pass(const GridDev& g, const float* src, float* dst, i
   return cudaGetLastError();
 }
 
+// The z-marching 3D pass.  The z-runs are as long as they can be with every
+// block resident at once (one wave: no block re-reads a run's two halo planes
+// from DRAM after its neighbour has evicted them, no tail wave); a grid with
+// more columns than resident blocks gets one run per column.
+static cudaError_t launch_pass_z3(const GridDev& g, const float* src, float* dst, int ncomp,
+                                  cudaStream_t st) {
+  static int resident = 0;
+  if (resident == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_z3, 256, 0);
+    resident = sms * per_sm > 0 ? sms * per_sm : 1;
+  }
+  const int ncx = (g.n[0] + ZX - 1) / ZX, ncy = (g.n[1] + ZY - 1) / ZY;
+  const long long streams = (long long)ncx * ncy * ncomp;
+  long long runs = resident / streams;
+  if (runs < 1) runs = 1;
+  if (runs > g.n[2]) runs = g.n[2];
+  const int zrun = (int)((g.n[2] + runs - 1) / runs);
+  const long long blocks = (long long)ncx * ncy * ((g.n[2] + zrun - 1) / zrun);
+  if (blocks > 0x7fffffffLL || ncomp > 65535) return cudaErrorInvalidValue;
+  // 16-byte copies and stores need 16-byte aligned rows: plane bases and n0
+  // multiples of 4 floats
+  const int vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0 &&
+                  g.n[0] % 4 == 0 && g.plane % 4 == 0;
+  k_filter_z3<<<dim3((unsigned)blocks, (unsigned)ncomp), 256, 0, st>>>(src, dst, g, ncx, ncy, zrun,
+                                                                      vec);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_filter_pass_f32(const GridDev& g, const float* src, float* dst, int ncomp,
                                    cudaStream_t st) {
   switch (g.dim) {
     case 1: return launch_pass<1, 1024, 1, 1>(g, src, dst, ncomp, st);
     case 2: return launch_pass<2, 32, 32, 1>(g, src, dst, ncomp, st);
-    case 3: return launch_pass<3, 32, 8, 8>(g, src, dst, ncomp, st);
+    case 3: return launch_pass_z3(g, src, dst, ncomp, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -64,6 +64,26 @@ def test_binomial_filter_matches_oracle(dim, passes):
     sim.close()
 
 
+@pytest.mark.parametrize("shape", [(37, 11, 9), (68, 19, 41), (4, 8, 2), (1, 1, 3), (2, 3, 1),
+                                   (1024, 256, 40)])
+def test_binomial_filter_3d_z_runs_match_oracle(shape):
+    """The 3D pass marches along z over (x, y) columns of 32 x 8 points: rows
+    whose x extent is not a multiple of 4 (4-byte copies only), ragged columns,
+    several z runs with a ragged last one, extents below the column and the
+    halo, and a box large enough for 32-plane runs (1024 x 256 x 40)."""
+    nx, ny, nz = shape
+    rs = np.random.default_rng(sum(shape))
+    F32 = np.zeros((9, nz, ny, nx), np.float32)
+    F32[6:9] = rs.normal(size=(3, nz, ny, nx)).astype(np.float32)
+    sim = _sim(3, shape, F32, _empty_species(3))
+    g = oracle.Grid(3, nx, ny, nz, 0.45)
+    F = F32.astype(np.float64)
+    sim.filter_current(3)
+    oracle.filter_binomial(g, F, 3)
+    compare_fields(sim.download()[0], F, tol=1e-6, comps=range(6, 9))
+    sim.close()
+
+
 def _plasma(dim, shape, ppc, theta, seed):
     nx, ny, nz = shape
     return workloads.uniform_plasma(dim, nx, ny, nz, 0.45, ppc, 0.02, theta, seed)
