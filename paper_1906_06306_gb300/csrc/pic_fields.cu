@@ -8,10 +8,24 @@
 
 namespace pic {
 
-static unsigned grid_for(long long n, int threads) {
-  long long b = (n + threads - 1) / threads;
-  if (b > (1LL << 20)) b = 1LL << 20;
-  return (unsigned)(b < 1 ? 1 : b);
+// The field updates run on a (x blocks, y, z) launch grid: a thread owns
+// point x of the rows (y, z) of its block, stepping over rows beyond the
+// launch grid's 65535 limit, so no lattice index is ever divided out of a
+// linear one.
+#define FOR_ROWS(j, k)                                  \
+  for (int k = blockIdx.z; k < n2; k += gridDim.z)      \
+    for (int j = blockIdx.y; j < n1; j += gridDim.y)
+
+struct RowLaunch {
+  dim3 grid;
+  unsigned threads;
+};
+static RowLaunch row_launch(const GridDev& g) {
+  const int n0 = g.n[0];
+  const unsigned t = n0 >= 256 ? 256 : n0 >= 128 ? 128 : n0 >= 64 ? 64 : 32;
+  return {dim3((unsigned)((n0 + t - 1) / t), (unsigned)min(g.n[1], 65535),
+               (unsigned)min(g.n[2], 65535)),
+          t};
 }
 
 // B -= (c/2) curl+ E (forward differences: B sits half a cell above E), and,
@@ -20,11 +34,10 @@ template <int D>
 __global__ void k_b_half(float* __restrict__ F, const GridDev g, float hc, int zero_j) {
   const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const long long P = g.plane;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(idx % n0);
-    const long long r = idx / n0;
-    const int j = (int)(r % n1), k = (int)(r / n1);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n0) return;
+  FOR_ROWS(j, k) {
+    const long long idx = (long long)i + (long long)n0 * (j + (long long)n1 * k);
     const long long sx = (i + 1 < n0) ? 1 : 1 - n0;
     const long long sy = (D >= 2) ? ((j + 1 < n1) ? n0 : (long long)n0 * (1 - n1)) : 0;
     const long long sz = (D >= 3) ? ((k + 1 < n2) ? (long long)n0 * n1 : (long long)n0 * n1 * (1 - n2)) : 0;
@@ -59,11 +72,10 @@ template <int D>
 __global__ void k_e_update(float* __restrict__ F, const GridDev g, float c) {
   const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const long long P = g.plane;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(idx % n0);
-    const long long r = idx / n0;
-    const int j = (int)(r % n1), k = (int)(r / n1);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n0) return;
+  FOR_ROWS(j, k) {
+    const long long idx = (long long)i + (long long)n0 * (j + (long long)n1 * k);
     const long long sx = (i > 0) ? 1 : 1 - n0;
     const long long sy = (D >= 2) ? ((j > 0) ? n0 : (long long)n0 * (1 - n1)) : 0;
     const long long sz = (D >= 3) ? ((k > 0) ? (long long)n0 * n1 : (long long)n0 * n1 * (1 - n2)) : 0;
@@ -363,12 +375,12 @@ __device__ __forceinline__ float d4m(const float* A, long long i, const Nb& b) {
 // FDTD4 versions of the two updates (same structure as above, wider stencil).
 template <int D>
 __global__ void k_b_half4(float* __restrict__ F, const GridDev g, float hc, int zero_j) {
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const long long P = g.plane;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(idx % g.n[0]);
-    const long long r = idx / g.n[0];
-    const int j = (int)(r % g.n[1]), k = (int)(r / g.n[1]);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n0) return;
+  FOR_ROWS(j, k) {
+    const long long idx = (long long)i + (long long)n0 * (j + (long long)n1 * k);
     const Nb nx = neighbours(i, g.n[0], 1);
     const Nb ny = neighbours(j, g.n[1], g.n[0]);
     const Nb nz = neighbours(k, g.n[2], (long long)g.n[0] * g.n[1]);
@@ -399,12 +411,12 @@ __global__ void k_b_half4(float* __restrict__ F, const GridDev g, float hc, int 
 
 template <int D>
 __global__ void k_e_update4(float* __restrict__ F, const GridDev g, float c) {
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const long long P = g.plane;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(idx % g.n[0]);
-    const long long r = idx / g.n[0];
-    const int j = (int)(r % g.n[1]), k = (int)(r / g.n[1]);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n0) return;
+  FOR_ROWS(j, k) {
+    const long long idx = (long long)i + (long long)n0 * (j + (long long)n1 * k);
     const Nb nx = neighbours(i, g.n[0], 1);
     const Nb ny = neighbours(j, g.n[1], g.n[0]);
     const Nb nz = neighbours(k, g.n[2], (long long)g.n[0] * g.n[1]);
@@ -429,29 +441,29 @@ __global__ void k_e_update4(float* __restrict__ F, const GridDev g, float c) {
 }
 
 cudaError_t launch_b_half(const GridDev& g, float* F, int zero_j, cudaStream_t st) {
-  const unsigned nb = grid_for(g.plane, 256);
+  const RowLaunch L = row_launch(g);
   const float hc = 0.5f * g.c;
   switch (g.dim * 10 + g.order) {
-    case 12: k_b_half<1><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
-    case 22: k_b_half<2><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
-    case 32: k_b_half<3><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
-    case 14: k_b_half4<1><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
-    case 24: k_b_half4<2><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
-    case 34: k_b_half4<3><<<nb, 256, 0, st>>>(F, g, hc, zero_j); break;
+    case 12: k_b_half<1><<<L.grid, L.threads, 0, st>>>(F, g, hc, zero_j); break;
+    case 22: k_b_half<2><<<L.grid, L.threads, 0, st>>>(F, g, hc, zero_j); break;
+    case 32: k_b_half<3><<<L.grid, L.threads, 0, st>>>(F, g, hc, zero_j); break;
+    case 14: k_b_half4<1><<<L.grid, L.threads, 0, st>>>(F, g, hc, zero_j); break;
+    case 24: k_b_half4<2><<<L.grid, L.threads, 0, st>>>(F, g, hc, zero_j); break;
+    case 34: k_b_half4<3><<<L.grid, L.threads, 0, st>>>(F, g, hc, zero_j); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_e_update(const GridDev& g, float* F, cudaStream_t st) {
-  const unsigned nb = grid_for(g.plane, 256);
+  const RowLaunch L = row_launch(g);
   switch (g.dim * 10 + g.order) {
-    case 12: k_e_update<1><<<nb, 256, 0, st>>>(F, g, g.c); break;
-    case 22: k_e_update<2><<<nb, 256, 0, st>>>(F, g, g.c); break;
-    case 32: k_e_update<3><<<nb, 256, 0, st>>>(F, g, g.c); break;
-    case 14: k_e_update4<1><<<nb, 256, 0, st>>>(F, g, g.c); break;
-    case 24: k_e_update4<2><<<nb, 256, 0, st>>>(F, g, g.c); break;
-    case 34: k_e_update4<3><<<nb, 256, 0, st>>>(F, g, g.c); break;
+    case 12: k_e_update<1><<<L.grid, L.threads, 0, st>>>(F, g, g.c); break;
+    case 22: k_e_update<2><<<L.grid, L.threads, 0, st>>>(F, g, g.c); break;
+    case 32: k_e_update<3><<<L.grid, L.threads, 0, st>>>(F, g, g.c); break;
+    case 14: k_e_update4<1><<<L.grid, L.threads, 0, st>>>(F, g, g.c); break;
+    case 24: k_e_update4<2><<<L.grid, L.threads, 0, st>>>(F, g, g.c); break;
+    case 34: k_e_update4<3><<<L.grid, L.threads, 0, st>>>(F, g, g.c); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
