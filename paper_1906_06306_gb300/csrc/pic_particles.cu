@@ -216,7 +216,8 @@ __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesD
   {
     const int q = fdiv(r.cell, P.div0);
     ijk[0] = r.cell - q * P.g.n[0];
-    if (D >= 2) {
+    if (D == 2) ijk[1] = q;  // q < n1: the cell is on the lattice
+    if (D == 3) {
       ijk[2] = fdiv(q, P.div1);
       ijk[1] = q - ijk[2] * P.g.n[1];
     }
