@@ -432,10 +432,15 @@ def run_ours(args):
     achieved = alg / avg_push_s / 1e9
     traffic = profiled_traffic() if args.workload == "turbulence_2d3v" and pl.nx == 1024 else None
     nsorts = -(-args.steps // tun["sort_every"])  # at most one sort per cadence in the loop
-    launches = args.steps * (4 + tun["filter_passes"] * pl.dim) + nsorts * 3 * sim.nspecies
-    if shock:  # per step: 3 wall-field passes, the wall kernel, the injection, and the tail
-        # kernel on every step that does not start with a sort
-        launches += args.steps * 5 + (args.steps - nsorts)
+    # per step: two B half steps, the tile particle kernel, the E update, one fused
+    # launch per filter pass and, in 3D or with the wall, the deferred-particle
+    # kernel; per sort: count, scan and scatter per species
+    deferred = 1 if pl.dim == 3 or shock else 0
+    launches = (args.steps * (4 + deferred + tun["filter_passes"]) +
+                nsorts * 3 * sim.nspecies)
+    if shock:  # per step: 3 wall-field passes, the injection, and the tail kernel on
+        # every step that does not start with a sort
+        launches += args.steps * 4 + (args.steps - nsorts)
     wl = workload_config(args.workload, pl)
     line = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
@@ -626,6 +631,12 @@ def run_adjoint(args):
     e_s, e_value = job_value(time.perf_counter() - te, npart * args.steps, dist, dev)
     adj_ms, adj_n = kt["adjoint"]
     avg_adj = adj_ms * 1e-3 / max(adj_n, 1)
+    # kernels behind the library's timed calls: a push is the tile kernel (2D,
+    # periodic: no deferred-particle kernel), an adjoint step 5 kernels plus one
+    # per filter pass
+    passes = sim.tuning()["filter_passes"]
+    launches = (kt["push"][1] + kt["b_half"][1] + kt["e_update"][1] + kt["filter"][1] +
+                (5 + passes) * kt["adjoint"][1])
     # per adjoint step: particle state read (4 + 8 + 12 B) and gradients read and
     # written (2 x (8 + 12) B); E, B read and their gradients added once per cell
     alg = npart * (24 + 40) + pl.ncells * 4 * (6 + 9 + 12)
@@ -650,6 +661,7 @@ def run_adjoint(args):
                      "peak_source": peak_kind, "avg_launch_us": avg_adj * 1e6,
                      "alg_bytes_per_launch": alg},
         "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in kt.items()},
+        "gpu_launches": launches,
         "clocks": clocks,
         "e2e": {"value": e_value, "unit": "particle-steps/s",
                 "h2d_bytes_per_step": int((ha.numel() + hu.numel()) * 4 / args.steps),

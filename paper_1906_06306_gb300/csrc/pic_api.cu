@@ -65,8 +65,8 @@ struct pic_ctx {
   long long tn[PIC_MAX_SPECIES] = {};        // template particles per species
   std::vector<double> txs[PIC_MAX_SPECIES];  // template x = i + off_x (host, sorted)
   void* d_tmpl = nullptr;                    // template records of every species
-  int* d_wlist = nullptr;                    // wall crossers, room for cap[s] per species
-  int* d_wcount = nullptr;                   // entries per species
+  int* d_dlist = nullptr;   // particles deferred to the global pass, room for cap[s] per species
+  int* d_dcount = nullptr;  // entries per species
   float* d_adjF = nullptr;                   // forward fields of an adjoint step (9 planes)
   long long steps = 0;
   bool timing = false;
@@ -125,8 +125,8 @@ void free_all(pic_ctx* ctx) {
   dfree(ctx->d_status);
   dfree(ctx->d_strays);
   dfree(ctx->d_tmpl);
-  dfree(ctx->d_wlist);
-  dfree(ctx->d_wcount);
+  dfree(ctx->d_dlist);
+  dfree(ctx->d_dcount);
   dfree(ctx->d_adjF);
   for (auto& t : ctx->pending) {
     cudaEventDestroy(t.a);
@@ -289,12 +289,13 @@ PushParams make_params(pic_ctx* ctx) {
     S.tstart = ctx->d_tstart[s];
     S.cell_old = ctx->d_cell_old ? ctx->d_cell_old + o : nullptr;
     S.off_old = ctx->d_off_old ? ctx->d_off_old + (long long)ctx->grid.dim * o : nullptr;
-    S.wlist = ctx->d_wlist ? ctx->d_wlist + o : nullptr;
-    S.wcount = ctx->d_wcount ? ctx->d_wcount + s : nullptr;
+    S.dlist = ctx->d_dlist + o;
+    S.dcount = ctx->d_dcount + s;
     o += ctx->cap[s];
   }
   P.wall = ctx->shock ? ctx->wall : 0;
   P.tail_blocks = tail_blocks(ctx);
+  P.dcount = ctx->d_dcount;
   return P;
 }
 
@@ -515,6 +516,9 @@ pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* spec
   } else if ((e = dalloc((char**)&ctx->d_sortbuf, (size_t)totcap * (4 + 4 * grid->dim + 12))) !=
              cudaSuccess) {
     s = cuda_fail(nullptr, "sort buffer", e);
+  } else if ((e = dalloc(&ctx->d_dlist, (size_t)totcap)) != cudaSuccess ||
+             (e = dalloc(&ctx->d_dcount, (size_t)PIC_MAX_SPECIES)) != cudaSuccess) {
+    s = cuda_fail(nullptr, "deferred-particle lists", e);
   } else if ((s = alloc_tiles(ctx)) != PIC_OK || (s = do_sort(ctx, true)) != PIC_OK) {
     g_init_error = ctx->err;
   }
@@ -629,10 +633,6 @@ pic_status pic_set_shock(pic_ctx* ctx, const pic_shock* sh) {
   PIC_CK(ctx, cudaStreamSynchronize(ctx->st));
   dfree(ctx->d_tmpl);
   PIC_CK(ctx, dalloc((char**)&ctx->d_tmpl, (size_t)words * 4));
-  if (!ctx->d_wlist) {
-    PIC_CK(ctx, dalloc(&ctx->d_wlist, (size_t)total_cap(ctx)));
-    PIC_CK(ctx, dalloc(&ctx->d_wcount, (size_t)PIC_MAX_SPECIES));
-  }
   long long o = 0;
   for (int s = 0; s < ctx->ns; ++s) {
     const long long nt = sh->nt[s];
@@ -807,13 +807,7 @@ pic_status pic_step(pic_ctx* ctx, int nsteps) {
     cudaError_t e = timed(ctx, PIC_KERNEL_BHALF, [&]() { return launch_b_half(ctx->g, ctx->F, 1, ctx->st); });
     if (e == cudaSuccess) e = wall_bc();
     if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
-    e = timed(ctx, PIC_KERNEL_PUSH, [&]() {
-      if (ctx->shock) {
-        const cudaError_t m = cudaMemsetAsync(ctx->d_wcount, 0, sizeof(int) * ctx->ns, ctx->st);
-        if (m != cudaSuccess) return m;
-      }
-      return launch_particles(ctx->grid.dim, 0, P, ctx->st);
-    });
+    e = timed(ctx, PIC_KERNEL_PUSH, [&]() { return launch_particles(ctx->grid.dim, 0, P, ctx->st); });
     if (e != cudaSuccess) return cuda_fail(ctx, "gather/push/deposit kernel", e);
     e = timed(ctx, PIC_KERNEL_BHALF, [&]() { return launch_b_half(ctx->g, ctx->F, 0, ctx->st); });
     if (e == cudaSuccess) e = wall_bc();

@@ -48,8 +48,9 @@ struct SpeciesDev {
   const int* tstart;  // [ntiles+1] tile bucket offsets
   int* cell_old;      // pre-move snapshot (split gather/deposit path)
   float* off_old;     // [D][ld]
-  int* wlist;         // particles whose move crossed the conducting wall (room for ld)
-  int* wcount;        // entries in wlist
+  int* dlist;         // particles deferred to the global-memory pass (room for ld):
+                      // stencil outside the tile window, or a move across the wall
+  int* dcount;        // entries in dlist
 };
 
 // Exact division of 0 <= x < 2^31 by a fixed divisor d >= 1 by multiply and
@@ -70,6 +71,13 @@ __device__ __forceinline__ int fdiv(int x, const FastDiv& f) {
 __device__ __forceinline__ int wrapi(int i, int n) {
   i %= n;
   return i < 0 ? i + n : i;
+}
+
+// Lanes below this one in its warp, as a bit mask.
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
 }
 
 // Periodic image of a lattice index that is at most one period away.

@@ -25,10 +25,10 @@ constexpr int kMaxSpecies = 4;
 #endif
 constexpr int kPushThreads = PIC_PUSH_THREADS;
 constexpr int kSpillEvery = PIC_SPILL_EVERY;  // batches of kPushThreads particles between spills
-// Shared-memory queue of particles outside the tile window.  It is drained at
-// every spill point where it holds anything, and between two spill points at
-// most kSpillEvery batches of kPushThreads particles can be queued, so this
-// capacity can never be exceeded.
+// Shared-memory queue of the 1D/2D tile kernels for particles outside the tile
+// window.  It is drained at every spill point where it could overflow before
+// the next one, and between two spill points at most kSpillEvery batches of
+// kPushThreads particles can be queued, so this capacity can never be exceeded.
 constexpr int kQueueCap = kPushThreads * kSpillEvery;
 
 struct PushParams {
@@ -48,6 +48,7 @@ struct PushParams {
   int pusher;                  // 0 Boris (Appendix C), 1 Higuera-Cary
   int wall;                    // conducting wall on the node plane x = wall (0: none)
   int tail_blocks;             // extra blocks for the unsorted tails [tail, n)
+  int* dcount;                 // [nspecies] entries of the deferred lists (zeroed per launch)
 };
 
 // Quantum of the fixed-point shared-memory current (a power of 2) for charges

@@ -17,10 +17,16 @@
 // batches of blockDim particles, before any int32 word can overflow.
 //
 // A particle whose stencil is not inside the window (it drifted more than
-// halo-1 cells since the last sort) is put on a shared-memory queue and
-// processed later, in full warps, through global memory: warps of in-window
-// particles never diverge into the global path, and correctness never
-// depends on the sort cadence.
+// halo-1 cells since the last sort) is a stray.  In 1D and 2D strays are put
+// on a shared-memory queue and processed by the block, in full warps, through
+// global memory, overlapped with the other blocks' work.  In 3D that global
+// path would set the registers of the whole kernel (128 against 80: 2 against
+// 3 resident blocks per SM), so strays are not touched: their warp appends
+// them to the species' deferred list with one atomic, and k_particles_deferred
+// runs them afterwards through global memory.  A move across the conducting
+// wall is deferred the same way in every dimension.  Warps of in-window
+// particles never diverge into a global path, and correctness never depends on
+// the sort cadence.
 #include <cmath>
 
 #include "pic_kernels.h"
@@ -187,17 +193,20 @@ __device__ __forceinline__ float wall_crossing(const int* dc, const float* o1, c
   return s;
 }
 
+// What one_particle did with a particle.
+enum : int { kDone = 0, kStray = 1, kWallCross = 2 };
+
 // One particle through gather -> Boris -> move -> ZigZag.  PATH 0: the
-// shared-memory window is used and a particle whose stencil leaves the window
-// is not touched (returns false, the caller queues it).  PATH 1: everything
-// goes through global memory (the deferred pass over the queue).  In both, a
-// move that crosses the conducting wall is not applied: the particle goes on
-// its species' wall list (k_particles_wall reflects it).  PATH 2: global
-// memory with the reflection applied here (tail and wall kernels).
+// shared-memory window is used; a particle whose stencil leaves the window
+// (kStray) is not touched.  PATH 1: everything goes through global memory
+// (the 1D/2D in-block pass over the stray queue).  In both, a particle whose
+// move crosses the conducting wall (kWallCross) is not touched either: the
+// caller defers it.  PATH 2: global memory with the reflection applied here
+// (the deferred and tail kernels).
 template <int D, int MODE, int PATH, int FW0 = 0, int FW1 = 0, int FW2 = 1>
-__device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesDev& S, int p,
-                                             PRec r, const float* sm, const SmemJ& SJ,
-                                             const GlobAcc& GA, const int* w0, float qs) {
+__device__ __forceinline__ int one_particle(const PushParams& P, const SpeciesDev& S, int p,
+                                            PRec r, const float* sm, const SmemJ& SJ,
+                                            const GlobAcc& GA, const int* w0, float qs) {
   constexpr bool GLOBAL = PATH != 0;
   const long long n = S.ld;
   // invalid data: cell outside the lattice, offset outside [0,1), non-finite u
@@ -209,7 +218,7 @@ __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesD
   if (bad_cell | bad_off | bad_u) {
     atomicOr(P.status, (bad_cell ? ST_BAD_CELL : 0) | (bad_off ? ST_BAD_OFF : 0) |
                            (bad_u ? ST_BAD_U : 0));
-    return true;
+    return kDone;
   }
 
   int ijk[3] = {0, 0, 0};
@@ -224,7 +233,7 @@ __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesD
   }
   if (MODE == 3 && ijk[0] < P.wall) {  // behind the conducting wall
     atomicOr(P.status, ST_BEHIND_WALL);
-    return true;
+    return kDone;
   }
   int l[3] = {0, 0, 0};
   if (!GLOBAL) {
@@ -241,7 +250,7 @@ __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesD
       l[d] = v;
       inwin &= (unsigned)(v - 1) <= (unsigned)(Win<FW0, FW1, FW2>::w(P, d) - 4);
     }
-    if (!inwin) return false;
+    if (!inwin) return kStray;
   }
 
   float* u = r.u;
@@ -264,13 +273,10 @@ __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesD
 
   // A move that ends below the wall plane (only from the wall's own cell: a
   // step is shorter than one cell) is reflected: x -> 2 wall - x, u_x -> -u_x.
-  // Paths 0 and 1 leave it to k_particles_wall (keeping the reflection out of
-  // the tile kernel keeps its registers); the record is not written.
+  // The tile kernel defers it (keeping the reflection out of the tile kernel
+  // keeps its registers); the record is not written.
   const bool refl = MODE == 3 && ijk[0] + dc[0] < P.wall;
-  if (PATH != 2 && refl) {
-    S.wlist[atomicAdd(S.wcount, 1)] = p;
-    return true;
-  }
+  if (PATH != 2 && refl) return kWallCross;
 
   if (MODE != 2) {
     int nc[3] = {0, 0, 0};
@@ -319,14 +325,17 @@ __device__ __forceinline__ bool one_particle(const PushParams& P, const SpeciesD
       zigzag<D>(SJ, l, dc, o1, o2, dn, qs);
     }
   }
-  return true;
+  return kDone;
 }
 
 template <int D, int MODE, int FW0 = 0, int FW1 = 0, int FW2 = 1>
 __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D : PIC_PUSH_MIN_BLOCKS)
     k_particles(const PushParams P) {
   extern __shared__ __align__(16) float sm[];
-  __shared__ int q_n;  // entries in the stray queue
+  // 1D/2D: strays queued and processed by the block; 3D: deferred
+  constexpr bool kDrain = D < 3;
+  __shared__ int q_n;      // entries in the stray queue (1D/2D)
+  __shared__ int n_stray;  // particles of this block deferred as strays (3D)
   const GlobAcc GA{P.F, P.g.plane, P.g.n[0], P.g.n[1], P.g.n[2]};
   const int tile = blockIdx.x / P.splits;
   const int split = blockIdx.x - tile * P.splits;
@@ -342,10 +351,14 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
   const int fw = field_words(NF, wc);
   int* ji = reinterpret_cast<int*>(sm + fw);
   float* jf = sm + fw + 3 * ws;
-  int* queue = reinterpret_cast<int*>(sm + fw + 6 * ws);
+  int* queue = reinterpret_cast<int*>(sm + fw + 6 * ws);  // kDrain only
   const SmemJ SJ{ji, W0, W0 * W1, ws};
+  const int lane = threadIdx.x & 31;
 
-  if (threadIdx.x == 0) q_n = 0;
+  if (threadIdx.x == 0) {
+    q_n = 0;
+    n_stray = 0;
+  }
   for (int w = threadIdx.x; w < wc; w += blockDim.x) {
     const int lx = w % W0, rr = w / W0, ly = rr % W1, lz = rr / W1;
     const long long gi = GA.at(w0[0] + lx, w0[1] + ly, w0[2] + lz);
@@ -394,12 +407,15 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
       }
     }
   };
-  // process the queued strays through global memory, then empty the queue
+  // 1D/2D: process the queued strays through global memory, then empty the
+  // queue (a wall crosser among them is deferred)
   auto drain = [&](const SpeciesDev& S, int cnt) {
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
       PRec r;
       load_rec<D, MODE>(S, queue[i], r);
-      one_particle<D, MODE, 1, FW0, FW1, FW2>(P, S, queue[i], r, sm, SJ, GA, w0, 0.f);
+      if (one_particle<D, MODE, 1, FW0, FW1, FW2>(P, S, queue[i], r, sm, SJ, GA, w0, 0.f) ==
+          kWallCross)
+        S.dlist[atomicAdd(S.dcount, 1)] = queue[i];
     }
     if (threadIdx.x == 0) atomicAdd(P.strays, (unsigned long long)cnt);
     __syncthreads();
@@ -407,10 +423,10 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
     __syncthreads();
   };
 
-  // Particles kPushThreads at a time; the record of the next batch is loaded
-  // while the current one is processed.  Every kSpillEvery batches (and only
-  // there) the block synchronises, folds the current and, if the stray queue
-  // could overflow in the next round, drains it.
+  // Particles kPushThreads at a time (with PIC_PREFETCH the record of the next
+  // batch is loaded while the current one is processed).  Every kSpillEvery
+  // batches (and only there) the block synchronises, folds the current and, in
+  // 1D/2D, drains the stray queue if it could overflow in the next round.
   int batches = 0;
   for (int s = 0; s < P.nspecies; ++s) {
     const SpeciesDev& S = P.sp[s];
@@ -428,8 +444,26 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
       } else if (p < b) {
         load_rec<D, MODE>(S, p, cur);
       }
-      if (p < b && !one_particle<D, MODE, 0, FW0, FW1, FW2>(P, S, p, cur, sm, SJ, GA, w0, qs))
-        queue[atomicAdd(&q_n, 1)] = p;
+      const int st = p < b ? one_particle<D, MODE, false, FW0, FW1, FW2>(P, S, p, cur, sm, SJ, GA,
+                                                                         w0, qs)
+                           : kDone;
+      if (kDrain && st == kStray) queue[atomicAdd(&q_n, 1)] = p;
+      if (!kDrain || MODE == 3) {
+        // deferred particles: one list slot range per warp, reserved by one atomic
+        const bool dfr = kDrain ? st == kWallCross : st != kDone;
+        const unsigned defer = __ballot_sync(0xffffffffu, dfr);
+        if (defer) {
+          const unsigned strays = __ballot_sync(0xffffffffu, st == kStray);
+          const int leader = __ffs(defer) - 1;
+          int at = 0;
+          if (lane == leader) {
+            at = atomicAdd(S.dcount, __popc(defer));
+            if (!kDrain && strays) atomicAdd(&n_stray, __popc(strays));
+          }
+          at = __shfl_sync(0xffffffffu, at, leader);
+          if (dfr) S.dlist[at + __popc(defer & lanemask_lt())] = p;
+        }
+      }
       if (PIC_PREFETCH) cur = nxt;
       if (++batches == kSpillEvery) {
         batches = 0;
@@ -437,16 +471,19 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
         const int qn = q_n;  // read by every thread before anyone can queue again
         if (MODE != 1) spill();
         __syncthreads();
-        if (qn > kQueueCap - kSpillEvery * (int)blockDim.x) drain(S, qn);
+        if (kDrain && qn > kQueueCap - kSpillEvery * (int)blockDim.x) drain(S, qn);
       }
     }
-    // end of species: everything queued for it is processed before the next
-    __syncthreads();
-    const int qn = q_n;
-    __syncthreads();
-    if (qn > 0) drain(S, qn);
+    if (kDrain) {  // end of species: everything queued for it is processed before the next
+      __syncthreads();
+      const int qn = q_n;
+      __syncthreads();
+      if (qn > 0) drain(S, qn);
+    }
   }
 
+  __syncthreads();
+  if (threadIdx.x == 0 && n_stray > 0) atomicAdd(P.strays, (unsigned long long)n_stray);
   if (MODE != 1) {
     spill();
     __syncthreads();
@@ -478,20 +515,21 @@ __global__ void __launch_bounds__(kPushThreads) k_particles_tail(const PushParam
   }
 }
 
-// Particles whose move crossed the conducting wall (listed by k_particles):
-// the whole update again through global memory, with the reflection.  The
-// records were not written, so they are read where k_particles read them.
-template <int D>
-__global__ void __launch_bounds__(kPushThreads) k_particles_wall(const PushParams P) {
+// Particles that k_particles deferred (strays outside their tile window, and
+// moves across the conducting wall): the whole update through global memory,
+// with the reflection.  Their records were not written, so they are read
+// where k_particles read them; each slot is listed at most once per launch.
+template <int D, int MODE>
+__global__ void __launch_bounds__(kPushThreads) k_particles_deferred(const PushParams P) {
   const GlobAcc GA{P.F, P.g.plane, P.g.n[0], P.g.n[1], P.g.n[2]};
   for (int s = 0; s < P.nspecies; ++s) {
     const SpeciesDev& S = P.sp[s];
-    const int cnt = *S.wcount;
+    const int cnt = *S.dcount;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
-      const int p = S.wlist[i];
+      const int p = S.dlist[i];
       PRec r;
-      load_rec<D, 3>(S, p, r);
-      one_particle<D, 3, 2>(P, S, p, r, nullptr, SmemJ{nullptr, 0, 0, 0}, GA, nullptr, 0.f);
+      load_rec<D, MODE>(S, p, r);
+      one_particle<D, MODE, 2>(P, S, p, r, nullptr, SmemJ{nullptr, 0, 0, 0}, GA, nullptr, 0.f);
     }
   }
 }
@@ -499,7 +537,7 @@ __global__ void __launch_bounds__(kPushThreads) k_particles_wall(const PushParam
 size_t particle_smem_bytes(int dim, const TileDev& t) {
   const int nf = dim == 1 ? field_floats<1>() : field_floats<2>();
   return sizeof(float) * ((size_t)field_words(nf, t.wcells) + 6 * (size_t)t.wstride) +
-         sizeof(int) * kQueueCap;
+         (dim < 3 ? sizeof(int) * kQueueCap : 0);  // the 1D/2D stray queue
 }
 
 float current_quantum(float max_abs_q, float c, int batch) {
@@ -545,8 +583,14 @@ cudaError_t set_particle_smem_limit(int bytes) {
 }
 
 template <int D, int MODE>
-static void launch(const PushParams& P, cudaStream_t st) {
+static cudaError_t launch(const PushParams& P, cudaStream_t st) {
   const unsigned nblocks = (unsigned)P.t.ntiles * (unsigned)P.splits;
+  // the deferred lists can have entries in 3D (strays) and with the wall
+  constexpr bool deferred = D == 3 || MODE == 3;
+  if (deferred) {
+    const cudaError_t e = cudaMemsetAsync(P.dcount, 0, sizeof(int) * P.nspecies, st);
+    if (e != cudaSuccess) return e;
+  }
   const size_t smem = particle_smem_bytes(D, P.t);
   // fixed-window instantiations: 2D windows of 16x8 and 16x16 tiles with
   // halo 3 (23 x 15, 23 x 23), the 3D window of 8x8x4 tiles with halo 2
@@ -564,28 +608,30 @@ static void launch(const PushParams& P, cudaStream_t st) {
     k_particles<D, MODE><<<nblocks, kPushThreads, smem, st>>>(P);
   if ((MODE == 0 || MODE == 3) && P.tail_blocks > 0)
     k_particles_tail<D><<<(unsigned)P.tail_blocks, kPushThreads, 0, st>>>(P);
-  if (MODE == 3) k_particles_wall<D><<<4 * 152, kPushThreads, 0, st>>>(P);
+  if (deferred) k_particles_deferred<D, MODE><<<4 * 152, kPushThreads, 0, st>>>(P);
+  return cudaSuccess;
 }
 
 cudaError_t launch_particles(int dim, int mode, const PushParams& P, cudaStream_t st) {
   if ((long long)P.t.ntiles * P.splits == 0) return cudaSuccess;
   if (mode == 0 && P.wall > 0) mode = 3;  // the fused kernel with the conducting wall
+  cudaError_t e;
   switch (dim * 4 + mode) {
-    case 4: launch<1, 0>(P, st); break;
-    case 5: launch<1, 1>(P, st); break;
-    case 6: launch<1, 2>(P, st); break;
-    case 7: launch<1, 3>(P, st); break;
-    case 8: launch<2, 0>(P, st); break;
-    case 9: launch<2, 1>(P, st); break;
-    case 10: launch<2, 2>(P, st); break;
-    case 11: launch<2, 3>(P, st); break;
-    case 12: launch<3, 0>(P, st); break;
-    case 13: launch<3, 1>(P, st); break;
-    case 14: launch<3, 2>(P, st); break;
-    case 15: launch<3, 3>(P, st); break;
+    case 4: e = launch<1, 0>(P, st); break;
+    case 5: e = launch<1, 1>(P, st); break;
+    case 6: e = launch<1, 2>(P, st); break;
+    case 7: e = launch<1, 3>(P, st); break;
+    case 8: e = launch<2, 0>(P, st); break;
+    case 9: e = launch<2, 1>(P, st); break;
+    case 10: e = launch<2, 2>(P, st); break;
+    case 11: e = launch<2, 3>(P, st); break;
+    case 12: e = launch<3, 0>(P, st); break;
+    case 13: e = launch<3, 1>(P, st); break;
+    case 14: e = launch<3, 2>(P, st); break;
+    case 15: e = launch<3, 3>(P, st); break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace pic

@@ -20,12 +20,6 @@ __device__ __forceinline__ int tile_key(const SortParams& P, int cell) {
   return fdiv(i, P.dt0) + P.t.nt[0] * (fdiv(j, P.dt1) + P.t.nt[1] * fdiv(k, P.dt2));
 }
 
-__device__ __forceinline__ unsigned lanemask_lt() {
-  unsigned m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
-
 // Reserve `1` slot of counter[key] for every active lane; returns this lane's
 // slot.  Lanes with equal keys share one atomic.
 __device__ __forceinline__ int warp_reserve(int* counter, int key, unsigned active) {
