@@ -29,7 +29,7 @@
  * Ownership: the caller owns the field and particle buffers and the stream;
  * the library owns the context, its scratch (sort buffers, tile tables,
  * pre-move snapshot, filter buffer, diagnostics, status word, injector
- * templates and wall list) and frees them in pic_destroy.  All calls enqueue
+ * templates, deferred-particle lists) and frees them in pic_destroy.  All calls enqueue
  * work on the context's stream and return without synchronising, except
  * pic_energies, pic_check, pic_step_host, pic_stats, pic_autotune,
  * pic_kernel_times and pic_set_shock (which copies the templates), which

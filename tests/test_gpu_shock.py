@@ -1,5 +1,5 @@
 """Shock boundaries on the GPU (Sect. 4.2): conducting wall (reflection in
-k_particles_wall, field images) and receding injector (k_inject, the unsorted
+k_particles_deferred, field images) and receding injector (k_inject, the unsorted
 tail kernel) against the FP64 oracle, plus the argument and state errors."""
 import numpy as np
 import pytest
