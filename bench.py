@@ -536,6 +536,11 @@ def run_batched(args):
     achieved = alg * args.steps / (ms * 1e-3) / 1e9
     peak, peak_kind = hbm_peak()
     cadences = sorted({sm.tuning()["sort_every"] for sm in sims})
+    # per box and step: two B half steps, the tile particle kernel, the E update
+    # (1D/2D periodic boxes: no deferred-particle kernel, no filter); per sort:
+    # count, scan and scatter per species
+    launches = sum(args.steps * 4 + -(-args.steps // sm.tuning()["sort_every"]) * 3 * sm.nspecies
+                   for sm in sims)
     line = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -552,6 +557,7 @@ def run_batched(args):
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "whole step of all boxes (graph replay; per-kernel events are not"
                                " recorded inside graphs)", "peak_source": peak_kind},
+        "gpu_launches": launches,
         "clocks": clocks, "e2e": None,
     }
     if rank == 0:
