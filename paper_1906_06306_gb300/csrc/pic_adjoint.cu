@@ -17,22 +17,15 @@
 
 namespace pic {
 
-static unsigned grid_for(long long n, int threads) {
-  long long b = (n + threads - 1) / threads;
-  if (b > (1LL << 20)) b = 1LL << 20;
-  return (unsigned)(b < 1 ? 1 : b);
-}
-
 // Adjoint of E' = E + c curl- B2 - Jf:  Bbar += c curl+ Ebar,  Jbar = -Ebar.
 template <int D>
 __global__ void k_adj_e(float* __restrict__ A, const GridDev g, float c) {
   const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const long long P = g.plane;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(idx % n0);
-    const long long r = idx / n0;
-    const int j = (int)(r % n1), k = (int)(r / n1);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n0) return;
+  FOR_ROWS(j, k) {
+    const long long idx = (long long)i + (long long)n0 * (j + (long long)n1 * k);
     const long long sx = (i + 1 < n0) ? 1 : 1 - n0;
     const long long sy = (D >= 2) ? ((j + 1 < n1) ? n0 : (long long)n0 * (1 - n1)) : 0;
     const long long sz = (D >= 3) ? ((k + 1 < n2) ? (long long)n0 * n1 : (long long)n0 * n1 * (1 - n2)) : 0;
@@ -66,11 +59,10 @@ template <int D>
 __global__ void k_adj_b(float* __restrict__ A, const GridDev g, float h) {
   const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const long long P = g.plane;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(idx % n0);
-    const long long r = idx / n0;
-    const int j = (int)(r % n1), k = (int)(r / n1);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n0) return;
+  FOR_ROWS(j, k) {
+    const long long idx = (long long)i + (long long)n0 * (j + (long long)n1 * k);
     const long long sx = (i > 0) ? 1 : 1 - n0;
     const long long sy = (D >= 2) ? ((j > 0) ? n0 : (long long)n0 * (1 - n1)) : 0;
     const long long sz = (D >= 3) ? ((k > 0) ? (long long)n0 * n1 : (long long)n0 * n1 * (1 - n2)) : 0;
@@ -370,23 +362,23 @@ __global__ void __launch_bounds__(256) k_adj_particles(const AdjParams P) {
 }
 
 cudaError_t launch_adj_e(const GridDev& g, float* A, cudaStream_t st) {
-  const unsigned nb = grid_for(g.plane, 256);
+  const RowLaunch L = row_launch(g);
   switch (g.dim) {
-    case 1: k_adj_e<1><<<nb, 256, 0, st>>>(A, g, g.c); break;
-    case 2: k_adj_e<2><<<nb, 256, 0, st>>>(A, g, g.c); break;
-    case 3: k_adj_e<3><<<nb, 256, 0, st>>>(A, g, g.c); break;
+    case 1: k_adj_e<1><<<L.grid, L.threads, 0, st>>>(A, g, g.c); break;
+    case 2: k_adj_e<2><<<L.grid, L.threads, 0, st>>>(A, g, g.c); break;
+    case 3: k_adj_e<3><<<L.grid, L.threads, 0, st>>>(A, g, g.c); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_adj_b_half(const GridDev& g, float* A, cudaStream_t st) {
-  const unsigned nb = grid_for(g.plane, 256);
+  const RowLaunch L = row_launch(g);
   const float h = 0.5f * g.c;
   switch (g.dim) {
-    case 1: k_adj_b<1><<<nb, 256, 0, st>>>(A, g, h); break;
-    case 2: k_adj_b<2><<<nb, 256, 0, st>>>(A, g, h); break;
-    case 3: k_adj_b<3><<<nb, 256, 0, st>>>(A, g, h); break;
+    case 1: k_adj_b<1><<<L.grid, L.threads, 0, st>>>(A, g, h); break;
+    case 2: k_adj_b<2><<<L.grid, L.threads, 0, st>>>(A, g, h); break;
+    case 3: k_adj_b<3><<<L.grid, L.threads, 0, st>>>(A, g, h); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -8,26 +8,6 @@
 
 namespace pic {
 
-// The field updates run on a (x blocks, y, z) launch grid: a thread owns
-// point x of the rows (y, z) of its block, stepping over rows beyond the
-// launch grid's 65535 limit, so no lattice index is ever divided out of a
-// linear one.
-#define FOR_ROWS(j, k)                                  \
-  for (int k = blockIdx.z; k < n2; k += gridDim.z)      \
-    for (int j = blockIdx.y; j < n1; j += gridDim.y)
-
-struct RowLaunch {
-  dim3 grid;
-  unsigned threads;
-};
-static RowLaunch row_launch(const GridDev& g) {
-  const int n0 = g.n[0];
-  const unsigned t = n0 >= 256 ? 256 : n0 >= 128 ? 128 : n0 >= 64 ? 64 : 32;
-  return {dim3((unsigned)((n0 + t - 1) / t), (unsigned)min(g.n[1], 65535),
-               (unsigned)min(g.n[2], 65535)),
-          t};
-}
-
 // B -= (c/2) curl+ E (forward differences: B sits half a cell above E), and,
 // when zero_j is set, clear J for the deposit that follows.
 template <int D>

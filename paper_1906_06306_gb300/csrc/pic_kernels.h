@@ -31,6 +31,26 @@ constexpr int kSpillEvery = PIC_SPILL_EVERY;  // batches of kPushThreads particl
 // kPushThreads particles can be queued, so this capacity can never be exceeded.
 constexpr int kQueueCap = kPushThreads * kSpillEvery;
 
+// Lattice kernels run on a (x blocks, y, z) launch grid: a thread owns point x
+// of the rows (y, z) of its block, stepping over rows beyond the launch grid's
+// 65535 limit, so no lattice index is ever divided out of a linear one.  The
+// kernel body names the extents n1, n2.
+#define FOR_ROWS(j, k)                             \
+  for (int k = blockIdx.z; k < n2; k += gridDim.z) \
+    for (int j = blockIdx.y; j < n1; j += gridDim.y)
+
+struct RowLaunch {
+  dim3 grid;
+  unsigned threads;
+};
+inline RowLaunch row_launch(const GridDev& g) {
+  const int n0 = g.n[0];
+  const unsigned t = n0 >= 256 ? 256 : n0 >= 128 ? 128 : n0 >= 64 ? 64 : 32;
+  const unsigned gy = (unsigned)(g.n[1] < 65535 ? g.n[1] : 65535);
+  const unsigned gz = (unsigned)(g.n[2] < 65535 ? g.n[2] : 65535);
+  return {dim3((unsigned)((n0 + t - 1) / t), gy, gz), t};
+}
+
 struct PushParams {
   GridDev g;
   TileDev t;

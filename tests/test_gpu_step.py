@@ -94,6 +94,61 @@ def test_step_with_frequent_sorts_and_strays_matches_oracle_fields():
     sim.close()
 
 
+@pytest.mark.parametrize("tile,halo", [((8, 8, 4), 2), ((4, 4, 4), 1)])
+def test_3d_strays_are_deferred_and_match_oracle(tile, halo):
+    """3D tile kernels leave strays (stencil outside the tile window) to the
+    deferred-particle kernel.  A hot plasma without re-sorting on a ragged box,
+    with the fixed 8x8x4-tile window (halo 2) and the generic kernel (halo 1):
+    particles and fields follow the oracle slot by slot, and strays occurred."""
+    from paper_1906_06306_gb300 import binding as B
+    from paper_1906_06306_gb300 import Simulation
+
+    pl = workloads.uniform_plasma(3, 21, 19, 13, 0.45, 2, 0.01, 2.0, seed=27)
+    sim = Simulation.from_plasma(pl, tuning=dict(tile=list(tile), halo=halo, sort_every=1000))
+    g, F, osp, _ = oracle_from_sim(sim)
+    B.pic_stats(sim.ctx)  # reset the counter
+    for _ in range(5):
+        sim.step(1)
+        oracle.step(g, F, osp)
+    assert B.pic_stats(sim.ctx) > 0
+    sim.check()
+    Fg, spg = sim.download()
+    compare_fields(Fg, F, floor=step_floor(g, osp, 5))
+    compare_particles(g, spg, osp)
+    sim.close()
+
+
+def test_3d_split_path_defers_strays_and_matches_oracle():
+    """pic_gather_push and pic_deposit in 3D after particles drifted out of
+    their tile windows: the deferred kernel runs the strays in both modes (the
+    push writes the pre-move snapshot, the deposit reads it)."""
+    from paper_1906_06306_gb300 import binding as B
+    from paper_1906_06306_gb300 import Simulation
+
+    pl = workloads.uniform_plasma(3, 21, 19, 13, 0.45, 2, 0.01, 2.0, seed=28)
+    sim = Simulation.from_plasma(pl, tuning=dict(tile=[8, 8, 4], halo=2, sort_every=1000))
+    sim.step(4)
+    g, F, osp, sp0 = oracle_from_sim(sim)
+    B.pic_stats(sim.ctx)
+    sim.gather_push()
+    assert B.pic_stats(sim.ctx) > 0
+    sim.deposit()
+    sim.check()
+    Fg, spg = sim.download()
+    for o in osp:
+        oracle.push_particles(g, F, o)
+    compare_particles(g, spg, osp, xtol=2e-6, utol=2e-6)
+    Fo = np.zeros_like(F)
+    for s0, s1 in zip(sp0, spg):
+        x_old = oracle.positions(g, s0["cell"], s0["off"])
+        x_new = oracle.positions(g, s1["cell"], s1["off"])
+        dx = periodic_dx(g, x_new, x_old)
+        oracle.deposit(g, Fo, np.ascontiguousarray(x_old), np.ascontiguousarray(dx), s0["q"])
+    for c in range(6, 9):
+        assert rel_err(Fg[c] - F[c], Fo[c]) < 1e-5, c
+    sim.close()
+
+
 def test_edge_cases_tiny_grid_offsets_and_empty_species():
     """Grid smaller than a tile window (every particle takes the global path),
     offsets exactly 0 and just below 1, and an empty third species."""
