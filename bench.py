@@ -312,6 +312,19 @@ def push_bytes_per_launch(pl, nparticles=None) -> float:
     return float(n * 2 * rec + pl.ncells * (6 + 3) * 4)
 
 
+def step_bytes(pl, nparticles, filter_passes, sort_every) -> float:
+    """Algorithmic DRAM bytes of one whole pic_step: the fused particle launch
+    (push_bytes_per_launch), the two B half steps (E and B read, B written: 36 B
+    per cell; the first also clears J: 12 B more), the E update (E, B, J read, E
+    written: 48 B), 24 B per cell for each filter pass, and the tile sort
+    amortised over its cadence (the cell keys read to count, every record read
+    and written by the scatter)."""
+    rec = 4 + 4 * pl.dim + 12
+    fields = pl.ncells * (36 + 48 + 48 + 24 * filter_passes)
+    sort = nparticles * (4 + 2 * rec) / sort_every
+    return push_bytes_per_launch(pl, nparticles) + fields + sort
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -431,6 +444,7 @@ def run_ours(args):
     alg = push_bytes_per_launch(pl, avg_n)
     achieved = alg / avg_push_s / 1e9
     traffic = profiled_traffic() if args.workload == "turbulence_2d3v" and pl.nx == 1024 else None
+    step_alg = step_bytes(pl, avg_n, tun["filter_passes"], tun["sort_every"])
     nsorts = -(-args.steps // tun["sort_every"])  # at most one sort per cadence in the loop
     # per step: two B half steps, the tile particle kernel, the E update, one fused
     # launch per filter pass and, in 3D or with the wall, the deferred-particle
@@ -462,6 +476,12 @@ def run_ours(args):
                                + (", conducting-wall variant)" if shock else ")"),
                      "peak_source": peak_kind, "avg_launch_us": avg_push_s * 1e6,
                      "alg_bytes_per_launch": alg},
+        "step_roofline": {"bound": "hbm", "achieved": step_alg / (ms_max * 1e-3 / args.steps) / 1e9,
+                          "peak": peak, "unit": "GB/s",
+                          "frac": step_alg / (ms_max * 1e-3 / args.steps) / 1e9 / peak,
+                          "alg_bytes_per_step": step_alg,
+                          "note": "whole pic_step: particle kernel, field updates, filter passes"
+                                  " and the tile sort amortised over its cadence"},
         "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in kt.items()},
         "gpu_launches": launches,
         "clocks": clocks,
