@@ -79,6 +79,32 @@ def test_batch_matches_each_box_stepped_alone():
         s.close()
 
 
+def test_batch_with_a_3d_box_defers_strays_inside_the_graph():
+    """A 3D box (hot plasma, halo 1: its tile kernel defers strays to the
+    deferred-particle kernel, which then runs inside the captured graph)
+    batched with a 2D one, against each stepped alone."""
+    from paper_1906_06306_gb300 import Batch, Simulation
+
+    plasmas = [workloads.uniform_plasma(3, 13, 11, 9, 0.45, 2, 0.01, 2.0, seed=520),
+               _boxes()[1]]
+    tun = [dict(tile=[4, 4, 4], halo=1, sort_every=5), dict(sort_every=5)]
+
+    def make():
+        return [Simulation.from_plasma(pl, tuning=t) for pl, t in zip(plasmas, tun)]
+
+    batched, alone = make(), make()
+    batch = Batch(batched)
+    batch.step(12)
+    for s in alone:
+        s.step(12)
+    for a, b in zip(batched, alone):
+        a.check()
+        _same_state(a, b, 12)
+    batch.close()
+    for s in batched + alone:
+        s.close()
+
+
 def test_batched_box_follows_the_oracle():
     from paper_1906_06306_gb300 import Batch
 

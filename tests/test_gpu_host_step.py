@@ -39,8 +39,8 @@ def _oracle_like(sim):
     return oracle.Grid(sim.dim, sim.nx, sim.ny, sim.nz, sim.c)
 
 
-@pytest.mark.parametrize("shock", [False, True])
-def test_step_host_equals_device_steps(shock):
+@pytest.mark.parametrize("shock,dim", [(False, 2), (True, 2), (False, 3)])
+def test_step_host_equals_device_steps(shock, dim):
     import oracle
 
     from paper_1906_06306_gb300 import Simulation
@@ -50,12 +50,16 @@ def test_step_host_equals_device_steps(shock):
         pl = workloads.shock_tube(dim=2, nx=48, ny=8, nz=1, ppc=3, gamma_flow=3.0, theta=0.05,
                                   r_p=3.0, wall=3, x_inj=20, x_max=40.0, lt=8, seed=93)
         cap = [s.n + workloads.injected_count(pl, 6) for s in pl.species]
-    else:
+    elif dim == 2:
         pl = workloads.turbulence_2d(n=64, ppc=4, r_p=4.0, theta=0.3, sigma=10.0, modes=4, seed=94)
         cap = None
+    else:  # hot 3D plasma, halo 1: strays go through the deferred-particle kernel
+        pl = workloads.uniform_plasma(3, 21, 19, 13, 0.45, 2, 0.01, 2.0, seed=95)
+        cap = None
+    tun = dict(sort_every=1000) if dim == 2 else dict(tile=[4, 4, 4], halo=1, sort_every=1000)
     sims = []
     for _ in range(2):
-        sim = Simulation.from_plasma(pl, capacity=cap, tuning=dict(sort_every=1000))
+        sim = Simulation.from_plasma(pl, capacity=cap, tuning=tun)
         if shock:
             sim.set_shock_from_plasma(pl)
         sims.append(sim)
