@@ -105,6 +105,31 @@ def test_batch_with_a_3d_box_defers_strays_inside_the_graph():
         s.close()
 
 
+def test_full_ensemble_batched_matches_sampled_boxes_alone():
+    """The benchmark's ensemble (256 uneven 1D/2D Weibel boxes, 252.7 M
+    particles) stepped as one batch, in the launch configuration of the
+    benchmark (one graph per sort cycle of all boxes): a seeded sample of
+    boxes against the same boxes stepped alone, over two sort cycles."""
+    from paper_1906_06306_gb300 import Batch, Simulation
+
+    recipe = workloads.weibel_ensemble(count=256)
+    plasmas = [workloads.weibel_box(*b) for b in recipe]
+    assert sum(p.nparticles for p in plasmas) > 2.5e8
+    batched = [Simulation.from_plasma(p, tuning=dict(sort_every=10)) for p in plasmas]
+    picks = sorted(np.random.default_rng(256).choice(256, size=6, replace=False))
+    alone = [Simulation.from_plasma(plasmas[i], tuning=dict(sort_every=10)) for i in picks]
+    batch = Batch(batched)
+    batch.step(21)
+    for s in alone:
+        s.step(21)
+    for i, s in zip(picks, alone):
+        batched[i].check()
+        _same_state(batched[i], s, 21)
+    batch.close()
+    for s in batched + alone:
+        s.close()
+
+
 def test_batched_box_follows_the_oracle():
     from paper_1906_06306_gb300 import Batch
 
