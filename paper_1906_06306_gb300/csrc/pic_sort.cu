@@ -32,15 +32,56 @@ __device__ __forceinline__ int warp_reserve(int* counter, int key, unsigned acti
   return base + __popc(peers & lanemask_lt());
 }
 
-__global__ void k_tile_count(const SortParams P, const int* __restrict__ cell, long long n,
-                             int* count) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const long long p = base + threadIdx.x;
-    const bool act = p < n;
-    const unsigned active = __ballot_sync(0xffffffffu, act);
-    if (act) warp_reserve(count, tile_key(P, cell[p]), active);
+// Tiles of a block's contiguous chunk of particles, counted in a shared-memory
+// table before the global counters: in a sorted or nearly sorted array a
+// chunk spans a few tiles and their neighbours, so each of those reaches the
+// global count once per block instead of once per warp (the same-address
+// global atomics of the per-warp count were its limit).  Lanes of a warp with
+// the same tile combine first; a table slot is claimed by compare-and-swap,
+// and a tile whose slot another tile holds goes straight to the global count.
+constexpr int kCountSlots = 1024;
+__global__ void __launch_bounds__(256) k_tile_count(const SortParams P, const int* __restrict__ cell,
+                                                    long long n, long long chunk, int* count) {
+  __shared__ int skey[kCountSlots];
+  __shared__ int scnt[kCountSlots];
+  for (int s = threadIdx.x; s < kCountSlots; s += blockDim.x) {
+    skey[s] = -1;
+    scnt[s] = 0;
   }
+  __syncthreads();
+  const long long lo = (long long)blockIdx.x * chunk;
+  const long long hi = lo + chunk < n ? lo + chunk : n;
+  const int lane = threadIdx.x & 31;
+  constexpr int U = 4;  // rounds whose loads are issued together (4 loads in flight per thread)
+  for (long long base = lo; base < hi; base += U * blockDim.x) {  // block-uniform trip count
+    int c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long p = base + u * blockDim.x + threadIdx.x;
+      c[u] = p < hi ? cell[p] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool act = base + u * blockDim.x + threadIdx.x < hi;
+      const unsigned active = __ballot_sync(0xffffffffu, act);
+      if (act) {
+        const int key = tile_key(P, c[u]);
+        const unsigned peers = __match_any_sync(active, key);
+        if (lane == __ffs(peers) - 1) {
+          const int n_same = __popc(peers);
+          const int slot = (int)(((unsigned)key * 2654435761u) >> 22);  // multiplicative hash, 10 bits
+          const int old = atomicCAS(&skey[slot], -1, key);
+          if (old == -1 || old == key)
+            atomicAdd(&scnt[slot], n_same);
+          else
+            atomicAdd(&count[key], n_same);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < kCountSlots; s += blockDim.x)
+    if (skey[s] >= 0) atomicAdd(&count[skey[s]], scnt[s]);
 }
 
 // Exclusive scan of count[0..ntiles) into start[0..ntiles] (start[ntiles] =
@@ -129,7 +170,13 @@ static unsigned blocks_for(long long n) {
 cudaError_t launch_tile_count(const SortParams& P, const int* cell, long long n, int* count,
                               cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_tile_count<<<blocks_for(n), 256, 0, st>>>(P, cell, n, count);
+  // contiguous chunks of at least 4096 particles (a multiple of 256), at most
+  // 16 blocks per SM
+  long long nb = (n + 4095) / 4096;
+  if (nb > 152LL * 16) nb = 152LL * 16;
+  const long long chunk = ((n + nb - 1) / nb + 255) / 256 * 256;
+  nb = (n + chunk - 1) / chunk;
+  k_tile_count<<<(unsigned)nb, 256, 0, st>>>(P, cell, n, chunk, count);
   return cudaGetLastError();
 }
 
