@@ -99,7 +99,9 @@ typedef struct {
  * halo-1 cells from its tile since the last sort takes the global-memory
  * path); sort_every: steps between tile sorts inside pic_step; filter_passes:
  * Binomial2 passes applied to J inside pic_step (Sect. 4.2 uses 8, the
- * 3D shock-shaped workload 4); chunk: target particles per thread block. */
+ * 3D shock-shaped workload 4); chunk: target particles per thread block (a box
+ * with fewer tiles than 4 per SM splits them further, down to 256 particles
+ * per block, until the particle launch has 4 blocks per SM). */
 typedef struct {
   int tile[3];
   int halo;

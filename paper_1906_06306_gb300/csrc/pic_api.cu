@@ -39,6 +39,8 @@ struct pic_ctx {
   GridDev g{};
   TileDev tile{};
   int splits = 1;
+  int splits_ens = 1;     // the same without the GPU-filling rule (inside a batch graph)
+  bool ensemble = false;  // being captured into a batch graph
   long long ntot = 0, nmax = 0;
   int* d_tstart[PIC_MAX_SPECIES] = {};
   int* d_count = nullptr;   // per tile
@@ -139,9 +141,23 @@ void free_all(pic_ctx* ctx) {
 
 int extent(const pic_grid& g, int d) { return d == 0 ? g.nx : d == 1 ? g.ny : g.nz; }
 
+// Streaming multiprocessors of the current device (looked up once).
+int device_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      sms = v;
+    else
+      return 152;
+  }
+  return sms;
+}
+
 // Tile geometry from the tuning; returns an error message or "".
 std::string derive_tiles(const pic_grid& grid, const pic_tuning& tun, long long ntot,
-                         TileDev* t, int* splits) {
+                         TileDev* t, int* splits, int* splits_ens) {
   if (tun.halo < 1) return "halo must be >= 1";
   if (tun.chunk < 32) return "chunk must be >= 32";
   TileDev r{};
@@ -170,11 +186,18 @@ std::string derive_tiles(const pic_grid& grid, const pic_tuning& tun, long long 
   if (ntiles > (1LL << 30)) return "too many tiles";
   r.ntiles = (int)ntiles;
   const long long per_tile = (ntot + ntiles - 1) / ntiles;
+  const auto clamp = [](long long v) { return (int)(v < 1 ? 1 : v > 1024 ? 1024 : v); };
   long long sp = (per_tile + tun.chunk - 1) / tun.chunk;
-  if (sp < 1) sp = 1;
-  if (sp > 1024) sp = 1024;
+  *splits_ens = clamp(sp);
+  // a box with few tiles splits them further, down to 256 particles per block,
+  // until a launch has 4 blocks per SM (else most of the GPU idles while each
+  // thread runs many particles in turn); inside a batch graph the ensemble
+  // fills the GPU and the finer split only adds window loads and flushes
+  const long long fill = (4LL * device_sms() + ntiles - 1) / ntiles;
+  const long long fine = (per_tile + 255) / 256;
+  if (sp < fill) sp = fill < fine ? fill : fine;
   *t = r;
-  *splits = (int)sp;
+  *splits = clamp(sp);
   return "";
 }
 
@@ -251,7 +274,7 @@ PushParams make_params(pic_ctx* ctx) {
   P.t = ctx->tile;
   P.F = ctx->F;
   P.nspecies = ctx->ns;
-  P.splits = ctx->splits;
+  P.splits = ctx->ensemble ? ctx->splits_ens : ctx->splits;
   P.status = ctx->d_status;
   P.strays = ctx->d_strays;
   P.pusher = ctx->pusher;
@@ -340,8 +363,11 @@ pic_status do_sort(pic_ctx* ctx, bool copy_back) {
   }
   if (ntot != ctx->ntot) {  // injection changed the count: re-derive the splits per tile
     TileDev td{};
-    int splits = 1;
-    if (derive_tiles(ctx->grid, ctx->tun, ntot, &td, &splits).empty()) ctx->splits = splits;
+    int splits = 1, splits_ens = 1;
+    if (derive_tiles(ctx->grid, ctx->tun, ntot, &td, &splits, &splits_ens).empty()) {
+      ctx->splits = splits;
+      ctx->splits_ens = splits_ens;
+    }
     ctx->ntot = ntot;
   }
   ctx->snapshot_valid = false;
@@ -498,7 +524,8 @@ pic_status pic_init(pic_ctx** out, const pic_grid* grid, const pic_species* spec
   ctx->tun.sort_every = grid->dim == 3 ? 3 : 10;
   ctx->tun.filter_passes = 0;
   ctx->tun.chunk = 4096;
-  const std::string msg = derive_tiles(ctx->grid, ctx->tun, ntot, &ctx->tile, &ctx->splits);
+  const std::string msg =
+      derive_tiles(ctx->grid, ctx->tun, ntot, &ctx->tile, &ctx->splits, &ctx->splits_ens);
   if (!msg.empty()) {
     delete ctx;
     return set_err(nullptr, PIC_ERR_ARG, msg);
@@ -550,12 +577,13 @@ pic_status pic_set_tuning(pic_ctx* ctx, const pic_tuning* t) {
   if (nt.sort_every < 1) return set_err(ctx, PIC_ERR_ARG, "sort_every must be >= 1");
   if (nt.filter_passes < 0) return set_err(ctx, PIC_ERR_ARG, "filter_passes must be >= 0");
   TileDev td{};
-  int splits = 1;
-  const std::string msg = derive_tiles(ctx->grid, nt, ctx->ntot, &td, &splits);
+  int splits = 1, splits_ens = 1;
+  const std::string msg = derive_tiles(ctx->grid, nt, ctx->ntot, &td, &splits, &splits_ens);
   if (!msg.empty()) return set_err(ctx, PIC_ERR_ARG, msg);
   const bool retile = std::memcmp(&td, &ctx->tile, sizeof(TileDev)) != 0;
   ctx->tun = nt;
   ctx->splits = splits;
+  ctx->splits_ens = splits_ens;
   if (retile) {
     PIC_CK(ctx, cudaStreamSynchronize(ctx->st));
     ctx->tile = td;
@@ -1111,7 +1139,9 @@ pic_status batch_capture(pic_batch* b) {
     saved_timing[i] = c->timing;
     c->st = b->branches[i % b->branches.size()];
     c->timing = false;
+    c->ensemble = true;
     st = pic_step(c, b->cycle);
+    c->ensemble = false;
     c->st = saved_st[i];
     c->timing = saved_timing[i];
     c->steps = saved_steps[i];  // the captured steps have not run yet
