@@ -79,7 +79,9 @@ def workload_config(name, pl):
     grid = [pl.nx, pl.ny, pl.nz][: pl.dim]
     return dict(workload=name, grid=grid, **w["desc"], filter_passes=w["filter_passes"])
 FALLBACK_HBM_GBS = 6800.0
-PROFILE = os.path.join(ROOT, "profiles", "push_turbulence_2d3v.md")
+# committed ncu summaries of the fused particle kernel, per workload
+PROFILES = {"turbulence_2d3v": os.path.join(ROOT, "profiles", "push_turbulence_2d3v.md"),
+            "shock_3d3v": os.path.join(ROOT, "profiles", "push_shock_3d3v.md")}
 
 
 def kernel_source_hash() -> str:
@@ -97,12 +99,14 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the fused particle kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+def profiled_traffic(workload, full_size, nparticles):
+    """DRAM bytes per launch of the fused particle kernel from the workload's
+    committed ncu summary, if it was taken on the current kernel source: the
+    bytes of a full-size launch when the summary gives them, else its bytes per
+    particle (a capture of a smaller box) times the particles of a launch."""
     try:
-        txt = open(PROFILE).read()
-    except OSError:
+        txt = open(PROFILES[workload]).read()
+    except (KeyError, OSError):
         return None
     vals = {}
     for line in txt.splitlines():
@@ -112,7 +116,9 @@ def profiled_traffic():
     if vals.get("kernel_source_hash") != kernel_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_full_launch"])
+        if "dram_bytes_per_full_launch" in vals:
+            return float(vals["dram_bytes_per_full_launch"]) if full_size else None
+        return float(vals["dram_bytes_per_particle"]) * nparticles
     except (KeyError, ValueError):
         return None
 
@@ -443,7 +449,7 @@ def run_ours(args):
     peak, peak_kind = hbm_peak()
     alg = push_bytes_per_launch(pl, avg_n)
     achieved = alg / avg_push_s / 1e9
-    traffic = profiled_traffic() if args.workload == "turbulence_2d3v" and pl.nx == 1024 else None
+    traffic = profiled_traffic(args.workload, pl.nx == 1024, avg_n)
     step_alg = step_bytes(pl, avg_n, tun["filter_passes"], tun["sort_every"])
     nsorts = -(-args.steps // tun["sort_every"])  # at most one sort per cadence in the loop
     # per step: two B half steps, the tile particle kernel, the E update, one fused

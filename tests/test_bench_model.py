@@ -33,3 +33,20 @@ def test_step_bytes_adds_fields_filter_and_amortised_sort():
     assert abs(b.step_bytes(pl, 1000, 4, 3) - (push + fields + sort)) < 1e-6
     # the fused launch at a different mean particle count
     assert b.push_bytes_per_launch(pl, 500) == 500 * 56 + 64 * 36
+
+
+def test_profiled_traffic_reads_the_summary_only_for_the_current_kernel(tmp_path, monkeypatch):
+    b = _bench()
+    h = b.kernel_source_hash()
+    full = tmp_path / "full.md"
+    full.write_text(f"text\n\n- kernel_source_hash: `{h}`\n- dram_bytes_per_full_launch: `1.5e9`\n")
+    per = tmp_path / "per.md"
+    per.write_text(f"- kernel_source_hash: `{h}`\n- dram_bytes_per_particle: `60.0`\n")
+    stale = tmp_path / "stale.md"
+    stale.write_text("- kernel_source_hash: `0000000000000000`\n- dram_bytes_per_particle: `60.0`\n")
+    monkeypatch.setattr(b, "PROFILES", {"a": str(full), "b": str(per), "c": str(stale)})
+    assert b.profiled_traffic("a", True, 123) == 1.5e9
+    assert b.profiled_traffic("a", False, 123) is None  # a full-launch figure needs the full box
+    assert b.profiled_traffic("b", False, 1000.0) == 60.0 * 1000.0
+    assert b.profiled_traffic("c", True, 1000.0) is None  # taken on other kernel source
+    assert b.profiled_traffic("missing", True, 1000.0) is None
