@@ -382,6 +382,7 @@ def run_ours(args):
     sampler.start()
     time.sleep(0.3)
     B.pic_kernel_times(sim.ctx)  # reset counters
+    B.pic_stats(sim.ctx)  # reset the stray count
     B.pic_timing(sim.ctx, True)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -395,6 +396,7 @@ def run_ours(args):
     ms = t0.elapsed_time(t1)
     kt = B.pic_kernel_times(sim.ctx)
     B.pic_timing(sim.ctx, False)
+    strays = B.pic_stats(sim.ctx)  # particle updates that left their tile window
     clocks = sampler.stop()
     if dist is not None:
         dist.barrier()
@@ -471,6 +473,7 @@ def run_ours(args):
                        {"start": pl.nparticles, "end": sum(sim.counts()), "mean_timed": avg_n},
                        sort_every=tun["sort_every"],
                        tile=tun["tile"][: pl.dim], halo=tun["halo"], autotuned=bool(autotuned),
+                       strays_per_particle_step=strays / max(done, 1),
                        parallelism="replicas" if world > 1 else "single-gpu",
                        l2=("inputs larger than L2 (particle SoA %.2f GB), no flush" if
                            pl.nparticles * (16 + 4 * pl.dim) > 2 * 129e6 else
