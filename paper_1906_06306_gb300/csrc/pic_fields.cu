@@ -330,6 +330,87 @@ __global__ void __launch_bounds__(256, 4) k_filter_z3(const float* __restrict__ 
   cp_async_wait<0>();
 }
 
+// One full 2D Binomial2 pass (x, then y sub-pass) of one plane src -> dst,
+// marching along y: a block of 256 threads owns YX = 1024 x-points (4 per
+// thread) over a run of `yrun` rows.  Each row plus its one-point periodic x
+// halo goes through a ring of ZS shared-memory stages by cp.async (16-byte
+// copies for aligned interior chunks, 4-byte ones for the halo and for ragged
+// or wrapped chunks), ZS - 1 rows ahead of the one being filtered; a thread
+// runs the x sub-pass of its 4 points from one 16-byte and two 4-byte shared
+// loads and keeps the last three results for the y sub-pass.  Every output
+// goes through the same arithmetic, in the same order, as two k_filter_axis
+// sub-passes.  Grid: x = x-column + columns x run, y = plane.
+constexpr int YX = 1024;
+constexpr int YROW = YX + 8;  // stage row: [3] left halo, [4, 4 + YX) interior, [4 + YX] right
+
+__global__ void __launch_bounds__(256) k_filter_y2(const float* __restrict__ src,
+                                                  float* __restrict__ dst, const GridDev g,
+                                                  int ncx, int yrun, int vec) {
+  __shared__ __align__(16) float stage[ZS][YROW];
+  const int n0 = g.n[0], n1 = g.n[1];
+  const int col = blockIdx.x % ncx, run = blockIdx.x / ncx;
+  const int x0 = col * YX, y0 = run * yrun;
+  const int yc = min(yrun, n1 - y0);  // rows y0 .. y0 + yc - 1 are written
+  const long long P = g.plane;
+  const float* s = src + (long long)blockIdx.y * P;
+  float* d = dst + (long long)blockIdx.y * P;
+  const int t = threadIdx.x;
+  // this thread's copies, the same for every row: interior chunk t (x0 + 4t ..
+  // x0 + 4t + 3), and for threads 0 and 1 the left and right halo point
+  const int xs = x0 + 4 * t;
+  const bool v16 = vec && xs + 3 < n0;
+  const int hx = t == 0 ? wrapi(x0 - 1, n0) : wrapi(x0 + YX, n0);
+  const int hcol = t == 0 ? 3 : 4 + YX;
+  auto issue = [&](int k) {  // copy halo row k (y = y0 - 1 + k) into stage k % ZS
+    if (k < yc + 2) {
+      int y = y0 - 1 + k;  // -1 <= y <= n1
+      y = y < 0 ? y + n1 : (y >= n1 ? y - n1 : y);
+      const float* row = s + (long long)n0 * y;
+      float* st = stage[k % ZS];
+      if (v16) {
+        cp_async16(st + 4 + 4 * t, row + xs);
+      } else {
+        for (int e = 0; e < 4; ++e) cp_async4(st + 4 + 4 * t + e, row + wrapi(xs + e, n0));
+      }
+      if (t < 2) cp_async4(st + hcol, row + hx);
+    }
+    cp_async_commit();  // an empty group keeps the group count uniform
+  };
+#pragma unroll
+  for (int k = 0; k < ZS - 1; ++k) issue(k);
+
+  float pm[4] = {0.f, 0.f, 0.f, 0.f}, p0[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k = 0; k < yc + 2; ++k) {
+    cp_async_wait<ZS - 2>();  // this thread's copies of row k have landed
+    __syncthreads();          // everyone's have; stage (k - 1) % ZS is no longer read
+    issue(k + ZS - 1);
+    const float* a = stage[k % ZS] + 4 * t + 3;  // column x - 1
+    const float l = a[0];
+    const float4 m = *reinterpret_cast<const float4*>(a + 1);
+    const float r = a[5];
+    const float p1[4] = {b3(l, m.x, m.y), b3(m.x, m.y, m.z), b3(m.y, m.z, m.w), b3(m.z, m.w, r)};
+    if (k >= 2) {  // y sub-pass of row y0 + k - 2
+      float o[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) o[i] = b3(pm[i], p0[i], p1[i]);
+      float* q = d + (long long)n0 * (y0 + k - 2) + xs;
+      if (v16) {
+        *reinterpret_cast<float4*>(q) = make_float4(o[0], o[1], o[2], o[3]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (xs + i < n0) q[i] = o[i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      pm[i] = p0[i];
+      p0[i] = p1[i];
+    }
+  }
+  cp_async_wait<0>();
+}
+
 // Offsets (elements) of the lattice points a-2, a-1, a+1, a+2 along an axis of
 // n points with stride s, periodic.
 struct Nb {
@@ -508,11 +589,36 @@ static cudaError_t launch_pass_z3(const GridDev& g, const float* src, float* dst
   return cudaGetLastError();
 }
 
+// The y-marching 2D pass; runs as long as one wave of resident blocks allows.
+static cudaError_t launch_pass_y2(const GridDev& g, const float* src, float* dst, int ncomp,
+                                  cudaStream_t st) {
+  static int resident = 0;
+  if (resident == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_y2, 256, 0);
+    resident = sms * per_sm > 0 ? sms * per_sm : 1;
+  }
+  const int ncx = (g.n[0] + YX - 1) / YX;
+  const long long streams = (long long)ncx * ncomp;
+  long long runs = resident / streams;
+  if (runs < 1) runs = 1;
+  if (runs > g.n[1]) runs = g.n[1];
+  const int yrun = (int)((g.n[1] + runs - 1) / runs);
+  const long long blocks = (long long)ncx * ((g.n[1] + yrun - 1) / yrun);
+  if (blocks > 0x7fffffffLL || ncomp > 65535) return cudaErrorInvalidValue;
+  const int vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0 &&
+                  g.n[0] % 4 == 0 && g.plane % 4 == 0;
+  k_filter_y2<<<dim3((unsigned)blocks, (unsigned)ncomp), 256, 0, st>>>(src, dst, g, ncx, yrun, vec);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_filter_pass_f32(const GridDev& g, const float* src, float* dst, int ncomp,
                                    cudaStream_t st) {
   switch (g.dim) {
     case 1: return launch_pass<1, 1024, 1, 1>(g, src, dst, ncomp, st);
-    case 2: return launch_pass<2, 32, 32, 1>(g, src, dst, ncomp, st);
+    case 2: return launch_pass_y2(g, src, dst, ncomp, st);
     case 3: return launch_pass_z3(g, src, dst, ncomp, st);
     default: return cudaErrorInvalidValue;
   }

@@ -67,16 +67,37 @@ def test_binomial_filter_matches_oracle(dim, passes):
 @pytest.mark.parametrize("shape", [(37, 11, 9), (68, 19, 41), (4, 8, 2), (1, 1, 3), (2, 3, 1),
                                    (1024, 256, 40)])
 def test_binomial_filter_3d_z_runs_match_oracle(shape):
-    """The 3D pass marches along z over (x, y) columns of 32 x 8 points: rows
+    """The 3D pass marches along z over (x, y) columns of 128 x 16 points: rows
     whose x extent is not a multiple of 4 (4-byte copies only), ragged columns,
     several z runs with a ragged last one, extents below the column and the
-    halo, and a box large enough for 32-plane runs (1024 x 256 x 40)."""
+    halo, and a box of many columns whose runs span all its planes
+    (1024 x 256 x 40)."""
     nx, ny, nz = shape
     rs = np.random.default_rng(sum(shape))
     F32 = np.zeros((9, nz, ny, nx), np.float32)
     F32[6:9] = rs.normal(size=(3, nz, ny, nx)).astype(np.float32)
     sim = _sim(3, shape, F32, _empty_species(3))
     g = oracle.Grid(3, nx, ny, nz, 0.45)
+    F = F32.astype(np.float64)
+    sim.filter_current(3)
+    oracle.filter_binomial(g, F, 3)
+    compare_fields(sim.download()[0], F, tol=1e-6, comps=range(6, 9))
+    sim.close()
+
+
+@pytest.mark.parametrize("shape", [(29, 23), (1030, 7), (4, 8), (1, 3), (2, 1), (2048, 64),
+                                   (1024, 1024)])
+def test_binomial_filter_2d_y_runs_match_oracle(shape):
+    """The 2D pass marches along y over 1024-point x columns: ragged columns
+    (1030, 2048 + halo), rows whose x extent is not a multiple of 4 (4-byte
+    copies only), extents below the halo, and the 1024^2 plane of the
+    turbulence box."""
+    nx, ny = shape
+    rs = np.random.default_rng(nx + 7 * ny)
+    F32 = np.zeros((9, 1, ny, nx), np.float32)
+    F32[6:9] = rs.normal(size=(3, 1, ny, nx)).astype(np.float32)
+    sim = _sim(2, (nx, ny, 1), F32, _empty_species(2))
+    g = oracle.Grid(2, nx, ny, 1, 0.45)
     F = F32.astype(np.float64)
     sim.filter_current(3)
     oracle.filter_binomial(g, F, 3)
