@@ -108,7 +108,10 @@ __global__ void k_filter_axis(const T* __restrict__ src, T* __restrict__ dst, co
 // the sub-passes on it in shared memory and writes the tile.  Every output
 // goes through the same arithmetic, in the same order, as three
 // k_filter_axis sub-passes, but a pass moves 24 B per cell instead of 72.
-// Grid: x = tile index, y = plane.
+// Grid: x = tile index, y = plane.  The library launches it for 1D grids
+// (1024-point tiles); 2D and 3D grids take the marching passes k_filter_y2
+// and k_filter_z3 below, which stream the planes instead of re-reading a
+// halo per tile.
 template <int D, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(256) k_filter_pass(const float* __restrict__ src,
                                                      float* __restrict__ dst, const GridDev g,
