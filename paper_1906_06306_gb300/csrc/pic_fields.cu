@@ -80,6 +80,141 @@ __global__ void k_e_update(float* __restrict__ F, const GridDev g, float c) {
   }
 }
 
+// The same two updates with four consecutive x points per thread (rows whose
+// length is a multiple of 4 and 16-byte aligned planes): 16-byte loads and
+// stores of the thread's points, one scalar load for the x neighbour outside
+// them.  Each point goes through the operations of k_b_half / k_e_update in
+// the same order, so the results are the same bits.
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, const float v[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void arr4(const float4 a, float v[4]) {
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = a.z;
+  v[3] = a.w;
+}
+
+template <int D>
+__global__ void k_b_half_x4(float* __restrict__ F, const GridDev g, float hc, int zero_j) {
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const long long P = g.plane;
+  const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= n0) return;
+  FOR_ROWS(j, k) {
+    const long long idx = (long long)i + (long long)n0 * (j + (long long)n1 * k);
+    const long long x4 = (i + 4 < n0) ? idx + 4 : idx + 4 - n0;  // x neighbour of the last point
+    const long long sy = (D >= 2) ? ((j + 1 < n1) ? n0 : (long long)n0 * (1 - n1)) : 0;
+    const long long sz = (D >= 3) ? ((k + 1 < n2) ? (long long)n0 * n1 : (long long)n0 * n1 * (1 - n2)) : 0;
+    const float* Ex = F + EX * P;
+    const float* Ey = F + EY * P;
+    const float* Ez = F + EZ * P;
+    float ex[4], ey[4], ez[4], eyx[4], ezx[4], ezy[4] = {}, exy[4] = {}, eyz[4] = {}, exz[4] = {};
+    arr4(ld4(Ex + idx), ex);
+    arr4(ld4(Ey + idx), ey);
+    arr4(ld4(Ez + idx), ez);
+    eyx[0] = ey[1], eyx[1] = ey[2], eyx[2] = ey[3], eyx[3] = Ey[x4];
+    ezx[0] = ez[1], ezx[1] = ez[2], ezx[2] = ez[3], ezx[3] = Ez[x4];
+    if (D >= 2) {
+      arr4(ld4(Ez + idx + sy), ezy);
+      arr4(ld4(Ex + idx + sy), exy);
+    }
+    if (D >= 3) {
+      arr4(ld4(Ey + idx + sz), eyz);
+      arr4(ld4(Ex + idx + sz), exz);
+    }
+    float bx[4], by[4], bz[4];
+    arr4(ld4(F + BX * P + idx), bx);
+    arr4(ld4(F + BY * P + idx), by);
+    arr4(ld4(F + BZ * P + idx), bz);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      float cx = 0.f, cy = 0.f, cz = 0.f;
+      cy -= ezx[l] - ez[l];
+      cz += eyx[l] - ey[l];
+      if (D >= 2) {
+        cx += ezy[l] - ez[l];
+        cz -= exy[l] - ex[l];
+      }
+      if (D >= 3) {
+        cx -= eyz[l] - ey[l];
+        cy += exz[l] - ex[l];
+      }
+      bx[l] = fmaf(-hc, cx, bx[l]);
+      by[l] = fmaf(-hc, cy, by[l]);
+      bz[l] = fmaf(-hc, cz, bz[l]);
+    }
+    st4(F + BX * P + idx, bx);
+    st4(F + BY * P + idx, by);
+    st4(F + BZ * P + idx, bz);
+    if (zero_j) {
+      const float z[4] = {0.f, 0.f, 0.f, 0.f};
+      st4(F + JX * P + idx, z);
+      st4(F + JY * P + idx, z);
+      st4(F + JZ * P + idx, z);
+    }
+  }
+}
+
+template <int D>
+__global__ void k_e_update_x4(float* __restrict__ F, const GridDev g, float c) {
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const long long P = g.plane;
+  const int i = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= n0) return;
+  FOR_ROWS(j, k) {
+    const long long idx = (long long)i + (long long)n0 * (j + (long long)n1 * k);
+    const long long xm = (i > 0) ? idx - 1 : idx + n0 - 1;  // x neighbour of the first point
+    const long long sy = (D >= 2) ? ((j > 0) ? n0 : (long long)n0 * (1 - n1)) : 0;
+    const long long sz = (D >= 3) ? ((k > 0) ? (long long)n0 * n1 : (long long)n0 * n1 * (1 - n2)) : 0;
+    const float* Bx = F + BX * P;
+    const float* By = F + BY * P;
+    const float* Bz = F + BZ * P;
+    float bx[4], by[4], bz[4], byx[4], bzx[4], bzy[4] = {}, bxy[4] = {}, byz[4] = {}, bxz[4] = {};
+    arr4(ld4(Bx + idx), bx);
+    arr4(ld4(By + idx), by);
+    arr4(ld4(Bz + idx), bz);
+    byx[0] = By[xm], byx[1] = by[0], byx[2] = by[1], byx[3] = by[2];
+    bzx[0] = Bz[xm], bzx[1] = bz[0], bzx[2] = bz[1], bzx[3] = bz[2];
+    if (D >= 2) {
+      arr4(ld4(Bz + idx - sy), bzy);
+      arr4(ld4(Bx + idx - sy), bxy);
+    }
+    if (D >= 3) {
+      arr4(ld4(By + idx - sz), byz);
+      arr4(ld4(Bx + idx - sz), bxz);
+    }
+    float ex[4], ey[4], ez[4], jx[4], jy[4], jz[4];
+    arr4(ld4(F + EX * P + idx), ex);
+    arr4(ld4(F + EY * P + idx), ey);
+    arr4(ld4(F + EZ * P + idx), ez);
+    arr4(ld4(F + JX * P + idx), jx);
+    arr4(ld4(F + JY * P + idx), jy);
+    arr4(ld4(F + JZ * P + idx), jz);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      float cx = 0.f, cy = 0.f, cz = 0.f;
+      cy -= bz[l] - bzx[l];
+      cz += by[l] - byx[l];
+      if (D >= 2) {
+        cx += bz[l] - bzy[l];
+        cz -= bx[l] - bxy[l];
+      }
+      if (D >= 3) {
+        cx -= by[l] - byz[l];
+        cy += bx[l] - bxz[l];
+      }
+      ex[l] = fmaf(c, cx, ex[l]) - jx[l];
+      ey[l] = fmaf(c, cy, ey[l]) - jy[l];
+      ez[l] = fmaf(c, cz, ez[l]) - jz[l];
+    }
+    st4(F + EX * P + idx, ex);
+    st4(F + EY * P + idx, ey);
+    st4(F + EZ * P + idx, ez);
+  }
+}
+
 // One Binomial2 sub-pass along one axis: dst = (1/4, 1/2, 1/4) * src along
 // `axis`, periodic.  Thread (x, y, z*ncomp) of a 3D launch grid owns one
 // lattice value, so neighbours along every axis are coalesced loads.
@@ -504,9 +639,29 @@ __global__ void k_e_update4(float* __restrict__ F, const GridDev g, float c) {
   }
 }
 
+// Launch of the four-points-per-thread kernels: rows of n0 / 4 threads.
+static bool x4_ok(const GridDev& g, const float* F) {
+  return g.n[0] % 4 == 0 && (reinterpret_cast<uintptr_t>(F) & 15) == 0;
+}
+static RowLaunch row_launch_x4(const GridDev& g) {
+  GridDev q = g;
+  q.n[0] = g.n[0] / 4;
+  return row_launch(q);
+}
+
 cudaError_t launch_b_half(const GridDev& g, float* F, int zero_j, cudaStream_t st) {
-  const RowLaunch L = row_launch(g);
   const float hc = 0.5f * g.c;
+  if (g.order == 2 && x4_ok(g, F)) {
+    const RowLaunch L = row_launch_x4(g);
+    switch (g.dim) {
+      case 1: k_b_half_x4<1><<<L.grid, L.threads, 0, st>>>(F, g, hc, zero_j); break;
+      case 2: k_b_half_x4<2><<<L.grid, L.threads, 0, st>>>(F, g, hc, zero_j); break;
+      case 3: k_b_half_x4<3><<<L.grid, L.threads, 0, st>>>(F, g, hc, zero_j); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+  const RowLaunch L = row_launch(g);
   switch (g.dim * 10 + g.order) {
     case 12: k_b_half<1><<<L.grid, L.threads, 0, st>>>(F, g, hc, zero_j); break;
     case 22: k_b_half<2><<<L.grid, L.threads, 0, st>>>(F, g, hc, zero_j); break;
@@ -520,6 +675,16 @@ cudaError_t launch_b_half(const GridDev& g, float* F, int zero_j, cudaStream_t s
 }
 
 cudaError_t launch_e_update(const GridDev& g, float* F, cudaStream_t st) {
+  if (g.order == 2 && x4_ok(g, F)) {
+    const RowLaunch L = row_launch_x4(g);
+    switch (g.dim) {
+      case 1: k_e_update_x4<1><<<L.grid, L.threads, 0, st>>>(F, g, g.c); break;
+      case 2: k_e_update_x4<2><<<L.grid, L.threads, 0, st>>>(F, g, g.c); break;
+      case 3: k_e_update_x4<3><<<L.grid, L.threads, 0, st>>>(F, g, g.c); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   const RowLaunch L = row_launch(g);
   switch (g.dim * 10 + g.order) {
     case 12: k_e_update<1><<<L.grid, L.threads, 0, st>>>(F, g, g.c); break;

@@ -48,6 +48,32 @@ def test_field_updates_match_oracle(dim):
     sim.close()
 
 
+@pytest.mark.parametrize("dim,shape", [(1, (64, 1, 1)), (2, (32, 20, 1)), (2, (4, 3, 1)),
+                                       (3, (16, 12, 8)), (3, (8, 5, 3))])
+def test_field_updates_four_points_per_thread_match_oracle(dim, shape):
+    """Rows whose length is a multiple of 4 take the FDTD2 kernels with four
+    x points per thread (16-byte loads and stores, wrapped x neighbours at
+    both row ends), down to a row of one quad."""
+    from paper_1906_06306_gb300 import PIC_FIELD_B_HALF, PIC_FIELD_E
+
+    nx, ny, nz = shape
+    rs = np.random.default_rng(110 + nx + ny + nz)
+    F32 = random_fields((nz, ny, nx), rs)
+    F32[6:9] = (0.01 * rs.normal(size=(3, nz, ny, nx))).astype(np.float32)
+    sim = _sim(dim, shape, F32, _empty_species(dim))
+    g = oracle.Grid(dim, nx, ny, nz, 0.45)
+    F = F32.astype(np.float64)
+    for _ in range(3):
+        sim.field_update(PIC_FIELD_B_HALF)
+        oracle.push_half_b(g, F)
+        compare_fields(sim.download()[0], F, tol=1e-6)
+        sim.field_update(PIC_FIELD_E)
+        oracle.push_e(g, F)
+        oracle.add_cur(g, F)
+        compare_fields(sim.download()[0], F, tol=1e-6)
+    sim.close()
+
+
 @pytest.mark.parametrize("dim", [1, 2, 3])
 @pytest.mark.parametrize("passes", [1, 2, 3])
 def test_binomial_filter_matches_oracle(dim, passes):
