@@ -51,9 +51,12 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The compiled oracle: liboracle.so built beside this file, or the library
+    named by the ORACLE_LIB environment variable (a deliberately mutated build,
+    used by ``oracle.mutation_check`` to show that the pins catch mistakes)."""
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        _lib = ctypes.CDLL(os.environ.get("ORACLE_LIB") or build())
         _lib.orc_kinetic_energy.restype = ctypes.c_double
         _lib.orc_inject.restype = ctypes.c_long
     return _lib
