@@ -74,6 +74,14 @@ WORKLOADS = {
 }
 
 
+def full_grid(name, n=0):
+    """Grid of a workload at its benchmark size (or at size n): n, n x n, or
+    n x n/8 x n/8 cells, as its recipe builds it."""
+    w = WORKLOADS[name]
+    n = n or w["grid"]
+    return [n, n, n][:1] if w["dim"] == 1 else [n, n] if w["dim"] == 2 else [n, n // 8, n // 8]
+
+
 def workload_config(name, pl):
     w = WORKLOADS[name]
     grid = [pl.nx, pl.ny, pl.nz][: pl.dim]
@@ -263,6 +271,44 @@ def _oracle_runner(w, pl, g, F, sp):
     return run
 
 
+def ensemble_cpu_baseline(boxes=256, sample=4, target_s=12.0):
+    """The FP64 oracle stepping a seeded sample of the ensemble's boxes one
+    after the other (the oracle has no batched form), as many steps as fit in
+    about target_s seconds."""
+    import numpy as np
+
+    import oracle
+    import workloads
+
+    oracle.build()
+    recipe = workloads.weibel_ensemble(count=boxes)
+    pick = sorted(np.random.default_rng(boxes).choice(len(recipe), size=sample, replace=False))
+    states = []
+    for i in pick:
+        pl = workloads.weibel_box(*recipe[i])
+        g, F, sp = oracle.from_plasma(pl)
+        states.append((pl, g, F, sp))
+    npart = sum(pl.nparticles for pl, _, _, _ in states)
+
+    def run(k):
+        for _, g, F, sp in states:
+            oracle.step(g, F, sp, passes=0, nsteps=k)
+        return npart * k
+
+    t0 = time.perf_counter()
+    run(1)
+    one = time.perf_counter() - t0
+    k = max(1, int(target_s / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    done = run(k)
+    dt = time.perf_counter() - t0
+    desc = ", ".join(f"{pl.dim}D {pl.nx}" + (f"x{pl.ny}" if pl.dim == 2 else "")
+                     for pl, _, _, _ in states)
+    return {"value": done / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample} of the {boxes} ensemble boxes ({desc}; {npart} particles), "
+                      f"stepped one after the other, {k} steps, FP64, 1 host thread"}
+
+
 def run_reference(args):
     """The oracle as it stands on the host cores, K timed steps after W warm-up
     steps; each step runs the workload's set-up on a box small enough that the
@@ -300,7 +346,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(args.workload, pl), sample=sample),
+            "config": dict(workload_config(args.workload, pl),
+                           grid=full_grid(args.workload, args.grid), sample=sample),
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
@@ -590,6 +637,8 @@ def run_batched(args):
         "clocks": clocks, "e2e": None,
     }
     if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = ensemble_cpu_baseline(len(sims))
         print(json.dumps(line), flush=True)
     batch.close()
     for sm in sims:
@@ -780,9 +829,19 @@ def main():
                                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
             return 0
         if args.workload == "batched_weibel":
-            print(json.dumps({"impl": "reference", "unavailable":
-                              "the oracle steps one box at a time; time it with "
-                              "--workload weibel_1d3v"}))
+            rank, _, _ = dist_env()
+            if rank == 0:
+                cb = ensemble_cpu_baseline(args.boxes)
+                print(json.dumps({"impl": "reference", "metric": METRIC, "value": cb["value"],
+                                  "unit": cb["unit"], "n_gpus": args.gpus, "steps": args.steps,
+                                  "warmup": args.warmup, "higher_is_better": True,
+                                  "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                                  "data": "synthetic",
+                                  "config": {"workload": "batched_weibel", "boxes": args.boxes,
+                                             "sample": cb["sample"]},
+                                  "cpu_baseline": cb,
+                                  "e2e": {"value": cb["value"], "unit": cb["unit"],
+                                          "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
             return 0
         return run_reference(args)
     if args.workload == "batched_weibel":

@@ -50,3 +50,32 @@ def test_profiled_traffic_reads_the_summary_only_for_the_current_kernel(tmp_path
     assert b.profiled_traffic("b", False, 1000.0) == 60.0 * 1000.0
     assert b.profiled_traffic("c", True, 1000.0) is None  # taken on other kernel source
     assert b.profiled_traffic("missing", True, 1000.0) is None
+
+
+def test_full_grid_of_each_workload():
+    b = _bench()
+    assert b.full_grid("turbulence_2d3v") == [1024, 1024]
+    assert b.full_grid("weibel_1d3v") == [512]
+    assert b.full_grid("shock_3d3v") == [1024, 128, 128]
+    assert b.full_grid("shock_3d3v_periodic", 512) == [512, 64, 64]
+
+
+def test_reference_line_carries_the_workload_config_and_the_contract_keys():
+    import json
+    import subprocess
+    import sys
+
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "3",
+                        "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    b = _bench()
+    assert d["impl"] == "reference" and d["metric"] == b.METRIC
+    assert d["unit"] == "particle-steps/s" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["config"]["workload"] == "turbulence_2d3v"
+    assert d["config"]["grid"] == [1024, 1024]  # the workload's, not the sample's
+    assert "sample" in d["config"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
