@@ -823,7 +823,11 @@ def main():
                                   "warmup": args.warmup, "higher_is_better": True,
                                   "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                                   "data": "synthetic",
-                                  "config": {"workload": "adjoint_2d3v", "sample": cb["sample"]},
+                                  "config": {"workload": "adjoint_2d3v",
+                                             "grid": [args.grid or 256, args.grid or 256],
+                                             "ppc_per_species": 32, "species": 2, "theta": 0.1,
+                                             "sigma": 1.0, "modes": 64, "checkpoint_every": 20,
+                                             "sample": cb["sample"]},
                                   "cpu_baseline": cb,
                                   "e2e": {"value": cb["value"], "unit": cb["unit"],
                                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
