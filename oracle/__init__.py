@@ -14,7 +14,11 @@ discrete continuity), FDTD2 (Yee dispersion relation, div B), Binomial2
 (Fourier response), whole step (Gauss law, energy, Weibel growth rate);
 ``tests/test_oracle_shock.py``: wall (specular reflection, charge continuity of
 reflected particles, conductor standing waves) and injector (the box fills
-with the advected upstream template, no gap and no duplicate).
+with the advected upstream template, no gap and no duplicate);
+``tests/test_oracle_adjoint.py``: the adjoint step (transpose identities and
+central differences).  ``oracle.mutation_check`` plants 30 mistakes in copies
+of the C sources and shows that each one fails a pin
+(``tests/test_oracle_mutations.py``).
 """
 from __future__ import annotations
 
