@@ -217,10 +217,60 @@ def dist_env():
     return rank, world, local
 
 
-def cpu_baseline(name="turbulence_2d3v", steps=0, sample_grid=None, target_s=12.0):
-    """The FP64 oracle, as it stands (one host thread), on a sample of the same
-    workload: the same set-up on a smaller box (same plasma per cell); `steps`
-    steps, or as many as fit in about target_s seconds."""
+def host_cores() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_worker(name, n, target_s, steps, barrier):
+    """One host process of the all-core oracle baseline: the workload's set-up
+    on an n-box, calibrated to about target_s seconds (or `steps` steps),
+    started together with the others; returns (particle-steps, seconds)."""
+    import oracle
+
+    w = WORKLOADS[name]
+    pl = w["make"](n)
+    g, F, sp = oracle.from_plasma(pl)
+    run = _oracle_runner(w, pl, g, F, sp)
+    k = steps
+    if k <= 0:
+        t0 = time.perf_counter()
+        run(1)
+        k = max(1, int(target_s / max(time.perf_counter() - t0, 1e-6)))
+    barrier.wait()
+    t0 = time.perf_counter()
+    done = run(k)
+    return done, time.perf_counter() - t0
+
+
+def oracle_all_cores(name, n, target_s=10.0, steps=0, cores=None):
+    """The FP64 oracle as it stands on every host core: one process per core
+    (spawned, so that no CUDA state is inherited), each stepping its own copy
+    of the seeded sample box; the processes start together behind a barrier.
+    Returns (particle-steps/s summed over the processes, processes)."""
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()  # once, before the workers load it
+    cores = cores or host_cores()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as man:
+        barrier = man.Barrier(cores)
+        with ctx.Pool(cores) as pool:
+            res = pool.starmap(_oracle_worker, [(name, n, target_s, steps, barrier)] * cores)
+    return sum(d / t for d, t in res), cores
+
+
+def cpu_baseline(name="turbulence_2d3v", steps=0, sample_grid=None, target_s=10.0,
+                 all_cores=True):
+    """The FP64 oracle, as it stands, on a sample of the same workload: the
+    same set-up on a smaller box (same plasma per cell); `steps` steps, or as
+    many as fit in about target_s seconds, on one host thread and (all_cores)
+    on every host core, one process per core."""
     import oracle
 
     oracle.build()
@@ -237,11 +287,107 @@ def cpu_baseline(name="turbulence_2d3v", steps=0, sample_grid=None, target_s=12.
     done = run(k)
     dt = time.perf_counter() - t0
     box = "x".join(str(v) for v in [pl.nx, pl.ny, pl.nz][: pl.dim])
-    return {"value": done / dt, "unit": "particle-steps/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"{name} on a {box} box ({pl.nparticles} particles at the start, same "
-                      f"plasma per cell), {k} steps, FP64, 1 host thread",
-            "seconds": dt, "steps": k, "particles": pl.nparticles}
+    sample = (f"{name} on a {box} box ({pl.nparticles} particles at the start, same plasma per "
+              f"cell), FP64")
+    one = {"value": done / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+           "sample": f"{sample}, {k} steps, 1 host thread"}
+    out = dict(one, seconds=dt, steps=k, particles=pl.nparticles, single_core=one)
+    if all_cores and host_cores() > 1:
+        v, cores = oracle_all_cores(name, n, target_s=target_s)
+        out.update(value=v, cores=cores,
+                   sample=f"{sample}: one process per host core, each stepping its own copy of "
+                          f"the box for about {target_s:.0f} s")
+    return out
+
+
+def parity_report(name, steps=10, sample_grid=None):
+    """The FP32 GPU path against the FP64 oracle, quantity by quantity, on the
+    workload's CPU-baseline sample box (same set-up and seed, no tile sort so
+    that particle slots match): over `steps` steps the largest normwise
+    error of each field component (max |GPU - oracle| / max |oracle|), of J
+    per cell against the oracle's sum of |ZigZag term| of that cell (at least
+    1/16 of the largest; oracle.deposit_abs), of the positions (cells) and
+    four-velocities (relative to max(1, |u|)); at the last step the relative
+    error of each energy term and the Gauss-law residual on both sides."""
+    import numpy as np
+
+    import oracle
+    import workloads
+    from paper_1906_06306_gb300 import Simulation
+
+    w = WORKLOADS[name]
+    n = sample_grid or w["sample_grid"]
+    pl = w["make"](n)
+    shock = bool(w.get("shock"))
+    cap = [s.n + workloads.injected_count(pl, steps + 2) for s in pl.species] if shock else None
+    sim = Simulation.from_plasma(pl, capacity=cap,
+                                 tuning=dict(filter_passes=w["filter_passes"], sort_every=10 ** 6))
+    if shock:
+        sim.set_shock_from_plasma(pl)
+    F32, sp0 = sim.download()
+    g = oracle.Grid(pl.dim, pl.nx, pl.ny, pl.nz, pl.c)
+    F = F32.astype(np.float64)
+    osp = [oracle.Species(s["q"], s["m"], oracle.positions(g, s["cell"], s["off"]),
+                          s["u"].astype(np.float64)) for s in sp0]
+    inj = None
+    if shock:
+        wall, i_zero, inj = oracle.shock_from_plasma(pl)
+        oracle.set_wall(wall, i_zero)
+    names = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz"]
+    ferr = dict.fromkeys(names, 0.0)
+    jterm = dict.fromkeys(names[6:], 0.0)
+    xerr = uerr = 0.0
+    ext = np.array([pl.nx, pl.ny, pl.nz][: pl.dim], dtype=np.float64)[:, None]
+    try:
+        for k in range(steps):
+            terms = []
+            sim.step(1)
+            oracle.step_shock(g, F, osp, inj, k, passes=w["filter_passes"], nsteps=1,
+                              terms=terms)
+            Fg, spg = sim.download()
+            for c, nm in enumerate(names):
+                d = np.abs(Fg[c].astype(np.float64) - F[c])
+                scale = np.abs(F[c]).max()
+                ferr[nm] = max(ferr[nm], float(d.max() / scale) if scale > 0 else float(d.max()))
+                if c >= 6:
+                    A = terms[-1][c - 6]
+                    A = np.maximum(A, A.max() / 16.0)
+                    if A.max() > 0:
+                        jterm[nm] = max(jterm[nm], float((d / np.where(A > 0, A, 1.0)).max()))
+            for s, o in zip(spg, osp):
+                if o.n == 0:
+                    continue
+                x = oracle.positions(g, s["cell"], s["off"])
+                dx = x[: pl.dim] - o.x[: pl.dim]
+                dx -= np.round(dx / ext) * ext
+                xerr = max(xerr, float(np.abs(dx).max()))
+                du = np.abs(s["u"].astype(np.float64) - o.u) / np.maximum(1.0, np.abs(o.u))
+                uerr = max(uerr, float(du.max()))
+        en = sim.energies()
+        ref = oracle.energies(g, F, osp)
+        res = oracle.gauss_residual(g, F, osp, passes=w["filter_passes"])
+        if shock:  # the plasma side: the wall node carries the conductor's surface charge
+            res = res[..., wall + 1:i_zero]
+        rho1 = float(np.abs(oracle.charge_density(g, osp[:1])).max())
+    finally:
+        if shock:
+            oracle.set_wall(0, 0)
+        sim.close()
+    ns = len(osp)
+    terms_names = ["E", "B"] + [f"K_species{s}" for s in range(ns)]
+    total = sum(abs(v) for v in ref)
+    energy = {nm: abs(a - b) / abs(b) if abs(b) > 1e-6 * total else abs(a - b) / total
+              for nm, a, b in zip(terms_names, en[: 2 + ns], ref)}
+    box = "x".join(str(v) for v in [pl.nx, pl.ny, pl.nz][: pl.dim])
+    return {"sample": f"{name} on a {box} box ({pl.nparticles} particles at the start), same "
+                      f"seed as the workload, {steps} steps from the same FP32 state, no tile sort",
+            "tolerance": 1e-5,
+            "fields_max_rel": ferr, "J_vs_cell_term_sum": jterm,
+            "x_max_abs_cells": xerr, "u_max_rel": uerr, "energy_rel": energy,
+            "gauss_max": {"gpu_fp64_reduction": float(en[2 + ns]),
+                          "oracle": float(np.abs(res).max()),
+                          "one_species_charge_density_max": rho1},
+            "note": "energy terms below 1e-6 of the total are compared relative to the total"}
 
 
 def _oracle_runner(w, pl, g, F, sp):
@@ -322,7 +468,7 @@ def run_reference(args):
 
     oracle.build()
     w = WORKLOADS[args.workload]
-    cal = cpu_baseline(args.workload, steps=1)
+    cal = cpu_baseline(args.workload, steps=1, all_cores=False)
     per_particle_step = 1.0 / cal["value"]
     budget = 90.0 / max(1, args.steps + args.warmup)
     # shrink the sample box until K + W steps fit the budget
@@ -332,28 +478,60 @@ def run_reference(args):
         n //= 2
         parts = max(1, parts // 2 ** w["dim"])
     pl = w["make"](n)
-    g, F, sp = oracle.from_plasma(pl)
-    run = _oracle_runner(w, pl, g, F, sp)
-    run(args.warmup)
-    t0 = time.perf_counter()
-    done = run(args.steps)
-    dt = time.perf_counter() - t0
-    value = done / dt
+    cores = host_cores()
+    value, secs = oracle_all_cores_steps(args.workload, n, args.steps, args.warmup, cores)
     box = "x".join(str(v) for v in [pl.nx, pl.ny, pl.nz][: pl.dim])
     sample = (f"{args.workload} on a {box} box ({pl.nparticles} particles, same plasma per cell) "
-              f"per step, FP64, 1 host thread")
+              f"per step and process, FP64, one process per host core ({cores}), each stepping "
+              f"its own copy of the box")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(workload_config(args.workload, pl),
                            grid=full_grid(args.workload, args.grid), sample=sample),
-            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1,
-                             "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores,
+                             "kind": "oracle", "sample": sample,
+                             "single_core": {"value": cal["value"], "cores": 1,
+                                             "unit": "particle-steps/s",
+                                             "sample": cal["sample"]}},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _oracle_steps_worker(name, n, steps, warmup, barrier):
+    """One process of the reference arm: `warmup` untimed steps of the set-up
+    on an n-box, then, started together with the others, `steps` timed steps;
+    returns (particle-steps, seconds)."""
+    import oracle
+
+    w = WORKLOADS[name]
+    pl = w["make"](n)
+    g, F, sp = oracle.from_plasma(pl)
+    run = _oracle_runner(w, pl, g, F, sp)
+    run(warmup)
+    barrier.wait()
+    t0 = time.perf_counter()
+    done = run(steps)
+    return done, time.perf_counter() - t0
+
+
+def oracle_all_cores_steps(name, n, steps, warmup, cores):
+    """The oracle on every host core for a fixed number of steps: returns
+    (particle-steps/s summed over the processes, the slowest process's seconds)."""
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as man:
+        barrier = man.Barrier(cores)
+        with ctx.Pool(cores) as pool:
+            res = pool.starmap(_oracle_steps_worker, [(name, n, steps, warmup, barrier)] * cores)
+    return sum(d / t for d, t in res), max(t for _, t in res)
 
 
 def push_bytes_per_launch(pl, nparticles=None) -> float:
@@ -376,6 +554,101 @@ def step_bytes(pl, nparticles, filter_passes, sort_every) -> float:
     fields = pl.ncells * (36 + 48 + 48 + 24 * filter_passes)
     sort = nparticles * (4 + 2 * rec) / sort_every
     return push_bytes_per_launch(pl, nparticles) + fields + sort
+
+
+def sub_record(name, steps, warmup, local=0):
+    """A bounded run of another set-up at its benchmark size, in the same
+    process as the headline: particle-steps/s and ms per step of `steps`
+    pic_step calls (one pic_step(steps) call, i.e. CUDA-graph replay of whole
+    sort cycles, where the box has no shock boundaries), then per-kernel
+    CUDA-event times of a timed pass of per-step calls (pic_timing on) for the
+    particle kernel's roofline; FP32 errors against the oracle on the
+    set-up's CPU-baseline sample box."""
+    import torch
+
+    import workloads
+    from paper_1906_06306_gb300 import Simulation
+    from paper_1906_06306_gb300 import binding as B
+
+    w = WORKLOADS[name]
+    t_gen = time.perf_counter()
+    pl = w["make"](w["grid"])
+    gen_s = time.perf_counter() - t_gen
+    shock = bool(w.get("shock"))
+    kt_steps = min(steps, 100)
+    cap = None
+    if shock:
+        cap = [s.n + workloads.injected_count(pl, warmup + steps + kt_steps + 4) for s in pl.species]
+    dev = torch.device(f"cuda:{local}")
+    sim = Simulation.from_plasma(pl, device=f"cuda:{local}",
+                                 tuning=dict(filter_passes=w["filter_passes"]), capacity=cap)
+    if shock:
+        sim.set_shock_from_plasma(pl)
+    del pl
+    sim.step(warmup)
+    torch.cuda.synchronize(dev)
+    sim.check()
+    tun = sim.tuning()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    done = 0
+    t0.record(sim.stream)
+    if shock:  # the injection grows the count every step
+        for _ in range(steps):
+            done += sum(sim.counts())
+            sim.step(1)
+    else:
+        done = sum(sim.counts()) * steps
+        sim.step(steps)
+    t1.record(sim.stream)
+    torch.cuda.synchronize(dev)
+    ms = t0.elapsed_time(t1)
+    clocks = sampler.stop()
+    # per-kernel times (events around every launch: per-step calls, no graph)
+    B.pic_kernel_times(sim.ctx)
+    B.pic_timing(sim.ctx, True)
+    kdone = 0
+    for _ in range(kt_steps):
+        kdone += sum(sim.counts())
+        sim.step(1)
+    torch.cuda.synchronize(dev)
+    kt = B.pic_kernel_times(sim.ctx)
+    B.pic_timing(sim.ctx, False)
+    sim.check()
+    sim.close()
+    peak, peak_kind = hbm_peak()
+    push_ms, push_n = kt["push"]
+    avg_push_s = push_ms * 1e-3 / max(push_n, 1)
+    avg_n = kdone / max(kt_steps, 1)
+    geo = _Geometry(w["dim"], full_grid(name))
+    alg = push_bytes_per_launch(geo, avg_n)
+    return {
+        "workload": name, "config": dict(workload_config(name, geo), particles_mean=avg_n,
+                                         sort_every=tun["sort_every"], tile=tun["tile"][: w["dim"]],
+                                         halo=tun["halo"], autotuned=False),
+        "steps": steps, "warmup": warmup, "value": done / (ms * 1e-3),
+        "unit": "particle-steps/s", "ms_per_step": ms / steps,
+        "step_graph": not shock,
+        "roofline": {"bound": "hbm", "achieved": alg / avg_push_s / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": alg / avg_push_s / 1e9 / peak,
+                     "kernel": f"k_particles<{w['dim']},{3 if shock else 0}>",
+                     "peak_source": peak_kind, "avg_launch_us": avg_push_s * 1e6,
+                     "alg_bytes_per_launch": alg, "timed_steps": kt_steps},
+        "kernel_ms_per_step": {k: v[0] / kt_steps for k, v in kt.items() if v[1] > 0},
+        "clocks": clocks, "setup_s": gen_s,
+    }
+
+
+class _Geometry:
+    """Cells of a box, for the byte counts (a Plasma's dim, extents, ncells)."""
+
+    def __init__(self, dim, grid):
+        self.dim = dim
+        g = list(grid) + [1] * (3 - len(grid))
+        self.nx, self.ny, self.nz = g
+        self.ncells = self.nx * self.ny * self.nz
 
 
 def run_ours(args):
@@ -545,9 +818,19 @@ def run_ours(args):
     }
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(args.workload)
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
-    print(json.dumps(line), flush=True)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample",
+                                                   "single_core")}
+        line["parity"] = parity_report(args.workload)
     sim.close()
+    if world == 1 and args.sub_records and args.workload == "turbulence_2d3v":
+        # the other set-ups of the paper at their benchmark sizes, bounded runs
+        line["other_workloads"] = {}
+        for nm, k, wu in (("weibel_1d3v", 1000, 20), ("shock_3d3v", 20, 5)):
+            rec = sub_record(nm, k, wu, local)
+            if not args.no_cpu_baseline:
+                rec["parity"] = parity_report(nm)
+            line["other_workloads"][nm] = rec
+    print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
@@ -804,6 +1087,8 @@ def main():
                     help="keep the default tuning instead of autotuning before the timed region")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub-records", dest="sub_records", action="store_false",
+                    help="skip the bounded 1D Weibel and 3D shock runs of the default line")
     ap.add_argument("--grid", type=int, default=0,
                     help="box size (2D side, 1D length, 3D x-length with y = z = x/8); "
                          "0 = the workload's benchmark size")

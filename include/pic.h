@@ -345,7 +345,10 @@ pic_status pic_kernel_times(pic_ctx* ctx, double* ms, int64_t* launches);
  *
  * The first call on a device looks up the device address of the scratch array
  * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Every call uses the same array, which keeps the last
+ * any stream capture.  The address is kept per device ordinal for the life of
+ * the process: after cudaDeviceReset (or when a caller makes a different
+ * driver-API context current on the same device) it is stale, and calls on
+ * that device must not be made again.  Every call uses the same array, which keeps the last
  * call's contents; each pass writes the whole part it later reads, so nothing
  * needs clearing.  Calls whose GPU work overlaps (on different streams or from
  * different host threads, on the same device) race on the array: the caller

@@ -16,7 +16,7 @@ discrete continuity), FDTD2 (Yee dispersion relation, div B), Binomial2
 reflected particles, conductor standing waves) and injector (the box fills
 with the advected upstream template, no gap and no duplicate);
 ``tests/test_oracle_adjoint.py``: the adjoint step (transpose identities and
-central differences).  ``oracle.mutation_check`` plants 30 mistakes in copies
+central differences).  ``oracle.mutation_check`` plants 31 mistakes in copies
 of the C sources and shows that each one fails a pin
 (``tests/test_oracle_mutations.py``).
 """
@@ -200,8 +200,19 @@ def deposit(g: Grid, F, x_old, dx, q: float):
                       ctypes.c_double(q))
 
 
-def step(g: Grid, F, species, passes: int = 0, nsteps: int = 1):
-    """`nsteps` full time steps in the order of Table 1 (in place)."""
+def deposit_abs(g: Grid, F, x_old, dx, q: float):
+    """deposit() with every ZigZag term added as its absolute value: per
+    current word, the sum of |contribution| over the moves (it bounds |J| and
+    equals it for a single move)."""
+    lib().orc_deposit_abs(g.c_struct(), _p(F), _p(x_old), _p(dx), ctypes.c_long(x_old.shape[1]),
+                          ctypes.c_double(q))
+
+
+def step(g: Grid, F, species, passes: int = 0, nsteps: int = 1, terms=None):
+    """`nsteps` full time steps in the order of Table 1 (in place).  With a
+    list `terms`, each step appends the 3 planes of its current's term
+    magnitudes: deposit_abs of the step's moves, through the same filter
+    passes (whose weights are positive, so the planes still bound |J|)."""
     ns = len(species)
     xs = (_D * ns)(*[_p(s.x) for s in species])
     us = (_D * ns)(*[_p(s.u) for s in species])
@@ -212,6 +223,16 @@ def step(g: Grid, F, species, passes: int = 0, nsteps: int = 1):
     for _ in range(nsteps):
         lib().orc_step(g.c_struct(), _p(F), xs, us, n, q, m, ctypes.c_int(ns),
                        ctypes.c_int(passes), _p(work))
+        if terms is not None:  # the step's moves are left in `work`: x_old, then dx
+            A = g.zeros()
+            o = 0
+            for s in species:
+                x_old = np.ascontiguousarray(work[o:o + 3 * s.n].reshape(3, s.n))
+                dx = np.ascontiguousarray(work[o + 3 * s.n:o + 6 * s.n].reshape(3, s.n))
+                deposit_abs(g, A, x_old, dx, s.q)
+                o += 6 * s.n
+            filter_binomial(g, A, passes)
+            terms.append(A[6:9].copy())
 
 
 def set_wall(w: int, i_zero: int = 0):
@@ -266,11 +287,13 @@ def shock_from_plasma(pl):
     return sh["wall"], int(np.floor(sh["x_max"])) + 2, inj
 
 
-def step_shock(g: Grid, F, species, injector, s0: int, passes: int = 0, nsteps: int = 1):
+def step_shock(g: Grid, F, species, injector, s0: int, passes: int = 0, nsteps: int = 1,
+               terms=None):
     """`nsteps` steps of the shock set-up from step index s0: each a full step
-    (with the wall set by set_wall) followed by the injection of that step."""
+    (with the wall set by set_wall) followed by the injection of that step;
+    `terms` as in step()."""
     for t in range(nsteps):
-        step(g, F, species, passes=passes, nsteps=1)
+        step(g, F, species, passes=passes, nsteps=1, terms=terms)
         if injector is not None:
             injector.inject(s0 + t, species)
 

@@ -43,6 +43,7 @@ MUTATIONS = [
     ("relay_min_max", _C, "xr[d] = fmin(lo, fmax(hi, 0.5 * (x1[d] + x2[d])));",
      "xr[d] = fmax(lo, fmin(hi, 0.5 * (x1[d] + x2[d])));", _PINS),
     ("segment_term_sign", _C, "(o[b] == o[c] ? 1.0 : -1.0)", "(o[b] == o[c] ? -1.0 : 1.0)", _PINS),
+    ("abs_term_dropped", _C, "+= g_abs ? fabs(v) : v;", "+= v;", _PINS),
     ("move_without_c", _C, "dx[d * n + p] = g->c * up[d] / gam;", "dx[d * n + p] = up[d] / gam;", _PINS),
     ("e_minus_j_sign", _C, "F[(EX + a) * P + p] -= F[(JX + a) * P + p];",
      "F[(EX + a) * P + p] += F[(JX + a) * P + p];", _PINS),

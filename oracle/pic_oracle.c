@@ -235,6 +235,7 @@ void orc_set_pusher(int pusher) { g_pusher = pusher; }
  * segment.  Appendices B and D require the deposit to conserve charge, so the
  * term is included in 3D (in 1D and 2D no gridded component has two gridded
  * transverse axes and the midpoint products are exact). */
+static int g_abs = 0; /* orc_deposit_abs: add |term| instead of term */
 static void deposit_segment(const orc_grid* g, double* F, const long* I, const double* Fl,
                             const double* W, const double* Ds) {
   const long P = ncell(g);
@@ -257,7 +258,8 @@ static void deposit_segment(const orc_grid* g, double* F, const long* I, const d
             const int b = (a + 1) % 3, c = (a + 2) % 3;
             wt += (o[b] == o[c] ? 1.0 : -1.0) * Ds[b] * Ds[c] / 12.0;
           }
-          F[(JX + a) * P + at(g, I[0] + c0, I[1] + c1, I[2] + c2)] += Fl[a] * wt;
+          const double v = Fl[a] * wt;
+          F[(JX + a) * P + at(g, I[0] + c0, I[1] + c1, I[2] + c2)] += g_abs ? fabs(v) : v;
         }
 }
 
@@ -363,6 +365,20 @@ void orc_deposit(const orc_grid* g, double* F, const double* x_old, const double
       orc_zigzag(g, F, x1, x2, q);
     }
   }
+}
+
+/* The same deposit with every term of Appendix D's ZigZag sum (one flux times
+ * one weight, per current word and segment) added as its absolute value: per
+ * word, the sum of |term| over the moves.  It bounds |J| on every word (the
+ * triangle inequality) and equals |J| for a single move (all of a move's terms
+ * on one component share the sign of its displacement: the weights are
+ * non-negative).  FP32 sums the terms in some order, so its rounding error on a
+ * word scales with this sum, not with the net J, which can cancel. */
+void orc_deposit_abs(const orc_grid* g, double* F, const double* x_old, const double* dx, long n,
+                     double q) {
+  g_abs = 1;
+  orc_deposit(g, F, x_old, dx, n, q);
+  g_abs = 0;
 }
 
 /* Field boundary of the conducting wall at the node x = w (Sect. 4.2): the

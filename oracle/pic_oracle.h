@@ -77,6 +77,10 @@ void orc_push_particles(const orc_grid* g, const double* F, double* x, double* u
 /* comp_curr of Table 1 for one species: ZigZag from x_old to x_old + dx. */
 void orc_deposit(const orc_grid* g, double* F, const double* x_old, const double* dx, long n,
                  double q);
+/* The same ZigZag deposit adding |term| for each of Appendix D's terms: per
+ * current word the sum of the magnitudes of its contributions. */
+void orc_deposit_abs(const orc_grid* g, double* F, const double* x_old, const double* dx, long n,
+                     double q);
 
 /* Shock boundaries (Sect. 4.2).  orc_set_wall(w, i_zero) with w >= 1 puts a
  * conducting wall on the node plane x = w for orc_push_particles, orc_deposit

@@ -71,6 +71,18 @@ struct pic_ctx {
   int* d_dcount = nullptr;  // entries per species
   float* d_adjF = nullptr;                   // forward fields of an adjoint step (9 planes)
   long long steps = 0;
+  long long sorted_step = -1;  // value of `steps` at the last tile sort
+  bool capturing = false;      // pic_step is being captured into a CUDA graph
+  // pic_step(n) replays whole sort cycles from a CUDA graph (boxes without
+  // shock boundaries, timing off), captured on cap_st; it stays valid while
+  // the tuning, the pusher and field solver, and the phase of the sort cycle
+  // are those of the capture
+  cudaStream_t cap_st = nullptr;
+  cudaGraph_t step_graph = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  pic_tuning step_tun{};
+  long long step_phase = -1;
+  int step_solver = -1;
   bool timing = false;
   std::vector<TimedLaunch> pending;
   std::vector<cudaEvent_t> pool;
@@ -130,6 +142,12 @@ void free_all(pic_ctx* ctx) {
   dfree(ctx->d_dlist);
   dfree(ctx->d_dcount);
   dfree(ctx->d_adjF);
+  if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+  if (ctx->step_graph) cudaGraphDestroy(ctx->step_graph);
+  ctx->step_exec = nullptr;
+  ctx->step_graph = nullptr;
+  if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
+  ctx->cap_st = nullptr;
   for (auto& t : ctx->pending) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
@@ -170,10 +188,15 @@ std::string derive_tiles(const pic_grid& grid, const pic_tuning& tun, long long 
       r.T[d] = tun.tile[d] < n ? tun.tile[d] : n;
       r.nt[d] = (n + r.T[d] - 1) / r.T[d];
       r.W[d] = r.T[d] + 2 * r.H + 1;
+      const int sub = kSubTile[d] > 0 && kSubTile[d] < r.T[d] ? kSubTile[d] : r.T[d];
+      r.S[d] = sub;
+      r.ns[d] = (r.T[d] + sub - 1) / sub;
     } else {
       r.T[d] = 1;
       r.nt[d] = 1;
       r.W[d] = 1;
+      r.S[d] = 1;
+      r.ns[d] = 1;
     }
     ntiles *= r.nt[d];
     wcells *= r.W[d];
@@ -185,6 +208,8 @@ std::string derive_tiles(const pic_grid& grid, const pic_tuning& tun, long long 
     return "tile + halo window exceeds 200 KB of shared memory";
   if (ntiles > (1LL << 30)) return "too many tiles";
   r.ntiles = (int)ntiles;
+  r.nsub = r.ns[0] * r.ns[1] * r.ns[2];
+  if (ntiles * r.nsub > (1LL << 30)) return "too many sort bins";
   const long long per_tile = (ntot + ntiles - 1) / ntiles;
   const auto clamp = [](long long v) { return (int)(v < 1 ? 1 : v > 1024 ? 1024 : v); };
   long long sp = (per_tile + tun.chunk - 1) / tun.chunk;
@@ -204,12 +229,12 @@ std::string derive_tiles(const pic_grid& grid, const pic_tuning& tun, long long 
 pic_status alloc_tiles(pic_ctx* ctx) {
   for (int s = 0; s < ctx->ns; ++s) {
     dfree(ctx->d_tstart[s]);
-    PIC_CK(ctx, dalloc(&ctx->d_tstart[s], (size_t)ctx->tile.ntiles + 1));
+    PIC_CK(ctx, dalloc(&ctx->d_tstart[s], sort_bins(ctx->tile) + 1));
   }
   dfree(ctx->d_count);
   dfree(ctx->d_cursor);
-  PIC_CK(ctx, dalloc(&ctx->d_count, (size_t)ctx->tile.ntiles));
-  PIC_CK(ctx, dalloc(&ctx->d_cursor, (size_t)ctx->tile.ntiles));
+  PIC_CK(ctx, dalloc(&ctx->d_count, sort_bins(ctx->tile)));
+  PIC_CK(ctx, dalloc(&ctx->d_cursor, sort_bins(ctx->tile)));
   return PIC_OK;
 }
 
@@ -331,11 +356,12 @@ pic_status do_sort(pic_ctx* ctx, bool copy_back) {
   const cudaError_t e = timed(ctx, PIC_KERNEL_SORT, [&]() -> cudaError_t {
     for (int s = 0; s < ctx->ns; ++s) {
       const long long n = ctx->sp[s].n, ld = ctx->cap[s];
-      cudaError_t r = cudaMemsetAsync(ctx->d_count, 0, sizeof(int) * ctx->tile.ntiles, ctx->st);
+      const int bins = (int)sort_bins(ctx->tile);
+      cudaError_t r = cudaMemsetAsync(ctx->d_count, 0, sizeof(int) * bins, ctx->st);
       if (r != cudaSuccess) return r;
       r = launch_tile_count(P, ctx->sp[s].cell, n, ctx->d_count, ctx->st);
       if (r != cudaSuccess) return r;
-      r = launch_tile_scan(ctx->d_count, ctx->tile.ntiles, ctx->d_tstart[s], ctx->d_cursor, ctx->st);
+      r = launch_tile_scan(ctx->d_count, bins, ctx->d_tstart[s], ctx->d_cursor, ctx->st);
       if (r != cudaSuccess) return r;
       if (n == 0) continue;
       int* cell_out = (int*)ctx->d_sortbuf + sortbuf_offset(ctx, s);
@@ -372,6 +398,7 @@ pic_status do_sort(pic_ctx* ctx, bool copy_back) {
   }
   ctx->snapshot_valid = false;
   ctx->sorted_pending = !copy_back;
+  ctx->sorted_step = ctx->steps;
   return PIC_OK;
 }
 
@@ -430,6 +457,57 @@ void plan_injection(const pic_ctx* ctx, long long s, InjectParams* P, long long*
     P->ld[sp] = ctx->cap[sp];
     o += ctx->tn[sp] * (1 + D + 3);
   }
+}
+
+// Longest sort cycle (steps) captured into one graph.
+constexpr int kMaxCycle = 240;
+
+bool step_graph_current(const pic_ctx* ctx) {
+  return ctx->step_exec && std::memcmp(&ctx->tun, &ctx->step_tun, sizeof(pic_tuning)) == 0 &&
+         ctx->steps % ctx->tun.sort_every == ctx->step_phase &&
+         ctx->pusher * 16 + ctx->g.order == ctx->step_solver;
+}
+
+// Capture one sort cycle of pic_step into the context's step graph (on a
+// private stream; nothing runs during the capture).
+pic_status step_capture(pic_ctx* ctx) {
+  if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+  if (ctx->step_graph) cudaGraphDestroy(ctx->step_graph);
+  ctx->step_exec = nullptr;
+  ctx->step_graph = nullptr;
+  // buffers that pic_step would allocate on first use: no allocation may
+  // happen during a capture
+  if (ctx->tun.filter_passes > 0 && !ctx->d_jtmp)
+    PIC_CK(ctx, dalloc(&ctx->d_jtmp, 3 * (size_t)ctx->g.plane));
+  if (!ctx->cap_st) PIC_CK(ctx, cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking));
+  // work already queued on the context's stream is ordered before the graph
+  // launches on that stream; the capture itself runs nothing
+  const cudaStream_t saved_st = ctx->st;
+  const long long saved_steps = ctx->steps;
+  PIC_CK(ctx, cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal));
+  ctx->st = ctx->cap_st;
+  ctx->capturing = true;
+  const pic_status st = pic_step(ctx, ctx->tun.sort_every);
+  ctx->capturing = false;
+  ctx->st = saved_st;
+  ctx->steps = saved_steps;  // the captured steps have not run yet
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(ctx->cap_st, &graph);
+  if (st != PIC_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return st != PIC_OK ? st : cuda_fail(ctx, "step graph capture", e);
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&ctx->step_exec, graph, 0);
+  if (ei != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    ctx->step_exec = nullptr;
+    return cuda_fail(ctx, "step graph instantiation", ei);
+  }
+  ctx->step_graph = graph;
+  ctx->step_tun = ctx->tun;
+  ctx->step_phase = ctx->steps % ctx->tun.sort_every;
+  ctx->step_solver = ctx->pusher * 16 + ctx->g.order;
+  return PIC_OK;
 }
 
 pic_status do_filter(pic_ctx* ctx, int passes) {
@@ -811,6 +889,24 @@ pic_status pic_field_update(pic_ctx* ctx, int which) {
 pic_status pic_step(pic_ctx* ctx, int nsteps) {
   if (!ctx) return PIC_ERR_ARG;
   if (nsteps < 0) return set_err(ctx, PIC_ERR_ARG, "nsteps must be >= 0");
+  // whole sort cycles from the context's step graph: the same kernels with the
+  // same arguments as the loop below, launched as one graph per cycle
+  const int cyc = ctx->tun.sort_every;
+  if (PIC_STEP_GRAPHS && !ctx->shock && !ctx->timing && !ctx->capturing && cyc <= kMaxCycle &&
+      nsteps >= 2 * cyc) {
+    if (!step_graph_current(ctx)) {
+      const pic_status s = step_capture(ctx);
+      if (s != PIC_OK) return s;
+    }
+    const int full = nsteps / cyc;
+    for (int i = 0; i < full; ++i) {
+      const cudaError_t e = cudaGraphLaunch(ctx->step_exec, ctx->st);
+      if (e != cudaSuccess) return cuda_fail(ctx, "step graph launch", e);
+    }
+    ctx->steps += (long long)full * cyc;
+    ctx->snapshot_valid = false;
+    nsteps -= full * cyc;
+  }
   const auto wall_bc = [&]() {
     if (!ctx->shock) return cudaSuccess;
     return timed(ctx, PIC_KERNEL_BOUNDARY, [&]() {
@@ -826,7 +922,11 @@ pic_status pic_step(pic_ctx* ctx, int nsteps) {
         if (ctx->sp[s].n + add[s] > ctx->cap[s])
           return set_err(ctx, PIC_ERR_ARG, "injection would exceed a species' cap");
     }
-    if (ctx->steps > 0 && ctx->steps % ctx->tun.sort_every == 0) {
+    // a sort opens every cycle of sort_every steps, unless the particles were
+    // sorted at this very step count already (at set-up, by pic_sort or a
+    // re-tiling); a captured cycle always sorts, since it is replayed later
+    if (ctx->steps % ctx->tun.sort_every == 0 &&
+        (ctx->capturing || ctx->sorted_step != ctx->steps)) {
       const pic_status s = do_sort(ctx, false);
       if (s != PIC_OK) return s;
     }
@@ -1086,7 +1186,6 @@ struct pic_batch {
 namespace {
 
 constexpr int kBatchBranches = 32;
-constexpr int kMaxCycle = 240;
 
 long long gcd_ll(long long a, long long b) {
   while (b) {
@@ -1140,7 +1239,9 @@ pic_status batch_capture(pic_batch* b) {
     c->st = b->branches[i % b->branches.size()];
     c->timing = false;
     c->ensemble = true;
+    c->capturing = true;
     st = pic_step(c, b->cycle);
+    c->capturing = false;
     c->ensemble = false;
     c->st = saved_st[i];
     c->timing = saved_timing[i];

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace pic {
 
 enum { EX = 0, EY, EZ, BX, BY, BZ, JX, JY, JZ };
@@ -31,6 +33,9 @@ struct TileDev {
   int wcells;   // W0*W1*W2
   int wstride;  // wcells rounded up to a multiple of 4 (16-byte aligned planes)
   int ntiles;
+  int S[3];     // sub-tile extents: the sort orders a tile's particles by sub-tile
+  int ns[3];    // sub-tiles per tile along each axis
+  int nsub;     // sub-tiles per tile (sort bins per tile)
 };
 
 struct SpeciesDev {
@@ -114,6 +119,41 @@ struct SmemJ {
     const int iv = __float2int_rn(v);
 #endif
     atomicAdd(&ji[(comp - JX) * wc + i + W0 * j + W01 * k], iv);
+  }
+};
+
+// 2D shared-memory current window with two int32 fixed-point words per 64-bit
+// shared atomic.  Three planes of 64-bit words, indexed by the lower corner c
+// of a ZigZag segment's cell (x fastest, row length W0):
+//   Q[c] = (Jx(i,j),   Jy(i,j))
+//   R[c] = (Jx(i,j+1), Jy(i+1,j))
+//   P[c] = (Jz(i,j),   Jz(i+1,j))        (row j+1 goes to P[c + W0])
+// so a segment's 8 words take 4 atomics.  A pair (a, b) of quantised values
+// is the integer b 2^32 + a: the low word's sign borrows from the high word,
+// so sums of pairs stay exact as long as each word's sum fits in int32, and
+// lo = (int32) S, hi = (S - lo) >> 32 recover both.  The pair is formed by one
+// packed add of 1.5 * 2^23 (rounding each value to an integer, as SmemJ does)
+// and one 64-bit subtract of the two biases.
+struct SmemJ64 {
+  unsigned long long* Q;  // P = Q + 2 ws, R = Q + ws
+  int W0, ws;
+  __device__ __forceinline__ static unsigned long long pair(float a, float b) {
+    const float2 t = __fadd2_rn(make_float2(a, b), make_float2(12582912.0f, 12582912.0f));
+    const unsigned long long bits =
+        ((unsigned long long)__float_as_uint(t.y) << 32) | __float_as_uint(t.x);
+    return bits - 0x4B4000004B400000ULL;
+  }
+  // the 8 words of zz_values<2> for a segment in the cell with corner I
+  __device__ __forceinline__ void deposit(const int* I, const float* v) const {
+    const int c = I[0] + W0 * I[1];
+    atomicAdd(&Q[c], pair(v[0], v[2]));
+    atomicAdd(&Q[ws + c], pair(v[1], v[3]));
+    atomicAdd(&Q[2 * ws + c], pair(v[4], v[5]));
+    atomicAdd(&Q[2 * ws + c + W0], pair(v[6], v[7]));
+  }
+  __device__ __forceinline__ static int lo(unsigned long long s) { return (int)(unsigned)s; }
+  __device__ __forceinline__ static int hi(unsigned long long s) {
+    return (int)((long long)(s - (unsigned long long)(long long)lo(s)) >> 32);
   }
 };
 
@@ -412,8 +452,13 @@ __device__ __forceinline__ void zigzag(const Acc& A, const int* b, const int* dc
 #pragma unroll
     for (int w = 0; w < zz_words<D>(); ++w) v1[w] += v2[w];
   }
-  zz_deposit<D>(A, b, v1);
-  if (crossed) zz_deposit<D>(A, b2, v2);
+  if constexpr (std::is_same<Acc, SmemJ64>::value) {
+    A.deposit(b, v1);
+    if (crossed) A.deposit(b2, v2);
+  } else {
+    zz_deposit<D>(A, b, v1);
+    if (crossed) zz_deposit<D>(A, b2, v2);
+  }
 }
 
 }  // namespace pic

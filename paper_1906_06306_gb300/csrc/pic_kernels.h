@@ -20,9 +20,46 @@ constexpr int kMaxSpecies = 4;
 #ifndef PIC_PUSH_MIN_BLOCKS_3D
 #define PIC_PUSH_MIN_BLOCKS_3D 2
 #endif
+// Blocks whose tile window lies inside the lattice skip the periodic-wrap
+// arithmetic (window-local indices and the new cell index).
+#ifndef PIC_INTERIOR
+#define PIC_INTERIOR 1
+#endif
+// 2D window layout with x-adjacent points paired: (Ex, By, Ex+, By+) and
+// (Ey, Bx, Ey+, Bx+) as float4, (Ez, Ez+) and (Bz, Bz+) as float2, so a
+// stencil row is one shared load per component pair.
+#ifndef PIC_XPAIR
+#define PIC_XPAIR 0
+#endif
+// 2D current window of 64-bit pairs of fixed-point words (SmemJ64): half the
+// shared atomics of the int32 window.
+#ifndef PIC_J64
+#define PIC_J64 0
+#endif
+template <int D>
+constexpr bool kJ64 = D == 2 && PIC_J64 != 0;
+// pic_step(n) replays whole sort cycles from a captured CUDA graph.
+#ifndef PIC_STEP_GRAPHS
+#define PIC_STEP_GRAPHS 1
+#endif
 #ifndef PIC_PREFETCH
 #define PIC_PREFETCH 0
 #endif
+// Sub-tile extents of the sort key (0: the whole tile).  The tile sort orders
+// a tile's particles by sub-tile, so the lanes of a warp gather from and
+// deposit into a small patch of the tile window.
+#ifndef PIC_SUBTILE_X
+#define PIC_SUBTILE_X 0
+#endif
+#ifndef PIC_SUBTILE_Y
+#define PIC_SUBTILE_Y 0
+#endif
+#ifndef PIC_SUBTILE_Z
+#define PIC_SUBTILE_Z 0
+#endif
+constexpr int kSubTile[3] = {PIC_SUBTILE_X, PIC_SUBTILE_Y, PIC_SUBTILE_Z};
+// Sort bins of a tiling: sub-tiles of every tile, tile-major.
+inline long long sort_bins(const TileDev& t) { return (long long)t.ntiles * t.nsub; }
 constexpr int kPushThreads = PIC_PUSH_THREADS;
 constexpr int kSpillEvery = PIC_SPILL_EVERY;  // batches of kPushThreads particles between spills
 // Shared-memory queue of the 1D/2D tile kernels for particles outside the tile
@@ -111,6 +148,7 @@ struct SortParams {
   int* status;
   FastDiv dn0, dn1;          // by the grid extents n0, n1: cell -> (i, j, k)
   FastDiv dt0, dt1, dt2;     // by the tile extents: lattice point -> tile
+  FastDiv ds0, ds1, ds2;     // by the sub-tile extents: tile-local point -> sub-tile
 };
 SortParams make_sort_params(const GridDev& g, const TileDev& t, int* status);
 cudaError_t launch_tile_count(const SortParams& P, const int* cell, long long n, int* count,

@@ -54,7 +54,7 @@ struct Win {
 
 template <int D>
 __host__ __device__ constexpr int field_floats() {
-  return D == 1 ? 8 : 6;
+  return D == 1 ? 8 : D == 2 && PIC_XPAIR ? 12 : 6;
 }
 
 // Words of the staged field region, rounded up so that the current planes
@@ -98,6 +98,39 @@ __device__ __forceinline__ void gather_smem(const float* sm, int wc, int W0, int
     e[1] = lerp(c0.x, c1.x, o[0]);
     e[2] = lerp(c0.y, c1.y, o[0]);
     b[0] = lerp(c0.z, c1.z, o[0]);
+  } else if (D == 2 && PIC_XPAIR) {
+    // x-paired layout: one 16-byte load per row for (Ex, By) and (Ey, Bx), one
+    // 8-byte load per row for Ez and Bz; the same operations as below
+    const float4* FA = reinterpret_cast<const float4*>(sm);
+    const float4* FB = FA + wc;
+    const float2* FC = reinterpret_cast<const float2*>(FB + wc);
+    const float2* FD = FC + wc;
+    const bool hx = o[0] >= 0.5f, hy = o[1] >= 0.5f;
+    const int bxh = hx ? l[0] : l[0] - 1, byh = hy ? l[1] : l[1] - 1;
+    const float wxh = hx ? o[0] - 0.5f : o[0] + 0.5f;
+    const float wyh = hy ? o[1] - 0.5f : o[1] + 0.5f;
+    int i = bxh + W0 * l[1];  // (1/2, 0): Ex, By
+    const float4 a0 = FA[i], a1 = FA[i + W0];
+    const float2 ra = bilerp2(make_float2(a0.x, a0.y), make_float2(a0.z, a0.w),
+                              make_float2(a1.x, a1.y), make_float2(a1.z, a1.w),
+                              make_float2(wxh, wxh), make_float2(o[1], o[1]));
+    i = l[0] + W0 * byh;  // (0, 1/2): Ey, Bx
+    const float4 b0 = FB[i], b1 = FB[i + W0];
+    const float2 rb = bilerp2(make_float2(b0.x, b0.y), make_float2(b0.z, b0.w),
+                              make_float2(b1.x, b1.y), make_float2(b1.z, b1.w),
+                              make_float2(o[0], o[0]), make_float2(wyh, wyh));
+    i = l[0] + W0 * l[1];  // (0, 0): Ez, paired with (1/2, 1/2): Bz
+    const int k = bxh + W0 * byh;
+    const float2 c0 = FC[i], c1 = FC[i + W0], d0 = FD[k], d1 = FD[k + W0];
+    const float2 rc = bilerp2(make_float2(c0.x, d0.x), make_float2(c0.y, d0.y),
+                              make_float2(c1.x, d1.x), make_float2(c1.y, d1.y),
+                              make_float2(o[0], wxh), make_float2(o[1], wyh));
+    e[0] = ra.x;
+    b[1] = ra.y;
+    e[1] = rb.x;
+    b[0] = rb.y;
+    e[2] = rc.x;
+    b[2] = rc.y;
   } else if (D == 2) {
     const float2* FA = reinterpret_cast<const float2*>(sm);
     const float2* FB = reinterpret_cast<const float2*>(sm + 2 * wc);
@@ -203,9 +236,15 @@ enum : int { kDone = 0, kStray = 1, kWallCross = 2 };
 // move crosses the conducting wall (kWallCross) is not touched either: the
 // caller defers it.  PATH 2: global memory with the reflection applied here
 // (the deferred and tail kernels).
-template <int D, int MODE, int PATH, int FW0 = 0, int FW1 = 0, int FW2 = 1>
+//
+// INTERIOR (PATH 0 only): the block's window lies inside the lattice on every
+// axis, so window-local indices need no periodic wrap and a particle whose
+// stencil is in the window moves to a cell inside the lattice: its new cell
+// index is the old one plus the cell offsets times the axis strides.
+template <int D, int MODE, int PATH, int FW0 = 0, int FW1 = 0, int FW2 = 1, bool INTERIOR = false,
+          class JA = SmemJ>
 __device__ __forceinline__ int one_particle(const PushParams& P, const SpeciesDev& S, int p,
-                                            PRec r, const float* sm, const SmemJ& SJ,
+                                            PRec r, const float* sm, const JA& SJ,
                                             const GlobAcc& GA, const int* w0, float qs) {
   constexpr bool GLOBAL = PATH != 0;
   const long long n = S.ld;
@@ -241,11 +280,13 @@ __device__ __forceinline__ int one_particle(const PushParams& P, const SpeciesDe
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       int v = ijk[d] - w0[d];
-      if (P.wrap_fast) {
-        v += (v < 0) ? P.g.n[d] : 0;
-        v -= (v >= P.g.n[d]) ? P.g.n[d] : 0;
-      } else {
-        v = wrapi(v, P.g.n[d]);
+      if (!INTERIOR) {  // periodic image of the window
+        if (P.wrap_fast) {
+          v += (v < 0) ? P.g.n[d] : 0;
+          v -= (v >= P.g.n[d]) ? P.g.n[d] : 0;
+        } else {
+          v = wrapi(v, P.g.n[d]);
+        }
       }
       l[d] = v;
       inwin &= (unsigned)(v - 1) <= (unsigned)(Win<FW0, FW1, FW2>::w(P, d) - 4);
@@ -279,11 +320,18 @@ __device__ __forceinline__ int one_particle(const PushParams& P, const SpeciesDe
   if (PATH != 2 && refl) return kWallCross;
 
   if (MODE != 2) {
-    int nc[3] = {0, 0, 0};
+    int cell2;
+    if (INTERIOR && !refl) {
+      cell2 = r.cell + dc[0];
+      if (D >= 2) cell2 += P.g.n[0] * dc[1];
+      if (D == 3) cell2 += P.g.n[0] * P.g.n[1] * dc[2];
+    } else {
+      int nc[3] = {0, 0, 0};
 #pragma unroll
-    for (int d = 0; d < D; ++d) nc[d] = wrap1(ijk[d] + dc[d], P.g.n[d]);
-    if (refl) nc[0] = ijk[0];
-    const int cell2 = nc[0] + P.g.n[0] * (nc[1] + P.g.n[1] * nc[2]);
+      for (int d = 0; d < D; ++d) nc[d] = wrap1(ijk[d] + dc[d], P.g.n[d]);
+      if (refl) nc[0] = ijk[0];
+      cell2 = nc[0] + P.g.n[0] * (nc[1] + P.g.n[1] * nc[2]);
+    }
     S.u[p] = refl ? -u[0] : u[0];
 #pragma unroll
     for (int a = 1; a < 3; ++a) S.u[a * n + p] = u[a];
@@ -344,15 +392,28 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
   int w0[3] = {0, 0, 0};
 #pragma unroll
   for (int d = 0; d < D; ++d) w0[d] = tc[d] * P.t.T[d] - P.t.H;
+  // the window lies inside the lattice: no periodic wrap (block-uniform)
+  bool interior = PIC_INTERIOR != 0;
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+    interior &= w0[d] >= 0 && w0[d] + Win<FW0, FW1, FW2>::w(P, d) <= P.g.n[d];
   const int wc = Win<FW0, FW1, FW2>::wc(P);
   const int ws = Win<FW0, FW1, FW2>::ws(P);  // plane stride of the current windows (wc rounded up to 4)
   const int W0 = Win<FW0, FW1, FW2>::w(P, 0), W1 = Win<FW0, FW1, FW2>::w(P, 1);
   constexpr int NF = field_floats<D>();
   const int fw = field_words(NF, wc);
+  // fixed-point window: 3 planes of int32 words, or (2D, kJ64<D>) of 64-bit
+  // pairs of them; then the float running sums and the 1D/2D stray queue
+  constexpr int JW = kJ64<D> ? 6 : 3;  // words per window cell of the int window
   int* ji = reinterpret_cast<int*>(sm + fw);
-  float* jf = sm + fw + 3 * ws;
-  int* queue = reinterpret_cast<int*>(sm + fw + 6 * ws);  // kDrain only
-  const SmemJ SJ{ji, W0, W0 * W1, ws};
+  float* jf = sm + fw + JW * ws;
+  int* queue = reinterpret_cast<int*>(sm + fw + (JW + 3) * ws);  // kDrain only
+  using JAcc = typename std::conditional<kJ64<D>, SmemJ64, SmemJ>::type;
+  JAcc SJ;
+  if constexpr (kJ64<D>)
+    SJ = SmemJ64{reinterpret_cast<unsigned long long*>(ji), W0, ws};
+  else
+    SJ = SmemJ{ji, W0, W0 * W1, ws};
   const int lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -369,6 +430,24 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
       if (D == 1) {
         reinterpret_cast<float4*>(sm)[w] = make_float4(ex, by, bz, 0.f);
         reinterpret_cast<float4*>(sm + 4 * wc)[w] = make_float4(ey, ez, bx, 0.f);
+      } else if (D == 2 && PIC_XPAIR) {
+        // point x goes to the low half of its own cell's pair and to the high
+        // half of the pair of the cell before it (the last column's high half
+        // is never read: stencils end at W0 - 2)
+        float4* FA = reinterpret_cast<float4*>(sm);
+        float4* FB = FA + wc;
+        float2* FC = reinterpret_cast<float2*>(FB + wc);
+        float2* FD = FC + wc;
+        reinterpret_cast<float2*>(FA + w)[0] = make_float2(ex, by);
+        reinterpret_cast<float2*>(FB + w)[0] = make_float2(ey, bx);
+        FC[w].x = ez;
+        FD[w].x = bz;
+        if (lx > 0) {
+          reinterpret_cast<float2*>(FA + w - 1)[1] = make_float2(ex, by);
+          reinterpret_cast<float2*>(FB + w - 1)[1] = make_float2(ey, bx);
+          FC[w - 1].y = ez;
+          FD[w - 1].y = bz;
+        }
       } else if (D == 2) {
         reinterpret_cast<float2*>(sm)[w] = make_float2(ex, by);
         reinterpret_cast<float2*>(sm + 2 * wc)[w] = make_float2(ey, bx);
@@ -386,12 +465,36 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
   }
   if (MODE != 1) {
     int4* j4 = reinterpret_cast<int4*>(ji);
-    for (int w = threadIdx.x; w < 6 * ws / 4; w += blockDim.x) j4[w] = make_int4(0, 0, 0, 0);
+    for (int w = threadIdx.x; w < (JW + 3) * ws / 4; w += blockDim.x)
+      j4[w] = make_int4(0, 0, 0, 0);
   }
   __syncthreads();
 
   // between barriers: fold the int32 window into the float window, clear it
   auto spill = [&]() {
+    if constexpr (kJ64<D>) {
+      // every float word gathers its two partial sums (SmemJ64's planes),
+      // then, after all threads have read, the pairs are cleared
+      const unsigned long long* Q = reinterpret_cast<const unsigned long long*>(ji);
+      const unsigned long long* R = Q + ws;
+      const unsigned long long* Pz = Q + 2 * ws;
+      for (int w = threadIdx.x; w < wc; w += blockDim.x) {
+        const bool x0 = w % W0 == 0, y0 = w < W0;
+        const unsigned long long q = Q[w], p = Pz[w];
+        const unsigned long long ry = y0 ? 0ULL : R[w - W0], rx = x0 ? 0ULL : R[w - 1];
+        const unsigned long long px = x0 ? 0ULL : Pz[w - 1];
+        const int vx = SmemJ64::lo(q) + SmemJ64::lo(ry);
+        const int vy = SmemJ64::hi(q) + SmemJ64::hi(rx);
+        const int vz = SmemJ64::lo(p) + SmemJ64::hi(px);
+        if (vx != 0) jf[w] = fmaf((float)vx, P.jq, jf[w]);
+        if (vy != 0) jf[ws + w] = fmaf((float)vy, P.jq, jf[ws + w]);
+        if (vz != 0) jf[2 * ws + w] = fmaf((float)vz, P.jq, jf[2 * ws + w]);
+      }
+      __syncthreads();
+      int4* i4 = reinterpret_cast<int4*>(ji);
+      for (int w = threadIdx.x; w < 6 * ws / 4; w += blockDim.x) i4[w] = make_int4(0, 0, 0, 0);
+      return;
+    }
     int4* i4 = reinterpret_cast<int4*>(ji);
     float4* f4 = reinterpret_cast<float4*>(jf);
     for (int w = threadIdx.x; w < 3 * ws / 4; w += blockDim.x) {
@@ -430,7 +533,7 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
   int batches = 0;
   for (int s = 0; s < P.nspecies; ++s) {
     const SpeciesDev& S = P.sp[s];
-    const long long lo = S.tstart[tile], hi = S.tstart[tile + 1];
+    const long long lo = S.tstart[tile * P.t.nsub], hi = S.tstart[(tile + 1) * P.t.nsub];
     const long long len = hi - lo;
     const int a = (int)(lo + len * split / P.splits);
     const int b = (int)(lo + len * (split + 1) / P.splits);
@@ -444,9 +547,10 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
       } else if (p < b) {
         load_rec<D, MODE>(S, p, cur);
       }
-      const int st = p < b ? one_particle<D, MODE, false, FW0, FW1, FW2>(P, S, p, cur, sm, SJ, GA,
-                                                                         w0, qs)
-                           : kDone;
+      int st = kDone;
+      if (p < b)
+        st = interior ? one_particle<D, MODE, 0, FW0, FW1, FW2, true>(P, S, p, cur, sm, SJ, GA, w0, qs)
+                      : one_particle<D, MODE, 0, FW0, FW1, FW2>(P, S, p, cur, sm, SJ, GA, w0, qs);
       if (kDrain && st == kStray) queue[atomicAdd(&q_n, 1)] = p;
       if (!kDrain || MODE == 3) {
         // deferred particles: one list slot range per warp, reserved by one atomic
@@ -535,8 +639,9 @@ __global__ void __launch_bounds__(kPushThreads) k_particles_deferred(const PushP
 }
 
 size_t particle_smem_bytes(int dim, const TileDev& t) {
-  const int nf = dim == 1 ? field_floats<1>() : field_floats<2>();
-  return sizeof(float) * ((size_t)field_words(nf, t.wcells) + 6 * (size_t)t.wstride) +
+  const int nf = dim == 1 ? field_floats<1>() : dim == 2 ? field_floats<2>() : field_floats<3>();
+  const int jw = (dim == 2 && kJ64<2>) ? 6 : 3;  // int window words per cell
+  return sizeof(float) * ((size_t)field_words(nf, t.wcells) + (jw + 3) * (size_t)t.wstride) +
          (dim < 3 ? sizeof(int) * kQueueCap : 0);  // the 1D/2D stray queue
 }
 

@@ -7,7 +7,8 @@
 
 namespace pic {
 
-// Tile of a cell; every division is an exact multiply-shift (FastDiv).
+// Sort bin of a cell: its tile, then the sub-tile inside it (tile-major); every
+// division is an exact multiply-shift (FastDiv).
 __device__ __forceinline__ int tile_key(const SortParams& P, int cell) {
   if (cell < 0 || (long long)cell >= P.g.plane) {
     atomicOr(P.status, ST_BAD_CELL);
@@ -17,7 +18,12 @@ __device__ __forceinline__ int tile_key(const SortParams& P, int cell) {
   const int i = cell - r * P.g.n[0];
   const int k = fdiv(r, P.dn1);
   const int j = r - k * P.g.n[1];
-  return fdiv(i, P.dt0) + P.t.nt[0] * (fdiv(j, P.dt1) + P.t.nt[1] * fdiv(k, P.dt2));
+  const int ti = fdiv(i, P.dt0), tj = fdiv(j, P.dt1), tk = fdiv(k, P.dt2);
+  const int tile = ti + P.t.nt[0] * (tj + P.t.nt[1] * tk);
+  if (P.t.nsub == 1) return tile;
+  const int si = fdiv(i - ti * P.t.T[0], P.ds0), sj = fdiv(j - tj * P.t.T[1], P.ds1),
+            sk = fdiv(k - tk * P.t.T[2], P.ds2);
+  return tile * P.t.nsub + si + P.t.ns[0] * (sj + P.t.ns[1] * sk);
 }
 
 // Reserve `1` slot of counter[key] for every active lane; returns this lane's
@@ -158,6 +164,9 @@ SortParams make_sort_params(const GridDev& g, const TileDev& t, int* status) {
   P.dt0 = make_fastdiv(t.T[0]);
   P.dt1 = make_fastdiv(t.T[1]);
   P.dt2 = make_fastdiv(t.T[2]);
+  P.ds0 = make_fastdiv(t.S[0]);
+  P.ds1 = make_fastdiv(t.S[1]);
+  P.ds2 = make_fastdiv(t.S[2]);
   return P;
 }
 

@@ -57,7 +57,6 @@ extern "C" pic_status pic_filter_current_static(const pic_grid* grid, float* J, 
     ncell *= n[d];
   }
   if (passes < 0) return fail(PIC_ERR_ARG, "passes must be >= 0");
-  if (n[1] > 65535 || n[2] > 21845) return fail(PIC_ERR_ARG, "ny must be <= 65535 and nz <= 21845");
   if (3 * ncell > PIC_FILTER_STATIC_MAX_FLOATS)
     return fail(PIC_ERR_ARG,
                 "3*nx*ny*nz exceeds PIC_FILTER_STATIC_MAX_FLOATS (the static scratch size); "
@@ -74,16 +73,16 @@ extern "C" pic_status pic_filter_current_static(const pic_grid* grid, float* J, 
   g.plane = ncell;
   g.order = 2;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the context path's fused passes (every axis in one launch), ping-ponging
+  // between J and the static scratch
   float* a = J;
   float* b = scratch;
   for (int p = 0; p < passes; ++p) {
-    for (int axis = 0; axis < g.dim; ++axis) {
-      e = pic::launch_filter_f32(g, a, b, 3, axis, st);
-      if (e != cudaSuccess) return fail(PIC_ERR_CUDA, cudaGetErrorString(e));
-      float* t = a;
-      a = b;
-      b = t;
-    }
+    e = pic::launch_filter_pass_f32(g, a, b, 3, st);
+    if (e != cudaSuccess) return fail(PIC_ERR_CUDA, cudaGetErrorString(e));
+    float* t = a;
+    a = b;
+    b = t;
   }
   if (a != J) {
     e = cudaMemcpyAsync(J, a, sizeof(float) * 3 * ncell, cudaMemcpyDeviceToDevice, st);

@@ -76,6 +76,8 @@ def test_reference_line_carries_the_workload_config_and_the_contract_keys():
     assert d["config"]["grid"] == [1024, 1024]  # the workload's, not the sample's
     assert "sample" in d["config"]
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"]
+    # every host core, with the one-core figure beside it
+    assert cb["kind"] == "oracle" and cb["cores"] == b.host_cores() and cb["value"] == d["value"]
+    assert cb["single_core"]["cores"] == 1 and cb["single_core"]["value"] > 0
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}

@@ -8,7 +8,7 @@ import oracle
 import workloads
 
 from gpu_helpers import (compare_fields, compare_particles, current_scale, oracle_from_sim,
-                         step_floor)
+                         step_floor, term_floor)
 
 pytestmark = pytest.mark.gpu
 
@@ -50,13 +50,14 @@ def test_shock_tube_matches_oracle(oracle_wall, dim, passes):
     oracle_wall(w, i_zero)
     n0 = sim.counts()
     sim.step(nsteps)
-    oracle.step_shock(g, F, osp, inj, 0, passes=passes, nsteps=nsteps)
+    terms = []
+    oracle.step_shock(g, F, osp, inj, 0, passes=passes, nsteps=nsteps, terms=terms)
     sim.check()
     counts = sim.counts()
     assert counts == [s.n for s in osp]
     assert counts[0] > n0[0]  # the injector let particles in
     Fg, spg = sim.download()
-    compare_fields(Fg, F, floor=step_floor(g, osp, nsteps))
+    compare_fields(Fg, F, floor=term_floor(g, terms))
     compare_particles(g, spg, osp)
     for s, o in zip(spg, osp):  # cell bookkeeping is exact (the oracle's cell of the GPU state)
         xg = oracle.positions(g, s["cell"], s["off"])
@@ -91,10 +92,11 @@ def test_reflection_and_injection_alone_match_the_oracle(oracle_wall):
     w, i_zero, inj = oracle.shock_from_plasma(pl)
     oracle_wall(w, i_zero)
     sim.step(1)
-    oracle.step_shock(g, F, osp, inj, 0, nsteps=1)
+    terms = []
+    oracle.step_shock(g, F, osp, inj, 0, nsteps=1, terms=terms)
     Fg, spg = sim.download()
     assert sim.counts() == [s.n for s in osp]
-    compare_fields(Fg, F, floor=step_floor(g, osp, 1))
+    compare_fields(Fg, F, floor=term_floor(g, terms))
     compare_particles(g, spg, osp)
     assert all((s["u"][0][: pl.species[0].n] > 0).all() for s in spg)  # every fill particle reflected
     sim.close()
@@ -114,14 +116,15 @@ def test_sorted_run_matches_unsorted_run_and_oracle_statistics(oracle_wall):
     oracle_wall(w, i_zero)
     a.step(nsteps)
     b.step(nsteps)
-    oracle.step_shock(g, F, osp, inj, 0, passes=1, nsteps=nsteps)
+    terms = []
+    oracle.step_shock(g, F, osp, inj, 0, passes=1, nsteps=nsteps, terms=terms)
     a.check()
     b.check()
     assert a.counts() == b.counts() == [s.n for s in osp]
     Fa, pa = a.download()
     Fb, pb = b.download()
     compare_fields(Fa, Fb.astype(np.float64), floor=step_floor(g, osp, nsteps))
-    compare_fields(Fa, F, tol=1e-4, floor=step_floor(g, osp, nsteps))
+    compare_fields(Fa, F, tol=1e-4, floor=term_floor(g, terms))
     for x, y in zip(pa, pb):
         ua = np.sort((x["u"].astype(np.float64) ** 2).sum(0))
         ub = np.sort((y["u"].astype(np.float64) ** 2).sum(0))
@@ -298,15 +301,16 @@ def test_shock_tube_with_fdtd4_and_higuera_cary_matches_oracle(oracle_wall, dim)
     oracle_wall(w, i_zero)
     oracle.set_field_order(4)
     oracle.set_pusher("higuera_cary")
+    terms = []
     try:
         sim.step(nsteps)
-        oracle.step_shock(g, F, osp, inj, 0, passes=2, nsteps=nsteps)
+        oracle.step_shock(g, F, osp, inj, 0, passes=2, nsteps=nsteps, terms=terms)
     finally:
         oracle.set_field_order(2)
         oracle.set_pusher("boris")
     sim.check()
     assert sim.counts() == [s.n for s in osp]
     Fg, spg = sim.download()
-    compare_fields(Fg, F, floor=step_floor(g, osp, nsteps))
+    compare_fields(Fg, F, floor=term_floor(g, terms))
     compare_particles(g, spg, osp)
     sim.close()

@@ -9,7 +9,7 @@ import oracle
 import workloads
 
 from gpu_helpers import (REL_TOL, compare_fields, compare_particles, oracle_from_sim,
-                         periodic_dx, rel_err, step_floor)
+                         periodic_dx, rel_err, term_floor)
 
 pytestmark = pytest.mark.gpu
 
@@ -33,11 +33,12 @@ def test_step_matches_oracle_over_short_run(name):
     pl, passes, tun = _small_configs()[name]
     sim = Simulation.from_plasma(pl, tuning=dict(tun, sort_every=1000, filter_passes=passes))
     g, F, osp, _ = oracle_from_sim(sim)
+    terms = []
     for k in range(1, 9):
         sim.step(1)
-        oracle.step(g, F, osp, passes=passes)
+        oracle.step(g, F, osp, passes=passes, terms=terms)
         Fg, spg = sim.download()
-        compare_fields(Fg, F, floor=step_floor(g, osp, k))
+        compare_fields(Fg, F, floor=term_floor(g, terms))
         compare_particles(g, spg, osp)
     sim.check()
     en = sim.energies()
@@ -62,11 +63,12 @@ def test_fixed_and_generic_window_kernels_match_oracle(tile, halo):
     sim = Simulation.from_plasma(pl, tuning=dict(tile=[tile[0], tile[1], 1], halo=halo,
                                                  sort_every=1000))
     g, F, osp, _ = oracle_from_sim(sim)
+    terms = []
     for k in range(1, 7):
         sim.step(1)
-        oracle.step(g, F, osp)
+        oracle.step(g, F, osp, terms=terms)
     Fg, spg = sim.download()
-    compare_fields(Fg, F, floor=step_floor(g, osp, 6))
+    compare_fields(Fg, F, floor=term_floor(g, terms))
     compare_particles(g, spg, osp)
     sim.close()
 
@@ -80,11 +82,12 @@ def test_step_with_frequent_sorts_and_strays_matches_oracle_fields():
     pl = workloads.uniform_plasma(2, 34, 30, 1, 0.45, 4, 0.01, 2.0, seed=25)
     sim = Simulation.from_plasma(pl, tuning=dict(tile=[8, 8, 1], halo=1, sort_every=5))
     g, F, osp, _ = oracle_from_sim(sim)
+    terms = []
     for _ in range(20):
         sim.step(1)
-        oracle.step(g, F, osp)
+        oracle.step(g, F, osp, terms=terms)
     Fg, spg = sim.download()
-    compare_fields(Fg, F, floor=step_floor(g, osp, 20))
+    compare_fields(Fg, F, floor=term_floor(g, terms))
     # same particles, in another order: compare sorted kinetic energies
     for s, o in zip(spg, osp):
         ug = np.sort((s["u"].astype(np.float64) ** 2).sum(0))
@@ -107,13 +110,14 @@ def test_3d_strays_are_deferred_and_match_oracle(tile, halo):
     sim = Simulation.from_plasma(pl, tuning=dict(tile=list(tile), halo=halo, sort_every=1000))
     g, F, osp, _ = oracle_from_sim(sim)
     B.pic_stats(sim.ctx)  # reset the counter
+    terms = []
     for _ in range(5):
         sim.step(1)
-        oracle.step(g, F, osp)
+        oracle.step(g, F, osp, terms=terms)
     assert B.pic_stats(sim.ctx) > 0
     sim.check()
     Fg, spg = sim.download()
-    compare_fields(Fg, F, floor=step_floor(g, osp, 5))
+    compare_fields(Fg, F, floor=term_floor(g, terms))
     compare_particles(g, spg, osp)
     sim.close()
 
@@ -170,11 +174,12 @@ def test_edge_cases_tiny_grid_offsets_and_empty_species():
                u=np.zeros((3, 0), np.float32))]
     sim = Simulation(2, nx, ny, 1, 0.45, fields, sp, tuning=dict(sort_every=1000))
     g, F, osp, _ = oracle_from_sim(sim)
+    terms = []
     for _ in range(5):
         sim.step(1)
-        oracle.step(g, F, osp)
+        oracle.step(g, F, osp, terms=terms)
     Fg, spg = sim.download()
-    compare_fields(Fg, F, floor=step_floor(g, osp, 5))
+    compare_fields(Fg, F, floor=term_floor(g, terms))
     compare_particles(g, spg[:2], osp[:2])
     assert spg[2]["cell"].shape == (0,)
     sim.check()
@@ -285,12 +290,13 @@ def test_shock_set_up_with_fdtd4_and_higuera_cary_matches_oracle():
     g, F, osp, _ = oracle_from_sim(sim)
     oracle.set_field_order(4)
     oracle.set_pusher("higuera_cary")
+    terms = []
     try:
         for k in range(1, 7):
             sim.step(1)
-            oracle.step(g, F, osp, passes=2)
+            oracle.step(g, F, osp, passes=2, terms=terms)
             Fg, spg = sim.download()
-            compare_fields(Fg, F, floor=step_floor(g, osp, k))
+            compare_fields(Fg, F, floor=term_floor(g, terms))
             compare_particles(g, spg, osp)
     finally:
         oracle.set_field_order(2)

@@ -204,6 +204,48 @@ def test_zigzag_total_current_is_charge_times_displacement(orc):
         assert np.allclose(F[6:9].reshape(3, -1).sum(axis=1), 0.8 * d, rtol=0, atol=1e-14)
 
 
+@pytest.mark.parametrize("case", _load_zigzag_cases(), ids=lambda c: c["name"])
+def test_zigzag_term_magnitudes_of_one_move_are_its_hand_sums(orc, case):
+    """deposit_abs of a single move equals |J| of the hand sums: every term of
+    one move on one component has the sign of its displacement."""
+    nx, ny, nz = case["n"]
+    g = orc.Grid(case["dim"], nx, ny, nz, C)
+    A = g.zeros()
+    x1 = np.asarray(case["x1"], dtype=np.float64).reshape(3, 1)
+    dx = np.asarray(case["x2"], dtype=np.float64).reshape(3, 1) - x1
+    orc.deposit_abs(g, A, x1, dx, case["q"])
+    expect = np.zeros((3,) + g.shape)
+    for comp, i, j, k, v in case["J"]:
+        expect[comp, k, j, i] += v
+    assert np.allclose(A[6:9], np.abs(expect), rtol=0, atol=1e-14)
+    assert np.all(A[:6] == 0)
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_zigzag_term_magnitudes_bound_the_current(orc, dim):
+    """Many moves of both charge signs: deposit_abs >= |deposit| on every word
+    (the triangle inequality), and per component its lattice sum is
+    sum_p |q_p| |dx_p| (each move's weights sum to one per segment; the 3D
+    +-D_b D_c / 12 corrections cancel over a segment's four words)."""
+    nx, ny, nz = (9, 7, 6)[:dim] + (1,) * (3 - dim)
+    g = orc.Grid(dim, nx, ny, nz, C)
+    rs = np.random.default_rng(70 + dim)
+    n = 300
+    ext = np.array([nx, ny, nz], dtype=np.float64)
+    x1 = np.zeros((3, n))
+    x1[:dim] = rs.uniform(0, 1, size=(dim, n)) * ext[:dim, None]
+    dx = rs.uniform(-0.45, 0.45, size=(3, n))
+    q = rs.choice([-1.3, 0.7], size=n)
+    J, A = g.zeros(), g.zeros()
+    for p in range(n):
+        orc.deposit(g, J, x1[:, p:p + 1].copy(), dx[:, p:p + 1].copy(), q[p])
+        orc.deposit_abs(g, A, x1[:, p:p + 1].copy(), dx[:, p:p + 1].copy(), q[p])
+    assert np.all(A[6:9] >= np.abs(J[6:9]) - 1e-14)
+    assert np.abs(J[6:9]).sum() < A[6:9].sum()  # charges of both signs cancel somewhere
+    tot = (np.abs(q)[None, :] * np.abs(dx)).sum(axis=1)
+    assert np.allclose(A[6:9].reshape(3, -1).sum(axis=1), tot, rtol=1e-12, atol=0)
+
+
 # ---------------------------------------------------------------- FDTD2 -----
 
 def _k_operator(kvec, order=2):
