@@ -344,6 +344,12 @@ PushParams make_params(pic_ctx* ctx) {
   P.wall = ctx->shock ? ctx->wall : 0;
   P.tail_blocks = tail_blocks(ctx);
   P.dcount = ctx->d_dcount;
+  P.rec_aligned = 1;
+  for (int s = 0; s < ctx->ns; ++s) {
+    const SpeciesDev& S = P.sp[s];
+    const auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    if (S.ld % 4 != 0 || !a16(S.rcell) || !a16(S.roff) || !a16(S.ru)) P.rec_aligned = 0;
+  }
   return P;
 }
 

@@ -15,7 +15,71 @@ namespace pic {
 enum { EX = 0, EY, EZ, BX, BY, BZ, JX, JY, JZ };
 
 // device status word bits (pic_check)
-enum : int { ST_BAD_CELL = 1, ST_BAD_OFF = 2, ST_BAD_U = 4, ST_BEHIND_WALL = 8 };
+enum : int { ST_BAD_CELL = 1, ST_BAD_OFF = 2, ST_BAD_U = 4, ST_BEHIND_WALL = 8, ST_TIMEOUT = 16 };
+
+// ---- bulk asynchronous copies (TMA engine) and shared-memory barriers ----
+// Hand-written PTX for sm_90+: a 1D cp.async.bulk copy from global to shared
+// memory completes on an mbarrier with a transaction count of its bytes.
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+// makes the initialised barriers visible to the copy engine (then a block barrier)
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
+                   smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of `parity` to complete, for at most about a second of
+// SM clock (2^31 cycles), and with a status word, no longer than until
+// another wait has timed out; false when it gave up, having set ST_TIMEOUT in
+// the status word (the caller stops using the barrier).
+constexpr long long kWaitCycles = 1LL << 31;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int* status) {
+  if (mbar_test(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    const bool others = status && (*reinterpret_cast<volatile int*>(status) & ST_TIMEOUT);
+    if (others || clock64() - t0 > kWaitCycles) {
+      if (status) atomicOr(status, ST_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+// bytes (a multiple of 16) from src to dst (both 16-byte aligned), completing
+// on bar
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
+                                          unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
 
 struct GridDev {
   int dim;
@@ -104,6 +168,11 @@ struct SmemAcc {
 // Shared-memory current window in int32 fixed point: the caller passes values
 // already divided by the quantum; integer shared atomics are native (FP32 ones
 // retry in a loop when lanes collide).  Planes Jx, Jy, Jz of W0 x W1 x W2 ints.
+// 2D shared-memory ZigZag with both segments in FP32x2 registers
+// (zigzag_smem2 below)
+#ifndef PIC_ZZ_PACKED
+#define PIC_ZZ_PACKED 1
+#endif
 #ifndef PIC_MAGIC_F2I
 #define PIC_MAGIC_F2I 1
 #endif
@@ -232,24 +301,32 @@ __device__ __forceinline__ void gather(const Acc& A, const int* b, const float* 
 // Relativistic Boris scheme, Appendix C: u1 = c u + (s/2) E,
 // gamma1 = sqrt(1 + u1^2/c^2), t = s B / (2 c gamma1), f = 2/(1 + t^2),
 // u2 = f (u1 + u1 x t), u3 = u1 + u2 x t + (s/2) E, u <- u3 / c.
+// Evaluated in units of u (every step divided by c, which drops the scalings
+// by c): k = s / (2 c), u1 = u + k E, gamma1 = sqrt(1 + u1^2),
+// t = k B / gamma1, v = f (u1 + u1 x t), u <- u1 + v x t + k E.
 // 1/gamma1 and f use the hardware reciprocal square root and fast divide
 // (a few ulp; far inside the FP32-vs-FP64 tolerance).
 __device__ __forceinline__ void boris(float* u, const float* e, const float* b, float qm, float c,
                                       float inv_c, float inv_c2) {
-  const float hs = 0.5f * qm;
-  float u1[3];
+  (void)c;
+  (void)inv_c2;
+  const float k = 0.5f * qm * inv_c;
+  float ke[3], u1[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) u1[a] = fmaf(c, u[a], hs * e[a]);
-  const float ig1 = rsqrtf(fmaf(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2], inv_c2, 1.0f));
-  const float tf = hs * inv_c * ig1;
+  for (int a = 0; a < 3; ++a) {
+    ke[a] = k * e[a];
+    u1[a] = u[a] + ke[a];
+  }
+  const float ig1 = rsqrtf(fmaf(u1[0], u1[0], fmaf(u1[1], u1[1], fmaf(u1[2], u1[2], 1.0f))));
+  const float tf = k * ig1;
   const float t0 = tf * b[0], t1 = tf * b[1], t2 = tf * b[2];
   const float f = __fdividef(2.0f, fmaf(t0, t0, fmaf(t1, t1, fmaf(t2, t2, 1.0f))));
   const float v0 = f * (u1[0] + (u1[1] * t2 - u1[2] * t1));
   const float v1 = f * (u1[1] + (u1[2] * t0 - u1[0] * t2));
   const float v2 = f * (u1[2] + (u1[0] * t1 - u1[1] * t0));
-  u[0] = (u1[0] + (v1 * t2 - v2 * t1) + hs * e[0]) * inv_c;
-  u[1] = (u1[1] + (v2 * t0 - v0 * t2) + hs * e[1]) * inv_c;
-  u[2] = (u1[2] + (v0 * t1 - v1 * t0) + hs * e[2]) * inv_c;
+  u[0] = (u1[0] + (v1 * t2 - v2 * t1)) + ke[0];
+  u[1] = (u1[1] + (v2 * t0 - v0 * t2)) + ke[1];
+  u[2] = (u1[2] + (v0 * t1 - v1 * t0)) + ke[2];
 }
 
 // Higuera-Cary pusher (Table 2; Higuera and Cary 2017): the Boris steps with
@@ -420,9 +497,79 @@ __device__ __forceinline__ void zz_deposit(const Acc& A, const int* I, const flo
 // particle stays in its cell both segments add to the same words, so their
 // values are summed first and only particles that crossed a face issue the
 // second set of atomics.
+//
+// The 2D shared-memory window path evaluates both segments at once with the
+// packed FP32x2 instructions, each register pair holding (segment 1,
+// segment 2) of one quantity, so no operand needs a lane swap: the relay
+// point is x_r = max(dc, 0) on an axis the move crossed and the midpoint
+// otherwise (the min/max above in those two cases), and the word values are
+// zz_values<2>'s products.
+__device__ __forceinline__ void zigzag_smem2(const SmemJ& A, const int* b, const int* dc,
+                                             const float* o1, const float* o2, const float* dn,
+                                             float q) {
+  float2 Dp[3], Wp[2];
+  bool crossed = false;
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    const float x1 = o1[d];
+    const float kf = (float)dc[d];
+    const float x2 = kf + o2[d];
+    const float xr = dc[d] != 0 ? fmaxf(kf, 0.0f) : 0.5f * (x1 + x2);
+    const float2 P = make_float2(x1, xr), Q = make_float2(xr, x2);
+    Dp[d] = __fadd2_rn(Q, make_float2(-P.x, -P.y));
+    Wp[d] = __ffma2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(P, Q), make_float2(0.0f, -kf));
+    crossed |= dc[d] != 0;
+  }
+  Dp[2] = make_float2(0.5f * dn[2], 0.5f * dn[2]);
+  const float2 q2 = make_float2(q, q), one = make_float2(1.0f, 1.0f);
+  const float2 fx = __fmul2_rn(q2, Dp[0]), fy = __fmul2_rn(q2, Dp[1]), fz = __fmul2_rn(q2, Dp[2]);
+  const float2 mx = __fadd2_rn(one, make_float2(-Wp[0].x, -Wp[0].y));
+  const float2 my = __fadd2_rn(one, make_float2(-Wp[1].x, -Wp[1].y));
+  const float2 fzmy = __fmul2_rn(fz, my), fzwy = __fmul2_rn(fz, Wp[1]);
+  float2 v[8] = {__fmul2_rn(fx, my),   __fmul2_rn(fx, Wp[1]), __fmul2_rn(fy, mx),
+                 __fmul2_rn(fy, Wp[0]), __fmul2_rn(fzmy, mx), __fmul2_rn(fzmy, Wp[0]),
+                 __fmul2_rn(fzwy, mx), __fmul2_rn(fzwy, Wp[0])};
+  if (!crossed) {
+#pragma unroll
+    for (int w = 0; w < 8; ++w) v[w].x += v[w].y;
+  }
+  // both segments' words rounded to the fixed-point quantum at once
+  int i1[8], i2[8];
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+#if PIC_MAGIC_F2I
+    const float2 t = __fadd2_rn(v[w], make_float2(12582912.0f, 12582912.0f));
+    i1[w] = __float_as_int(t.x) - 0x4B400000;
+    i2[w] = __float_as_int(t.y) - 0x4B400000;
+#else
+    i1[w] = __float2int_rn(v[w].x);
+    i2[w] = __float2int_rn(v[w].y);
+#endif
+  }
+  // words in the order of zz_deposit<2>: Jx(i,j) Jx(i,j+1) Jy(i,j) Jy(i+1,j)
+  // Jz(i,j) Jz(i+1,j) Jz(i,j+1) Jz(i+1,j+1)
+  auto put = [&](int bi, int bj, const int* iv) {
+    int* J = A.ji + bi + A.W0 * bj;
+    atomicAdd(J, iv[0]);
+    atomicAdd(J + A.W0, iv[1]);
+    atomicAdd(J + A.wc, iv[2]);
+    atomicAdd(J + A.wc + 1, iv[3]);
+    atomicAdd(J + 2 * A.wc, iv[4]);
+    atomicAdd(J + 2 * A.wc + 1, iv[5]);
+    atomicAdd(J + 2 * A.wc + A.W0, iv[6]);
+    atomicAdd(J + 2 * A.wc + A.W0 + 1, iv[7]);
+  };
+  put(b[0], b[1], i1);
+  if (crossed) put(b[0] + dc[0], b[1] + dc[1], i2);
+}
+
 template <int D, class Acc>
 __device__ __forceinline__ void zigzag(const Acc& A, const int* b, const int* dc, const float* o1,
                                        const float* o2, const float* dn, float q) {
+  if constexpr (D == 2 && PIC_ZZ_PACKED && std::is_same<Acc, SmemJ>::value) {
+    zigzag_smem2(A, b, dc, o1, o2, dn, q);
+    return;
+  }
   float D1[3], D2[3], W1[3] = {0.f, 0.f, 0.f}, W2[3] = {0.f, 0.f, 0.f};
   int b2[3] = {b[0], b[1], b[2]};
   bool crossed = false;

@@ -17,6 +17,9 @@ constexpr int kMaxSpecies = 4;
 #ifndef PIC_PUSH_MIN_BLOCKS
 #define PIC_PUSH_MIN_BLOCKS 5
 #endif
+#ifndef PIC_PUSH_MIN_BLOCKS_TMA
+#define PIC_PUSH_MIN_BLOCKS_TMA 5
+#endif
 #ifndef PIC_PUSH_MIN_BLOCKS_3D
 #define PIC_PUSH_MIN_BLOCKS_3D 2
 #endif
@@ -38,6 +41,11 @@ constexpr int kMaxSpecies = 4;
 #endif
 template <int D>
 constexpr bool kJ64 = D == 2 && PIC_J64 != 0;
+// The 1D/2D fused kernels stream each batch's particle records into shared
+// memory with bulk copies when every record row is 16-byte aligned.
+#ifndef PIC_TMA_RECORDS
+#define PIC_TMA_RECORDS 0
+#endif
 // pic_step(n) replays whole sort cycles from a captured CUDA graph.
 #ifndef PIC_STEP_GRAPHS
 #define PIC_STEP_GRAPHS 1
@@ -63,10 +71,13 @@ inline long long sort_bins(const TileDev& t) { return (long long)t.ntiles * t.ns
 constexpr int kPushThreads = PIC_PUSH_THREADS;
 constexpr int kSpillEvery = PIC_SPILL_EVERY;  // batches of kPushThreads particles between spills
 // Shared-memory queue of the 1D/2D tile kernels for particles outside the tile
-// window.  It is drained at every spill point where it could overflow before
-// the next one, and between two spill points at most kSpillEvery batches of
-// kPushThreads particles can be queued, so this capacity can never be exceeded.
-constexpr int kQueueCap = kPushThreads * kSpillEvery;
+// window (about 0.5 % of the particles between sorts).  It is drained at the
+// end of each species and at a spill point where it is more than half full; a
+// stray that finds it full is processed at once by its own lane.
+constexpr int kQueueCap = 512;
+// Particle records of a batch streamed into shared memory by bulk copies
+// (1D/2D fused kernels): a ring of this many stages of kPushThreads records.
+constexpr int kRecStages = 2;
 
 // Lattice kernels run on a (x blocks, y, z) launch grid: a thread owns point x
 // of the rows (y, z) of its block, stepping over rows beyond the launch grid's
@@ -106,6 +117,7 @@ struct PushParams {
   int wall;                    // conducting wall on the node plane x = wall (0: none)
   int tail_blocks;             // extra blocks for the unsorted tails [tail, n)
   int* dcount;                 // [nspecies] entries of the deferred lists (zeroed per launch)
+  int rec_aligned;             // every record row read by the push starts 16-byte aligned
 };
 
 // Quantum of the fixed-point shared-memory current (a power of 2) for charges

@@ -376,10 +376,22 @@ __device__ __forceinline__ int one_particle(const PushParams& P, const SpeciesDe
   return kDone;
 }
 
-template <int D, int MODE, int FW0 = 0, int FW1 = 0, int FW2 = 1>
-__global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D : PIC_PUSH_MIN_BLOCKS)
+// TMA (1D/2D, modes 0 and 3, every record row 16-byte aligned): the records
+// of each batch arrive in a shared-memory ring by bulk copies that thread 0
+// issues one batch ahead (mbarriers `full` per stage, completed by the copies'
+// bytes; `empty` per stage, one arrival per warp once it has read the stage).
+// The batches start at the bucket's first index rounded down to a multiple of
+// 4 (16-byte aligned copies); lanes outside [a, b) idle.
+template <int D, int MODE, int FW0 = 0, int FW1 = 0, int FW2 = 1, bool TMA = false>
+__global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D
+                                                : TMA  ? PIC_PUSH_MIN_BLOCKS_TMA
+                                                       : PIC_PUSH_MIN_BLOCKS)
     k_particles(const PushParams P) {
   extern __shared__ __align__(16) float sm[];
+  static_assert(!TMA || D < 3, "the record stream is for the 1D/2D kernels");
+  constexpr int NR = 1 + D + 3;  // record rows: cell, D offsets, 3 four-velocity components
+  __shared__ unsigned long long bar_full[kRecStages], bar_empty[kRecStages];
+  __shared__ int rng_a[kMaxSpecies], rng_b[kMaxSpecies];  // each species' particles [a, b)
   // 1D/2D: strays queued and processed by the block; 3D: deferred
   constexpr bool kDrain = D < 3;
   __shared__ int q_n;      // entries in the stray queue (1D/2D)
@@ -416,9 +428,65 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
     SJ = SmemJ{ji, W0, W0 * W1, ws};
   const int lane = threadIdx.x & 31;
 
+  float* ring = reinterpret_cast<float*>(queue + kQueueCap);  // TMA only
+  // the particles of this block: a contiguous share of each species' tile bucket
+  auto bucket = [&](int s, int& a, int& b) {
+    const SpeciesDev& S = P.sp[s];
+    const long long lo = S.tstart[tile * P.t.nsub], hi = S.tstart[(tile + 1) * P.t.nsub];
+    const long long len = hi - lo;
+    a = (int)(lo + len * split / P.splits);
+    b = (int)(lo + len * (split + 1) / P.splits);
+  };
+  // producer state of the record stream (thread 0): species and first index of
+  // the next batch to issue; pr_s == nspecies when everything is issued
+  // (in shared memory: only thread 0 uses it, and registers are scarce)
+  __shared__ struct {
+    int s, base;  // species and first index of the next batch to issue (s == nspecies: done)
+    int issued;   // batches issued
+    int seen;     // batches thread 0 found complete
+  } pr;
+  auto pr_next_species = [&](int s) {
+    while (s < P.nspecies && rng_a[s] >= rng_b[s]) ++s;
+    pr.s = s;
+    if (s < P.nspecies) pr.base = rng_a[s] & ~3;
+  };
+  // issue batch j (the producer's next) into stage j % kRecStages
+  auto pr_issue = [&](int j) {
+    const SpeciesDev& S = P.sp[pr.s];
+    const int base = pr.base;
+    const int end4 = (rng_b[pr.s] + 3) & ~3;
+    const int cnt = end4 - base < kPushThreads ? end4 - base : kPushThreads;
+    const unsigned bytes = 4u * (unsigned)cnt;
+    unsigned long long* bar = &bar_full[j % kRecStages];
+    float* dst = ring + (j % kRecStages) * NR * kPushThreads;
+    mbar_arrive_expect_tx(bar, bytes * NR);
+    bulk_load(dst, S.rcell + base, bytes, bar);
+#pragma unroll
+    for (int d = 0; d < D; ++d) bulk_load(dst + (1 + d) * kPushThreads, S.roff + d * S.ld + base, bytes, bar);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      bulk_load(dst + (1 + D + a) * kPushThreads, S.ru + a * S.ld + base, bytes, bar);
+    pr.issued = j + 1;
+    pr.base = base + kPushThreads;
+    if (pr.base >= rng_b[pr.s]) pr_next_species(pr.s + 1);
+  };
+  bool dead = false;  // this thread gave up on the stream after a timed-out wait
+
   if (threadIdx.x == 0) {
     q_n = 0;
     n_stray = 0;
+    if (TMA) {
+      for (int s = 0; s < P.nspecies; ++s) bucket(s, rng_a[s], rng_b[s]);
+      for (int k = 0; k < kRecStages; ++k) {
+        mbar_init(&bar_full[k], 1);
+        mbar_init(&bar_empty[k], blockDim.x / 32);
+      }
+      mbar_init_fence();
+      pr.issued = 0;
+      pr.seen = 0;
+      pr_next_species(0);
+      if (pr.s < P.nspecies) pr_issue(0);  // overlaps the window staging
+    }
   }
   for (int w = threadIdx.x; w < wc; w += blockDim.x) {
     const int lx = w % W0, rr = w / W0, ly = rr % W1, lz = rr / W1;
@@ -531,27 +599,74 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
   // batches (and only there) the block synchronises, folds the current and, in
   // 1D/2D, drains the stray queue if it could overflow in the next round.
   int batches = 0;
+  int kk = 0;  // batches of every species so far (the record stream's index)
   for (int s = 0; s < P.nspecies; ++s) {
     const SpeciesDev& S = P.sp[s];
-    const long long lo = S.tstart[tile * P.t.nsub], hi = S.tstart[(tile + 1) * P.t.nsub];
-    const long long len = hi - lo;
-    const int a = (int)(lo + len * split / P.splits);
-    const int b = (int)(lo + len * (split + 1) / P.splits);
+    int a, b;
+    if (TMA) {
+      a = rng_a[s];
+      b = rng_b[s];
+    } else {
+      bucket(s, a, b);
+    }
     const float qs = S.q * P.jq_inv;
     PRec cur, nxt;
-    if (PIC_PREFETCH && a + (int)threadIdx.x < b) load_rec<D, MODE>(S, a + threadIdx.x, cur);
-    for (int base = a; base < b; base += blockDim.x) {  // block-uniform trip count
+    if (PIC_PREFETCH && !TMA && a + (int)threadIdx.x < b) load_rec<D, MODE>(S, a + threadIdx.x, cur);
+    // block-uniform trip count; with the stream the batches start 16-byte aligned
+    for (int base = TMA && a < b ? a & ~3 : a; base < b; base += blockDim.x) {
       const int p = base + threadIdx.x;
-      if (PIC_PREFETCH) {
+      bool in = p >= a && p < b;
+      if (TMA) {
+        const int stage = kk % kRecStages;
+        if (!dead) {
+          if (!mbar_wait(&bar_full[stage], (kk / kRecStages) & 1, P.status))
+            dead = true;
+          else if (threadIdx.x == 0)
+            pr.seen = kk + 1;
+        }
+        if (in && !dead) {
+          const float* rec = ring + stage * NR * kPushThreads + threadIdx.x;
+          cur.cell = __float_as_int(rec[0]);
+#pragma unroll
+          for (int d = 0; d < D; ++d) cur.o[d] = rec[(1 + d) * kPushThreads];
+#pragma unroll
+          for (int d = D; d < 3; ++d) cur.o[d] = 0.f;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) cur.u[c] = rec[(1 + D + c) * kPushThreads];
+        }
+        in &= !dead;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar_empty[stage]);
+        if (threadIdx.x == 0 && pr.s < P.nspecies && !dead) {
+          // batch j = kk + 1 reuses the stage that batch j - kRecStages read
+          const int j = pr.issued;
+          if (j < kRecStages ||
+              mbar_wait(&bar_empty[j % kRecStages], ((j - kRecStages) / kRecStages) & 1, P.status))
+            pr_issue(j);
+          else
+            dead = true;
+        }
+        ++kk;
+      } else if (PIC_PREFETCH) {
         if (p + (int)blockDim.x < b) load_rec<D, MODE>(S, p + blockDim.x, nxt);
-      } else if (p < b) {
+      } else if (in) {
         load_rec<D, MODE>(S, p, cur);
       }
       int st = kDone;
-      if (p < b)
+      if (in)
         st = interior ? one_particle<D, MODE, 0, FW0, FW1, FW2, true>(P, S, p, cur, sm, SJ, GA, w0, qs)
                       : one_particle<D, MODE, 0, FW0, FW1, FW2>(P, S, p, cur, sm, SJ, GA, w0, qs);
-      if (kDrain && st == kStray) queue[atomicAdd(&q_n, 1)] = p;
+      if (kDrain && st == kStray) {
+        const int slot = atomicAdd(&q_n, 1);
+        if (slot < kQueueCap) {
+          queue[slot] = p;
+        } else {  // full queue: this lane runs the stray through global memory now
+          if (one_particle<D, MODE, 1, FW0, FW1, FW2>(P, S, p, cur, sm, SJ, GA, w0, 0.f) ==
+              kWallCross)
+            S.dlist[atomicAdd(S.dcount, 1)] = p;
+          atomicAdd(P.strays, 1ULL);
+        }
+      }
       if (!kDrain || MODE == 3) {
         // deferred particles: one list slot range per warp, reserved by one atomic
         const bool dfr = kDrain ? st == kWallCross : st != kDone;
@@ -575,17 +690,23 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D 
         const int qn = q_n;  // read by every thread before anyone can queue again
         if (MODE != 1) spill();
         __syncthreads();
-        if (kDrain && qn > kQueueCap - kSpillEvery * (int)blockDim.x) drain(S, qn);
+        if (kDrain && qn > kQueueCap / 2) drain(S, qn < kQueueCap ? qn : kQueueCap);
       }
     }
     if (kDrain) {  // end of species: everything queued for it is processed before the next
       __syncthreads();
       const int qn = q_n;
       __syncthreads();
-      if (qn > 0) drain(S, qn);
+      if (qn > 0) drain(S, qn < kQueueCap ? qn : kQueueCap);
     }
   }
 
+  if (TMA && threadIdx.x == 0) {
+    // after a timed-out wait: copies issued but never found complete must land
+    // before the block's shared memory is released
+    for (int j = pr.seen; j < pr.issued; ++j)
+      mbar_wait(&bar_full[j % kRecStages], (j / kRecStages) & 1, nullptr);
+  }
   __syncthreads();
   if (threadIdx.x == 0 && n_stray > 0) atomicAdd(P.strays, (unsigned long long)n_stray);
   if (MODE != 1) {
@@ -641,8 +762,10 @@ __global__ void __launch_bounds__(kPushThreads) k_particles_deferred(const PushP
 size_t particle_smem_bytes(int dim, const TileDev& t) {
   const int nf = dim == 1 ? field_floats<1>() : dim == 2 ? field_floats<2>() : field_floats<3>();
   const int jw = (dim == 2 && kJ64<2>) ? 6 : 3;  // int window words per cell
+  // 1D/2D: the stray queue and the ring of streamed particle records
+  const size_t ring = (size_t)kRecStages * (1 + dim + 3) * kPushThreads;
   return sizeof(float) * ((size_t)field_words(nf, t.wcells) + (jw + 3) * (size_t)t.wstride) +
-         (dim < 3 ? sizeof(int) * kQueueCap : 0);  // the 1D/2D stray queue
+         (dim < 3 ? sizeof(int) * kQueueCap + sizeof(float) * ring : 0);
 }
 
 float current_quantum(float max_abs_q, float c, int batch) {
@@ -663,9 +786,9 @@ FastDiv make_fastdiv(int d) {
   return f;
 }
 
-template <int D, int MODE, int FW0 = 0, int FW1 = 0, int FW2 = 1>
+template <int D, int MODE, int FW0 = 0, int FW1 = 0, int FW2 = 1, bool TMA = false>
 static cudaError_t set_limit(int bytes) {
-  return cudaFuncSetAttribute(k_particles<D, MODE, FW0, FW1, FW2>,
+  return cudaFuncSetAttribute(k_particles<D, MODE, FW0, FW1, FW2, TMA>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
@@ -682,6 +805,14 @@ cudaError_t set_particle_smem_limit(int bytes) {
 #undef PIC_SET
   if (e == cudaSuccess) e = set_limit<2, 0, 23, 15>(bytes);
   if (e == cudaSuccess) e = set_limit<2, 0, 23, 23>(bytes);
+#if PIC_TMA_RECORDS
+  if (e == cudaSuccess) e = set_limit<2, 0, 23, 15, 1, true>(bytes);
+  if (e == cudaSuccess) e = set_limit<2, 0, 23, 23, 1, true>(bytes);
+  if (e == cudaSuccess) e = set_limit<1, 0, 0, 0, 1, true>(bytes);
+  if (e == cudaSuccess) e = set_limit<1, 3, 0, 0, 1, true>(bytes);
+  if (e == cudaSuccess) e = set_limit<2, 0, 0, 0, 1, true>(bytes);
+  if (e == cudaSuccess) e = set_limit<2, 3, 0, 0, 1, true>(bytes);
+#endif
   if (e == cudaSuccess) e = set_limit<3, 0, 13, 13, 9>(bytes);
   if (e == cudaSuccess) e = set_limit<3, 3, 13, 13, 9>(bytes);
   return e;
@@ -701,10 +832,19 @@ static cudaError_t launch(const PushParams& P, cudaStream_t st) {
   // halo 3 (23 x 15, 23 x 23), the 3D window of 8x8x4 tiles with halo 2
   // (13 x 13 x 9); any other window takes the generic kernel
   const bool w3 = P.t.W[0] == 13 && P.t.W[1] == 13 && P.t.W[2] == 9;
-  if (D == 2 && MODE == 0 && P.t.W[0] == 23 && P.t.W[1] == 15)
+  // the record stream needs 16-byte aligned rows (bulk copies)
+  constexpr bool kStreamable = PIC_TMA_RECORDS && D < 3 && (MODE == 0 || MODE == 3);
+  const bool tma = kStreamable && P.rec_aligned;
+  if (D == 2 && MODE == 0 && P.t.W[0] == 23 && P.t.W[1] == 15 && tma)
+    k_particles<2, 0, 23, 15, 1, kStreamable><<<nblocks, kPushThreads, smem, st>>>(P);
+  else if (D == 2 && MODE == 0 && P.t.W[0] == 23 && P.t.W[1] == 23 && tma)
+    k_particles<2, 0, 23, 23, 1, kStreamable><<<nblocks, kPushThreads, smem, st>>>(P);
+  else if (D == 2 && MODE == 0 && P.t.W[0] == 23 && P.t.W[1] == 15)
     k_particles<2, 0, 23, 15><<<nblocks, kPushThreads, smem, st>>>(P);
   else if (D == 2 && MODE == 0 && P.t.W[0] == 23 && P.t.W[1] == 23)
     k_particles<2, 0, 23, 23><<<nblocks, kPushThreads, smem, st>>>(P);
+  else if (tma)
+    k_particles<D, MODE, 0, 0, 1, kStreamable><<<nblocks, kPushThreads, smem, st>>>(P);
   else if (D == 3 && MODE == 0 && w3)
     k_particles<3, 0, 13, 13, 9><<<nblocks, kPushThreads, smem, st>>>(P);
   else if (D == 3 && MODE == 3 && w3)

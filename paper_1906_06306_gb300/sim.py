@@ -17,10 +17,14 @@ class Simulation:
     fields: float32[9, nz, ny, nx] (Ex Ey Ez Bx By Bz Jx Jy Jz);
     species: list of dicts with q, m, cell int32[n], off float32[D, n],
     u float32[3, n].  capacity (one per species, or None): row length of the
-    device arrays, the room an injector (set_shock) may fill."""
+    device arrays, the room an injector (set_shock) may fill.  With
+    align_rows the row length is rounded up to a multiple of 4, so that every
+    row starts 16-byte aligned and the 1D/2D particle kernel can stream the
+    records with bulk copies (without, rows of another length take its plain
+    loads)."""
 
     def __init__(self, dim, nx, ny, nz, c, fields, species, device="cuda:0", stream=None,
-                 tuning=None, capacity=None):
+                 tuning=None, capacity=None, align_rows=True):
         import torch
 
         self.torch = torch
@@ -33,6 +37,8 @@ class Simulation:
         for i, s in enumerate(species):
             n = int(np.asarray(s["cell"]).shape[0])
             cap = max(n, int(capacity[i])) if capacity is not None else n
+            if align_rows:
+                cap = (cap + 3) // 4 * 4
             if cap == n:
                 cell = np.ascontiguousarray(s["cell"], dtype=np.int32)
                 off = np.ascontiguousarray(s["off"], dtype=np.float32).reshape(dim, n)

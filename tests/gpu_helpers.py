@@ -40,50 +40,32 @@ def current_scale(g, species):
 
 
 def compare_fields(Fg, Fo, tol=REL_TOL, comps=range(9), floor=None):
-    """Per component: max |GPU - oracle| <= tol * max(max |oracle|, floor[c]).
-
-    With a floor from term_floor (a dict), E and B take its global floors and
-    J is compared cell by cell against that cell's own term magnitudes."""
-    cell = None
-    if isinstance(floor, dict):
-        floor, cell = floor["floor"], floor["cell"]
+    """Per component: max |GPU - oracle| <= tol * max(max |oracle|, floor[c])."""
     for c in comps:
-        diff = np.abs(np.asarray(Fg[c], dtype=np.float64) - Fo[c])
-        if cell is not None and c >= 6:
-            scale = cell[c - 6]
-            assert np.all(diff[scale == 0.0] == 0.0), c
-            e = (diff / np.where(scale > 0.0, scale, 1.0)).max()
-            assert e < tol, (c, e, float(np.abs(Fo[c]).max()), float(scale.max()))
-            continue
         scale = np.abs(Fo[c]).max()
         if floor is not None:
             scale = max(scale, floor[c])
         if scale == 0.0:
-            assert diff.max() == 0.0, c
+            assert np.abs(Fg[c]).max() == 0.0, c
             continue
-        e = diff.max() / scale
+        e = np.abs(np.asarray(Fg[c], dtype=np.float64) - Fo[c]).max() / scale
         assert e < tol, (c, e, float(np.abs(Fo[c]).max()), scale)
-
-
-# Per-cell J floors are not taken below this fraction of the largest cell's:
-# the fixed-point shared-memory current rounds every term to a quantum of about
-# 2^-19 |q| (current_quantum in the library), which a cell holding only a few
-# small terms would see as a large relative error of its tiny term sum.
-CELL_FLOOR_FRACTION = 1.0 / 16.0
 
 
 def term_floor(g, terms):
     """Floors for compare_fields from the oracle's current-term magnitudes
     (oracle.step(..., terms=...): per step, the per-word sum of |ZigZag term|
-    through the filter).  J, which holds the last step's deposit: per cell its
-    own term sum, at least CELL_FLOOR_FRACTION of the largest.  E, which adds
-    -J every step: the sum over steps of the largest term sum of its
-    component.  B, driven by c curl E: 2 D c times the largest of those."""
-    acc = sum(t.reshape(3, -1).max(axis=1) for t in terms)
-    last = terms[-1]
-    cell = [np.maximum(last[a], CELL_FLOOR_FRACTION * last[a].max()) for a in range(3)]
-    return {"floor": [float(v) for v in acc] + [2 * g.dim * g.c * float(acc.max())] * 3 +
-            [None] * 3, "cell": cell}
+    through the filter).  The scale is the largest such sum on any current
+    word: FP32 sums the terms (not the net J, which cancels for co-moving
+    pairs), rounds each to the fixed-point quantum of the shared-memory
+    current, which is the same for every component, and follows a trajectory
+    that drifts from the FP64 one by about 1e-6 of a cell within a few steps,
+    so a word's error scales with the terms around it rather than with its own
+    sum.  J holds the last step's deposit: that step's scale.  E adds -J every
+    step: the sum of the steps' scales.  B, driven by c curl E: 2 D c times
+    that."""
+    acc = sum(float(t.max()) for t in terms)
+    return [acc] * 3 + [2 * g.dim * g.c * acc] * 3 + [float(terms[-1].max())] * 3
 
 
 def step_floor(g, species, k):

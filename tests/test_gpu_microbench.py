@@ -1,17 +1,24 @@
-"""The per-kernel microbenchmark runs through the library's own timers: it
-reports every timed field kernel with its launch count, a positive time and
+"""bench.py --micro times the field kernels alone through the library's own
+timers: every timed field kernel with its launch count, a positive time and
 the algorithmic bytes of its grid."""
+import os
+import sys
+
 import pytest
 
 pytestmark = pytest.mark.gpu
 
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
 
 @pytest.mark.parametrize("kind,grid,keys", [("filter", (68, 19, 41), ["filter"]),
                                             ("fields", (64, 48, 1), ["b_half", "e_update"])])
-def test_microbench_reports_each_kernel(kind, grid, keys):
-    from paper_1906_06306_gb300 import microbench
+def test_micro_mode_reports_each_kernel(kind, grid, keys):
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
 
-    out = microbench.run(kind, grid, iters=4)
+    out = bench.micro_run(kind, grid, iters=4)
     cells = grid[0] * grid[1] * grid[2]
     assert out["cells"] == cells
     for k in keys:

@@ -51,17 +51,23 @@ def test_step_matches_oracle_over_short_run(name):
     sim.close()
 
 
-@pytest.mark.parametrize("tile,halo", [((16, 8), 3), ((16, 16), 3), ((16, 8), 2)])
-def test_fixed_and_generic_window_kernels_match_oracle(tile, halo):
+@pytest.mark.parametrize("tile,halo,aligned", [((16, 8), 3, True), ((16, 16), 3, True),
+                                               ((16, 8), 2, True), ((16, 8), 3, False),
+                                               ((16, 8), 2, False)])
+def test_fixed_and_generic_window_kernels_match_oracle(tile, halo, aligned):
     """The 2D particle kernel has compile-time window instantiations for the
     windows of 16x8 and 16x16 tiles with halo 3; each of them and the generic
     kernel (halo 2) against the oracle on a box that spans several tiles with
-    ragged edges, with sorts and strays."""
+    ragged edges, with sorts and strays.  Rows of a multiple of 4 particles
+    stream the records with bulk copies; rows of another length (one spare
+    slot) take the plain loads."""
     from paper_1906_06306_gb300 import Simulation
 
     pl = workloads.turbulence_2d(n=52, ppc=4, r_p=4.0, theta=0.3, sigma=10.0, modes=4, seed=26)
+    cap = None if aligned else [s.n + 1 for s in pl.species]
     sim = Simulation.from_plasma(pl, tuning=dict(tile=[tile[0], tile[1], 1], halo=halo,
-                                                 sort_every=1000))
+                                                 sort_every=1000),
+                                 capacity=cap, align_rows=aligned)
     g, F, osp, _ = oracle_from_sim(sim)
     terms = []
     for k in range(1, 7):
@@ -94,6 +100,34 @@ def test_step_with_frequent_sorts_and_strays_matches_oracle_fields():
         uo = np.sort((o.u ** 2).sum(0))
         assert np.abs(ug - uo).max() < 1e-4 * max(1.0, uo.max())
     sim.check()
+    sim.close()
+
+
+def test_strays_beyond_the_queue_are_run_by_their_lanes():
+    """A plasma drifting at 0.99 c along x, 4x4 tiles with halo 1 (a particle
+    strays as soon as it leaves its tile) and no sort: after a few steps most
+    of a block's ~680 particles per species stray, more than the stray queue
+    holds, so lanes that find it full run their particle through global memory
+    at once.  Fields and particles follow the oracle slot by slot."""
+    from paper_1906_06306_gb300 import binding as B
+    from paper_1906_06306_gb300 import Simulation
+
+    ppc = 128
+    pl = workloads.uniform_plasma(2, 64, 64, 1, 0.45, ppc, 1e-4, 0.01, seed=29, drift_axis=0,
+                                  drift_beta_per_slot=np.full(ppc, 0.99))
+    sim = Simulation.from_plasma(pl, tuning=dict(tile=[4, 4, 1], halo=1, sort_every=1000))
+    g, F, osp, _ = oracle_from_sim(sim)
+    B.pic_stats(sim.ctx)
+    terms = []
+    for _ in range(8):
+        sim.step(1)
+        oracle.step(g, F, osp, terms=terms)
+    strays = B.pic_stats(sim.ctx)
+    assert strays > 0.3 * 8 * sum(s.n for s in osp)  # many updates strayed
+    sim.check()
+    Fg, spg = sim.download()
+    compare_fields(Fg, F, floor=term_floor(g, terms))
+    compare_particles(g, spg, osp)
     sim.close()
 
 
