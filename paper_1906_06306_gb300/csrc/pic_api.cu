@@ -233,7 +233,8 @@ pic_status alloc_tiles(pic_ctx* ctx) {
   }
   dfree(ctx->d_count);
   dfree(ctx->d_cursor);
-  PIC_CK(ctx, dalloc(&ctx->d_count, sort_bins(ctx->tile)));
+  // the counts, then the multi-block scan's scratch
+  PIC_CK(ctx, dalloc(&ctx->d_count, sort_bins(ctx->tile) + scan_scratch(sort_bins(ctx->tile))));
   PIC_CK(ctx, dalloc(&ctx->d_cursor, sort_bins(ctx->tile)));
   return PIC_OK;
 }
@@ -367,7 +368,8 @@ pic_status do_sort(pic_ctx* ctx, bool copy_back) {
       if (r != cudaSuccess) return r;
       r = launch_tile_count(P, ctx->sp[s].cell, n, ctx->d_count, ctx->st);
       if (r != cudaSuccess) return r;
-      r = launch_tile_scan(ctx->d_count, bins, ctx->d_tstart[s], ctx->d_cursor, ctx->st);
+      r = launch_tile_scan(ctx->d_count, bins, ctx->d_tstart[s], ctx->d_cursor,
+                           ctx->d_count + bins, ctx->st);
       if (r != cudaSuccess) return r;
       if (n == 0) continue;
       int* cell_out = (int*)ctx->d_sortbuf + sortbuf_offset(ctx, s);

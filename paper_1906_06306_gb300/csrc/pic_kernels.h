@@ -46,6 +46,15 @@ constexpr bool kJ64 = D == 2 && PIC_J64 != 0;
 #ifndef PIC_TMA_RECORDS
 #define PIC_TMA_RECORDS 0
 #endif
+// 3D window with x-adjacent points paired per component (one 8-byte shared
+// load per stencil corner pair); the 3D fixed-point current then folds into
+// the global J planes instead of a float window, which keeps the shared
+// memory of a block at the size of three blocks per SM.
+#ifndef PIC_X3PAIR
+#define PIC_X3PAIR 0
+#endif
+template <int D>
+constexpr bool kFoldGlobal = D == 3 && PIC_X3PAIR != 0;
 // pic_step(n) replays whole sort cycles from a captured CUDA graph.
 #ifndef PIC_STEP_GRAPHS
 #define PIC_STEP_GRAPHS 1
@@ -165,8 +174,11 @@ struct SortParams {
 SortParams make_sort_params(const GridDev& g, const TileDev& t, int* status);
 cudaError_t launch_tile_count(const SortParams& P, const int* cell, long long n, int* count,
                               cudaStream_t st);
-cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* cursor,
+// exclusive scan of count[0..n) into start[0..n] and cursor; n above 4096 uses
+// scratch (scan_scratch(n) ints)
+cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* cursor, int* scratch,
                              cudaStream_t st);
+inline long long scan_scratch(long long n) { return 3 * ((n + 4095) / 4096 + 1); }
 // arrays with rows of ld elements, the first n of which are particles
 cudaError_t launch_tile_scatter(const SortParams& P, const int* cell, const float* off,
                                 const float* u, long long n, long long ld, int* cursor,

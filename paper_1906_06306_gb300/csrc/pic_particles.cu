@@ -54,7 +54,7 @@ struct Win {
 
 template <int D>
 __host__ __device__ constexpr int field_floats() {
-  return D == 1 ? 8 : D == 2 && PIC_XPAIR ? 12 : 6;
+  return D == 1 ? 8 : (D == 2 && PIC_XPAIR) || (D == 3 && PIC_X3PAIR) ? 12 : 6;
 }
 
 // Words of the staged field region, rounded up so that the current planes
@@ -78,6 +78,33 @@ __device__ __forceinline__ float2 lerp2(float2 a, float2 b, float2 w) {
 __device__ __forceinline__ float2 bilerp2(float2 f00, float2 f10, float2 f01, float2 f11, float2 wx,
                                           float2 wy) {
   return lerp2(lerp2(f00, f10, wx), lerp2(f01, f11, wx), wy);
+}
+
+// Linear interpolation of one staggered 3D component (stag bit d: half a cell
+// up axis d) from x-paired planes: FP[w] = (f(x), f(x+1)) at window cell w.
+// The x lerps at the four (y, z) corners, then y, then z: interp1<3>'s order.
+template <int STAG>
+__device__ __forceinline__ float interp3x(const float2* FP, int W0, int W01, const int* l,
+                                          const float* o) {
+  int i0[3];
+  float w[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (STAG & (1 << d)) {
+      const bool up = o[d] >= 0.5f;
+      i0[d] = up ? l[d] : l[d] - 1;
+      w[d] = up ? o[d] - 0.5f : o[d] + 0.5f;
+    } else {
+      i0[d] = l[d];
+      w[d] = o[d];
+    }
+  }
+  const int i = i0[0] + W0 * i0[1] + W01 * i0[2];
+  const float2 p00 = FP[i], p10 = FP[i + W0], p01 = FP[i + W01], p11 = FP[i + W0 + W01];
+  const float a = lerp(p00.x, p00.y, w[0]), c = lerp(p10.x, p10.y, w[0]);
+  const float a1 = lerp(p01.x, p01.y, w[0]), c1 = lerp(p11.x, p11.y, w[0]);
+  const float r0 = lerp(a, c, w[1]), r1 = lerp(a1, c1, w[1]);
+  return lerp(r0, r1, w[2]);
 }
 
 // Linear gather from the staged window (layout above), window-local cell l.
@@ -158,6 +185,16 @@ __device__ __forceinline__ void gather_smem(const float* sm, int wc, int W0, int
     b[0] = rb.y;
     e[2] = rc.x;
     b[2] = rc.y;
+  } else if (PIC_X3PAIR) {
+    // x-paired planes: one 8-byte load per (y, z) corner of a stencil, the
+    // same operations in the same order as interp1<3>
+    const float2* FP = reinterpret_cast<const float2*>(sm);
+    e[0] = interp3x<1>(FP + EX * wc, W0, W01, l, o);
+    e[1] = interp3x<2>(FP + EY * wc, W0, W01, l, o);
+    e[2] = interp3x<4>(FP + EZ * wc, W0, W01, l, o);
+    b[0] = interp3x<6>(FP + BX * wc, W0, W01, l, o);
+    b[1] = interp3x<5>(FP + BY * wc, W0, W01, l, o);
+    b[2] = interp3x<3>(FP + BZ * wc, W0, W01, l, o);
   } else {
     const SmemAcc A{const_cast<float*>(sm), W0, W01, wc};
     gather<3>(A, l, o, e, b);
@@ -417,9 +454,11 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D
   // fixed-point window: 3 planes of int32 words, or (2D, kJ64<D>) of 64-bit
   // pairs of them; then the float running sums and the 1D/2D stray queue
   constexpr int JW = kJ64<D> ? 6 : 3;  // words per window cell of the int window
+  // float running sums of the current (none where folds go to global memory)
+  constexpr int JF = kFoldGlobal<D> ? 0 : 3;
   int* ji = reinterpret_cast<int*>(sm + fw);
   float* jf = sm + fw + JW * ws;
-  int* queue = reinterpret_cast<int*>(sm + fw + (JW + 3) * ws);  // kDrain only
+  int* queue = reinterpret_cast<int*>(sm + fw + (JW + JF) * ws);  // kDrain only
   using JAcc = typename std::conditional<kJ64<D>, SmemJ64, SmemJ>::type;
   JAcc SJ;
   if constexpr (kJ64<D>)
@@ -521,6 +560,17 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D
         reinterpret_cast<float2*>(sm + 2 * wc)[w] = make_float2(ey, bx);
         sm[4 * wc + w] = ez;
         sm[5 * wc + w] = bz;
+      } else if (PIC_X3PAIR) {
+        // point x goes to the low half of its own cell's pair and to the high
+        // half of the pair of the cell before it (the last column's high half
+        // is never read: stencils end at W0 - 2)
+        float2* FP = reinterpret_cast<float2*>(sm);
+        const float v[6] = {ex, ey, ez, bx, by, bz};
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          FP[c * wc + w].x = v[c];
+          if (lx > 0) FP[c * wc + w - 1].y = v[c];
+        }
       } else {
         sm[EX * wc + w] = ex;
         sm[EY * wc + w] = ey;
@@ -533,13 +583,28 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D
   }
   if (MODE != 1) {
     int4* j4 = reinterpret_cast<int4*>(ji);
-    for (int w = threadIdx.x; w < (JW + 3) * ws / 4; w += blockDim.x)
+    for (int w = threadIdx.x; w < (JW + JF) * ws / 4; w += blockDim.x)
       j4[w] = make_int4(0, 0, 0, 0);
   }
   __syncthreads();
 
   // between barriers: fold the int32 window into the float window, clear it
   auto spill = [&]() {
+    if constexpr (kFoldGlobal<D>) {
+      // the fixed-point sums go straight to the global J planes, then are cleared
+      for (int c = 0; c < 3; ++c) {
+        for (int w = threadIdx.x; w < wc; w += blockDim.x) {
+          const int v = ji[c * ws + w];
+          if (v != 0) {
+            const int lx = w % W0, rr = w / W0, ly = rr % W1, lz = rr / W1;
+            const long long gi = GA.at(w0[0] + lx, w0[1] + ly, w0[2] + lz);
+            atomicAdd(&P.F[(JX + c) * P.g.plane + gi], (float)v * P.jq);
+            ji[c * ws + w] = 0;
+          }
+        }
+      }
+      return;
+    }
     if constexpr (kJ64<D>) {
       // every float word gathers its two partial sums (SmemJ64's planes),
       // then, after all threads have read, the pairs are cleared
@@ -712,7 +777,7 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D
   if (MODE != 1) {
     spill();
     __syncthreads();
-    for (int w = threadIdx.x; w < wc; w += blockDim.x) {
+    for (int w = threadIdx.x; w < (kFoldGlobal<D> ? 0 : wc); w += blockDim.x) {
       const int lx = w % W0, rr = w / W0, ly = rr % W1, lz = rr / W1;
       const long long gi = GA.at(w0[0] + lx, w0[1] + ly, w0[2] + lz);
 #pragma unroll
@@ -762,9 +827,10 @@ __global__ void __launch_bounds__(kPushThreads) k_particles_deferred(const PushP
 size_t particle_smem_bytes(int dim, const TileDev& t) {
   const int nf = dim == 1 ? field_floats<1>() : dim == 2 ? field_floats<2>() : field_floats<3>();
   const int jw = (dim == 2 && kJ64<2>) ? 6 : 3;  // int window words per cell
+  const int jf = dim == 3 && kFoldGlobal<3> ? 0 : 3;  // float window words per cell
   // 1D/2D: the stray queue and the ring of streamed particle records
   const size_t ring = (size_t)kRecStages * (1 + dim + 3) * kPushThreads;
-  return sizeof(float) * ((size_t)field_words(nf, t.wcells) + (jw + 3) * (size_t)t.wstride) +
+  return sizeof(float) * ((size_t)field_words(nf, t.wcells) + (jw + jf) * (size_t)t.wstride) +
          (dim < 3 ? sizeof(int) * kQueueCap + sizeof(float) * ring : 0);
 }
 
@@ -815,6 +881,8 @@ cudaError_t set_particle_smem_limit(int bytes) {
 #endif
   if (e == cudaSuccess) e = set_limit<3, 0, 13, 13, 9>(bytes);
   if (e == cudaSuccess) e = set_limit<3, 3, 13, 13, 9>(bytes);
+  if (e == cudaSuccess) e = set_limit<3, 0, 13, 13, 7>(bytes);
+  if (e == cudaSuccess) e = set_limit<3, 3, 13, 13, 7>(bytes);
   return e;
 }
 
@@ -832,6 +900,7 @@ static cudaError_t launch(const PushParams& P, cudaStream_t st) {
   // halo 3 (23 x 15, 23 x 23), the 3D window of 8x8x4 tiles with halo 2
   // (13 x 13 x 9); any other window takes the generic kernel
   const bool w3 = P.t.W[0] == 13 && P.t.W[1] == 13 && P.t.W[2] == 9;
+  const bool w37 = P.t.W[0] == 13 && P.t.W[1] == 13 && P.t.W[2] == 7;  // 8x8x2 tiles, halo 2
   // the record stream needs 16-byte aligned rows (bulk copies)
   constexpr bool kStreamable = PIC_TMA_RECORDS && D < 3 && (MODE == 0 || MODE == 3);
   const bool tma = kStreamable && P.rec_aligned;
@@ -849,6 +918,10 @@ static cudaError_t launch(const PushParams& P, cudaStream_t st) {
     k_particles<3, 0, 13, 13, 9><<<nblocks, kPushThreads, smem, st>>>(P);
   else if (D == 3 && MODE == 3 && w3)
     k_particles<3, 3, 13, 13, 9><<<nblocks, kPushThreads, smem, st>>>(P);
+  else if (D == 3 && MODE == 0 && w37)
+    k_particles<3, 0, 13, 13, 7><<<nblocks, kPushThreads, smem, st>>>(P);
+  else if (D == 3 && MODE == 3 && w37)
+    k_particles<3, 3, 13, 13, 7><<<nblocks, kPushThreads, smem, st>>>(P);
   else
     k_particles<D, MODE><<<nblocks, kPushThreads, smem, st>>>(P);
   if ((MODE == 0 || MODE == 3) && P.tail_blocks > 0)

@@ -132,6 +132,64 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int* __restrict__ coun
   if (threadIdx.x == 0) start[ntiles] = carry;
 }
 
+// Multi-block form of the same exclusive scan for long count arrays (sub-tile
+// sort bins): each block scans kScanChunk counts into start and leaves its
+// total in part[]; one block scans part[]; every block then adds its offset
+// (start[bins] = total, cursor = start).
+constexpr int kScanChunk = 4096;  // counts per block: 4 per thread of 1024
+__global__ void __launch_bounds__(1024) k_scan_chunks(const int* __restrict__ count, int n,
+                                                      int* start, int* part) {
+  __shared__ int warp_sums[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int base = blockIdx.x * kScanChunk + 4 * threadIdx.x;
+  int v[4], s = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[i] = base + i < n ? count[base + i] : 0;
+    s += v[i];
+  }
+  int x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int w = warp_sums[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    warp_sums[lane] = w;
+  }
+  __syncthreads();
+  int run = x - s + (wid > 0 ? warp_sums[wid - 1] : 0);  // exclusive offset in the chunk
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (base + i < n) start[base + i] = run;
+    run += v[i];
+  }
+  if (threadIdx.x == 1023) part[blockIdx.x] = run;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_add(int* start, int* cursor, int n,
+                                                   const int* part_scan) {
+  const int off = part_scan[blockIdx.x];
+  const int base = blockIdx.x * kScanChunk + 4 * threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (base + i < n) {
+      const int v = start[base + i] + off;
+      start[base + i] = v;
+      cursor[base + i] = v;
+    }
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) start[n] = part_scan[gridDim.x];
+}
+
 template <int D>
 __global__ void k_tile_scatter(const SortParams P, const int* __restrict__ cell,
                                const float* __restrict__ off, const float* __restrict__ u,
@@ -189,9 +247,20 @@ cudaError_t launch_tile_count(const SortParams& P, const int* cell, long long n,
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* cursor,
+cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* cursor, int* scratch,
                              cudaStream_t st) {
-  k_tile_scan<<<1, 1024, 0, st>>>(count, ntiles, start, cursor);
+  if (ntiles <= kScanChunk) {
+    k_tile_scan<<<1, 1024, 0, st>>>(count, ntiles, start, cursor);
+    return cudaGetLastError();
+  }
+  // scratch: block totals [nb], their scan [nb + 1], the scan's cursor [nb]
+  const int nb = (ntiles + kScanChunk - 1) / kScanChunk;
+  int* part = scratch;
+  int* part_scan = scratch + nb;
+  int* part_cursor = scratch + 2 * nb + 1;
+  k_scan_chunks<<<nb, 1024, 0, st>>>(count, ntiles, start, part);
+  k_tile_scan<<<1, 1024, 0, st>>>(part, nb, part_scan, part_cursor);
+  k_scan_add<<<nb, 1024, 0, st>>>(start, cursor, ntiles, part_scan);
   return cudaGetLastError();
 }
 
