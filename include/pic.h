@@ -283,9 +283,11 @@ pic_status pic_particle_counts(pic_ctx* ctx, int64_t* n, int nout);
  * double precision on the GPU.  nout must be >= 4 + nspecies. */
 pic_status pic_energies(pic_ctx* ctx, double* out, int nout);
 
-/* Synchronise the stream and read the device status word: PIC_ERR_STATE if
- * any kernel since the last check met invalid particle data (the word is then
- * cleared), otherwise PIC_OK. */
+/* Synchronise the stream and read the device status word: PIC_ERR_TIMEOUT if
+ * a kernel since the last check gave up a bounded wait on one of its own
+ * shared-memory copies (that step's results are not valid), else
+ * PIC_ERR_STATE if one met invalid particle data, otherwise PIC_OK.  The word
+ * is cleared when it was set. */
 pic_status pic_check(pic_ctx* ctx);
 
 /* End-to-end step from host memory: copies every species' particles from

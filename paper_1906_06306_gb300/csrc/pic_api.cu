@@ -70,6 +70,12 @@ struct pic_ctx {
   int* d_dlist = nullptr;   // particles deferred to the global pass, room for cap[s] per species
   int* d_dcount = nullptr;  // entries per species
   float* d_adjF = nullptr;                   // forward fields of an adjoint step (9 planes)
+  // 2D field window by tensor copy: the map over E and B, box and shift
+  // (window_map); win_tma == 0 when the grid or tiling does not allow it
+  CUtensorMap win_map{};
+  int win_tma = 0;
+  int win_box[2] = {0, 0};
+  int win_shift = 0;
   long long steps = 0;
   long long sorted_step = -1;  // value of `steps` at the last tile sort
   bool capturing = false;      // pic_step is being captured into a CUDA graph
@@ -188,7 +194,8 @@ std::string derive_tiles(const pic_grid& grid, const pic_tuning& tun, long long 
       r.T[d] = tun.tile[d] < n ? tun.tile[d] : n;
       r.nt[d] = (n + r.T[d] - 1) / r.T[d];
       r.W[d] = r.T[d] + 2 * r.H + 1;
-      const int sub = kSubTile[d] > 0 && kSubTile[d] < r.T[d] ? kSubTile[d] : r.T[d];
+      const int ks = grid.dim == 3 ? kSubTile3[d] : kSubTile[d];
+      const int sub = ks > 0 && ks < r.T[d] ? ks : r.T[d];
       r.S[d] = sub;
       r.ns[d] = (r.T[d] + sub - 1) / sub;
     } else {
@@ -226,6 +233,8 @@ std::string derive_tiles(const pic_grid& grid, const pic_tuning& tun, long long 
   return "";
 }
 
+void window_map(pic_ctx* ctx);
+
 pic_status alloc_tiles(pic_ctx* ctx) {
   for (int s = 0; s < ctx->ns; ++s) {
     dfree(ctx->d_tstart[s]);
@@ -236,7 +245,62 @@ pic_status alloc_tiles(pic_ctx* ctx) {
   // the counts, then the multi-block scan's scratch
   PIC_CK(ctx, dalloc(&ctx->d_count, sort_bins(ctx->tile) + scan_scratch(sort_bins(ctx->tile))));
   PIC_CK(ctx, dalloc(&ctx->d_cursor, sort_bins(ctx->tile)));
+  window_map(ctx);
   return PIC_OK;
+}
+
+// cuTensorMapEncodeTiled, from the driver through the runtime (no link to
+// libcuda); null when the driver does not provide it
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  }
+  return fn;
+}
+
+// The tensor map of the 2D window copy: the field buffer as a 3D tensor
+// (x, y, plane) of FP32, box (box_x, W1, 6) over the E and B planes, whose x
+// origin is the window's rounded down to a multiple of 4 floats (tensor
+// copies start 16-byte aligned; the window starts at tile x * T0 - H, the same
+// residue mod 4 for every tile when T0 is a multiple of 4).  Out-of-range box
+// points (up to 3 past the lattice's x end) are filled with zeros and never
+// read.
+void window_map(pic_ctx* ctx) {
+  ctx->win_tma = 0;
+  const TileDev& t = ctx->tile;
+  const int nx = ctx->grid.nx, ny = ctx->grid.ny;
+  if (!PIC_TMA_WINDOW || ctx->grid.dim != 2 || t.T[0] % 4 != 0 || nx % 4 != 0 ||
+      (reinterpret_cast<uintptr_t>(ctx->F) & 15) != 0)
+    return;
+  const int shift = ((-t.H) % 4 + 4) % 4;
+  const int bx = (t.W[0] + shift + 3) / 4 * 4, by = t.W[1];
+  if (bx > 256 || by > 256 || 6LL * bx * by > window_landing_floats(2, t)) return;
+  EncodeTiled enc = encode_tiled();
+  if (!enc) return;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 9};
+  const cuuint64_t strides[2] = {4ULL * nx, 4ULL * nx * ny};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 6};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (enc(&ctx->win_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ctx->F, dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return;
+  ctx->win_tma = 1;
+  ctx->win_box[0] = bx;
+  ctx->win_box[1] = by;
+  ctx->win_shift = shift;
 }
 
 cudaEvent_t take_event(pic_ctx* ctx) {
@@ -345,6 +409,11 @@ PushParams make_params(pic_ctx* ctx) {
   P.wall = ctx->shock ? ctx->wall : 0;
   P.tail_blocks = tail_blocks(ctx);
   P.dcount = ctx->d_dcount;
+  P.win_tma = ctx->win_tma;
+  P.win_box[0] = ctx->win_box[0];
+  P.win_box[1] = ctx->win_box[1];
+  P.win_shift = ctx->win_shift;
+  P.win_map = ctx->win_map;
   P.rec_aligned = 1;
   for (int s = 0; s < ctx->ns; ++s) {
     const SpeciesDev& S = P.sp[s];
@@ -1022,6 +1091,10 @@ pic_status pic_check(pic_ctx* ctx) {
   if (h & ST_BAD_CELL) m += " cell index out of range;";
   if (h & ST_BAD_OFF) m += " offset outside [0,1);";
   if (h & ST_BAD_U) m += " non-finite four-velocity;";
+  // a bounded wait on a shared-memory copy gave up: the results of that step
+  // are not to be trusted, the context stays usable
+  if (h & ST_TIMEOUT)
+    return set_err(ctx, PIC_ERR_TIMEOUT, "a bounded device-side wait on a tensor copy gave up");
   return set_err(ctx, PIC_ERR_STATE, m);
 }
 

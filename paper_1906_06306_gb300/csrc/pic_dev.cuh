@@ -70,6 +70,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   }
   return true;
 }
+// box of a 3D tensor map at coordinates (x, y, z) into dst (128-byte aligned),
+// completing on bar; the map lives in kernel parameter space
+__device__ __forceinline__ void tensor_load_3d(void* dst, const void* map, int x, int y, int z,
+                                               unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
 // bytes (a multiple of 16) from src to dst (both 16-byte aligned), completing
 // on bar
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,

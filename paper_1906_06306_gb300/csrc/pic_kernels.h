@@ -1,6 +1,7 @@
 // Host-side launchers of the PIC kernels (internal to libpic).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "pic_dev.cuh"
@@ -55,6 +56,11 @@ constexpr bool kJ64 = D == 2 && PIC_J64 != 0;
 #endif
 template <int D>
 constexpr bool kFoldGlobal = D == 3 && PIC_X3PAIR != 0;
+// The 2D particle kernel stages the field window of a tile inside the lattice
+// by one tensor copy (TMA) instead of per-thread loads.
+#ifndef PIC_TMA_WINDOW
+#define PIC_TMA_WINDOW 1
+#endif
 // pic_step(n) replays whole sort cycles from a captured CUDA graph.
 #ifndef PIC_STEP_GRAPHS
 #define PIC_STEP_GRAPHS 1
@@ -62,9 +68,12 @@ constexpr bool kFoldGlobal = D == 3 && PIC_X3PAIR != 0;
 #ifndef PIC_PREFETCH
 #define PIC_PREFETCH 0
 #endif
-// Sub-tile extents of the sort key (0: the whole tile).  The tile sort orders
-// a tile's particles by sub-tile, so the lanes of a warp gather from and
-// deposit into a small patch of the tile window.
+// Sub-tile extents of the sort key (0: the whole tile), for 1D/2D and for 3D.
+// The tile sort orders a tile's particles by sub-tile, so the lanes of a warp
+// gather from and deposit into a small patch of the tile window: fewer shared
+// memory bank conflicts, more sort bins.  Measured on the 2D 16x8 tiles it
+// does not pay (4x4: -1 %); on the 3D 8x8x4 tiles 4x4x2 cut the particle
+// kernel's shared-memory wavefronts by 12 %.
 #ifndef PIC_SUBTILE_X
 #define PIC_SUBTILE_X 0
 #endif
@@ -74,7 +83,17 @@ constexpr bool kFoldGlobal = D == 3 && PIC_X3PAIR != 0;
 #ifndef PIC_SUBTILE_Z
 #define PIC_SUBTILE_Z 0
 #endif
+#ifndef PIC_SUBTILE3_X
+#define PIC_SUBTILE3_X 4
+#endif
+#ifndef PIC_SUBTILE3_Y
+#define PIC_SUBTILE3_Y 4
+#endif
+#ifndef PIC_SUBTILE3_Z
+#define PIC_SUBTILE3_Z 2
+#endif
 constexpr int kSubTile[3] = {PIC_SUBTILE_X, PIC_SUBTILE_Y, PIC_SUBTILE_Z};
+constexpr int kSubTile3[3] = {PIC_SUBTILE3_X, PIC_SUBTILE3_Y, PIC_SUBTILE3_Z};
 // Sort bins of a tiling: sub-tiles of every tile, tile-major.
 inline long long sort_bins(const TileDev& t) { return (long long)t.ntiles * t.nsub; }
 constexpr int kPushThreads = PIC_PUSH_THREADS;
@@ -127,6 +146,14 @@ struct PushParams {
   int tail_blocks;             // extra blocks for the unsorted tails [tail, n)
   int* dcount;                 // [nspecies] entries of the deferred lists (zeroed per launch)
   int rec_aligned;             // every record row read by the push starts 16-byte aligned
+  // 2D field window by one tensor copy (TMA): a 3D map over the E, B planes
+  // (x, y, component) with a box of win_box[0] x W1 x 6 whose x origin is the
+  // window's rounded down to a multiple of 4 floats (win_shift below it);
+  // used by blocks whose window lies inside the lattice
+  int win_tma;
+  int win_box[2];   // box extents x (a multiple of 4), y
+  int win_shift;    // window x origin - box x origin
+  alignas(64) CUtensorMap win_map;
 };
 
 // Quantum of the fixed-point shared-memory current (a power of 2) for charges
@@ -149,6 +176,9 @@ void set_global_error(const char* msg);
 cudaError_t launch_particles(int dim, int mode, const PushParams& P, cudaStream_t st);
 cudaError_t set_particle_smem_limit(int bytes);
 size_t particle_smem_bytes(int dim, const TileDev& t);
+// floats of a block's shared memory past the staged field window, from the
+// first 128-byte boundary on: room for the 2D window's tensor copy
+long long window_landing_floats(int dim, const TileDev& t);
 
 cudaError_t launch_b_half(const GridDev& g, float* F, int zero_j, cudaStream_t st);
 cudaError_t launch_e_update(const GridDev& g, float* F, cudaStream_t st);

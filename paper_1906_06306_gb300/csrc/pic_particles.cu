@@ -423,8 +423,8 @@ template <int D, int MODE, int FW0 = 0, int FW1 = 0, int FW2 = 1, bool TMA = fal
 __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D
                                                 : TMA  ? PIC_PUSH_MIN_BLOCKS_TMA
                                                        : PIC_PUSH_MIN_BLOCKS)
-    k_particles(const PushParams P) {
-  extern __shared__ __align__(16) float sm[];
+    k_particles(const __grid_constant__ PushParams P) {
+  extern __shared__ __align__(128) float sm[];
   static_assert(!TMA || D < 3, "the record stream is for the 1D/2D kernels");
   constexpr int NR = 1 + D + 3;  // record rows: cell, D offsets, 3 four-velocity components
   __shared__ unsigned long long bar_full[kRecStages], bar_empty[kRecStages];
@@ -527,13 +527,47 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D
       if (pr.s < P.nspecies) pr_issue(0);  // overlaps the window staging
     }
   }
+  // 2D, window inside the lattice: E and B of the window (with its guard
+  // cells) arrive by one tensor copy into the current and queue area, which is
+  // not in use yet; the loop below reads them there instead of global memory
+  __shared__ unsigned long long bar_win;
+  const bool win_tma = D == 2 && MODE != 2 && !TMA && P.win_tma != 0 && interior;
+  // tensor copies land on a 128-byte boundary (at most 31 floats of padding)
+  const float* land =
+      reinterpret_cast<const float*>((reinterpret_cast<uintptr_t>(sm + fw) + 127) & ~uintptr_t(127));
+  if (win_tma) {
+    if (threadIdx.x == 0) {
+      mbar_init(&bar_win, 1);
+      mbar_init_fence();
+      mbar_arrive_expect_tx(&bar_win, 24u * (unsigned)(P.win_box[0] * P.win_box[1]));
+      tensor_load_3d(const_cast<float*>(land), &P.win_map, w0[0] - P.win_shift, w0[1], 0,
+                     &bar_win);
+    }
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    mbar_wait(&bar_win, 0, P.status);
+  }
   for (int w = threadIdx.x; w < wc; w += blockDim.x) {
     const int lx = w % W0, rr = w / W0, ly = rr % W1, lz = rr / W1;
     const long long gi = GA.at(w0[0] + lx, w0[1] + ly, w0[2] + lz);
     if (MODE != 2) {
-      const float ex = __ldg(&P.F[EX * P.g.plane + gi]), ey = __ldg(&P.F[EY * P.g.plane + gi]);
-      const float ez = __ldg(&P.F[EZ * P.g.plane + gi]), bx = __ldg(&P.F[BX * P.g.plane + gi]);
-      const float by = __ldg(&P.F[BY * P.g.plane + gi]), bz = __ldg(&P.F[BZ * P.g.plane + gi]);
+      float ex, ey, ez, bx, by, bz;
+      if (win_tma) {  // box planes Ex .. Bz of box_x x box_y floats, x fastest
+        const int pl = P.win_box[0] * P.win_box[1];
+        const float* L = land + ly * P.win_box[0] + lx + P.win_shift;
+        ex = L[0];
+        ey = L[pl];
+        ez = L[2 * pl];
+        bx = L[3 * pl];
+        by = L[4 * pl];
+        bz = L[5 * pl];
+      } else {
+        ex = __ldg(&P.F[EX * P.g.plane + gi]);
+        ey = __ldg(&P.F[EY * P.g.plane + gi]);
+        ez = __ldg(&P.F[EZ * P.g.plane + gi]);
+        bx = __ldg(&P.F[BX * P.g.plane + gi]);
+        by = __ldg(&P.F[BY * P.g.plane + gi]);
+        bz = __ldg(&P.F[BZ * P.g.plane + gi]);
+      }
       if (D == 1) {
         reinterpret_cast<float4*>(sm)[w] = make_float4(ex, by, bz, 0.f);
         reinterpret_cast<float4*>(sm + 4 * wc)[w] = make_float4(ey, ez, bx, 0.f);
@@ -581,6 +615,7 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D
       }
     }
   }
+  if (win_tma) __syncthreads();  // the landing area is read before it is cleared
   if (MODE != 1) {
     int4* j4 = reinterpret_cast<int4*>(ji);
     for (int w = threadIdx.x; w < (JW + JF) * ws / 4; w += blockDim.x)
@@ -824,14 +859,28 @@ __global__ void __launch_bounds__(kPushThreads) k_particles_deferred(const PushP
   }
 }
 
+long long window_landing_floats(int dim, const TileDev& t) {
+  const int nf = dim == 1 ? field_floats<1>() : dim == 2 ? field_floats<2>() : field_floats<3>();
+  // the landing area starts on the first 128-byte boundary past the field words
+  return (long long)(particle_smem_bytes(dim, t) / sizeof(float)) - field_words(nf, t.wcells) - 31;
+}
+
 size_t particle_smem_bytes(int dim, const TileDev& t) {
   const int nf = dim == 1 ? field_floats<1>() : dim == 2 ? field_floats<2>() : field_floats<3>();
   const int jw = (dim == 2 && kJ64<2>) ? 6 : 3;  // int window words per cell
   const int jf = dim == 3 && kFoldGlobal<3> ? 0 : 3;  // float window words per cell
   // 1D/2D: the stray queue and the ring of streamed particle records
-  const size_t ring = (size_t)kRecStages * (1 + dim + 3) * kPushThreads;
-  return sizeof(float) * ((size_t)field_words(nf, t.wcells) + (jw + jf) * (size_t)t.wstride) +
-         (dim < 3 ? sizeof(int) * kQueueCap + sizeof(float) * ring : 0);
+  const size_t ring = PIC_TMA_RECORDS ? (size_t)kRecStages * (1 + dim + 3) * kPushThreads : 0;
+  size_t words = (size_t)(jw + jf) * t.wstride + (dim < 3 ? kQueueCap + ring : 0);
+  // 2D: the same area first takes the window's tensor copy, E and B over a box
+  // whose x extent is the window's widened to 16-byte ends, after up to 31
+  // floats of padding to a 128-byte boundary
+  if (dim == 2 && PIC_TMA_WINDOW) {
+    const int shift = ((-t.H) % 4 + 4) % 4;
+    const size_t box = 6 * (size_t)((t.W[0] + shift + 3) / 4 * 4) * t.W[1] + 31;
+    words = box > words ? box : words;
+  }
+  return sizeof(float) * ((size_t)field_words(nf, t.wcells) + words);
 }
 
 float current_quantum(float max_abs_q, float c, int batch) {
