@@ -290,6 +290,16 @@ pic_status pic_energies(pic_ctx* ctx, double* out, int nout);
  * is cleared when it was set. */
 pic_status pic_check(pic_ctx* ctx);
 
+/* Failure-path check of the bounded device waits (the paper has no
+ * counterpart): enqueues on the context's stream one warp that waits on a
+ * shared-memory barrier that nothing completes.  Its wait gives up after about
+ * a second of SM clock and sets the timeout bit of the context's status word,
+ * exactly as a particle block's wait on a tensor copy that did not land would;
+ * the next pic_check returns PIC_ERR_TIMEOUT and clears the word, and the
+ * context stays usable.  No copy is in flight and no GPU fault is raised.
+ * PIC_ERR_ARG for a NULL context, PIC_ERR_CUDA if the launch fails. */
+pic_status pic_wait_probe(pic_ctx* ctx);
+
 /* End-to-end step from host memory: copies every species' particles from
  * `hs` and the 9 field planes from `host_fields` into the context's device
  * buffers, runs pic_step(nsteps), copies particles and fields back into the

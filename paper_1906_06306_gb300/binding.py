@@ -69,6 +69,7 @@ SIGNATURES = {
     "pic_step": (c_int, [_P, c_int]),
     "pic_energies": (c_int, [_P, ctypes.POINTER(c_double), c_int]),
     "pic_check": (c_int, [_P]),
+    "pic_wait_probe": (c_int, [_P]),
     "pic_step_host": (c_int, [_P, ctypes.POINTER(pic_host_species), c_void_p, c_int]),
     "pic_autotune": (c_int, [_P, ctypes.POINTER(pic_tuning), c_int, c_int, ctypes.POINTER(c_int)]),
     "pic_stats": (c_int, [_P, ctypes.POINTER(c_int64)]),
@@ -198,6 +199,10 @@ def pic_energies(ctx, nspecies: int):
 
 def pic_check(ctx) -> None:
     _check(_lib.pic_check(ctx), ctx)
+
+
+def pic_wait_probe(ctx) -> None:
+    _check(_lib.pic_wait_probe(ctx), ctx)
 
 
 def pic_step_host(ctx, host_species, host_fields_ptr: int, nsteps: int) -> None:

@@ -1098,6 +1098,12 @@ pic_status pic_check(pic_ctx* ctx) {
   return set_err(ctx, PIC_ERR_STATE, m);
 }
 
+pic_status pic_wait_probe(pic_ctx* ctx) {
+  if (!ctx) return PIC_ERR_ARG;
+  PIC_CK(ctx, launch_wait_probe(ctx->d_status, ctx->st));
+  return PIC_OK;
+}
+
 pic_status pic_step_host(pic_ctx* ctx, const pic_host_species* hs, float* host_fields, int nsteps) {
   if (!ctx || !hs || !host_fields) return set_err(ctx, PIC_ERR_ARG, "NULL argument");
   const int D = ctx->grid.dim;

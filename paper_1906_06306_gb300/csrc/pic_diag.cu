@@ -168,4 +168,23 @@ cudaError_t launch_gauss(const GridDev& g, const float* F, const double* rho, in
   return cudaGetLastError();
 }
 
+// One warp waits on a shared-memory barrier that nothing completes: its
+// bounded wait gives up after about a second of SM clock and sets ST_TIMEOUT
+// in the status word, as a particle block's wait on a tensor copy that never
+// landed would.  No copy is in flight, so leaving is safe.
+__global__ void k_wait_probe(int* status) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  mbar_wait(&bar, 0, status);
+}
+
+cudaError_t launch_wait_probe(int* status, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(status);
+  return cudaGetLastError();
+}
+
 }  // namespace pic

@@ -222,6 +222,8 @@ cudaError_t launch_rho(const GridDev& g, const int* cell, const float* off, long
                        long long ld, double q, double* rho, cudaStream_t st);
 // over the nodes with i_lo <= i < i_hi: acc_max (as the bit pattern of a
 // non-negative double), acc_sq += sum res^2
+// one warp whose bounded barrier wait runs out (sets ST_TIMEOUT)
+cudaError_t launch_wait_probe(int* status, cudaStream_t st);
 cudaError_t launch_gauss(const GridDev& g, const float* F, const double* rho, int i_lo, int i_hi,
                          unsigned long long* acc_max, double* acc_sq, cudaStream_t st);
 

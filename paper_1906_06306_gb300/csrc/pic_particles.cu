@@ -544,7 +544,14 @@ __global__ void __launch_bounds__(kPushThreads, D == 3 ? PIC_PUSH_MIN_BLOCKS_3D
                      &bar_win);
     }
     __syncthreads();  // the barrier is initialised before anyone waits on it
-    mbar_wait(&bar_win, 0, P.status);
+    const bool landed = mbar_wait(&bar_win, 0, P.status);
+    // a copy that did not land in time (the status word says so): the block
+    // leaves, all of it, once a second bounded wait has seen the copy land or
+    // expired too
+    if (__syncthreads_or(!landed)) {
+      if (threadIdx.x == 0) mbar_wait(&bar_win, 0, nullptr);
+      return;
+    }
   }
   for (int w = threadIdx.x; w < wc; w += blockDim.x) {
     const int lx = w % W0, rr = w / W0, ly = rr % W1, lz = rr / W1;

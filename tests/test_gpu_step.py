@@ -236,6 +236,36 @@ def test_invalid_particle_data_is_reported_not_used():
     sim.close()
 
 
+def test_a_timed_out_device_wait_is_reported_and_the_context_stays_usable():
+    """A bounded wait that runs out (one warp on a barrier that nothing
+    completes) sets the timeout bit: pic_check reports PIC_ERR_TIMEOUT once,
+    and the context then steps exactly as a twin that never timed out."""
+    from paper_1906_06306_gb300 import PicError, Simulation, binding
+
+    pl = workloads.turbulence_2d(n=48, ppc=4, r_p=4.0, theta=0.3, sigma=10.0, modes=4, seed=29)
+    sim = Simulation.from_plasma(pl, tuning=dict(tile=[16, 8, 1]))
+    twin = Simulation.from_plasma(pl, tuning=dict(tile=[16, 8, 1]))
+    sim.step(1)
+    twin.step(1)
+    sim.check()
+    binding.pic_wait_probe(sim.ctx)
+    with pytest.raises(PicError) as ei:
+        sim.check()
+    assert ei.value.status == 4 and "wait" in str(ei.value)
+    sim.check()  # the status word was cleared
+    sim.step(3)
+    twin.step(3)
+    sim.check()
+    Fa, spa = sim.download()
+    Fb, spb = twin.download()
+    np.testing.assert_allclose(Fa, Fb, rtol=0, atol=1e-5 * np.abs(Fb).max())
+    for a, b in zip(spa, spb):
+        np.testing.assert_array_equal(a["cell"], b["cell"])
+        np.testing.assert_allclose(a["u"], b["u"], rtol=1e-6, atol=0)
+    sim.close()
+    twin.close()
+
+
 def test_gauss_residual_stays_at_fp32_round_off():
     """Appendix B: with the charge-conserving deposit div E - rho keeps its
     initial value (0 for co-located pairs and E = 0).  In FP32 the residual is
