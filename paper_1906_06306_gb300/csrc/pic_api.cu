@@ -595,7 +595,7 @@ pic_status do_filter(pic_ctx* ctx, int passes) {
   float* b = ctx->d_jtmp;
   for (int p = 0; p < passes; ++p) {
     const cudaError_t e = timed(
-        ctx, PIC_KERNEL_FILTER, [&]() { return launch_filter_pass_f32(ctx->g, a, b, 3, ctx->st); });
+        ctx, PIC_KERNEL_FILTER, [&]() { return launch_filter_pass_f32(ctx->g, a, b, 3, ctx->st, ctx->d_status); });
     if (e != cudaSuccess) return cuda_fail(ctx, "binomial filter", e);
     float* t = a;
     a = b;
@@ -886,7 +886,7 @@ pic_status pic_adjoint_step(pic_ctx* ctx, const float* fwd_fields, const pic_adj
     float* a = J;
     float* b = ctx->d_jtmp;
     for (int p = 0; p < ctx->tun.filter_passes && r == cudaSuccess; ++p) {  // Jf = F^p J
-      r = launch_filter_pass_f32(ctx->g, a, b, 3, ctx->st);
+      r = launch_filter_pass_f32(ctx->g, a, b, 3, ctx->st, ctx->d_status);
       float* t = a;
       a = b;
       b = t;

@@ -80,6 +80,12 @@ __device__ __forceinline__ void tensor_load_3d(void* dst, const void* map, int x
       "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
       : "memory");
 }
+// orders this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (bulk copy) writes to it: a stage is re-filled by a copy
+// only after every thread has read it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 // bytes (a multiple of 16) from src to dst (both 16-byte aligned), completing
 // on bar
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,

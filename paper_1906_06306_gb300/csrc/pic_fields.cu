@@ -316,15 +316,19 @@ __global__ void __launch_bounds__(256) k_filter_pass(const float* __restrict__ s
 // marching along z.  A block of 256 threads owns a ZX x ZY = 128 x 16 column
 // of (x, y) points over a run of `zrun` z-planes; a thread owns a 4 (x) x 2
 // (y) patch of it.  Each z-plane of the column plus its one-point periodic
-// (x, y) halo is copied into a ring of ZS shared-memory stages with cp.async
-// (16-byte copies for the aligned interior, 4-byte ones for the halo and for
-// ragged or wrapped rows), ZS - 1 planes ahead of the one being filtered.  A
-// thread reads its four rows (y - 1 .. y + 2) with one 16-byte and two 4-byte
-// shared loads each, runs the x and y sub-passes in registers and keeps the
-// last three y results for the z sub-pass.  Reads: the column, its (x, y)
-// halo (rows of neighbouring columns, mostly from L2) and two extra planes
-// per run; writes: the column, 16 bytes per store.  Every output goes through
-// the same arithmetic, in the same order, as three k_filter_axis sub-passes.
+// (x, y) halo is copied into a ring of ZS shared-memory stages, ZS - 1 planes
+// ahead of the one being filtered.  BULK (rows of a multiple of 4 floats,
+// 16-byte aligned planes, a status word): the ZY + 2 stage rows arrive by one
+// bulk copy each (`cp.async.bulk`, issued by the lanes of warp 0, completing
+// on the stage's mbarrier) and the two halo points of each row by 4-byte
+// cp.async; otherwise every thread copies by cp.async (16-byte copies for the
+// aligned interior, 4-byte ones for the halo and for ragged or wrapped rows).
+// A thread reads its four rows (y - 1 .. y + 2) with one 16-byte and two
+// 4-byte shared loads each, runs the x and y sub-passes in registers and keeps
+// the last three y results for the z sub-pass.  Reads: the column, its (x, y)
+// halo (rows of neighbouring columns, mostly from L2) and two extra planes per
+// run; writes: the column, 16 bytes per store.  Every output goes through the
+// same arithmetic, in the same order, as three k_filter_axis sub-passes.
 // Grid: x = column index + columns x run, y = plane.
 constexpr int ZX = 128, ZY = 16, ZS = 4;
 constexpr int ZROW = ZX + 8;  // stage row: [3] left halo, [4, 4 + ZX) interior, [4 + ZX] right
@@ -352,10 +356,28 @@ __device__ __forceinline__ float b3(float l, float c, float r) {
   return 0.25f * l + 0.5f * c + 0.25f * r;
 }
 
+// A marching pass's wait, by every thread, for the bulk copies of step k
+// (stage k % ZS, phase parity (k / ZS) & 1; steps k .. min(k + ZS - 2,
+// nk - 1) are in flight); true when the whole block may go on.  When a wait
+// ran out (the status word has the timeout bit), thread 0 waits once more,
+// bounded, for each step still in flight, and the block leaves together.
+__device__ __forceinline__ bool stage_landed(unsigned long long* full, int k, int nk, int* status) {
+  const bool ok = mbar_wait(&full[k % ZS], (unsigned)(k / ZS) & 1u, status);
+  if (!__syncthreads_or(!ok)) return true;
+  if (threadIdx.x == 0)
+    for (int j = k; j < k + ZS - 1 && j < nk; ++j)
+      mbar_wait(&full[j % ZS], (unsigned)(j / ZS) & 1u, nullptr);
+  cp_async_wait<0>();
+  return false;
+}
+
+template <bool BULK>
 __global__ void __launch_bounds__(256, 4) k_filter_z3(const float* __restrict__ src,
                                                      float* __restrict__ dst, const GridDev g,
-                                                     int ncx, int ncy, int zrun, int vec) {
+                                                     int ncx, int ncy, int zrun, int vec,
+                                                     int* status) {
   __shared__ __align__(16) float stage[ZS][ZPLANE];
+  __shared__ unsigned long long full[ZS];  // BULK: stage's rows have landed
   const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const long long nxy = (long long)n0 * n1;
   const int col = blockIdx.x % (ncx * ncy), run = blockIdx.x / (ncx * ncy);
@@ -364,30 +386,58 @@ __global__ void __launch_bounds__(256, 4) k_filter_z3(const float* __restrict__ 
   const long long P = g.plane;
   const float* s = src + (long long)blockIdx.y * P;
   float* d = dst + (long long)blockIdx.y * P;
+  const int len = min(ZX, n0 - x0);  // interior points of the column's rows
 
   // This thread's copy operations op = threadIdx.x + 256 j, the same for every
   // z-plane: stage row op / ZCH (y = y0 - 1 + row) and either a 4-point
   // interior chunk (c < ZX / 4), the left halo point (c = ZX / 4) or the right.
+  // BULK: lane r < ZY + 2 of warp 0 copies the interior of stage row r, and
+  // threads 64 .. 64 + 2 (ZY + 2) - 1 its halo points (the right one after
+  // the last interior point, where a ragged column's x sub-pass reads it).
   long long yoff[ZOPT];
   int xs[ZOPT], dofs[ZOPT], kind[ZOPT];  // kind: 0 none, 1 16-byte, 2 four 4-byte, 3 one 4-byte
 #pragma unroll
   for (int j = 0; j < ZOPT; ++j) {
-    const int op = threadIdx.x + 256 * j;
-    const int row = op / ZCH, c = op % ZCH;
     kind[j] = 0;
     yoff[j] = 0;
     xs[j] = 0;
     dofs[j] = 0;
-    if (op < ZOPS) {
-      yoff[j] = (long long)n0 * wrapi(y0 - 1 + row, n1);
-      if (c < ZX / 4) {
-        xs[j] = x0 + 4 * c;
-        dofs[j] = row * ZROW + 4 + 4 * c;
-        kind[j] = vec && xs[j] + 3 < n0 ? 1 : 2;
-      } else {
-        xs[j] = wrapi(c == ZX / 4 ? x0 - 1 : x0 + ZX, n0);
-        dofs[j] = row * ZROW + (c == ZX / 4 ? 3 : 4 + ZX);
-        kind[j] = 3;
+  }
+  if (BULK) {
+    const int t = threadIdx.x;
+    if (t < ZY + 2) {  // interior of row t
+      yoff[0] = (long long)n0 * wrapi(y0 - 1 + t, n1);
+      xs[0] = x0;
+      dofs[0] = t * ZROW + 4;
+      kind[0] = 1;
+    } else if (t >= 64 && t < 64 + 2 * (ZY + 2)) {  // a halo point of row (t - 64) / 2
+      const int row = (t - 64) >> 1, right = (t - 64) & 1;
+      yoff[0] = (long long)n0 * wrapi(y0 - 1 + row, n1);
+      xs[0] = wrapi(right ? x0 + len : x0 - 1, n0);
+      dofs[0] = row * ZROW + (right ? 4 + len : 3);
+      kind[0] = 3;
+    }
+    if (t == 0) {
+      for (int i = 0; i < ZS; ++i) mbar_init(&full[i], 1);
+      mbar_init_fence();
+    }
+    __syncthreads();  // the barriers are initialised before any copy or wait
+  } else {
+#pragma unroll
+    for (int j = 0; j < ZOPT; ++j) {
+      const int op = threadIdx.x + 256 * j;
+      const int row = op / ZCH, c = op % ZCH;
+      if (op < ZOPS) {
+        yoff[j] = (long long)n0 * wrapi(y0 - 1 + row, n1);
+        if (c < ZX / 4) {
+          xs[j] = x0 + 4 * c;
+          dofs[j] = row * ZROW + 4 + 4 * c;
+          kind[j] = vec && xs[j] + 3 < n0 ? 1 : 2;
+        } else {
+          xs[j] = wrapi(c == ZX / 4 ? x0 - 1 : x0 + ZX, n0);
+          dofs[j] = row * ZROW + (c == ZX / 4 ? 3 : 4 + ZX);
+          kind[j] = 3;
+        }
       }
     }
   }
@@ -397,15 +447,29 @@ __global__ void __launch_bounds__(256, 4) k_filter_z3(const float* __restrict__ 
       z = z < 0 ? z + n2 : (z >= n2 ? z - n2 : z);
       const float* base = s + nxy * z;
       float* st = stage[k % ZS];
+      if (BULK) {
+        if (threadIdx.x < 32) {
+          if (threadIdx.x == 0)
+            mbar_arrive_expect_tx(&full[k % ZS], (unsigned)((ZY + 2) * len * 4));
+          __syncwarp();
+          if (kind[0] == 1) {
+            fence_proxy_async_smem();
+            bulk_load(st + dofs[0], base + yoff[0] + xs[0], (unsigned)(len * 4), &full[k % ZS]);
+          }
+        } else if (kind[0] == 3) {
+          cp_async4(st + dofs[0], base + yoff[0] + xs[0]);
+        }
+      } else {
 #pragma unroll
-      for (int j = 0; j < ZOPT; ++j) {
-        const float* sr = base + yoff[j];
-        if (kind[j] == 1) {
-          cp_async16(st + dofs[j], sr + xs[j]);
-        } else if (kind[j] == 3) {
-          cp_async4(st + dofs[j], sr + xs[j]);
-        } else if (kind[j] == 2) {
-          for (int e = 0; e < 4; ++e) cp_async4(st + dofs[j] + e, sr + wrapi(xs[j] + e, n0));
+        for (int j = 0; j < ZOPT; ++j) {
+          const float* sr = base + yoff[j];
+          if (kind[j] == 1) {
+            cp_async16(st + dofs[j], sr + xs[j]);
+          } else if (kind[j] == 3) {
+            cp_async4(st + dofs[j], sr + xs[j]);
+          } else if (kind[j] == 2) {
+            for (int e = 0; e < 4; ++e) cp_async4(st + dofs[j] + e, sr + wrapi(xs[j] + e, n0));
+          }
         }
       }
     }
@@ -421,7 +485,13 @@ __global__ void __launch_bounds__(256, 4) k_filter_z3(const float* __restrict__ 
   for (int i = 0; i < 8; ++i) pm[i] = p0[i] = 0.f;
   for (int k = 0; k < zc + 2; ++k) {
     cp_async_wait<ZS - 2>();  // this thread's copies of plane k have landed
-    __syncthreads();          // everyone's have; stage (k - 1) % ZS is no longer read
+    if (BULK) {
+      // and the bulk copies of every thread's rows; then stage (k - 1) % ZS
+      // is no longer read
+      if (!stage_landed(full, k, zc + 2, status)) return;
+    } else {
+      __syncthreads();  // everyone's have; stage (k - 1) % ZS is no longer read
+    }
     issue(k + ZS - 1);
     const float* a = stage[k % ZS] + 2 * ty * ZROW + 4 * tx + 3;  // row y - 1, column x - 1
     float xf[4][4];
@@ -471,20 +541,26 @@ __global__ void __launch_bounds__(256, 4) k_filter_z3(const float* __restrict__ 
 // One full 2D Binomial2 pass (x, then y sub-pass) of one plane src -> dst,
 // marching along y: a block of 256 threads owns YX = 1024 x-points (4 per
 // thread) over a run of `yrun` rows.  Each row plus its one-point periodic x
-// halo goes through a ring of ZS shared-memory stages by cp.async (16-byte
-// copies for aligned interior chunks, 4-byte ones for the halo and for ragged
-// or wrapped chunks), ZS - 1 rows ahead of the one being filtered; a thread
-// runs the x sub-pass of its 4 points from one 16-byte and two 4-byte shared
-// loads and keeps the last three results for the y sub-pass.  Every output
-// goes through the same arithmetic, in the same order, as two k_filter_axis
-// sub-passes.  Grid: x = x-column + columns x run, y = plane.
+// halo goes through a ring of ZS shared-memory stages, ZS - 1 rows ahead of
+// the one being filtered.  BULK (rows of a multiple of 4 floats, 16-byte
+// aligned planes, a status word): the row's points arrive by one bulk copy
+// (`cp.async.bulk`, issued by thread 0, completing on the stage's mbarrier)
+// and its two halo points by 4-byte cp.async; otherwise every thread copies
+// by cp.async (16-byte copies for aligned interior chunks, 4-byte ones for the
+// halo and for ragged or wrapped chunks).  A thread runs the x sub-pass of its
+// 4 points from one 16-byte and two 4-byte shared loads and keeps the last
+// three results for the y sub-pass.  Every output goes through the same
+// arithmetic, in the same order, as two k_filter_axis sub-passes.
+// Grid: x = x-column + columns x run, y = plane.
 constexpr int YX = 1024;
 constexpr int YROW = YX + 8;  // stage row: [3] left halo, [4, 4 + YX) interior, [4 + YX] right
 
+template <bool BULK>
 __global__ void __launch_bounds__(256) k_filter_y2(const float* __restrict__ src,
                                                   float* __restrict__ dst, const GridDev g,
-                                                  int ncx, int yrun, int vec) {
+                                                  int ncx, int yrun, int vec, int* status) {
   __shared__ __align__(16) float stage[ZS][YROW];
+  __shared__ unsigned long long full[ZS];  // BULK: the stage's row has landed
   const int n0 = g.n[0], n1 = g.n[1];
   const int col = blockIdx.x % ncx, run = blockIdx.x / ncx;
   const int x0 = col * YX, y0 = run * yrun;
@@ -493,19 +569,35 @@ __global__ void __launch_bounds__(256) k_filter_y2(const float* __restrict__ src
   const float* s = src + (long long)blockIdx.y * P;
   float* d = dst + (long long)blockIdx.y * P;
   const int t = threadIdx.x;
+  const int len = min(YX, n0 - x0);  // interior points of the column's rows
   // this thread's copies, the same for every row: interior chunk t (x0 + 4t ..
-  // x0 + 4t + 3), and for threads 0 and 1 the left and right halo point
+  // x0 + 4t + 3), and for threads 0 and 1 the left and right halo point (BULK:
+  // the right one right after the last interior point, where a ragged
+  // column's x sub-pass reads it; thread 0 also issues the row's bulk copy)
   const int xs = x0 + 4 * t;
   const bool v16 = vec && xs + 3 < n0;
-  const int hx = t == 0 ? wrapi(x0 - 1, n0) : wrapi(x0 + YX, n0);
-  const int hcol = t == 0 ? 3 : 4 + YX;
+  const int hx = t == 0 ? wrapi(x0 - 1, n0) : wrapi(BULK ? x0 + len : x0 + YX, n0);
+  const int hcol = t == 0 ? 3 : 4 + (BULK ? len : YX);
+  if (BULK) {
+    if (t == 0) {
+      for (int i = 0; i < ZS; ++i) mbar_init(&full[i], 1);
+      mbar_init_fence();
+    }
+    __syncthreads();  // the barriers are initialised before any copy or wait
+  }
   auto issue = [&](int k) {  // copy halo row k (y = y0 - 1 + k) into stage k % ZS
     if (k < yc + 2) {
       int y = y0 - 1 + k;  // -1 <= y <= n1
       y = y < 0 ? y + n1 : (y >= n1 ? y - n1 : y);
       const float* row = s + (long long)n0 * y;
       float* st = stage[k % ZS];
-      if (v16) {
+      if (BULK) {
+        if (t == 0) {
+          fence_proxy_async_smem();
+          mbar_arrive_expect_tx(&full[k % ZS], (unsigned)(len * 4));
+          bulk_load(st + 4, row + x0, (unsigned)(len * 4), &full[k % ZS]);
+        }
+      } else if (v16) {
         cp_async16(st + 4 + 4 * t, row + xs);
       } else {
         for (int e = 0; e < 4; ++e) cp_async4(st + 4 + 4 * t + e, row + wrapi(xs + e, n0));
@@ -520,7 +612,12 @@ __global__ void __launch_bounds__(256) k_filter_y2(const float* __restrict__ src
   float pm[4] = {0.f, 0.f, 0.f, 0.f}, p0[4] = {0.f, 0.f, 0.f, 0.f};
   for (int k = 0; k < yc + 2; ++k) {
     cp_async_wait<ZS - 2>();  // this thread's copies of row k have landed
-    __syncthreads();          // everyone's have; stage (k - 1) % ZS is no longer read
+    if (BULK) {
+      // and the row's bulk copy; then stage (k - 1) % ZS is no longer read
+      if (!stage_landed(full, k, yc + 2, status)) return;
+    } else {
+      __syncthreads();  // everyone's have; stage (k - 1) % ZS is no longer read
+    }
     issue(k + ZS - 1);
     const float* a = stage[k % ZS] + 4 * t + 3;  // column x - 1
     const float l = a[0];
@@ -731,13 +828,13 @@ static cudaError_t launch_pass(const GridDev& g, const float* src, float* dst, i
 // from DRAM after its neighbour has evicted them, no tail wave); a grid with
 // more columns than resident blocks gets one run per column.
 static cudaError_t launch_pass_z3(const GridDev& g, const float* src, float* dst, int ncomp,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, int* status) {
   static int resident = 0;
   if (resident == 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_z3, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_z3<true>, 256, 0);
     resident = sms * per_sm > 0 ? sms * per_sm : 1;
   }
   const int ncx = (g.n[0] + ZX - 1) / ZX, ncy = (g.n[1] + ZY - 1) / ZY;
@@ -752,20 +849,24 @@ static cudaError_t launch_pass_z3(const GridDev& g, const float* src, float* dst
   // multiples of 4 floats
   const int vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0 &&
                   g.n[0] % 4 == 0 && g.plane % 4 == 0;
-  k_filter_z3<<<dim3((unsigned)blocks, (unsigned)ncomp), 256, 0, st>>>(src, dst, g, ncx, ncy, zrun,
-                                                                      vec);
+  // bulk row copies where a status word can report a wait that ran out
+  const dim3 grid((unsigned)blocks, (unsigned)ncomp);
+  if (vec && status && PIC_BULK_FILTER)
+    k_filter_z3<true><<<grid, 256, 0, st>>>(src, dst, g, ncx, ncy, zrun, vec, status);
+  else
+    k_filter_z3<false><<<grid, 256, 0, st>>>(src, dst, g, ncx, ncy, zrun, vec, status);
   return cudaGetLastError();
 }
 
 // The y-marching 2D pass; runs as long as one wave of resident blocks allows.
 static cudaError_t launch_pass_y2(const GridDev& g, const float* src, float* dst, int ncomp,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, int* status) {
   static int resident = 0;
   if (resident == 0) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_y2, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_y2<true>, 256, 0);
     resident = sms * per_sm > 0 ? sms * per_sm : 1;
   }
   const int ncx = (g.n[0] + YX - 1) / YX;
@@ -778,16 +879,20 @@ static cudaError_t launch_pass_y2(const GridDev& g, const float* src, float* dst
   if (blocks > 0x7fffffffLL || ncomp > 65535) return cudaErrorInvalidValue;
   const int vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0 &&
                   g.n[0] % 4 == 0 && g.plane % 4 == 0;
-  k_filter_y2<<<dim3((unsigned)blocks, (unsigned)ncomp), 256, 0, st>>>(src, dst, g, ncx, yrun, vec);
+  const dim3 grid((unsigned)blocks, (unsigned)ncomp);
+  if (vec && status && PIC_BULK_FILTER)
+    k_filter_y2<true><<<grid, 256, 0, st>>>(src, dst, g, ncx, yrun, vec, status);
+  else
+    k_filter_y2<false><<<grid, 256, 0, st>>>(src, dst, g, ncx, yrun, vec, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_filter_pass_f32(const GridDev& g, const float* src, float* dst, int ncomp,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, int* status) {
   switch (g.dim) {
     case 1: return launch_pass<1, 1024, 1, 1>(g, src, dst, ncomp, st);
-    case 2: return launch_pass_y2(g, src, dst, ncomp, st);
-    case 3: return launch_pass_z3(g, src, dst, ncomp, st);
+    case 2: return launch_pass_y2(g, src, dst, ncomp, st, status);
+    case 3: return launch_pass_z3(g, src, dst, ncomp, st, status);
     default: return cudaErrorInvalidValue;
   }
 }

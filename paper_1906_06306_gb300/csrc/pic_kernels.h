@@ -61,6 +61,11 @@ constexpr bool kFoldGlobal = D == 3 && PIC_X3PAIR != 0;
 #ifndef PIC_TMA_WINDOW
 #define PIC_TMA_WINDOW 1
 #endif
+// The 2D/3D filter passes stage their rows by bulk copies (cp.async.bulk)
+// where the rows allow it and a status word can report a wait that ran out.
+#ifndef PIC_BULK_FILTER
+#define PIC_BULK_FILTER 1
+#endif
 // pic_step(n) replays whole sort cycles from a captured CUDA graph.
 #ifndef PIC_STEP_GRAPHS
 #define PIC_STEP_GRAPHS 1
@@ -189,9 +194,11 @@ cudaError_t launch_filter_f32(const GridDev& g, const float* src, float* dst, in
 cudaError_t launch_filter_f64(const GridDev& g, const double* src, double* dst, int ncomp,
                               int axis, cudaStream_t st);
 // one full Binomial2 pass (every gridded axis, x first) over ncomp consecutive
-// planes, src -> dst, the sub-passes fused through shared memory
+// planes, src -> dst, the sub-passes fused through shared memory; with a
+// status word (2D/3D, aligned rows) the rows are staged by bulk copies whose
+// bounded waits report there, without one (nullptr) by per-thread copies
 cudaError_t launch_filter_pass_f32(const GridDev& g, const float* src, float* dst, int ncomp,
-                                   cudaStream_t st);
+                                   cudaStream_t st, int* status);
 
 struct SortParams {
   GridDev g;

@@ -78,7 +78,7 @@ extern "C" pic_status pic_filter_current_static(const pic_grid* grid, float* J, 
   float* a = J;
   float* b = scratch;
   for (int p = 0; p < passes; ++p) {
-    e = pic::launch_filter_pass_f32(g, a, b, 3, st);
+    e = pic::launch_filter_pass_f32(g, a, b, 3, st, nullptr);
     if (e != cudaSuccess) return fail(PIC_ERR_CUDA, cudaGetErrorString(e));
     float* t = a;
     a = b;

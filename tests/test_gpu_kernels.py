@@ -91,13 +91,13 @@ def test_binomial_filter_matches_oracle(dim, passes):
 
 
 @pytest.mark.parametrize("shape", [(37, 11, 9), (68, 19, 41), (4, 8, 2), (1, 1, 3), (2, 3, 1),
-                                   (1024, 256, 40)])
+                                   (1024, 256, 40), (132, 20, 6)])
 def test_binomial_filter_3d_z_runs_match_oracle(shape):
     """The 3D pass marches along z over (x, y) columns of 128 x 16 points: rows
-    whose x extent is not a multiple of 4 (4-byte copies only), ragged columns,
-    several z runs with a ragged last one, extents below the column and the
-    halo, and a box of many columns whose runs span all its planes
-    (1024 x 256 x 40)."""
+    whose x extent is not a multiple of 4 (4-byte copies only), ragged columns
+    (68; 132 = 128 + 4, whose bulk row copies are 4 points long), several z
+    runs with a ragged last one, extents below the column and the halo, and a
+    box of many columns whose runs span all its planes (1024 x 256 x 40)."""
     nx, ny, nz = shape
     rs = np.random.default_rng(sum(shape))
     F32 = np.zeros((9, nz, ny, nx), np.float32)
@@ -112,12 +112,12 @@ def test_binomial_filter_3d_z_runs_match_oracle(shape):
 
 
 @pytest.mark.parametrize("shape", [(29, 23), (1030, 7), (4, 8), (1, 3), (2, 1), (2048, 64),
-                                   (1024, 1024)])
+                                   (1024, 1024), (1036, 9)])
 def test_binomial_filter_2d_y_runs_match_oracle(shape):
     """The 2D pass marches along y over 1024-point x columns: ragged columns
-    (1030, 2048 + halo), rows whose x extent is not a multiple of 4 (4-byte
-    copies only), extents below the halo, and the 1024^2 plane of the
-    turbulence box."""
+    (1030; 1036 = 1024 + 12, whose bulk row copies are 12 points long; 2048 +
+    halo), rows whose x extent is not a multiple of 4 (4-byte copies only),
+    extents below the halo, and the 1024^2 plane of the turbulence box."""
     nx, ny = shape
     rs = np.random.default_rng(nx + 7 * ny)
     F32 = np.zeros((9, 1, ny, nx), np.float32)
