@@ -162,6 +162,23 @@ pic_status pic_set_pusher(pic_ctx* ctx, int pusher);
  * Particles are grouped by tile; the order inside a tile is not specified. */
 pic_status pic_sort(pic_ctx* ctx);
 
+/* Number of sort bins of the current tiling (tiles, times sub-tiles where
+ * the tiles are sorted by sub-tile): the length, minus one, of the bucket
+ * starts that pic_sort_record writes.  *nbins is set; PIC_ERR_ARG on NULL. */
+pic_status pic_sort_bins(pic_ctx* ctx, int64_t* nbins);
+
+/* pic_sort, recorded, for the adjoint of a run that sorts (the paper has no
+ * counterpart).  The particles are sorted in place (their own rows hold the
+ * sorted order on return) and for every species s with particles:
+ * perm[s] (int32[n_s], device) receives, for each slot i, the slot that the
+ * particle now in slot i held before the sort; tstart[s] (int32[nbins + 1],
+ * device, nbins from pic_sort_bins) the first slot of each sort bin, the
+ * last entry n_s.  pic_adjoint_step runs its tile pass on particles grouped
+ * this way, and pic_adjoint_unsort carries gradients back through perm.
+ * Entries for species without particles may be NULL.  PIC_ERR_ARG on NULL
+ * arguments; enqueued on the context's stream. */
+pic_status pic_sort_record(pic_ctx* ctx, int32_t* const* perm, int32_t* const* tstart);
+
 /* interp_em + push of Table 1 for every species: linear gather of E and B at
  * x^n (Sect. 2.3.2), relativistic Boris push u^(n-1/2) -> u^(n+1/2)
  * (Appendix C), position update x^(n+1) = x^n + c u / gamma (Eq. fdX) with
@@ -267,9 +284,45 @@ typedef struct {
   const float* u;
   float* xbar;
   float* ubar;
+  const int32_t* tstart;
 } pic_adjoint_species;
 pic_status pic_adjoint_step(pic_ctx* ctx, const float* fwd_fields, const pic_adjoint_species* sp,
                             float* adj_fields);
+
+/* The particles' rows were put back (by the caller) into an order that
+ * pic_sort_record produced: the context takes its bucket starts tstart[s]
+ * (int32[nbins + 1], device) as the grouping of every species, so the next
+ * steps run their tile kernels on it, and sorts nothing itself.  For
+ * restoring a checkpoint taken after pic_sort_record (the paper has no
+ * counterpart).  Starts that do not run from 0 to n_s without decreasing
+ * are replaced by one bucket (correct, but every particle then takes the
+ * stray path) and the next pic_check reports PIC_ERR_STATE.  PIC_ERR_ARG on
+ * NULL arguments; enqueued on the context's stream. */
+pic_status pic_sort_assume(pic_ctx* ctx, const int32_t* const* tstart);
+
+/* sp[s].tstart of pic_adjoint_step: NULL, or the bucket starts written by the
+ * pic_sort_record that grouped cell/off/u (since then the particles may have
+ * moved, as pic_step moves them, but not been reordered; the context's
+ * tiling unchanged).  When every species with particles gives one (and the
+ * tile window's 15 planes fit in 200 KB of shared memory), a tile
+ * pass stages E, B and the current adjoint of each tile's window in shared
+ * memory and sums the E and B adjoints there; particles whose stencil left
+ * the window go through global memory, as all particles do otherwise.  The
+ * result is the same up to the order of floating-point sums.  Starts that are
+ * not a partition of the species' particles are replaced, for this step, by
+ * one bucket, and the next pic_check reports PIC_ERR_STATE. */
+
+/* The gradients of pic_adjoint_step carried back through a recorded sort:
+ * for every species with particles, sp[s].xbar and sp[s].ubar (rows of the
+ * species' cap) are permuted in place from the order after the sort to the
+ * order before it (row entry i moves to slot perm[s][i]), perm[s] as written
+ * by pic_sort_record (entries outside [0, n_s) are skipped and reported by
+ * the next pic_check).  The other fields of sp are not used.  PIC_ERR_ARG on
+ * NULL arguments, PIC_ERR_STATE while a sorted copy of the particles awaits
+ * its push (the library's sort buffer is the scratch); enqueued on the
+ * context's stream. */
+pic_status pic_adjoint_unsort(pic_ctx* ctx, const int32_t* const* perm,
+                              const pic_adjoint_species* sp);
 
 /* Current particle count of each species (grows with injection): writes
  * nout >= nspecies values.  No synchronisation: the counts are host state. */

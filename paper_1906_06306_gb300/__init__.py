@@ -24,7 +24,8 @@ Use (device memory and the stream come from PyTorch):
 """
 _API = {
     "PicError", "pic_init", "pic_set_pusher", "pic_set_field_solver", "pic_get_tuning",
-    "pic_set_tuning", "pic_set_shock", "pic_particle_counts", "pic_adjoint_step", "pic_sort", "pic_gather_push",
+    "pic_set_tuning", "pic_set_shock", "pic_particle_counts", "pic_adjoint_step", "pic_sort",
+    "pic_sort_bins", "pic_sort_record", "pic_sort_assume", "pic_adjoint_unsort", "pic_gather_push",
     "pic_deposit", "pic_filter_current", "pic_field_update", "pic_step", "pic_energies",
     "pic_check", "pic_wait_probe", "pic_step_host", "pic_autotune", "pic_stats", "pic_timing", "pic_kernel_times",
     "pic_destroy", "pic_last_error", "pic_filter_current_static", "pic_batch_create",

@@ -22,18 +22,41 @@ NO_SORT = 1 << 30  # sort cadence for adjoint runs: particle slots stay fixed
 
 class Adjoint:
     """Forward run of `sim` with checkpoints every `checkpoint_every` steps and
-    the reverse sweep.  Tile sorting is switched off on `sim` (the adjoint
-    arrays follow the particle slots, which a sort would permute); particles
-    that leave their tile take the global-memory path instead."""
+    the reverse sweep.  The steps themselves do not sort (the adjoint arrays
+    follow the particle slots); with `tiled` (the default) the particles are
+    tile-sorted in place at each checkpoint by pic_sort_record, which keeps the
+    permutation and the bucket starts: the forward steps and the adjoint's tile
+    pass then run on tile-grouped particles, and the reverse sweep carries the
+    gradients back through each checkpoint's permutation (pic_adjoint_unsort).
+    Without it every adjoint step takes the global-memory pass."""
 
-    def __init__(self, sim, checkpoint_every: int = 20):
+    def __init__(self, sim, checkpoint_every: int = 20, tiled: bool = True):
         if checkpoint_every < 1:
             raise ValueError("checkpoint_every must be >= 1")
         self.sim = sim
         self.K = int(checkpoint_every)
+        self.tiled = bool(tiled)
         self.nsteps = 0
         self.ckpt = []
         sim.set_tuning(sort_every=NO_SORT)
+
+    def _sort(self):
+        """Tile sort in place, recorded: (perm, tstart) per species (None for a
+        species without particles)."""
+        s = self.sim
+        torch = s.torch
+        nb = B.pic_sort_bins(s.ctx)
+        perm, tst = [], []
+        for n in s.counts():
+            perm.append(torch.empty(n, dtype=torch.int32, device=s.device) if n else None)
+            tst.append(torch.empty(nb + 1, dtype=torch.int32, device=s.device) if n else None)
+        B.pic_sort_record(s.ctx, [p.data_ptr() if p is not None else 0 for p in perm],
+                          [t.data_ptr() if t is not None else 0 for t in tst])
+        return perm, tst
+
+    def _assume(self, rec):
+        if rec is not None:
+            B.pic_sort_assume(self.sim.ctx, [t.data_ptr() if t is not None else 0 for t in rec[1]])
 
     def _state(self):
         s = self.sim
@@ -49,12 +72,14 @@ class Adjoint:
             d["u"].copy_(u)
 
     def forward(self, nsteps: int):
-        """nsteps steps of the simulation, keeping a checkpoint every K."""
+        """nsteps steps of the simulation, keeping a checkpoint every K (taken
+        after the checkpoint's tile sort, which it records)."""
         self.nsteps = int(nsteps)
         self.ckpt = []
         for t in range(self.nsteps):
             if t % self.K == 0:
-                self.ckpt.append(self._state())
+                rec = self._sort() if self.tiled else None
+                self.ckpt.append((self._state(), rec))
             self.sim.step(1)
 
     def zeros(self):
@@ -78,17 +103,28 @@ class Adjoint:
         for seg in reversed(range(len(self.ckpt))):
             t0 = seg * self.K
             t1 = min(self.nsteps, t0 + self.K)
-            self._restore(self.ckpt[seg])
+            st, rec = self.ckpt[seg]
+            self._restore(st)
+            self._assume(rec)
             states = []
             for _ in range(t0, t1):
                 states.append(self._state())
                 sim.step(1)
+            tst = rec[1] if rec is not None else [None] * len(xbar)
             for F, sp in reversed(states):
                 asp = [B.pic_adjoint_species(c.data_ptr(), o.data_ptr(), u.data_ptr(),
-                                             xb.data_ptr(), ub.data_ptr())
-                       for (c, o, u), xb, ub in zip(sp, xbar, ubar)]
+                                             xb.data_ptr(), ub.data_ptr(),
+                                             t.data_ptr() if t is not None else None)
+                       for (c, o, u), xb, ub, t in zip(sp, xbar, ubar, tst)]
                 B.pic_adjoint_step(sim.ctx, F.data_ptr(), asp, A.data_ptr())
+            if rec is not None:  # back through the checkpoint's sort
+                asp = [B.pic_adjoint_species(None, None, None, xb.data_ptr(), ub.data_ptr())
+                       for xb, ub in zip(xbar, ubar)]
+                B.pic_adjoint_unsort(sim.ctx, [p.data_ptr() if p is not None else 0
+                                               for p in rec[0]], asp)
         self._restore(final)
+        if self.ckpt:
+            self._assume(self.ckpt[-1][1])
         return A, xbar, ubar
 
 

@@ -42,7 +42,7 @@ class pic_shock(ctypes.Structure):
 
 class pic_adjoint_species(ctypes.Structure):
     _fields_ = [("cell", c_void_p), ("off", c_void_p), ("u", c_void_p), ("xbar", c_void_p),
-                ("ubar", c_void_p)]
+                ("ubar", c_void_p), ("tstart", c_void_p)]
 
 
 class pic_tuning(ctypes.Structure):
@@ -62,6 +62,11 @@ SIGNATURES = {
     "pic_particle_counts": (c_int, [_P, ctypes.POINTER(c_int64), c_int]),
     "pic_adjoint_step": (c_int, [_P, c_void_p, ctypes.POINTER(pic_adjoint_species), c_void_p]),
     "pic_sort": (c_int, [_P]),
+    "pic_sort_bins": (c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "pic_sort_record": (c_int, [_P, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p)]),
+    "pic_sort_assume": (c_int, [_P, ctypes.POINTER(c_void_p)]),
+    "pic_adjoint_unsort": (c_int, [_P, ctypes.POINTER(c_void_p),
+                                   ctypes.POINTER(pic_adjoint_species)]),
     "pic_gather_push": (c_int, [_P]),
     "pic_deposit": (c_int, [_P]),
     "pic_filter_current": (c_int, [_P, c_int]),
@@ -168,6 +173,32 @@ def pic_particle_counts(ctx, nspecies: int):
 
 def pic_sort(ctx) -> None:
     _check(_lib.pic_sort(ctx), ctx)
+
+
+def pic_sort_bins(ctx) -> int:
+    n = ctypes.c_int64(0)
+    _check(_lib.pic_sort_bins(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def pic_sort_record(ctx, perm_ptrs, tstart_ptrs) -> None:
+    """perm_ptrs, tstart_ptrs: device addresses (int32[n], int32[nbins + 1])
+    per species, 0 for species without particles."""
+    p = (c_void_p * len(perm_ptrs))(*[c_void_p(x or None) for x in perm_ptrs])
+    t = (c_void_p * len(tstart_ptrs))(*[c_void_p(x or None) for x in tstart_ptrs])
+    _check(_lib.pic_sort_record(ctx, p, t), ctx)
+
+
+def pic_sort_assume(ctx, tstart_ptrs) -> None:
+    t = (c_void_p * len(tstart_ptrs))(*[c_void_p(x or None) for x in tstart_ptrs])
+    _check(_lib.pic_sort_assume(ctx, t), ctx)
+
+
+def pic_adjoint_unsort(ctx, perm_ptrs, species) -> None:
+    """species: pic_adjoint_species per species (xbar and ubar are used)."""
+    p = (c_void_p * len(perm_ptrs))(*[c_void_p(x or None) for x in perm_ptrs])
+    arr = (pic_adjoint_species * len(species))(*species)
+    _check(_lib.pic_adjoint_unsort(ctx, p, arr), ctx)
 
 
 def pic_gather_push(ctx) -> None:

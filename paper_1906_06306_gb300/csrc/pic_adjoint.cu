@@ -8,9 +8,14 @@
 // On the periodic lattice (curl+)^T = curl- and (curl-)^T = curl+, and the
 // Binomial2 filter is symmetric, so the field part is two stencil kernels
 // and the filter; the particle part is the chain rule through gather, Boris,
-// move and ZigZag for every particle, one thread each, through global memory
-// (the cell of a particle and the branch of the ZigZag relay point are locally
-// constant, so they are taken from the forward step).
+// move and ZigZag for every particle, one thread each (the cell of a particle
+// and the branch of the ZigZag relay point are locally constant, so they are
+// taken from the forward step).  Particles grouped by tile (given the bucket
+// starts of the sort that grouped them) go through k_adj_tiles: a block stages
+// its tile window of E, B and the current adjoint in shared memory and sums
+// the field adjoints there, and the particles whose stencil left the window
+// are deferred to the global-memory pass; ungrouped particles all take the
+// global-memory pass.
 #include <cmath>
 
 #include "pic_kernels.h"
@@ -89,8 +94,8 @@ __global__ void k_adj_b(float* __restrict__ A, const GridDev g, float h) {
 
 // Reverse of the linear gather of one staggered component (stag bit d: half a
 // cell up axis d): Abar[comp] += weights * vb (atomic), xb += dvalue/dx * vb.
-template <int D>
-__device__ __forceinline__ void gather_adj(const GlobAcc& F, const GlobAcc& Ab, int comp, int stag,
+template <int D, class AF, class AB>
+__device__ __forceinline__ void gather_adj(const AF& F, const AB& Ab, int comp, int stag,
                                            const int* b, const float* o, float vb, float* xb) {
   int i0[3] = {0, 0, 0};
   float w[3] = {0.f, 0.f, 0.f};
@@ -195,8 +200,8 @@ __device__ __forceinline__ void boris_adj(const float* u, const float* e, const 
 // Reverse of one ZigZag segment's words (the forward zz_values / zz_deposit,
 // Appendix D) in the cell with lower corner I: from Jbar, the gradients of the
 // segment displacement Dl and of its weights W.
-template <int D>
-__device__ __forceinline__ void segment_adj(const GlobAcc& Ab, const int* I, float q,
+template <int D, class AB>
+__device__ __forceinline__ void segment_adj(const AB& Ab, const int* I, float q,
                                             const float* Dl, const float* W, float* Db,
                                             float* Wb) {
   const int i = I[0], j = I[1], k = I[2];
@@ -255,108 +260,212 @@ __device__ __forceinline__ void segment_adj(const GlobAcc& Ab, const int* I, flo
   }
 }
 
-// Reverse of the whole particle update for every particle of every species.
+// Reverse of the whole particle update of particle p of species S, in cell b
+// (accessor coordinates of F and Ab): the forward gather, Boris and move are
+// recomputed with the forward kernel's own routines, then ZigZag, move, Boris
+// and gather are reversed; xbar and ubar of p are updated in place and the
+// field adjoints added through Ab.
+template <int D, class AF, class AB>
+__device__ __forceinline__ void adj_particle(const AF& F, const AB& Ab, const AdjSpecies& S,
+                                             long long p, const int* b, float c) {
+  const long long ld = S.ld;
+  float o1[3] = {0.f, 0.f, 0.f}, u[3];
+#pragma unroll
+  for (int d = 0; d < D; ++d) o1[d] = S.off[d * ld + p];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u[a] = S.u[a * ld + p];
+  // forward: gather, Boris, move (the forward kernel's own routines)
+  float e[3], bf[3];
+  gather<D>(F, b, o1, e, bf);
+  float u2[3] = {u[0], u[1], u[2]};
+  boris(u2, e, bf, S.qm, c, 1.0f / c, 1.0f / (c * c));
+  float o2[3] = {0.f, 0.f, 0.f}, dn[3];
+  int dc[3] = {0, 0, 0};
+  move<D>(u2, o1, c, o2, dc, dn);
+  const float g2 = fmaf(u2[0], u2[0], fmaf(u2[1], u2[1], fmaf(u2[2], u2[2], 1.0f)));
+  const float ig = rsqrtf(g2);
+  // reverse of x' = x + dn: xbar passes through, dn gets xbar
+  float xb[3] = {0.f, 0.f, 0.f}, dnb[3] = {0.f, 0.f, 0.f}, u2b[3];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    xb[d] = S.xbar[d * ld + p];
+    dnb[d] = xb[d];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u2b[a] = S.ubar[a * ld + p];
+  // reverse of ZigZag(x, x + dn), positions relative to the old cell
+  float D1[3], D2[3], W1[3] = {0.f, 0.f, 0.f}, W2[3] = {0.f, 0.f, 0.f};
+  bool mid[3] = {false, false, false};
+  int b2[3] = {b[0], b[1], b[2]};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (d < D) {
+      const float x1 = o1[d], x2 = (float)dc[d] + o2[d];
+      const float lo = (float)(dc[d] < 0 ? dc[d] : 0) + 1.0f;
+      const float hi = (float)(dc[d] > 0 ? dc[d] : 0);
+      const float m = 0.5f * (x1 + x2);
+      const float xr = fminf(lo, fmaxf(hi, m));
+      mid[d] = m > hi && m < lo;
+      D1[d] = xr - x1;
+      D2[d] = x2 - xr;
+      W1[d] = 0.5f * (x1 + xr);
+      W2[d] = 0.5f * (x2 + xr) - (float)dc[d];
+      b2[d] = b[d] + dc[d];
+    } else {
+      D1[d] = D2[d] = 0.5f * dn[d];
+    }
+  }
+  float D1b[3] = {0.f, 0.f, 0.f}, D2b[3] = {0.f, 0.f, 0.f};
+  float W1b[3] = {0.f, 0.f, 0.f}, W2b[3] = {0.f, 0.f, 0.f};
+  segment_adj<D>(Ab, b, S.q, D1, W1, D1b, W1b);
+  segment_adj<D>(Ab, b2, S.q, D2, W2, D2b, W2b);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (d < D) {
+      const float xrb = D1b[d] - D2b[d] + 0.5f * (W1b[d] + W2b[d]);
+      float x1b = -D1b[d] + 0.5f * W1b[d];
+      float x2b = D2b[d] + 0.5f * W2b[d];
+      if (mid[d]) {
+        x1b += 0.5f * xrb;
+        x2b += 0.5f * xrb;
+      }
+      xb[d] += x1b + x2b;  // x2 = x1 + dn
+      dnb[d] += x2b;
+    } else {
+      dnb[d] += 0.5f * (D1b[d] + D2b[d]);
+    }
+  }
+  // reverse of dn = c u2 / gamma
+  const float ud = u2[0] * dnb[0] + u2[1] * dnb[1] + u2[2] * dnb[2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u2b[a] += c * ig * (dnb[a] - u2[a] * ud * ig * ig);
+  float ub[3], eb[3], bb[3];
+  boris_adj(u, e, bf, S.qm, c, u2b, ub, eb, bb);
+  // reverse of the gather: Ex (1/2,0,0) Ey (0,1/2,0) Ez (0,0,1/2)
+  // Bx (0,1/2,1/2) By (1/2,0,1/2) Bz (1/2,1/2,0)
+  gather_adj<D>(F, Ab, EX, 1, b, o1, eb[0], xb);
+  gather_adj<D>(F, Ab, EY, 2, b, o1, eb[1], xb);
+  gather_adj<D>(F, Ab, EZ, 4, b, o1, eb[2], xb);
+  gather_adj<D>(F, Ab, BX, 6, b, o1, bb[0], xb);
+  gather_adj<D>(F, Ab, BY, 5, b, o1, bb[1], xb);
+  gather_adj<D>(F, Ab, BZ, 3, b, o1, bb[2], xb);
+#pragma unroll
+  for (int d = 0; d < D; ++d) S.xbar[d * ld + p] = xb[d];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) S.ubar[a * ld + p] = ub[a];
+}
+
+// The lattice cell (i, j, k) of a linear cell index.
+__device__ __forceinline__ void cell_ijk(const AdjParams& P, int cell, int* b) {
+  const int r = fdiv(cell, P.div0);
+  b[0] = cell - r * P.g.n[0];
+  b[2] = fdiv(r, P.div1);
+  b[1] = r - b[2] * P.g.n[1];
+}
+
+// Global-memory pass: every particle of every species, or (deferred) the
+// particles listed by k_adj_tiles.
 template <int D>
-__global__ void __launch_bounds__(256) k_adj_particles(const AdjParams P) {
+__global__ void __launch_bounds__(256) k_adj_particles(const AdjParams P, int deferred) {
   const GlobAcc F{const_cast<float*>(P.F1), P.g.plane, P.g.n[0], P.g.n[1], P.g.n[2]};
   const GlobAcc Ab{P.A, P.g.plane, P.g.n[0], P.g.n[1], P.g.n[2]};
   const float c = P.g.c;
   for (int s = 0; s < P.nspecies; ++s) {
     const AdjSpecies& S = P.sp[s];
-    const long long n = S.n, ld = S.ld;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-         p += (long long)gridDim.x * blockDim.x) {
+    const long long n = deferred ? (long long)P.dcount[s] : S.n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+      const long long p = deferred ? (long long)S.dlist[i] : i;
       const int cell = S.cell[p];
       if (cell < 0 || (long long)cell >= P.g.plane) continue;
-      int b[3] = {0, 0, 0};
-      const int r = fdiv(cell, P.div0);
-      b[0] = cell - r * P.g.n[0];
-      b[2] = fdiv(r, P.div1);
-      b[1] = r - b[2] * P.g.n[1];
-      float o1[3] = {0.f, 0.f, 0.f}, u[3];
+      int b[3];
+      cell_ijk(P, cell, b);
+      adj_particle<D>(F, Ab, S, p, b, c);
+    }
+  }
+}
+
+// The tile window of the adjoint pass in shared memory, window-local
+// coordinates: planes 0..5 forward E and B1, 6..8 the current adjoint (read),
+// 9..14 the sums of the E and B adjoints of the block's particles.  One
+// accessor serves as both the forward fields and the adjoint planes.
+struct AdjWin {
+  float* S;
+  int W0, W01, ws;
+  __device__ __forceinline__ int at(int i, int j, int k) const { return i + W0 * j + W01 * k; }
+  __device__ __forceinline__ float ld(int comp, int i, int j, int k) const {
+    return S[comp * ws + at(i, j, k)];
+  }
+  __device__ __forceinline__ void add(int comp, int i, int j, int k, float v) const {
+    atomicAdd(&S[(9 + comp) * ws + at(i, j, k)], v);
+  }
+};
+
+// Particles grouped by tile: one block per (tile, split) runs its share of
+// each species' bucket against the staged window; a particle whose stencil
+// (cells b - 1 .. b + 2 on every gridded axis, as in the forward tile kernel)
+// is not inside the window is appended to the species' deferred list.  The
+// block's E and B adjoint sums go to the global planes once per window cell.
+template <int D>
+__global__ void __launch_bounds__(256, 2) k_adj_tiles(const AdjParams P) {
+  extern __shared__ __align__(16) float sm[];
+  const TileDev& t = P.t;
+  const int tile = blockIdx.x / P.splits, split = blockIdx.x % P.splits;
+  const int tc[3] = {tile % t.nt[0], (tile / t.nt[0]) % t.nt[1], tile / (t.nt[0] * t.nt[1])};
+  int w0[3] = {0, 0, 0}, W[3] = {1, 1, 1};
 #pragma unroll
-      for (int d = 0; d < D; ++d) o1[d] = S.off[d * ld + p];
+  for (int d = 0; d < D; ++d) {
+    w0[d] = tc[d] * t.T[d] - t.H;
+    W[d] = t.W[d];
+  }
+  const int wc = t.wcells, ws = t.wstride;
+  const long long plane = P.g.plane;
+  const GlobAcc G{P.A, plane, P.g.n[0], P.g.n[1], P.g.n[2]};
+  for (int w = threadIdx.x; w < wc; w += blockDim.x) {
+    const int lx = w % W[0], rr = w / W[0], ly = rr % W[1], lz = rr / W[1];
+    const long long gi = G.at(w0[0] + lx, w0[1] + ly, w0[2] + lz);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) u[a] = S.u[a * ld + p];
-      // forward: gather, Boris, move (the forward kernel's own routines)
-      float e[3], bf[3];
-      gather<D>(F, b, o1, e, bf);
-      float u2[3] = {u[0], u[1], u[2]};
-      boris(u2, e, bf, S.qm, c, 1.0f / c, 1.0f / (c * c));
-      float o2[3] = {0.f, 0.f, 0.f}, dn[3];
-      int dc[3] = {0, 0, 0};
-      move<D>(u2, o1, c, o2, dc, dn);
-      const float g2 = fmaf(u2[0], u2[0], fmaf(u2[1], u2[1], fmaf(u2[2], u2[2], 1.0f)));
-      const float ig = rsqrtf(g2);
-      // reverse of x' = x + dn: xbar passes through, dn gets xbar
-      float xb[3] = {0.f, 0.f, 0.f}, dnb[3] = {0.f, 0.f, 0.f}, u2b[3];
+    for (int c = 0; c < 6; ++c) sm[c * ws + w] = __ldg(&P.F1[c * plane + gi]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) sm[(6 + a) * ws + w] = P.A[(JX + a) * plane + gi];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sm[(9 + c) * ws + w] = 0.f;
+  }
+  __syncthreads();
+  const AdjWin WN{sm, W[0], W[0] * W[1], ws};
+  const float c = P.g.c;
+  for (int s = 0; s < P.nspecies; ++s) {
+    const AdjSpecies& S = P.sp[s];
+    if (S.n == 0) continue;
+    const long long lo = S.tstart[tile * t.nsub], hi = S.tstart[(tile + 1) * t.nsub];
+    const long long a = lo + (hi - lo) * split / P.splits;
+    const long long b = lo + (hi - lo) * (split + 1) / P.splits;
+    for (long long p = a + threadIdx.x; p < b; p += blockDim.x) {
+      const int cell = S.cell[p];
+      if (cell < 0 || (long long)cell >= plane) continue;
+      int ijk[3], l[3] = {0, 0, 0};
+      cell_ijk(P, cell, ijk);
+      bool inwin = true;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        xb[d] = S.xbar[d * ld + p];
-        dnb[d] = xb[d];
+        l[d] = wrapi(ijk[d] - w0[d], P.g.n[d]);
+        inwin &= (unsigned)(l[d] - 1) <= (unsigned)(W[d] - 4);
       }
-#pragma unroll
-      for (int a = 0; a < 3; ++a) u2b[a] = S.ubar[a * ld + p];
-      // reverse of ZigZag(x, x + dn), positions relative to the old cell
-      float D1[3], D2[3], W1[3] = {0.f, 0.f, 0.f}, W2[3] = {0.f, 0.f, 0.f};
-      bool mid[3] = {false, false, false};
-      int b2[3] = {b[0], b[1], b[2]};
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        if (d < D) {
-          const float x1 = o1[d], x2 = (float)dc[d] + o2[d];
-          const float lo = (float)(dc[d] < 0 ? dc[d] : 0) + 1.0f;
-          const float hi = (float)(dc[d] > 0 ? dc[d] : 0);
-          const float m = 0.5f * (x1 + x2);
-          const float xr = fminf(lo, fmaxf(hi, m));
-          mid[d] = m > hi && m < lo;
-          D1[d] = xr - x1;
-          D2[d] = x2 - xr;
-          W1[d] = 0.5f * (x1 + xr);
-          W2[d] = 0.5f * (x2 + xr) - (float)dc[d];
-          b2[d] = b[d] + dc[d];
-        } else {
-          D1[d] = D2[d] = 0.5f * dn[d];
-        }
+      if (!inwin) {
+        S.dlist[atomicAdd(&P.dcount[s], 1)] = (int)p;
+        continue;
       }
-      float D1b[3] = {0.f, 0.f, 0.f}, D2b[3] = {0.f, 0.f, 0.f};
-      float W1b[3] = {0.f, 0.f, 0.f}, W2b[3] = {0.f, 0.f, 0.f};
-      segment_adj<D>(Ab, b, S.q, D1, W1, D1b, W1b);
-      segment_adj<D>(Ab, b2, S.q, D2, W2, D2b, W2b);
+      adj_particle<D>(WN, WN, S, p, l, c);
+    }
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < wc; w += blockDim.x) {
+    const int lx = w % W[0], rr = w / W[0], ly = rr % W[1], lz = rr / W[1];
+    const long long gi = G.at(w0[0] + lx, w0[1] + ly, w0[2] + lz);
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        if (d < D) {
-          const float xrb = D1b[d] - D2b[d] + 0.5f * (W1b[d] + W2b[d]);
-          float x1b = -D1b[d] + 0.5f * W1b[d];
-          float x2b = D2b[d] + 0.5f * W2b[d];
-          if (mid[d]) {
-            x1b += 0.5f * xrb;
-            x2b += 0.5f * xrb;
-          }
-          xb[d] += x1b + x2b;  // x2 = x1 + dn
-          dnb[d] += x2b;
-        } else {
-          dnb[d] += 0.5f * (D1b[d] + D2b[d]);
-        }
-      }
-      // reverse of dn = c u2 / gamma
-      const float ud = u2[0] * dnb[0] + u2[1] * dnb[1] + u2[2] * dnb[2];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) u2b[a] += c * ig * (dnb[a] - u2[a] * ud * ig * ig);
-      float ub[3], eb[3], bb[3];
-      boris_adj(u, e, bf, S.qm, c, u2b, ub, eb, bb);
-      // reverse of the gather: Ex (1/2,0,0) Ey (0,1/2,0) Ez (0,0,1/2)
-      // Bx (0,1/2,1/2) By (1/2,0,1/2) Bz (1/2,1/2,0)
-      gather_adj<D>(F, Ab, EX, 1, b, o1, eb[0], xb);
-      gather_adj<D>(F, Ab, EY, 2, b, o1, eb[1], xb);
-      gather_adj<D>(F, Ab, EZ, 4, b, o1, eb[2], xb);
-      gather_adj<D>(F, Ab, BX, 6, b, o1, bb[0], xb);
-      gather_adj<D>(F, Ab, BY, 5, b, o1, bb[1], xb);
-      gather_adj<D>(F, Ab, BZ, 3, b, o1, bb[2], xb);
-#pragma unroll
-      for (int d = 0; d < D; ++d) S.xbar[d * ld + p] = xb[d];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) S.ubar[a * ld + p] = ub[a];
+    for (int c2 = 0; c2 < 6; ++c2) {
+      const float v = sm[(9 + c2) * ws + w];
+      if (v != 0.f) atomicAdd(&P.A[c2 * plane + gi], v);
     }
   }
 }
@@ -384,16 +493,49 @@ cudaError_t launch_adj_b_half(const GridDev& g, float* A, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+size_t adj_tile_smem_bytes(const TileDev& t) { return sizeof(float) * 15 * (size_t)t.wstride; }
+
 cudaError_t launch_adj_particles(const AdjParams& P, cudaStream_t st) {
   long long nmax = 0;
   for (int s = 0; s < P.nspecies; ++s) nmax = P.sp[s].n > nmax ? P.sp[s].n : nmax;
   if (nmax == 0) return cudaSuccess;
-  long long nb = (nmax + 255) / 256;
+  // the tile pass when every species with particles has its tile grouping
+  bool tiled = true;
+  for (int s = 0; s < P.nspecies; ++s) tiled &= P.sp[s].n == 0 || P.sp[s].tstart != nullptr;
+  tiled &= adj_tile_smem_bytes(P.t) <= 200 * 1024;  // else the window does not fit
+  const int D = P.g.dim;
+  if (tiled) {
+    static bool attr[4] = {false, false, false, false};
+    const size_t smem = adj_tile_smem_bytes(P.t);
+    cudaError_t e = cudaMemsetAsync(P.dcount, 0, sizeof(int) * P.nspecies, st);
+    if (e != cudaSuccess) return e;
+    if (!attr[D]) {
+      const void* k = D == 1 ? (const void*)k_adj_tiles<1> : D == 2 ? (const void*)k_adj_tiles<2>
+                                                                     : (const void*)k_adj_tiles<3>;
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e != cudaSuccess) return e;
+      attr[D] = true;
+    }
+    const long long blocks = (long long)P.t.ntiles * P.splits;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    switch (D) {
+      case 1: k_adj_tiles<1><<<(unsigned)blocks, 256, smem, st>>>(P); break;
+      case 2: k_adj_tiles<2><<<(unsigned)blocks, 256, smem, st>>>(P); break;
+      case 3: k_adj_tiles<3><<<(unsigned)blocks, 256, smem, st>>>(P); break;
+      default: return cudaErrorInvalidValue;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // the global pass: every particle, or those the tile pass deferred (their
+  // count is on the device: a grid that strides over any count)
+  long long nb = tiled ? 152LL * 8 : (nmax + 255) / 256;
   if (nb > 152LL * 32) nb = 152LL * 32;
-  switch (P.g.dim) {
-    case 1: k_adj_particles<1><<<(unsigned)nb, 256, 0, st>>>(P); break;
-    case 2: k_adj_particles<2><<<(unsigned)nb, 256, 0, st>>>(P); break;
-    case 3: k_adj_particles<3><<<(unsigned)nb, 256, 0, st>>>(P); break;
+  const int deferred = tiled ? 1 : 0;
+  switch (D) {
+    case 1: k_adj_particles<1><<<(unsigned)nb, 256, 0, st>>>(P, deferred); break;
+    case 2: k_adj_particles<2><<<(unsigned)nb, 256, 0, st>>>(P, deferred); break;
+    case 3: k_adj_particles<3><<<(unsigned)nb, 256, 0, st>>>(P, deferred); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -67,6 +67,8 @@ struct pic_ctx {
   long long tn[PIC_MAX_SPECIES] = {};        // template particles per species
   std::vector<double> txs[PIC_MAX_SPECIES];  // template x = i + off_x (host, sorted)
   void* d_tmpl = nullptr;                    // template records of every species
+  int* d_adj_tstart = nullptr;  // checked copies of the adjoint's bucket starts
+  size_t adj_tstart_len = 0;
   int* d_dlist = nullptr;   // particles deferred to the global pass, room for cap[s] per species
   int* d_dcount = nullptr;  // entries per species
   float* d_adjF = nullptr;                   // forward fields of an adjoint step (9 planes)
@@ -145,6 +147,7 @@ void free_all(pic_ctx* ctx) {
   dfree(ctx->d_status);
   dfree(ctx->d_strays);
   dfree(ctx->d_tmpl);
+  dfree(ctx->d_adj_tstart);
   dfree(ctx->d_dlist);
   dfree(ctx->d_dcount);
   dfree(ctx->d_adjF);
@@ -426,7 +429,7 @@ PushParams make_params(pic_ctx* ctx) {
 // Sort every species by tile into the sorted buffer.  With copy_back the
 // sorted particles are copied into the caller's arrays; without, the next push
 // reads them from the buffer and writes the caller's arrays (pic_step).
-pic_status do_sort(pic_ctx* ctx, bool copy_back) {
+pic_status do_sort(pic_ctx* ctx, bool copy_back, int32_t* const* perm = nullptr) {
   const SortParams P = make_sort_params(ctx->g, ctx->tile, ctx->d_status);
   const int D = ctx->grid.dim;
   const cudaError_t e = timed(ctx, PIC_KERNEL_SORT, [&]() -> cudaError_t {
@@ -445,7 +448,8 @@ pic_status do_sort(pic_ctx* ctx, bool copy_back) {
       float* off_out = (float*)(cell_out + ld);
       float* u_out = off_out + (long long)D * ld;
       r = launch_tile_scatter(P, ctx->sp[s].cell, ctx->sp[s].off, ctx->sp[s].u, n, ld,
-                              ctx->d_cursor, cell_out, off_out, u_out, ctx->st);
+                              ctx->d_cursor, cell_out, off_out, u_out, ctx->st,
+                              perm ? perm[s] : nullptr);
       if (r != cudaSuccess) return r;
       if (!copy_back) continue;
       const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
@@ -858,13 +862,41 @@ pic_status pic_adjoint_step(pic_ctx* ctx, const float* fwd_fields, const pic_adj
   if (!ctx->d_jtmp) PIC_CK(ctx, dalloc(&ctx->d_jtmp, 3 * (size_t)P));
   AdjParams AP{};
   AP.g = ctx->g;
+  AP.t = ctx->tile;
+  AP.splits = ctx->splits;
   AP.F1 = ctx->d_adjF;
   AP.A = adj_fields;
   AP.div0 = make_fastdiv(ctx->g.n[0]);
   AP.div1 = make_fastdiv(ctx->g.n[1]);
   AP.nspecies = ctx->ns;
+  AP.dcount = ctx->d_dcount;
+  // the tile grouping: the caller's bucket starts, copied and checked (a tile
+  // block must never read a slot outside [0, n); see pic_sort_assume)
+  bool tiled = true;
+  for (int s = 0; s < ctx->ns; ++s) tiled &= ctx->sp[s].n == 0 || sp[s].tstart != nullptr;
+  const long long nb = sort_bins(ctx->tile);
+  if (tiled) {
+    const size_t need = (size_t)ctx->ns * (size_t)(nb + 1);
+    if (ctx->adj_tstart_len < need) {
+      dfree(ctx->d_adj_tstart);
+      ctx->adj_tstart_len = 0;
+      PIC_CK(ctx, dalloc(&ctx->d_adj_tstart, need));
+      ctx->adj_tstart_len = need;
+    }
+  }
+  long long o = 0;
   for (int s = 0; s < ctx->ns; ++s) {
     AdjSpecies& S = AP.sp[s];
+    S.tstart = nullptr;
+    if (tiled && ctx->sp[s].n > 0) {
+      int* t = ctx->d_adj_tstart + (long long)s * (nb + 1);
+      PIC_CK(ctx, cudaMemcpyAsync(t, sp[s].tstart, sizeof(int) * (nb + 1),
+                                  cudaMemcpyDeviceToDevice, ctx->st));
+      PIC_CK(ctx, launch_check_buckets(t, nb, ctx->sp[s].n, ctx->d_status, ctx->st));
+      S.tstart = t;
+    }
+    S.dlist = ctx->d_dlist + o;
+    o += ctx->cap[s];
     S.q = ctx->sp[s].q;
     S.qm = ctx->sp[s].q / ctx->sp[s].m;
     S.n = ctx->sp[s].n;
@@ -913,6 +945,74 @@ pic_status pic_particle_counts(pic_ctx* ctx, int64_t* n, int nout) {
 pic_status pic_sort(pic_ctx* ctx) {
   if (!ctx) return PIC_ERR_ARG;
   return do_sort(ctx, true);
+}
+
+pic_status pic_sort_bins(pic_ctx* ctx, int64_t* nbins) {
+  if (!ctx || !nbins) return set_err(ctx, PIC_ERR_ARG, "NULL argument");
+  *nbins = sort_bins(ctx->tile);
+  return PIC_OK;
+}
+
+pic_status pic_sort_record(pic_ctx* ctx, int32_t* const* perm, int32_t* const* tstart) {
+  if (!ctx || !perm || !tstart) return set_err(ctx, PIC_ERR_ARG, "NULL argument");
+  for (int s = 0; s < ctx->ns; ++s)
+    if (ctx->sp[s].n > 0 && (!perm[s] || !tstart[s]))
+      return set_err(ctx, PIC_ERR_ARG, "perm or tstart of a species with particles is NULL");
+  const pic_status st = do_sort(ctx, true, perm);
+  if (st != PIC_OK) return st;
+  const long long nb = sort_bins(ctx->tile) + 1;
+  for (int s = 0; s < ctx->ns; ++s)
+    if (tstart[s])
+      PIC_CK(ctx, cudaMemcpyAsync(tstart[s], ctx->d_tstart[s], sizeof(int) * nb,
+                                  cudaMemcpyDeviceToDevice, ctx->st));
+  return PIC_OK;
+}
+
+pic_status pic_sort_assume(pic_ctx* ctx, const int32_t* const* tstart) {
+  if (!ctx || !tstart) return set_err(ctx, PIC_ERR_ARG, "NULL argument");
+  for (int s = 0; s < ctx->ns; ++s)
+    if (ctx->sp[s].n > 0 && !tstart[s])
+      return set_err(ctx, PIC_ERR_ARG, "tstart of a species with particles is NULL");
+  const long long nb = sort_bins(ctx->tile);
+  for (int s = 0; s < ctx->ns; ++s) {
+    const long long n = ctx->sp[s].n;
+    if (n > 0)
+      PIC_CK(ctx, cudaMemcpyAsync(ctx->d_tstart[s], tstart[s], sizeof(int) * (nb + 1),
+                                  cudaMemcpyDeviceToDevice, ctx->st));
+    else
+      PIC_CK(ctx, cudaMemsetAsync(ctx->d_tstart[s], 0, sizeof(int) * (nb + 1), ctx->st));
+    // a tile kernel must never read a slot outside [0, n): starts that are
+    // not a partition are replaced by one bucket (correct, through the stray
+    // path) and reported by pic_check
+    PIC_CK(ctx, launch_check_buckets(ctx->d_tstart[s], nb, n, ctx->d_status, ctx->st));
+    ctx->sorted_n[s] = n;
+  }
+  ctx->snapshot_valid = false;
+  ctx->sorted_pending = false;
+  ctx->sorted_step = ctx->steps;
+  return PIC_OK;
+}
+
+pic_status pic_adjoint_unsort(pic_ctx* ctx, const int32_t* const* perm,
+                              const pic_adjoint_species* sp) {
+  if (!ctx || !perm || !sp) return set_err(ctx, PIC_ERR_ARG, "NULL argument");
+  if (ctx->sorted_pending)
+    return set_err(ctx, PIC_ERR_STATE, "a sorted copy of the particles awaits its push");
+  const int D = ctx->grid.dim;
+  for (int s = 0; s < ctx->ns; ++s) {
+    const long long n = ctx->sp[s].n, ld = ctx->cap[s];
+    if (n == 0) continue;
+    if (!perm[s] || !sp[s].xbar || !sp[s].ubar)
+      return set_err(ctx, PIC_ERR_ARG, "perm, xbar or ubar of a species with particles is NULL");
+    // through the sort buffer of the species (room for 1 + D + 3 rows of ld)
+    float* tmp = (float*)((int*)ctx->d_sortbuf + sortbuf_offset(ctx, s));
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    PIC_CK(ctx, launch_unpermute(perm[s], sp[s].xbar, tmp, n, ld, D, ctx->d_status, ctx->st));
+    PIC_CK(ctx, copy_rows(sp[s].xbar, tmp, sizeof(float), n, ld, D, k, ctx->st));
+    PIC_CK(ctx, launch_unpermute(perm[s], sp[s].ubar, tmp, n, ld, 3, ctx->d_status, ctx->st));
+    PIC_CK(ctx, copy_rows(sp[s].ubar, tmp, sizeof(float), n, ld, 3, k, ctx->st));
+  }
+  return PIC_OK;
 }
 
 pic_status pic_gather_push(pic_ctx* ctx) {
@@ -1091,6 +1191,10 @@ pic_status pic_check(pic_ctx* ctx) {
   if (h & ST_BAD_CELL) m += " cell index out of range;";
   if (h & ST_BAD_OFF) m += " offset outside [0,1);";
   if (h & ST_BAD_U) m += " non-finite four-velocity;";
+  if (h & ST_BEHIND_WALL) m += " particle behind the conducting wall;";
+  if (h & ST_BAD_BUCKETS)
+    m += " bucket starts or a permutation handed in were not valid (starts replaced by one"
+         " bucket, permutation entries outside [0, n) skipped);";
   // a bounded wait on a shared-memory copy gave up: the results of that step
   // are not to be trusted, the context stays usable
   if (h & ST_TIMEOUT)

@@ -15,7 +15,14 @@ namespace pic {
 enum { EX = 0, EY, EZ, BX, BY, BZ, JX, JY, JZ };
 
 // device status word bits (pic_check)
-enum : int { ST_BAD_CELL = 1, ST_BAD_OFF = 2, ST_BAD_U = 4, ST_BEHIND_WALL = 8, ST_TIMEOUT = 16 };
+enum : int {
+  ST_BAD_CELL = 1,
+  ST_BAD_OFF = 2,
+  ST_BAD_U = 4,
+  ST_BEHIND_WALL = 8,
+  ST_TIMEOUT = 16,
+  ST_BAD_BUCKETS = 32  // bucket starts handed in were not a partition of the particles
+};
 
 // ---- bulk asynchronous copies (TMA engine) and shared-memory barriers ----
 // Hand-written PTX for sm_90+: a 1D cp.async.bulk copy from global to shared

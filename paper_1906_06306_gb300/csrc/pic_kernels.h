@@ -158,7 +158,7 @@ struct PushParams {
   int win_tma;
   int win_box[2];   // box extents x (a multiple of 4), y
   int win_shift;    // window x origin - box x origin
-  alignas(64) CUtensorMap win_map;
+  CUtensorMap win_map;  // (the type carries the alignment a tensor map needs)
 };
 
 // Quantum of the fixed-point shared-memory current (a power of 2) for charges
@@ -217,9 +217,19 @@ cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* curs
                              cudaStream_t st);
 inline long long scan_scratch(long long n) { return 3 * ((n + 4095) / 4096 + 1); }
 // arrays with rows of ld elements, the first n of which are particles
+// perm (or null): perm[new slot] = old slot
 cudaError_t launch_tile_scatter(const SortParams& P, const int* cell, const float* off,
                                 const float* u, long long n, long long ld, int* cursor,
-                                int* cell_out, float* off_out, float* u_out, cudaStream_t st);
+                                int* cell_out, float* off_out, float* u_out, cudaStream_t st,
+                                int* perm = nullptr);
+// bucket starts t[0..nb] from outside: unless they are a partition of [0, n)
+// they become one bucket, and ST_BAD_BUCKETS is set
+cudaError_t launch_check_buckets(int* tstart, long long nb, long long n, int* status,
+                                 cudaStream_t st);
+// out[r * ld + perm[i]] = in[r * ld + i] for i < n, r < rows (entries of perm
+// outside [0, n) skipped, ST_BAD_BUCKETS set)
+cudaError_t launch_unpermute(const int* perm, const float* in, float* out, long long n,
+                             long long ld, int rows, int* status, cudaStream_t st);
 
 // diagnostics: acc[0] += 0.5 sum E^2, acc[1] += 0.5 sum B^2
 cudaError_t launch_field_energy(const GridDev& g, const float* F, double* acc, cudaStream_t st);
@@ -274,20 +284,27 @@ struct AdjSpecies {
   const float* u;         // [3][ld]
   float* xbar;            // [D][ld] gradient of the position (in: after, out: before)
   float* ubar;            // [3][ld] gradient of u
+  const int* tstart;      // sort-bin starts of the tile grouping, or null (global pass only)
+  int* dlist;             // particles the tile pass deferred to the global pass
 };
 struct AdjParams {
   GridDev g;
+  TileDev t;        // the tiling the particles were grouped by
+  int splits;       // blocks per tile
   const float* F1;  // forward E and the B of the first half step (9-plane layout)
   float* A;         // adjoint planes: Ebar, Bbar, Jbar
   FastDiv div0, div1;  // by n0 and n1: cell -> (i, j, k)
   int nspecies;
+  int* dcount;      // [nspecies] entries of the deferred lists
   AdjSpecies sp[kMaxSpecies];
 };
 // Bbar += c curl+ Ebar, Jbar = -Ebar (adjoint of the E update with -J)
 cudaError_t launch_adj_e(const GridDev& g, float* A, cudaStream_t st);
 // Ebar -= (c/2) curl- Bbar (adjoint of a B half step)
 cudaError_t launch_adj_b_half(const GridDev& g, float* A, cudaStream_t st);
-// adjoint of gather + Boris + move + ZigZag for every particle
+// adjoint of gather + Boris + move + ZigZag for every particle: the tile pass
+// where every species gives its tile grouping (then the deferred ones through
+// global memory), else all through global memory
 cudaError_t launch_adj_particles(const AdjParams& P, cudaStream_t st);
 
 }  // namespace pic

@@ -194,7 +194,8 @@ template <int D>
 __global__ void k_tile_scatter(const SortParams P, const int* __restrict__ cell,
                                const float* __restrict__ off, const float* __restrict__ u,
                                long long n, long long ld, int* cursor, int* __restrict__ cell_out,
-                               float* __restrict__ off_out, float* __restrict__ u_out) {
+                               float* __restrict__ off_out, float* __restrict__ u_out,
+                               int* __restrict__ perm) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
     const long long p = base + threadIdx.x;
@@ -208,6 +209,7 @@ __global__ void k_tile_scatter(const SortParams P, const int* __restrict__ cell,
       for (int d = 0; d < D; ++d) off_out[d * ld + q] = off[d * ld + p];
 #pragma unroll
       for (int a = 0; a < 3; ++a) u_out[a * ld + q] = u[a * ld + p];
+      if (perm) perm[q] = (int)p;  // the slot the particle held before the sort
     }
   }
 }
@@ -266,15 +268,63 @@ cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* curs
 
 cudaError_t launch_tile_scatter(const SortParams& P, const int* cell, const float* off,
                                 const float* u, long long n, long long ld, int* cursor,
-                                int* cell_out, float* off_out, float* u_out, cudaStream_t st) {
+                                int* cell_out, float* off_out, float* u_out, cudaStream_t st,
+                                int* perm) {
   if (n == 0) return cudaSuccess;
   const unsigned nb = blocks_for(n);
   switch (P.g.dim) {
-    case 1: k_tile_scatter<1><<<nb, 256, 0, st>>>(P, cell, off, u, n, ld, cursor, cell_out, off_out, u_out); break;
-    case 2: k_tile_scatter<2><<<nb, 256, 0, st>>>(P, cell, off, u, n, ld, cursor, cell_out, off_out, u_out); break;
-    case 3: k_tile_scatter<3><<<nb, 256, 0, st>>>(P, cell, off, u, n, ld, cursor, cell_out, off_out, u_out); break;
+    case 1: k_tile_scatter<1><<<nb, 256, 0, st>>>(P, cell, off, u, n, ld, cursor, cell_out, off_out, u_out, perm); break;
+    case 2: k_tile_scatter<2><<<nb, 256, 0, st>>>(P, cell, off, u, n, ld, cursor, cell_out, off_out, u_out, perm); break;
+    case 3: k_tile_scatter<3><<<nb, 256, 0, st>>>(P, cell, off, u, n, ld, cursor, cell_out, off_out, u_out, perm); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+// Bucket starts handed in from outside: one block checks that they run from
+// 0 to n without decreasing; if not, every start but the last becomes 0 (one
+// bucket: the last tile's blocks take every particle, all through the stray
+// path) and the status word says so.
+__global__ void k_check_buckets(int* __restrict__ t, long long nb, long long n, int* status) {
+  bool bad = threadIdx.x == 0 && (t[0] != 0 || t[nb] != n);
+  for (long long i = threadIdx.x; i < nb; i += blockDim.x) bad |= t[i] > t[i + 1];
+  if (!__syncthreads_or(bad)) return;
+  for (long long i = threadIdx.x; i < nb; i += blockDim.x) t[i] = 0;
+  if (threadIdx.x == 0) {
+    t[nb] = (int)n;
+    atomicOr(status, ST_BAD_BUCKETS);
+  }
+}
+
+cudaError_t launch_check_buckets(int* tstart, long long nb, long long n, int* status,
+                                 cudaStream_t st) {
+  k_check_buckets<<<1, 1024, 0, st>>>(tstart, nb, n, status);
+  return cudaGetLastError();
+}
+
+// Adjoint of a sort's permutation: the gradient rows of the particle now in
+// slot i go to the slot it held before the sort, perm[i] (out[perm[i]] =
+// in[i] on each of the `rows` rows of length ld).  An entry outside [0, n)
+// is skipped and reported (ST_BAD_BUCKETS): the permutation came from the
+// caller.
+__global__ void k_unpermute(const int* __restrict__ perm, const float* __restrict__ in,
+                            float* __restrict__ out, long long n, long long ld, int rows,
+                            int* status) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const long long q = perm[i];
+    if (q < 0 || q >= n) {
+      atomicOr(status, ST_BAD_BUCKETS);
+      continue;
+    }
+    for (int r = 0; r < rows; ++r) out[r * ld + q] = in[r * ld + i];
+  }
+}
+
+cudaError_t launch_unpermute(const int* perm, const float* in, float* out, long long n,
+                             long long ld, int rows, int* status, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_unpermute<<<blocks_for(n), 256, 0, st>>>(perm, in, out, n, ld, rows, status);
   return cudaGetLastError();
 }
 

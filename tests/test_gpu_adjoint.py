@@ -75,6 +75,109 @@ def test_adjoint_step_matches_oracle(dim, passes):
     sim.close()
 
 
+@pytest.mark.parametrize("dim,passes", [(1, 0), (2, 0), (2, 2), (3, 0), (3, 1)])
+def test_adjoint_tile_pass_matches_oracle_and_sort_record_permutes(dim, passes):
+    """The tile pass of pic_adjoint_step (particles grouped by
+    pic_sort_record, then moved 3 steps so that some left their tile's window
+    and go through the deferred global pass) against the oracle's adjoint
+    step; pic_sort_record's permutation against the particles before and
+    after the sort, bit for bit; pic_adjoint_unsort as the inverse
+    permutation of gradient rows."""
+    import torch
+
+    from paper_1906_06306_gb300 import binding as B
+
+    sim, rs = _random_sim(dim, 400 + 10 * dim + passes, passes)
+    sim.set_tuning(tile=[4, 4, 4], halo=1)
+    sim.step(2)
+    before = [(d["cell"].clone(), d["off"].clone(), d["u"].clone()) for d in sim.species]
+    nb = B.pic_sort_bins(sim.ctx)
+    counts = sim.counts()
+    perm = [torch.empty(n, dtype=torch.int32, device=sim.device) for n in counts]
+    tst = [torch.empty(nb + 1, dtype=torch.int32, device=sim.device) for _ in counts]
+    B.pic_sort_record(sim.ctx, [p.data_ptr() for p in perm], [t.data_ptr() for t in tst])
+    torch.cuda.synchronize()
+    for d, (c0, o0, u0), p, t, n in zip(sim.species, before, perm, tst, counts):
+        pl = p.long()
+        assert torch.equal(torch.sort(pl).values, torch.arange(n, device=sim.device))
+        assert torch.equal(d["cell"][:n], c0[pl])
+        assert torch.equal(d["off"][:, :n], o0[:, pl])
+        assert torch.equal(d["u"][:, :n], u0[:, pl])
+        assert int(t[0]) == 0 and int(t[-1]) == n and bool((t[1:] >= t[:-1]).all())
+    sim.step(3)
+    g, F, osp, _ = oracle_from_sim(sim)
+    shape = F.shape[1:]
+    A = rs.normal(size=(9,) + shape).astype(np.float32)
+    A[6:9] = 0.0
+    xb = [rs.normal(size=(dim, s.n)).astype(np.float32) for s in osp]
+    ub = [rs.normal(size=(3, s.n)).astype(np.float32) for s in osp]
+    At = torch.from_numpy(A).cuda()
+
+    def rows(a, d):
+        r = torch.zeros((a.shape[0], d["cap"]), dtype=torch.float32)
+        r[:, : a.shape[1]] = torch.from_numpy(a)
+        return r.cuda()
+
+    xbt = [rows(x, d) for x, d in zip(xb, sim.species)]
+    ubt = [rows(u, d) for u, d in zip(ub, sim.species)]
+    Fw = sim.fields.clone()
+    asp = [B.pic_adjoint_species(d["cell"].data_ptr(), d["off"].data_ptr(), d["u"].data_ptr(),
+                                 x.data_ptr(), u.data_ptr(), t.data_ptr())
+           for d, x, u, t in zip(sim.species, xbt, ubt, tst)]
+    B.pic_adjoint_step(sim.ctx, Fw.data_ptr(), asp, At.data_ptr())
+    sim.check()
+    A64 = A.astype(np.float64)
+    xb64 = [np.zeros((3, s.n)) for s in osp]
+    for a, x in zip(xb64, xb):
+        a[:dim] = x
+    ub64 = [u.astype(np.float64) for u in ub]
+    oracle.adj_step(g, F, osp, xb64, ub64, A64, passes=passes)
+    Ag = At.cpu().numpy()
+    assert np.abs(Ag[6:9]).max() == 0.0
+    assert _rel(Ag[0:6], A64[0:6]) < 2e-5
+    for xg, xo, ug, uo in zip(xbt, xb64, ubt, ub64):
+        n = uo.shape[1]
+        assert _rel(xg.cpu().numpy()[:, :n], xo[:dim]) < 2e-5
+        assert _rel(ug.cpu().numpy()[:, :n], uo) < 2e-5
+    # back through the sort: row entry i goes to slot perm[i]
+    xs = [x.clone() for x in xbt]
+    us = [u.clone() for u in ubt]
+    B.pic_adjoint_unsort(sim.ctx, [p.data_ptr() for p in perm], asp)
+    torch.cuda.synchronize()
+    for x0, u0, x1, u1, p, n in zip(xs, us, xbt, ubt, perm, counts):
+        pl = p.long()
+        assert torch.equal(x1[:, pl], x0[:, :n])
+        assert torch.equal(u1[:, pl], u0[:, :n])
+    sim.close()
+
+
+def test_sort_assume_replaces_bucket_starts_that_are_not_a_partition():
+    """pic_sort_assume with starts that decrease: the context falls back to
+    one bucket (steps stay correct through the stray path) and pic_check
+    reports it once."""
+    import torch
+
+    from paper_1906_06306_gb300 import PicError
+    from paper_1906_06306_gb300 import binding as B
+
+    sim, _ = _random_sim(2, 77, 0)
+    twin, _ = _random_sim(2, 77, 0)
+    nb = B.pic_sort_bins(sim.ctx)
+    bad = [torch.arange(nb + 1, 0, -1, dtype=torch.int32, device=sim.device) for _ in sim.species]
+    B.pic_sort_assume(sim.ctx, [t.data_ptr() for t in bad])
+    with pytest.raises(PicError) as ei:
+        sim.check()
+    assert ei.value.status == 5 and "bucket" in str(ei.value)
+    sim.check()
+    sim.step(3)
+    twin.step(3)
+    sim.check()
+    Fa, Fb = sim.download()[0], twin.download()[0]
+    np.testing.assert_allclose(Fa, Fb, rtol=0, atol=1e-5 * np.abs(Fb).max())
+    sim.close()
+    twin.close()
+
+
 def _problem(nsteps=12, k=5):
     from paper_1906_06306_gb300 import Simulation
     from paper_1906_06306_gb300.adjoint import MagneticEnergyProblem
@@ -104,13 +207,20 @@ def test_magnetic_energy_gradient_matches_oracle_and_differences():
     prob, mf, amps = _problem()
     sim = prob.sim
     a = torch.tensor(amps, device=sim.device)
-    loss = prob.run(a, prob.u0())
+    u0 = prob.u0()
+    loss = prob.run(a, u0)
     g_a, g_u = prob.gradient()
-    F0 = prob.adj.ckpt[0][0].cpu().numpy().astype(np.float64)
+    # the initial state in the caller's slot order (the gradient's order; the
+    # checkpoint holds it tile-sorted)
+    F0 = prob.adj.ckpt[0][0][0].cpu().numpy().astype(np.float64)
     g = oracle.Grid(sim.dim, sim.nx, sim.ny, sim.nz, sim.c)
-    sp0 = [oracle.Species(d["q"], d["m"], oracle.positions(g, c.cpu().numpy(), o.cpu().numpy()),
-                          u.cpu().numpy().astype(np.float64))
-           for d, (c, o, u) in zip(sim.species, prob.adj.ckpt[0][1])]
+    u0h = u0.cpu().numpy().astype(np.float64)
+    sp0, k = [], 0
+    for d, (c, o), n in zip(sim.species, prob.base, prob.counts):
+        sp0.append(oracle.Species(d["q"], d["m"],
+                                  oracle.positions(g, c[:n].cpu().numpy(), o[:, :n].cpu().numpy()),
+                                  u0h[:, k:k + n].copy()))
+        k += n
     assert loss == pytest.approx(_oracle_run(g, F0, sp0, 12), rel=1e-5)
 
     def loss_grad(Ff, spf):
