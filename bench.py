@@ -307,8 +307,12 @@ def parity_report(name, steps=10, sample_grid=None):
 
     - independent trajectories (the oracle steps its own FP64 state): the
       largest normwise error of each field component (max |GPU - oracle| /
-      max |oracle|), of J against the largest sum of |ZigZag term| on any
-      current word (oracle.deposit_abs; the scale FP32 sums at), of the
+      max |oracle|; and against the larger of max |oracle| and the running sum
+      over the steps of the current's term scale, the field a step's currents
+      can build, which is what matters where opposite charges cancel the
+      current and the field stays near zero), of J against the largest sum of
+      |ZigZag term| on any current word (oracle.deposit_abs; the scale FP32
+      sums at), of the
       positions (cells) and four-velocities (relative to max(1, |u|)); at the
       last step each energy term and the Gauss-law residual on both sides;
     - the cell decisions where the two runs differ (a particle that ends
@@ -343,6 +347,8 @@ def parity_report(name, steps=10, sample_grid=None):
         oracle.set_wall(wall, i_zero)
     names = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz"]
     ferr = dict.fromkeys(names, 0.0)
+    fscale = dict.fromkeys(names, 0.0)
+    jsum = 0.0
     jterm = dict.fromkeys(names[6:], 0.0)
     jsame = dict.fromkeys(names[6:], 0.0) if not shock else None
     xerr = uerr = 0.0
@@ -357,10 +363,13 @@ def parity_report(name, steps=10, sample_grid=None):
                               terms=terms)
             Fg, spg = sim.download()
             scale = float(terms[-1].max())
+            jsum += scale
             for c, nm in enumerate(names):
                 d = np.abs(Fg[c].astype(np.float64) - F[c])
                 ref = np.abs(F[c]).max()
                 ferr[nm] = max(ferr[nm], float(d.max() / ref) if ref > 0 else float(d.max()))
+                big = max(ref, jsum if c < 6 else scale)
+                fscale[nm] = max(fscale[nm], float(d.max() / big) if big > 0 else float(d.max()))
                 if c >= 6 and scale > 0:
                     jterm[nm] = max(jterm[nm], float(d.max() / scale))
             xg_new = [oracle.positions(g, s["cell"], s["off"]) for s in spg]
@@ -410,14 +419,17 @@ def parity_report(name, steps=10, sample_grid=None):
     out = {"sample": f"{name} on a {box} box ({pl.nparticles} particles at the start), same "
                      f"seed as the workload, {steps} steps from the same FP32 state, no tile sort",
            "tolerance": 1e-5,
-           "fields_max_rel": ferr, "J_vs_term_scale": jterm,
+           "fields_max_rel": ferr, "fields_vs_current_scale": fscale, "J_vs_term_scale": jterm,
            "x_max_abs_cells": xerr, "u_max_rel": uerr, "energy_rel": energy,
            "cell_decision_flips": {"particles_max": flips, "first_at_steps": flip_steps},
            "gauss_max": {"gpu_fp64_reduction": float(en[2 + ns]),
                          "oracle": float(np.abs(res).max()),
                          "one_species_charge_density_max": rho1},
            "note": "energy terms below 1e-6 of the total are compared relative to the total; "
-                   "J_vs_term_scale divides by the largest sum of |ZigZag term| on a word"}
+                   "J_vs_term_scale divides by the largest sum of |ZigZag term| on a word; "
+                   "fields_vs_current_scale divides E and B by the larger of their maximum "
+                   "and the running sum of that term scale over the steps, J by the larger "
+                   "of its maximum and the step's term scale"}
     if jsame is not None:
         out["J_same_moves_vs_term_scale"] = jsame
     return out
