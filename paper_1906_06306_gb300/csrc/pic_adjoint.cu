@@ -266,8 +266,8 @@ __device__ __forceinline__ void segment_adj(const AB& Ab, const int* I, float q,
 // and gather are reversed; xbar and ubar of p are updated in place and the
 // field adjoints added through Ab.
 template <int D, class AF, class AB>
-__device__ __forceinline__ void adj_particle(const AF& F, const AB& Ab, const AdjSpecies& S,
-                                             long long p, const int* b, float c) {
+__device__ __forceinline__ float adj_particle(const AF& F, const AB& Ab, const AdjSpecies& S,
+                                              long long p, const int* b, float c) {
   const long long ld = S.ld;
   float o1[3] = {0.f, 0.f, 0.f}, u[3];
 #pragma unroll
@@ -353,6 +353,15 @@ __device__ __forceinline__ void adj_particle(const AF& F, const AB& Ab, const Ad
   for (int d = 0; d < D; ++d) S.xbar[d * ld + p] = xb[d];
 #pragma unroll
   for (int a = 0; a < 3; ++a) S.ubar[a * ld + p] = ub[a];
+  if (!AB::kAdds) {  // the E and B adjoints of the particle, kept for the deposit pass
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      S.eb[a * ld + p] = eb[a];
+      S.eb[(3 + a) * ld + p] = bb[a];
+    }
+  }
+  return fmaxf(fmaxf(fmaxf(fabsf(eb[0]), fabsf(eb[1])), fmaxf(fabsf(eb[2]), fabsf(bb[0]))),
+               fmaxf(fabsf(bb[1]), fabsf(bb[2])));
 }
 
 // The lattice cell (i, j, k) of a linear cell index.
@@ -380,91 +389,209 @@ __global__ void __launch_bounds__(256) k_adj_particles(const AdjParams P, int de
       if (cell < 0 || (long long)cell >= P.g.plane) continue;
       int b[3];
       cell_ijk(P, cell, b);
-      adj_particle<D>(F, Ab, S, p, b, c);
+      (void)adj_particle<D>(F, Ab, S, p, b, c);
     }
   }
 }
 
 // The tile window of the adjoint pass in shared memory, window-local
-// coordinates: planes 0..5 forward E and B1, 6..8 the current adjoint (read),
-// 9..14 the sums of the E and B adjoints of the block's particles.  One
-// accessor serves as both the forward fields and the adjoint planes.
+// coordinates: planes 0..5 forward E and B1, 6..8 the current adjoint.  One
+// accessor serves as both the forward fields and the adjoint planes; it adds
+// nothing (kAdds false): the particles' E and B adjoints are recorded and
+// summed by the deposit pass.
 struct AdjWin {
-  float* S;
+  static constexpr bool kAdds = false;
+  const float* S;
   int W0, W01, ws;
   __device__ __forceinline__ int at(int i, int j, int k) const { return i + W0 * j + W01 * k; }
   __device__ __forceinline__ float ld(int comp, int i, int j, int k) const {
     return S[comp * ws + at(i, j, k)];
   }
-  __device__ __forceinline__ void add(int comp, int i, int j, int k, float v) const {
-    atomicAdd(&S[(9 + comp) * ws + at(i, j, k)], v);
-  }
+  __device__ __forceinline__ void add(int, int, int, int, float) const {}
 };
 
-// Particles grouped by tile: one block per (tile, split) runs its share of
-// each species' bucket against the staged window; a particle whose stencil
-// (cells b - 1 .. b + 2 on every gridded axis, as in the forward tile kernel)
-// is not inside the window is appended to the species' deferred list.  The
-// block's E and B adjoint sums go to the global planes once per window cell.
+// Window geometry of block (tile, split) of a tile pass.
+struct AdjBlock {
+  int tile, split;
+  int w0[3], W[3];
+};
+template <int D>
+__device__ __forceinline__ AdjBlock adj_block(const AdjParams& P) {
+  const TileDev& t = P.t;
+  AdjBlock B;
+  B.tile = blockIdx.x / P.splits;
+  B.split = blockIdx.x % P.splits;
+  const int tc[3] = {B.tile % t.nt[0], (B.tile / t.nt[0]) % t.nt[1], B.tile / (t.nt[0] * t.nt[1])};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    B.w0[d] = d < D ? tc[d] * t.T[d] - t.H : 0;
+    B.W[d] = d < D ? t.W[d] : 1;
+  }
+  return B;
+}
+// Window-local cell of a particle and whether its stencil (cells b - 1 ..
+// b + 2 on every gridded axis, as in the forward tile kernel) is inside the
+// window; the same test in both tile passes.
+template <int D>
+__device__ __forceinline__ bool adj_in_window(const AdjParams& P, const AdjBlock& B, int cell,
+                                              int* l) {
+  int ijk[3];
+  cell_ijk(P, cell, ijk);
+  bool inwin = true;
+  l[0] = l[1] = l[2] = 0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    l[d] = wrapi(ijk[d] - B.w0[d], P.g.n[d]);
+    inwin &= (unsigned)(l[d] - 1) <= (unsigned)(B.W[d] - 4);
+  }
+  return inwin;
+}
+// This block's share [a, b) of species s's tile bucket.
+__device__ __forceinline__ void adj_share(const AdjParams& P, const AdjSpecies& S,
+                                          const AdjBlock& B, long long& a, long long& b) {
+  const long long lo = S.tstart[B.tile * P.t.nsub], hi = S.tstart[(B.tile + 1) * P.t.nsub];
+  a = lo + (hi - lo) * B.split / P.splits;
+  b = lo + (hi - lo) * (B.split + 1) / P.splits;
+}
+
+// First tile pass (particles grouped by tile): one block per (tile, split)
+// stages its window of E, B1 and the current adjoint and runs its share of
+// each species' bucket through the reverse chain, reading the fields there;
+// instead of adding its E and B adjoints to the lattice it records them (eb,
+// six rows) and the largest of their magnitudes (ebmax, float bits).  A
+// particle whose stencil is not inside the window goes on the species'
+// deferred list for the global pass, which does everything through global
+// memory.
 template <int D>
 __global__ void __launch_bounds__(256, 2) k_adj_tiles(const AdjParams P) {
   extern __shared__ __align__(16) float sm[];
-  const TileDev& t = P.t;
-  const int tile = blockIdx.x / P.splits, split = blockIdx.x % P.splits;
-  const int tc[3] = {tile % t.nt[0], (tile / t.nt[0]) % t.nt[1], tile / (t.nt[0] * t.nt[1])};
-  int w0[3] = {0, 0, 0}, W[3] = {1, 1, 1};
-#pragma unroll
-  for (int d = 0; d < D; ++d) {
-    w0[d] = tc[d] * t.T[d] - t.H;
-    W[d] = t.W[d];
-  }
-  const int wc = t.wcells, ws = t.wstride;
+  const AdjBlock B = adj_block<D>(P);
+  const int wc = P.t.wcells, ws = P.t.wstride;
   const long long plane = P.g.plane;
   const GlobAcc G{P.A, plane, P.g.n[0], P.g.n[1], P.g.n[2]};
   for (int w = threadIdx.x; w < wc; w += blockDim.x) {
-    const int lx = w % W[0], rr = w / W[0], ly = rr % W[1], lz = rr / W[1];
-    const long long gi = G.at(w0[0] + lx, w0[1] + ly, w0[2] + lz);
+    const int lx = w % B.W[0], rr = w / B.W[0], ly = rr % B.W[1], lz = rr / B.W[1];
+    const long long gi = G.at(B.w0[0] + lx, B.w0[1] + ly, B.w0[2] + lz);
 #pragma unroll
     for (int c = 0; c < 6; ++c) sm[c * ws + w] = __ldg(&P.F1[c * plane + gi]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) sm[(6 + a) * ws + w] = P.A[(JX + a) * plane + gi];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) sm[(9 + c) * ws + w] = 0.f;
   }
   __syncthreads();
-  const AdjWin WN{sm, W[0], W[0] * W[1], ws};
+  const AdjWin WN{sm, B.W[0], B.W[0] * B.W[1], ws};
   const float c = P.g.c;
+  float vmax = 0.f;
   for (int s = 0; s < P.nspecies; ++s) {
     const AdjSpecies& S = P.sp[s];
     if (S.n == 0) continue;
-    const long long lo = S.tstart[tile * t.nsub], hi = S.tstart[(tile + 1) * t.nsub];
-    const long long a = lo + (hi - lo) * split / P.splits;
-    const long long b = lo + (hi - lo) * (split + 1) / P.splits;
+    long long a, b;
+    adj_share(P, S, B, a, b);
     for (long long p = a + threadIdx.x; p < b; p += blockDim.x) {
       const int cell = S.cell[p];
       if (cell < 0 || (long long)cell >= plane) continue;
-      int ijk[3], l[3] = {0, 0, 0};
-      cell_ijk(P, cell, ijk);
-      bool inwin = true;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        l[d] = wrapi(ijk[d] - w0[d], P.g.n[d]);
-        inwin &= (unsigned)(l[d] - 1) <= (unsigned)(W[d] - 4);
-      }
-      if (!inwin) {
+      int l[3];
+      if (!adj_in_window<D>(P, B, cell, l)) {
         S.dlist[atomicAdd(&P.dcount[s], 1)] = (int)p;
         continue;
       }
-      adj_particle<D>(WN, WN, S, p, l, c);
+      vmax = fmaxf(vmax, adj_particle<D>(WN, WN, S, p, l, c));
     }
   }
+  // non-negative floats order as their bit patterns
+  const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(vmax));
+  if ((threadIdx.x & 31) == 0 && m != 0u) atomicMax(P.ebmax, m);
+}
+
+// Second tile pass: the recorded E and B adjoints of the in-window particles
+// go back through the transposed gather, weights times the value, onto the
+// window (the same stencils and weights as gather_adj).  The sums are kept
+// as int32 fixed point with the quantum q = 2^(e - 22), 2^e >= the largest
+// recorded magnitude, so that one term is at most 2^22 quanta and a batch of
+// 256 particles (at most one term per particle and word) at most 2^30: native
+// integer atomics, no overflow; after every batch they are folded into an
+// FP32 window, which goes to the lattice once per window cell.  Strays were
+// handled whole by the global pass.
+template <int D>
+__global__ void __launch_bounds__(256) k_adj_deposit(const AdjParams P) {
+  extern __shared__ __align__(16) float sm[];
+  const float vmax = __uint_as_float(*P.ebmax);
+  if (!(vmax > 0.f)) return;  // nothing was recorded (the same for every block)
+  const AdjBlock B = adj_block<D>(P);
+  const int wc = P.t.wcells, ws = P.t.wstride;
+  int* wi = reinterpret_cast<int*>(sm);
+  float* wf = sm + 6 * ws;
+  int e;
+  frexpf(vmax, &e);  // vmax < 2^e
+  const float q = ldexpf(1.0f, e - 22), inv_q = ldexpf(1.0f, 22 - e);
+  for (int w = threadIdx.x; w < 6 * ws; w += blockDim.x) {
+    wi[w] = 0;
+    wf[w] = 0.f;
+  }
   __syncthreads();
+  const int W0 = B.W[0], W01 = B.W[0] * B.W[1];
+  for (int s = 0; s < P.nspecies; ++s) {
+    const AdjSpecies& S = P.sp[s];
+    if (S.n == 0) continue;
+    long long a, b;
+    adj_share(P, S, B, a, b);
+    const long long ld = S.ld;
+    for (long long base = a; base < b; base += blockDim.x) {  // the same count for every thread
+      const long long p = base + threadIdx.x;
+      int l[3];
+      int cell = -1;
+      if (p < b) cell = S.cell[p];
+      if (cell >= 0 && (long long)cell < P.g.plane && adj_in_window<D>(P, B, cell, l)) {
+        float o[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int d = 0; d < D; ++d) o[d] = S.off[d * ld + p];
+        // Ex (1/2,0,0) Ey (0,1/2,0) Ez (0,0,1/2) Bx (0,1/2,1/2) By (1/2,0,1/2) Bz (1/2,1/2,0)
+        constexpr int kStag[6] = {1, 2, 4, 6, 5, 3};
+#pragma unroll
+        for (int comp = 0; comp < 6; ++comp) {
+          const float v = S.eb[comp * ld + p] * inv_q;
+          int i0[3] = {0, 0, 0};
+          float w[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            if (kStag[comp] & (1 << d)) {
+              const bool up = o[d] >= 0.5f;
+              i0[d] = up ? l[d] : l[d] - 1;
+              w[d] = up ? o[d] - 0.5f : o[d] + 0.5f;
+            } else {
+              i0[d] = l[d];
+              w[d] = o[d];
+            }
+          }
+#pragma unroll
+          for (int cn = 0; cn < (1 << D); ++cn) {
+            const int oc[3] = {cn & 1, (cn >> 1) & 1, (cn >> 2) & 1};
+            float wt = 1.f;
+#pragma unroll
+            for (int d = 0; d < D; ++d) wt *= oc[d] ? w[d] : 1.f - w[d];
+            const int at = (i0[0] + oc[0]) + W0 * (i0[1] + oc[1]) + W01 * (i0[2] + oc[2]);
+            atomicAdd(&wi[comp * ws + at], __float2int_rn(wt * v));
+          }
+        }
+      }
+      __syncthreads();
+      for (int w = threadIdx.x; w < 6 * ws; w += blockDim.x) {
+        const int v = wi[w];
+        if (v != 0) {
+          wf[w] += (float)v * q;
+          wi[w] = 0;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const long long plane = P.g.plane;
+  const GlobAcc G{P.A, plane, P.g.n[0], P.g.n[1], P.g.n[2]};
   for (int w = threadIdx.x; w < wc; w += blockDim.x) {
-    const int lx = w % W[0], rr = w / W[0], ly = rr % W[1], lz = rr / W[1];
-    const long long gi = G.at(w0[0] + lx, w0[1] + ly, w0[2] + lz);
+    const int lx = w % B.W[0], rr = w / B.W[0], ly = rr % B.W[1], lz = rr / B.W[1];
+    const long long gi = G.at(B.w0[0] + lx, B.w0[1] + ly, B.w0[2] + lz);
 #pragma unroll
     for (int c2 = 0; c2 < 6; ++c2) {
-      const float v = sm[(9 + c2) * ws + w];
+      const float v = wf[c2 * ws + w];
       if (v != 0.f) atomicAdd(&P.A[c2 * plane + gi], v);
     }
   }
@@ -493,26 +620,36 @@ cudaError_t launch_adj_b_half(const GridDev& g, float* A, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-size_t adj_tile_smem_bytes(const TileDev& t) { return sizeof(float) * 15 * (size_t)t.wstride; }
+// shared memory of the tile passes: 9 float planes (first), 6 int32 + 6 float
+// planes (deposit)
+size_t adj_tile_smem_bytes(const TileDev& t) { return sizeof(float) * 12 * (size_t)t.wstride; }
 
 cudaError_t launch_adj_particles(const AdjParams& P, cudaStream_t st) {
   long long nmax = 0;
   for (int s = 0; s < P.nspecies; ++s) nmax = P.sp[s].n > nmax ? P.sp[s].n : nmax;
   if (nmax == 0) return cudaSuccess;
-  // the tile pass when every species with particles has its tile grouping
-  bool tiled = true;
-  for (int s = 0; s < P.nspecies; ++s) tiled &= P.sp[s].n == 0 || P.sp[s].tstart != nullptr;
+  // the tile passes when every species with particles has its tile grouping
+  // and a record buffer
+  bool tiled = P.ebmax != nullptr;
+  for (int s = 0; s < P.nspecies; ++s)
+    tiled &= P.sp[s].n == 0 || (P.sp[s].tstart != nullptr && P.sp[s].eb != nullptr);
   tiled &= adj_tile_smem_bytes(P.t) <= 200 * 1024;  // else the window does not fit
   const int D = P.g.dim;
   if (tiled) {
     static bool attr[4] = {false, false, false, false};
     const size_t smem = adj_tile_smem_bytes(P.t);
     cudaError_t e = cudaMemsetAsync(P.dcount, 0, sizeof(int) * P.nspecies, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P.ebmax, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     if (!attr[D]) {
-      const void* k = D == 1 ? (const void*)k_adj_tiles<1> : D == 2 ? (const void*)k_adj_tiles<2>
-                                                                     : (const void*)k_adj_tiles<3>;
-      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      const void* k1 = D == 1 ? (const void*)k_adj_tiles<1> : D == 2 ? (const void*)k_adj_tiles<2>
+                                                                      : (const void*)k_adj_tiles<3>;
+      const void* k2 = D == 1   ? (const void*)k_adj_deposit<1>
+                       : D == 2 ? (const void*)k_adj_deposit<2>
+                                : (const void*)k_adj_deposit<3>;
+      e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       if (e != cudaSuccess) return e;
       attr[D] = true;
     }
@@ -522,6 +659,14 @@ cudaError_t launch_adj_particles(const AdjParams& P, cudaStream_t st) {
       case 1: k_adj_tiles<1><<<(unsigned)blocks, 256, smem, st>>>(P); break;
       case 2: k_adj_tiles<2><<<(unsigned)blocks, 256, smem, st>>>(P); break;
       case 3: k_adj_tiles<3><<<(unsigned)blocks, 256, smem, st>>>(P); break;
+      default: return cudaErrorInvalidValue;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    switch (D) {
+      case 1: k_adj_deposit<1><<<(unsigned)blocks, 256, smem, st>>>(P); break;
+      case 2: k_adj_deposit<2><<<(unsigned)blocks, 256, smem, st>>>(P); break;
+      case 3: k_adj_deposit<3><<<(unsigned)blocks, 256, smem, st>>>(P); break;
       default: return cudaErrorInvalidValue;
     }
     e = cudaGetLastError();
