@@ -463,7 +463,7 @@ __device__ __forceinline__ void adj_share(const AdjParams& P, const AdjSpecies& 
 // deferred list for the global pass, which does everything through global
 // memory.
 template <int D>
-__global__ void __launch_bounds__(256, PIC_ADJ_MIN_BLOCKS) k_adj_tiles(const AdjParams P) {
+__global__ void __launch_bounds__(256, 2) k_adj_tiles(const AdjParams P) {
   extern __shared__ __align__(16) float sm[];
   const AdjBlock B = adj_block<D>(P);
   const int wc = P.t.wcells, ws = P.t.wstride;
@@ -537,27 +537,13 @@ __global__ void __launch_bounds__(256) k_adj_deposit(const AdjParams P) {
     const long long ld = S.ld;
     for (long long base = a; base < b; base += blockDim.x) {  // the same count for every thread
       const long long p = base + threadIdx.x;
-      int l[3] = {0, 0, 0};
+      int l[3];
       int cell = -1;
       if (p < b) cell = S.cell[p];
-      const bool ok = cell >= 0 && (long long)cell < P.g.plane && adj_in_window<D>(P, B, cell, l);
-      float o[3] = {0.f, 0.f, 0.f};
-      if (ok) {
+      if (cell >= 0 && (long long)cell < P.g.plane && adj_in_window<D>(P, B, cell, l)) {
+        float o[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int d = 0; d < D; ++d) o[d] = S.off[d * ld + p];
-      }
-      // Lanes whose particles share the cell and the half of it on every axis
-      // add to the same words: their terms are summed across the lanes
-      // (integer warp reduction) and one of them adds the sum.  Particles of
-      // a freshly sorted bucket often sit in one cell, where lanes adding to
-      // one word one after another would serialise.
-      const unsigned act = __ballot_sync(0xffffffffu, ok);
-      if (ok) {
-        unsigned long long key = (unsigned long long)(unsigned)cell << 3;
-#pragma unroll
-        for (int d = 0; d < D; ++d) key |= (unsigned long long)(o[d] >= 0.5f) << d;
-        const unsigned peers = __match_any_sync(act, key);
-        const bool leader = (threadIdx.x & 31) == __ffs(peers) - 1;
         // Ex (1/2,0,0) Ey (0,1/2,0) Ez (0,0,1/2) Bx (0,1/2,1/2) By (1/2,0,1/2) Bz (1/2,1/2,0)
         constexpr int kStag[6] = {1, 2, 4, 6, 5, 3};
 #pragma unroll
@@ -583,9 +569,7 @@ __global__ void __launch_bounds__(256) k_adj_deposit(const AdjParams P) {
 #pragma unroll
             for (int d = 0; d < D; ++d) wt *= oc[d] ? w[d] : 1.f - w[d];
             const int at = (i0[0] + oc[0]) + W0 * (i0[1] + oc[1]) + W01 * (i0[2] + oc[2]);
-            // at most 32 terms of at most 2^22 quanta: no overflow
-            const int sum = __reduce_add_sync(peers, __float2int_rn(wt * v));
-            if (leader) atomicAdd(&wi[comp * ws + at], sum);
+            atomicAdd(&wi[comp * ws + at], __float2int_rn(wt * v));
           }
         }
       }

@@ -66,10 +66,6 @@ constexpr bool kFoldGlobal = D == 3 && PIC_X3PAIR != 0;
 #ifndef PIC_BULK_FILTER
 #define PIC_BULK_FILTER 1
 #endif
-// Resident blocks per SM the adjoint's first tile pass is compiled for.
-#ifndef PIC_ADJ_MIN_BLOCKS
-#define PIC_ADJ_MIN_BLOCKS 2
-#endif
 // pic_step(n) replays whole sort cycles from a captured CUDA graph.
 #ifndef PIC_STEP_GRAPHS
 #define PIC_STEP_GRAPHS 1
