@@ -13,9 +13,9 @@
 // taken from the forward step).  Particles grouped by tile (given the bucket
 // starts of the sort that grouped them) go through k_adj_tiles: a block stages
 // its tile window of E, B and the current adjoint in shared memory and sums
-// the field adjoints there, and the particles whose stencil left the window
-// are deferred to the global-memory pass; ungrouped particles all take the
-// global-memory pass.
+// the field adjoints there (int32 fixed point), and the particles whose
+// stencil left the window are deferred to the global-memory pass; ungrouped
+// particles all take the global-memory pass.
 #include <cmath>
 
 #include "pic_kernels.h"
@@ -266,8 +266,9 @@ __device__ __forceinline__ void segment_adj(const AB& Ab, const int* I, float q,
 // and gather are reversed; xbar and ubar of p are updated in place and the
 // field adjoints added through Ab.
 template <int D, class AF, class AB>
-__device__ __forceinline__ float adj_particle(const AF& F, const AB& Ab, const AdjSpecies& S,
-                                              long long p, const int* b, float c) {
+__device__ __forceinline__ void adj_particle(const AF& F, const AB& Ab, const AdjSpecies& S,
+                                             long long p, const int* b, float c,
+                                             float* ebb = nullptr) {
   const long long ld = S.ld;
   float o1[3] = {0.f, 0.f, 0.f}, u[3];
 #pragma unroll
@@ -353,15 +354,13 @@ __device__ __forceinline__ float adj_particle(const AF& F, const AB& Ab, const A
   for (int d = 0; d < D; ++d) S.xbar[d * ld + p] = xb[d];
 #pragma unroll
   for (int a = 0; a < 3; ++a) S.ubar[a * ld + p] = ub[a];
-  if (!AB::kAdds) {  // the E and B adjoints of the particle, kept for the deposit pass
+  if (ebb) {  // the E and B adjoints of the particle, for the caller to add
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      S.eb[a * ld + p] = eb[a];
-      S.eb[(3 + a) * ld + p] = bb[a];
+      ebb[a] = eb[a];
+      ebb[3 + a] = bb[a];
     }
   }
-  return fmaxf(fmaxf(fmaxf(fabsf(eb[0]), fabsf(eb[1])), fmaxf(fabsf(eb[2]), fabsf(bb[0]))),
-               fmaxf(fabsf(bb[1]), fabsf(bb[2])));
 }
 
 // The lattice cell (i, j, k) of a linear cell index.
@@ -389,7 +388,7 @@ __global__ void __launch_bounds__(256) k_adj_particles(const AdjParams P, int de
       if (cell < 0 || (long long)cell >= P.g.plane) continue;
       int b[3];
       cell_ijk(P, cell, b);
-      (void)adj_particle<D>(F, Ab, S, p, b, c);
+      adj_particle<D>(F, Ab, S, p, b, c);
     }
   }
 }
@@ -397,10 +396,9 @@ __global__ void __launch_bounds__(256) k_adj_particles(const AdjParams P, int de
 // The tile window of the adjoint pass in shared memory, window-local
 // coordinates: planes 0..5 forward E and B1, 6..8 the current adjoint.  One
 // accessor serves as both the forward fields and the adjoint planes; it adds
-// nothing (kAdds false): the particles' E and B adjoints are recorded and
-// summed by the deposit pass.
+// nothing: the tile pass takes each particle's E and B adjoints and adds
+// them itself.
 struct AdjWin {
-  static constexpr bool kAdds = false;
   const float* S;
   int W0, W01, ws;
   __device__ __forceinline__ int at(int i, int j, int k) const { return i + W0 * j + W01 * k; }
@@ -454,21 +452,29 @@ __device__ __forceinline__ void adj_share(const AdjParams& P, const AdjSpecies& 
   b = lo + (hi - lo) * (B.split + 1) / P.splits;
 }
 
-// First tile pass (particles grouped by tile): one block per (tile, split)
+// The tile pass (particles grouped by tile): one block per (tile, split)
 // stages its window of E, B1 and the current adjoint and runs its share of
-// each species' bucket through the reverse chain, reading the fields there;
-// instead of adding its E and B adjoints to the lattice it records them (eb,
-// six rows) and the largest of their magnitudes (ebmax, float bits).  A
-// particle whose stencil is not inside the window goes on the species'
-// deferred list for the global pass, which does everything through global
-// memory.
+// each species' bucket, in batches of 256, through the reverse chain, reading
+// the fields there.  The particles' E and B adjoints go back through the
+// transposed gather (weights times the value, the stencils of gather_adj)
+// onto the window as int32 fixed point: native integer shared-memory atomics
+// (an FP32 shared atomic is a retry loop, which lanes sharing a word turn into
+// a queue).  The quantum is set per batch from the batch's largest magnitude
+// M (a block reduction): q = 2^(e - 22) with M < 2^e, so one term is below
+// 2^22 quanta and a batch (at most one term per particle and word) below
+// 2^30; after every batch the integers are folded into an FP32 window, which
+// goes to the lattice once per window cell.  A particle whose stencil is not
+// inside the window goes on the species' deferred list for the global pass.
 template <int D>
 __global__ void __launch_bounds__(256, 2) k_adj_tiles(const AdjParams P) {
   extern __shared__ __align__(16) float sm[];
+  __shared__ unsigned wmax[8];  // per warp of the block (256 threads)
   const AdjBlock B = adj_block<D>(P);
   const int wc = P.t.wcells, ws = P.t.wstride;
   const long long plane = P.g.plane;
   const GlobAcc G{P.A, plane, P.g.n[0], P.g.n[1], P.g.n[2]};
+  int* wi = reinterpret_cast<int*>(sm + 9 * ws);  // 6 planes of fixed-point sums
+  float* wf = sm + 15 * ws;                       // 6 planes of their FP32 folds
   for (int w = threadIdx.x; w < wc; w += blockDim.x) {
     const int lx = w % B.W[0], rr = w / B.W[0], ly = rr % B.W[1], lz = rr / B.W[1];
     const long long gi = G.at(B.w0[0] + lx, B.w0[1] + ly, B.w0[2] + lz);
@@ -477,58 +483,14 @@ __global__ void __launch_bounds__(256, 2) k_adj_tiles(const AdjParams P) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) sm[(6 + a) * ws + w] = P.A[(JX + a) * plane + gi];
   }
-  __syncthreads();
-  const AdjWin WN{sm, B.W[0], B.W[0] * B.W[1], ws};
-  const float c = P.g.c;
-  float vmax = 0.f;
-  for (int s = 0; s < P.nspecies; ++s) {
-    const AdjSpecies& S = P.sp[s];
-    if (S.n == 0) continue;
-    long long a, b;
-    adj_share(P, S, B, a, b);
-    for (long long p = a + threadIdx.x; p < b; p += blockDim.x) {
-      const int cell = S.cell[p];
-      if (cell < 0 || (long long)cell >= plane) continue;
-      int l[3];
-      if (!adj_in_window<D>(P, B, cell, l)) {
-        S.dlist[atomicAdd(&P.dcount[s], 1)] = (int)p;
-        continue;
-      }
-      vmax = fmaxf(vmax, adj_particle<D>(WN, WN, S, p, l, c));
-    }
-  }
-  // non-negative floats order as their bit patterns
-  const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(vmax));
-  if ((threadIdx.x & 31) == 0 && m != 0u) atomicMax(P.ebmax, m);
-}
-
-// Second tile pass: the recorded E and B adjoints of the in-window particles
-// go back through the transposed gather, weights times the value, onto the
-// window (the same stencils and weights as gather_adj).  The sums are kept
-// as int32 fixed point with the quantum q = 2^(e - 22), 2^e >= the largest
-// recorded magnitude, so that one term is at most 2^22 quanta and a batch of
-// 256 particles (at most one term per particle and word) at most 2^30: native
-// integer atomics, no overflow; after every batch they are folded into an
-// FP32 window, which goes to the lattice once per window cell.  Strays were
-// handled whole by the global pass.
-template <int D>
-__global__ void __launch_bounds__(256) k_adj_deposit(const AdjParams P) {
-  extern __shared__ __align__(16) float sm[];
-  const float vmax = __uint_as_float(*P.ebmax);
-  if (!(vmax > 0.f)) return;  // nothing was recorded (the same for every block)
-  const AdjBlock B = adj_block<D>(P);
-  const int wc = P.t.wcells, ws = P.t.wstride;
-  int* wi = reinterpret_cast<int*>(sm);
-  float* wf = sm + 6 * ws;
-  int e;
-  frexpf(vmax, &e);  // vmax < 2^e
-  const float q = ldexpf(1.0f, e - 22), inv_q = ldexpf(1.0f, 22 - e);
   for (int w = threadIdx.x; w < 6 * ws; w += blockDim.x) {
     wi[w] = 0;
     wf[w] = 0.f;
   }
   __syncthreads();
+  const AdjWin WN{sm, B.W[0], B.W[0] * B.W[1], ws};
   const int W0 = B.W[0], W01 = B.W[0] * B.W[1];
+  const float c = P.g.c;
   for (int s = 0; s < P.nspecies; ++s) {
     const AdjSpecies& S = P.sp[s];
     if (S.n == 0) continue;
@@ -537,10 +499,35 @@ __global__ void __launch_bounds__(256) k_adj_deposit(const AdjParams P) {
     const long long ld = S.ld;
     for (long long base = a; base < b; base += blockDim.x) {  // the same count for every thread
       const long long p = base + threadIdx.x;
-      int l[3];
-      int cell = -1;
-      if (p < b) cell = S.cell[p];
-      if (cell >= 0 && (long long)cell < P.g.plane && adj_in_window<D>(P, B, cell, l)) {
+      float ebb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      int l[3] = {0, 0, 0};
+      bool mine = false;
+      if (p < b) {
+        const int cell = S.cell[p];
+        if (cell >= 0 && (long long)cell < plane) {
+          if (adj_in_window<D>(P, B, cell, l)) {
+            adj_particle<D>(WN, WN, S, p, l, c, ebb);
+            mine = true;
+          } else {
+            S.dlist[atomicAdd(&P.dcount[s], 1)] = (int)p;
+          }
+        }
+      }
+      // the batch's largest magnitude (non-negative floats order as their bits)
+      float m = 0.f;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) m = fmaxf(m, fabsf(ebb[k]));
+      const unsigned mw = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+      if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mw;
+      __syncthreads();
+      unsigned mb = 0u;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) mb = max(mb, wmax[k]);
+      const float M = __uint_as_float(mb);
+      int e = 0;
+      frexpf(M, &e);  // M < 2^e
+      const float q = ldexpf(1.0f, e - 22), inv_q = ldexpf(1.0f, 22 - e);
+      if (mine) {
         float o[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int d = 0; d < D; ++d) o[d] = S.off[d * ld + p];
@@ -548,7 +535,7 @@ __global__ void __launch_bounds__(256) k_adj_deposit(const AdjParams P) {
         constexpr int kStag[6] = {1, 2, 4, 6, 5, 3};
 #pragma unroll
         for (int comp = 0; comp < 6; ++comp) {
-          const float v = S.eb[comp * ld + p] * inv_q;
+          const float v = ebb[comp] * inv_q;
           int i0[3] = {0, 0, 0};
           float w[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -574,18 +561,18 @@ __global__ void __launch_bounds__(256) k_adj_deposit(const AdjParams P) {
         }
       }
       __syncthreads();
-      for (int w = threadIdx.x; w < 6 * ws; w += blockDim.x) {
-        const int v = wi[w];
-        if (v != 0) {
-          wf[w] += (float)v * q;
-          wi[w] = 0;
+      if (mb != 0u) {
+        for (int w = threadIdx.x; w < 6 * ws; w += blockDim.x) {
+          const int v = wi[w];
+          if (v != 0) {
+            wf[w] += (float)v * q;
+            wi[w] = 0;
+          }
         }
       }
       __syncthreads();
     }
   }
-  const long long plane = P.g.plane;
-  const GlobAcc G{P.A, plane, P.g.n[0], P.g.n[1], P.g.n[2]};
   for (int w = threadIdx.x; w < wc; w += blockDim.x) {
     const int lx = w % B.W[0], rr = w / B.W[0], ly = rr % B.W[1], lz = rr / B.W[1];
     const long long gi = G.at(B.w0[0] + lx, B.w0[1] + ly, B.w0[2] + lz);
@@ -620,36 +607,28 @@ cudaError_t launch_adj_b_half(const GridDev& g, float* A, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// shared memory of the tile passes: 9 float planes (first), 6 int32 + 6 float
-// planes (deposit)
-size_t adj_tile_smem_bytes(const TileDev& t) { return sizeof(float) * 12 * (size_t)t.wstride; }
+// shared memory of the tile pass: 9 float planes (E, B1, current adjoint),
+// 6 int32 and 6 float planes (the E and B adjoint sums)
+size_t adj_tile_smem_bytes(const TileDev& t) { return sizeof(float) * 21 * (size_t)t.wstride; }
 
 cudaError_t launch_adj_particles(const AdjParams& P, cudaStream_t st) {
   long long nmax = 0;
   for (int s = 0; s < P.nspecies; ++s) nmax = P.sp[s].n > nmax ? P.sp[s].n : nmax;
   if (nmax == 0) return cudaSuccess;
-  // the tile passes when every species with particles has its tile grouping
-  // and a record buffer
-  bool tiled = P.ebmax != nullptr;
-  for (int s = 0; s < P.nspecies; ++s)
-    tiled &= P.sp[s].n == 0 || (P.sp[s].tstart != nullptr && P.sp[s].eb != nullptr);
+  // the tile pass when every species with particles has its tile grouping
+  bool tiled = true;
+  for (int s = 0; s < P.nspecies; ++s) tiled &= P.sp[s].n == 0 || P.sp[s].tstart != nullptr;
   tiled &= adj_tile_smem_bytes(P.t) <= 200 * 1024;  // else the window does not fit
   const int D = P.g.dim;
   if (tiled) {
     static bool attr[4] = {false, false, false, false};
     const size_t smem = adj_tile_smem_bytes(P.t);
     cudaError_t e = cudaMemsetAsync(P.dcount, 0, sizeof(int) * P.nspecies, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(P.ebmax, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     if (!attr[D]) {
       const void* k1 = D == 1 ? (const void*)k_adj_tiles<1> : D == 2 ? (const void*)k_adj_tiles<2>
                                                                       : (const void*)k_adj_tiles<3>;
-      const void* k2 = D == 1   ? (const void*)k_adj_deposit<1>
-                       : D == 2 ? (const void*)k_adj_deposit<2>
-                                : (const void*)k_adj_deposit<3>;
       e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       if (e != cudaSuccess) return e;
       attr[D] = true;
     }
@@ -659,14 +638,6 @@ cudaError_t launch_adj_particles(const AdjParams& P, cudaStream_t st) {
       case 1: k_adj_tiles<1><<<(unsigned)blocks, 256, smem, st>>>(P); break;
       case 2: k_adj_tiles<2><<<(unsigned)blocks, 256, smem, st>>>(P); break;
       case 3: k_adj_tiles<3><<<(unsigned)blocks, 256, smem, st>>>(P); break;
-      default: return cudaErrorInvalidValue;
-    }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    switch (D) {
-      case 1: k_adj_deposit<1><<<(unsigned)blocks, 256, smem, st>>>(P); break;
-      case 2: k_adj_deposit<2><<<(unsigned)blocks, 256, smem, st>>>(P); break;
-      case 3: k_adj_deposit<3><<<(unsigned)blocks, 256, smem, st>>>(P); break;
       default: return cudaErrorInvalidValue;
     }
     e = cudaGetLastError();

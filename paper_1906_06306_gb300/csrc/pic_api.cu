@@ -69,8 +69,6 @@ struct pic_ctx {
   void* d_tmpl = nullptr;                    // template records of every species
   int* d_adj_tstart = nullptr;  // checked copies of the adjoint's bucket starts
   size_t adj_tstart_len = 0;
-  float* d_adj_eb = nullptr;     // the adjoint tile pass's records: 6 rows of cap per species
-  unsigned* d_adj_max = nullptr;  // and their largest magnitude
   int* d_dlist = nullptr;   // particles deferred to the global pass, room for cap[s] per species
   int* d_dcount = nullptr;  // entries per species
   float* d_adjF = nullptr;                   // forward fields of an adjoint step (9 planes)
@@ -150,8 +148,6 @@ void free_all(pic_ctx* ctx) {
   dfree(ctx->d_strays);
   dfree(ctx->d_tmpl);
   dfree(ctx->d_adj_tstart);
-  dfree(ctx->d_adj_eb);
-  dfree(ctx->d_adj_max);
   dfree(ctx->d_dlist);
   dfree(ctx->d_dcount);
   dfree(ctx->d_adjF);
@@ -887,9 +883,6 @@ pic_status pic_adjoint_step(pic_ctx* ctx, const float* fwd_fields, const pic_adj
       PIC_CK(ctx, dalloc(&ctx->d_adj_tstart, need));
       ctx->adj_tstart_len = need;
     }
-    if (!ctx->d_adj_eb) PIC_CK(ctx, dalloc(&ctx->d_adj_eb, 6 * (size_t)total_cap(ctx)));
-    if (!ctx->d_adj_max) PIC_CK(ctx, dalloc(&ctx->d_adj_max, 1));
-    AP.ebmax = ctx->d_adj_max;
   }
   long long o = 0;
   for (int s = 0; s < ctx->ns; ++s) {
@@ -903,7 +896,6 @@ pic_status pic_adjoint_step(pic_ctx* ctx, const float* fwd_fields, const pic_adj
       S.tstart = t;
     }
     S.dlist = ctx->d_dlist + o;
-    S.eb = tiled ? ctx->d_adj_eb + 6 * o : nullptr;
     o += ctx->cap[s];
     S.q = ctx->sp[s].q;
     S.qm = ctx->sp[s].q / ctx->sp[s].m;

@@ -252,7 +252,6 @@ struct SmemJ64 {
 // Global field planes with periodic wrap; indices are lattice indices that may
 // lie up to one period outside [0, n).
 struct GlobAcc {
-  static constexpr bool kAdds = true;  // add() reaches the lattice
   float* F;
   long long plane;
   int n0, n1, n2;

@@ -286,7 +286,6 @@ struct AdjSpecies {
   float* ubar;            // [3][ld] gradient of u
   const int* tstart;      // sort-bin starts of the tile grouping, or null (global pass only)
   int* dlist;             // particles the tile pass deferred to the global pass
-  float* eb;              // [6][ld] E and B adjoints recorded by the first tile pass
 };
 struct AdjParams {
   GridDev g;
@@ -297,7 +296,6 @@ struct AdjParams {
   FastDiv div0, div1;  // by n0 and n1: cell -> (i, j, k)
   int nspecies;
   int* dcount;      // [nspecies] entries of the deferred lists
-  unsigned* ebmax;  // largest recorded E or B adjoint magnitude (float bits)
   AdjSpecies sp[kMaxSpecies];
 };
 // Bbar += c curl+ Ebar, Jbar = -Ebar (adjoint of the E update with -J)
