@@ -1114,14 +1114,24 @@ pic_status pic_step(pic_ctx* ctx, int nsteps) {
     if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
     e = timed(ctx, PIC_KERNEL_PUSH, [&]() { return launch_particles(ctx->grid.dim, 0, P, ctx->st); });
     if (e != cudaSuccess) return cuda_fail(ctx, "gather/push/deposit kernel", e);
-    e = timed(ctx, PIC_KERNEL_BHALF, [&]() { return launch_b_half(ctx->g, ctx->F, 0, ctx->st); });
-    if (e == cudaSuccess) e = wall_bc();
-    if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
-    const pic_status s = do_filter(ctx, ctx->tun.filter_passes);
-    if (s != PIC_OK) return s;
-    e = timed(ctx, PIC_KERNEL_EUPD, [&]() { return launch_e_update(ctx->g, ctx->F, ctx->st); });
-    if (e == cudaSuccess) e = wall_bc();
-    if (e != cudaSuccess) return cuda_fail(ctx, "E update", e);
+    if (!ctx->shock && fields_small_ok(ctx->g)) {
+      // small periodic lattice: the filter (on J) first, then the second B
+      // half step and the E update in one launch (the B half step touches B
+      // only, the filter J only: the order between them does not matter)
+      const pic_status s = do_filter(ctx, ctx->tun.filter_passes);
+      if (s != PIC_OK) return s;
+      e = timed(ctx, PIC_KERNEL_EUPD, [&]() { return launch_fields_small(ctx->g, ctx->F, ctx->st); });
+      if (e != cudaSuccess) return cuda_fail(ctx, "B half step and E update", e);
+    } else {
+      e = timed(ctx, PIC_KERNEL_BHALF, [&]() { return launch_b_half(ctx->g, ctx->F, 0, ctx->st); });
+      if (e == cudaSuccess) e = wall_bc();
+      if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
+      const pic_status s = do_filter(ctx, ctx->tun.filter_passes);
+      if (s != PIC_OK) return s;
+      e = timed(ctx, PIC_KERNEL_EUPD, [&]() { return launch_e_update(ctx->g, ctx->F, ctx->st); });
+      if (e == cudaSuccess) e = wall_bc();
+      if (e != cudaSuccess) return cuda_fail(ctx, "E update", e);
+    }
     if (ctx->shock) {
       if (IP.nruns > 0) {
         e = timed(ctx, PIC_KERNEL_BOUNDARY, [&]() { return launch_inject(IP, ctx->st); });

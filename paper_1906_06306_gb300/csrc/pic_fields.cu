@@ -11,72 +11,103 @@ namespace pic {
 // B -= (c/2) curl+ E (forward differences: B sits half a cell above E), and,
 // when zero_j is set, clear J for the deposit that follows.
 template <int D>
-__global__ void k_b_half(float* __restrict__ F, const GridDev g, float hc, int zero_j) {
+__device__ __forceinline__ void b_half_point(float* __restrict__ F, const GridDev& g, int i, int j,
+                                             int k, float hc, int zero_j) {
   const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const long long P = g.plane;
+  const long long idx = (long long)i + (long long)n0 * (j + (long long)n1 * k);
+  const long long sx = (i + 1 < n0) ? 1 : 1 - n0;
+  const long long sy = (D >= 2) ? ((j + 1 < n1) ? n0 : (long long)n0 * (1 - n1)) : 0;
+  const long long sz = (D >= 3) ? ((k + 1 < n2) ? (long long)n0 * n1 : (long long)n0 * n1 * (1 - n2)) : 0;
+  const float* Ex = F + EX * P;
+  const float* Ey = F + EY * P;
+  const float* Ez = F + EZ * P;
+  const float ex = Ex[idx], ey = Ey[idx], ez = Ez[idx];
+  float cx = 0.f, cy = 0.f, cz = 0.f;
+  cy -= Ez[idx + sx] - ez;
+  cz += Ey[idx + sx] - ey;
+  if (D >= 2) {
+    cx += Ez[idx + sy] - ez;
+    cz -= Ex[idx + sy] - ex;
+  }
+  if (D >= 3) {
+    cx -= Ey[idx + sz] - ey;
+    cy += Ex[idx + sz] - ex;
+  }
+  F[BX * P + idx] = fmaf(-hc, cx, F[BX * P + idx]);
+  F[BY * P + idx] = fmaf(-hc, cy, F[BY * P + idx]);
+  F[BZ * P + idx] = fmaf(-hc, cz, F[BZ * P + idx]);
+  if (zero_j) {
+    F[JX * P + idx] = 0.f;
+    F[JY * P + idx] = 0.f;
+    F[JZ * P + idx] = 0.f;
+  }
+}
+
+template <int D>
+__global__ void k_b_half(float* __restrict__ F, const GridDev g, float hc, int zero_j) {
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n0) return;
-  FOR_ROWS(j, k) {
-    const long long idx = (long long)i + (long long)n0 * (j + (long long)n1 * k);
-    const long long sx = (i + 1 < n0) ? 1 : 1 - n0;
-    const long long sy = (D >= 2) ? ((j + 1 < n1) ? n0 : (long long)n0 * (1 - n1)) : 0;
-    const long long sz = (D >= 3) ? ((k + 1 < n2) ? (long long)n0 * n1 : (long long)n0 * n1 * (1 - n2)) : 0;
-    const float* Ex = F + EX * P;
-    const float* Ey = F + EY * P;
-    const float* Ez = F + EZ * P;
-    const float ex = Ex[idx], ey = Ey[idx], ez = Ez[idx];
-    float cx = 0.f, cy = 0.f, cz = 0.f;
-    cy -= Ez[idx + sx] - ez;
-    cz += Ey[idx + sx] - ey;
-    if (D >= 2) {
-      cx += Ez[idx + sy] - ez;
-      cz -= Ex[idx + sy] - ex;
-    }
-    if (D >= 3) {
-      cx -= Ey[idx + sz] - ey;
-      cy += Ex[idx + sz] - ex;
-    }
-    F[BX * P + idx] = fmaf(-hc, cx, F[BX * P + idx]);
-    F[BY * P + idx] = fmaf(-hc, cy, F[BY * P + idx]);
-    F[BZ * P + idx] = fmaf(-hc, cz, F[BZ * P + idx]);
-    if (zero_j) {
-      F[JX * P + idx] = 0.f;
-      F[JY * P + idx] = 0.f;
-      F[JZ * P + idx] = 0.f;
-    }
-  }
+  FOR_ROWS(j, k) { b_half_point<D>(F, g, i, j, k, hc, zero_j); }
 }
 
 // E += c curl- B - J (backward differences: E sits half a cell below B).
 template <int D>
-__global__ void k_e_update(float* __restrict__ F, const GridDev g, float c) {
+__device__ __forceinline__ void e_update_point(float* __restrict__ F, const GridDev& g, int i,
+                                               int j, int k, float c) {
   const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const long long P = g.plane;
+  const long long idx = (long long)i + (long long)n0 * (j + (long long)n1 * k);
+  const long long sx = (i > 0) ? 1 : 1 - n0;
+  const long long sy = (D >= 2) ? ((j > 0) ? n0 : (long long)n0 * (1 - n1)) : 0;
+  const long long sz = (D >= 3) ? ((k > 0) ? (long long)n0 * n1 : (long long)n0 * n1 * (1 - n2)) : 0;
+  const float* Bx = F + BX * P;
+  const float* By = F + BY * P;
+  const float* Bz = F + BZ * P;
+  const float bx = Bx[idx], by = By[idx], bz = Bz[idx];
+  float cx = 0.f, cy = 0.f, cz = 0.f;
+  cy -= bz - Bz[idx - sx];
+  cz += by - By[idx - sx];
+  if (D >= 2) {
+    cx += bz - Bz[idx - sy];
+    cz -= bx - Bx[idx - sy];
+  }
+  if (D >= 3) {
+    cx -= by - By[idx - sz];
+    cy += bx - Bx[idx - sz];
+  }
+  F[EX * P + idx] = fmaf(c, cx, F[EX * P + idx]) - F[JX * P + idx];
+  F[EY * P + idx] = fmaf(c, cy, F[EY * P + idx]) - F[JY * P + idx];
+  F[EZ * P + idx] = fmaf(c, cz, F[EZ * P + idx]) - F[JZ * P + idx];
+}
+
+template <int D>
+__global__ void k_e_update(float* __restrict__ F, const GridDev g, float c) {
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n0) return;
-  FOR_ROWS(j, k) {
-    const long long idx = (long long)i + (long long)n0 * (j + (long long)n1 * k);
-    const long long sx = (i > 0) ? 1 : 1 - n0;
-    const long long sy = (D >= 2) ? ((j > 0) ? n0 : (long long)n0 * (1 - n1)) : 0;
-    const long long sz = (D >= 3) ? ((k > 0) ? (long long)n0 * n1 : (long long)n0 * n1 * (1 - n2)) : 0;
-    const float* Bx = F + BX * P;
-    const float* By = F + BY * P;
-    const float* Bz = F + BZ * P;
-    const float bx = Bx[idx], by = By[idx], bz = Bz[idx];
-    float cx = 0.f, cy = 0.f, cz = 0.f;
-    cy -= bz - Bz[idx - sx];
-    cz += by - By[idx - sx];
-    if (D >= 2) {
-      cx += bz - Bz[idx - sy];
-      cz -= bx - Bx[idx - sy];
-    }
-    if (D >= 3) {
-      cx -= by - By[idx - sz];
-      cy += bx - Bx[idx - sz];
-    }
-    F[EX * P + idx] = fmaf(c, cx, F[EX * P + idx]) - F[JX * P + idx];
-    F[EY * P + idx] = fmaf(c, cy, F[EY * P + idx]) - F[JY * P + idx];
-    F[EZ * P + idx] = fmaf(c, cz, F[EZ * P + idx]) - F[JZ * P + idx];
+  FOR_ROWS(j, k) { e_update_point<D>(F, g, i, j, k, c); }
+}
+
+// The second B half step and the E update of a small lattice by one block:
+// every point's B half step, a block barrier (which orders the block's
+// global-memory writes before its later reads), every point's E update; the
+// operations of k_b_half and k_e_update point by point, so the same bits.  One
+// launch instead of two where launch latency, not bandwidth, bounds the step.
+template <int D>
+__global__ void __launch_bounds__(1024) k_fields_small(float* __restrict__ F, const GridDev g,
+                                                       float hc, float c) {
+  const int n0 = g.n[0], n1 = g.n[1];
+  const int cells = (int)g.plane;
+  for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+    const int i = t % n0, r = t / n0;
+    b_half_point<D>(F, g, i, r % n1, r / n1, hc, 0);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+    const int i = t % n0, r = t / n0;
+    e_update_point<D>(F, g, i, r % n1, r / n1, c);
   }
 }
 
@@ -766,6 +797,21 @@ cudaError_t launch_b_half(const GridDev& g, float* F, int zero_j, cudaStream_t s
     case 14: k_b_half4<1><<<L.grid, L.threads, 0, st>>>(F, g, hc, zero_j); break;
     case 24: k_b_half4<2><<<L.grid, L.threads, 0, st>>>(F, g, hc, zero_j); break;
     case 34: k_b_half4<3><<<L.grid, L.threads, 0, st>>>(F, g, hc, zero_j); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+bool fields_small_ok(const GridDev& g) {
+  return PIC_SMALL_FIELDS && g.order == 2 && g.plane <= kSmallFieldCells;
+}
+
+cudaError_t launch_fields_small(const GridDev& g, float* F, cudaStream_t st) {
+  const int threads = g.plane < 1024 ? (int)((g.plane + 31) / 32 * 32) : 1024;
+  switch (g.dim) {
+    case 1: k_fields_small<1><<<1, threads, 0, st>>>(F, g, 0.5f * g.c, g.c); break;
+    case 2: k_fields_small<2><<<1, threads, 0, st>>>(F, g, 0.5f * g.c, g.c); break;
+    case 3: k_fields_small<3><<<1, threads, 0, st>>>(F, g, 0.5f * g.c, g.c); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

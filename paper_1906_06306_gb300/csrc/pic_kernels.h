@@ -66,6 +66,11 @@ constexpr bool kFoldGlobal = D == 3 && PIC_X3PAIR != 0;
 #ifndef PIC_BULK_FILTER
 #define PIC_BULK_FILTER 1
 #endif
+// Small periodic FDTD2 lattices take the second B half step and the E update
+// of a step in one launch.
+#ifndef PIC_SMALL_FIELDS
+#define PIC_SMALL_FIELDS 1
+#endif
 // pic_step(n) replays whole sort cycles from a captured CUDA graph.
 #ifndef PIC_STEP_GRAPHS
 #define PIC_STEP_GRAPHS 1
@@ -187,6 +192,11 @@ long long window_landing_floats(int dim, const TileDev& t);
 
 cudaError_t launch_b_half(const GridDev& g, float* F, int zero_j, cudaStream_t st);
 cudaError_t launch_e_update(const GridDev& g, float* F, cudaStream_t st);
+// FDTD2 lattices of at most kSmallFieldCells points: the second B half step
+// and the E update in one single-block launch (the same bits as the two)
+constexpr long long kSmallFieldCells = 4096;
+bool fields_small_ok(const GridDev& g);
+cudaError_t launch_fields_small(const GridDev& g, float* F, cudaStream_t st);
 // one Binomial2 sub-pass along gridded axis `axis` over ncomp consecutive planes,
 // src -> dst (a full pass is one sub-pass per gridded axis, x first)
 cudaError_t launch_filter_f32(const GridDev& g, const float* src, float* dst, int ncomp, int axis,
