@@ -107,6 +107,23 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def launches_per_step(sim, shock=False):
+    """Kernels of one pic_step on `sim`'s tuning, and of one tile sort: per
+    step the first B half step, the tile particle kernel, one fused launch per
+    filter pass, the deferred-particle kernel in 3D or with the wall, and the
+    second B half step with the E update (one launch on a periodic FDTD2
+    lattice of at most 4096 points, else two); per sort and species the count,
+    the scan (three kernels past 4096 bins) and the scatter."""
+    from paper_1906_06306_gb300 import binding as B
+
+    tun = sim.tuning()
+    cells = sim.nx * sim.ny * sim.nz
+    fields = 2 if (not shock and cells <= 4096) else 3
+    step = fields + 1 + tun["filter_passes"] + (1 if sim.dim == 3 or shock else 0)
+    sort = (3 if B.pic_sort_bins(sim.ctx) <= 4096 else 5) * sim.nspecies
+    return step, sort
+
+
 def profiled_traffic(workload, full_size, nparticles):
     """DRAM bytes per launch of the fused particle kernel from the workload's
     committed ncu summary, if it was taken on the current kernel source: the
@@ -838,12 +855,8 @@ def run_ours(args):
     traffic = profiled_traffic(args.workload, pl.nx == 1024, avg_n)
     step_alg = step_bytes(pl, avg_n, tun["filter_passes"], tun["sort_every"])
     nsorts = -(-args.steps // tun["sort_every"])  # at most one sort per cadence in the loop
-    # per step: two B half steps, the tile particle kernel, the E update, one fused
-    # launch per filter pass and, in 3D or with the wall, the deferred-particle
-    # kernel; per sort: count, scan and scatter per species
-    deferred = 1 if pl.dim == 3 or shock else 0
-    launches = (args.steps * (4 + deferred + tun["filter_passes"]) +
-                nsorts * 3 * sim.nspecies)
+    per_step, per_sort = launches_per_step(sim, shock)
+    launches = args.steps * per_step + nsorts * per_sort
     if shock:  # per step: 3 wall-field passes, the injection, and the tail kernel on
         # every step that does not start with a sort
         launches += args.steps * 4 + (args.steps - nsorts)
@@ -969,11 +982,10 @@ def run_batched(args):
     achieved = alg * args.steps / (ms * 1e-3) / 1e9
     peak, peak_kind = hbm_peak()
     cadences = sorted({sm.tuning()["sort_every"] for sm in sims})
-    # per box and step: two B half steps, the tile particle kernel, the E update
-    # (1D/2D periodic boxes: no deferred-particle kernel, no filter); per sort:
-    # count, scan and scatter per species
-    launches = sum(args.steps * 4 + -(-args.steps // sm.tuning()["sort_every"]) * 3 * sm.nspecies
-                   for sm in sims)
+    launches = 0
+    for sm in sims:
+        per_step, per_sort = launches_per_step(sm)
+        launches += args.steps * per_step + -(-args.steps // sm.tuning()["sort_every"]) * per_sort
     line = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -1073,11 +1085,12 @@ def run_adjoint(args):
     adj_ms, adj_n = kt["adjoint"]
     avg_adj = adj_ms * 1e-3 / max(adj_n, 1)
     # kernels behind the library's timed calls: a push is the tile kernel (2D,
-    # periodic: no deferred-particle kernel), an adjoint step 5 kernels plus one
-    # per filter pass
+    # periodic: no deferred-particle kernel), an adjoint step (tile pass) the B
+    # rebuild, 2 adjoint B half steps, the adjoint E update, one per filter
+    # pass, a bucket check per species, the tile pass and the deferred pass
     passes = sim.tuning()["filter_passes"]
     launches = (kt["push"][1] + kt["b_half"][1] + kt["e_update"][1] + kt["filter"][1] +
-                (5 + passes) * kt["adjoint"][1])
+                kt["sort"][1] + (6 + passes + sim.nspecies) * kt["adjoint"][1])
     # per adjoint step: particle state read (4 + 8 + 12 B) and gradients read and
     # written (2 x (8 + 12) B); E, B read and their gradients added once per cell
     alg = npart * (24 + 40) + pl.ncells * 4 * (6 + 9 + 12)

@@ -260,17 +260,20 @@ __device__ __forceinline__ void segment_adj(const AB& Ab, const int* I, float q,
   }
 }
 
-// Reverse of the whole particle update of particle p of species S, in cell b
-// (accessor coordinates of F and Ab): the forward gather, Boris and move are
-// recomputed with the forward kernel's own routines, then ZigZag, move, Boris
-// and gather are reversed; xbar and ubar of p are updated in place and the
-// field adjoints added through Ab.
+// Reverse of the particle update of particle p of species S, in cell b
+// (accessor coordinates of F and Ab), up to the gather: the forward gather,
+// Boris and move are recomputed with the forward kernel's own routines, then
+// ZigZag, move and Boris are reversed.  ubar of p is updated in place; out:
+// the offsets o1, the position gradient so far xb, and the particle's E and B
+// adjoints ebb (Ex, Ey, Ez, Bx, By, Bz), which the caller takes back through
+// the gather (gather_adj).
 template <int D, class AF, class AB>
-__device__ __forceinline__ void adj_particle(const AF& F, const AB& Ab, const AdjSpecies& S,
-                                             long long p, const int* b, float c,
-                                             float* ebb = nullptr) {
+__device__ __forceinline__ void adj_chain(const AF& F, const AB& Ab, const AdjSpecies& S,
+                                          long long p, const int* b, float c, float* o1,
+                                          float* xb, float* ebb) {
   const long long ld = S.ld;
-  float o1[3] = {0.f, 0.f, 0.f}, u[3];
+  float u[3];
+  o1[0] = o1[1] = o1[2] = 0.f;
 #pragma unroll
   for (int d = 0; d < D; ++d) o1[d] = S.off[d * ld + p];
 #pragma unroll
@@ -286,7 +289,8 @@ __device__ __forceinline__ void adj_particle(const AF& F, const AB& Ab, const Ad
   const float g2 = fmaf(u2[0], u2[0], fmaf(u2[1], u2[1], fmaf(u2[2], u2[2], 1.0f)));
   const float ig = rsqrtf(g2);
   // reverse of x' = x + dn: xbar passes through, dn gets xbar
-  float xb[3] = {0.f, 0.f, 0.f}, dnb[3] = {0.f, 0.f, 0.f}, u2b[3];
+  float dnb[3] = {0.f, 0.f, 0.f}, u2b[3];
+  xb[0] = xb[1] = xb[2] = 0.f;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     xb[d] = S.xbar[d * ld + p];
@@ -340,27 +344,29 @@ __device__ __forceinline__ void adj_particle(const AF& F, const AB& Ab, const Ad
   const float ud = u2[0] * dnb[0] + u2[1] * dnb[1] + u2[2] * dnb[2];
 #pragma unroll
   for (int a = 0; a < 3; ++a) u2b[a] += c * ig * (dnb[a] - u2[a] * ud * ig * ig);
-  float ub[3], eb[3], bb[3];
-  boris_adj(u, e, bf, S.qm, c, u2b, ub, eb, bb);
-  // reverse of the gather: Ex (1/2,0,0) Ey (0,1/2,0) Ez (0,0,1/2)
-  // Bx (0,1/2,1/2) By (1/2,0,1/2) Bz (1/2,1/2,0)
-  gather_adj<D>(F, Ab, EX, 1, b, o1, eb[0], xb);
-  gather_adj<D>(F, Ab, EY, 2, b, o1, eb[1], xb);
-  gather_adj<D>(F, Ab, EZ, 4, b, o1, eb[2], xb);
-  gather_adj<D>(F, Ab, BX, 6, b, o1, bb[0], xb);
-  gather_adj<D>(F, Ab, BY, 5, b, o1, bb[1], xb);
-  gather_adj<D>(F, Ab, BZ, 3, b, o1, bb[2], xb);
-#pragma unroll
-  for (int d = 0; d < D; ++d) S.xbar[d * ld + p] = xb[d];
+  float ub[3];
+  boris_adj(u, e, bf, S.qm, c, u2b, ub, ebb, ebb + 3);
 #pragma unroll
   for (int a = 0; a < 3; ++a) S.ubar[a * ld + p] = ub[a];
-  if (ebb) {  // the E and B adjoints of the particle, for the caller to add
+}
+
+// Stagger bits of the six components: Ex (1/2,0,0) Ey (0,1/2,0) Ez (0,0,1/2)
+// Bx (0,1/2,1/2) By (1/2,0,1/2) Bz (1/2,1/2,0).
+__device__ constexpr int kStagger[6] = {1, 2, 4, 6, 5, 3};
+
+// The whole reverse for one particle through global memory: the chain, then
+// the gather's reverse with the field adjoints added through Ab; xbar of p
+// is written.
+template <int D, class AF, class AB>
+__device__ __forceinline__ void adj_particle(const AF& F, const AB& Ab, const AdjSpecies& S,
+                                             long long p, const int* b, float c) {
+  float o1[3], xb[3], ebb[6];
+  adj_chain<D>(F, Ab, S, p, b, c, o1, xb, ebb);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      ebb[a] = eb[a];
-      ebb[3 + a] = bb[a];
-    }
-  }
+  for (int comp = 0; comp < 6; ++comp)
+    gather_adj<D>(F, Ab, EX + comp, kStagger[comp], b, o1, ebb[comp], xb);
+#pragma unroll
+  for (int d = 0; d < D; ++d) S.xbar[d * S.ld + p] = xb[d];
 }
 
 // The lattice cell (i, j, k) of a linear cell index.
@@ -466,7 +472,7 @@ __device__ __forceinline__ void adj_share(const AdjParams& P, const AdjSpecies& 
 // goes to the lattice once per window cell.  A particle whose stencil is not
 // inside the window goes on the species' deferred list for the global pass.
 template <int D>
-__global__ void __launch_bounds__(256, 2) k_adj_tiles(const AdjParams P) {
+__global__ void __launch_bounds__(256, PIC_ADJ_MIN_BLOCKS) k_adj_tiles(const AdjParams P) {
   extern __shared__ __align__(16) float sm[];
   __shared__ unsigned wmax[8];  // per warp of the block (256 threads)
   const AdjBlock B = adj_block<D>(P);
@@ -499,14 +505,14 @@ __global__ void __launch_bounds__(256, 2) k_adj_tiles(const AdjParams P) {
     const long long ld = S.ld;
     for (long long base = a; base < b; base += blockDim.x) {  // the same count for every thread
       const long long p = base + threadIdx.x;
-      float ebb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float ebb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, o[3] = {0.f, 0.f, 0.f}, xb[3];
       int l[3] = {0, 0, 0};
       bool mine = false;
       if (p < b) {
         const int cell = S.cell[p];
         if (cell >= 0 && (long long)cell < plane) {
           if (adj_in_window<D>(P, B, cell, l)) {
-            adj_particle<D>(WN, WN, S, p, l, c, ebb);
+            adj_chain<D>(WN, WN, S, p, l, c, o, xb, ebb);
             mine = true;
           } else {
             S.dlist[atomicAdd(&P.dcount[s], 1)] = (int)p;
@@ -528,19 +534,16 @@ __global__ void __launch_bounds__(256, 2) k_adj_tiles(const AdjParams P) {
       frexpf(M, &e);  // M < 2^e
       const float q = ldexpf(1.0f, e - 22), inv_q = ldexpf(1.0f, 22 - e);
       if (mine) {
-        float o[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int d = 0; d < D; ++d) o[d] = S.off[d * ld + p];
-        // Ex (1/2,0,0) Ey (0,1/2,0) Ez (0,0,1/2) Bx (0,1/2,1/2) By (1/2,0,1/2) Bz (1/2,1/2,0)
-        constexpr int kStag[6] = {1, 2, 4, 6, 5, 3};
+        // the gather's reverse (gather_adj's operations, in its order, for the
+        // position gradient) with each term also added, in quanta, to the window
 #pragma unroll
         for (int comp = 0; comp < 6; ++comp) {
-          const float v = ebb[comp] * inv_q;
+          const float vb = ebb[comp], v = vb * inv_q;
           int i0[3] = {0, 0, 0};
           float w[3] = {0.f, 0.f, 0.f};
 #pragma unroll
           for (int d = 0; d < D; ++d) {
-            if (kStag[comp] & (1 << d)) {
+            if (kStagger[comp] & (1 << d)) {
               const bool up = o[d] >= 0.5f;
               i0[d] = up ? l[d] : l[d] - 1;
               w[d] = up ? o[d] - 0.5f : o[d] + 0.5f;
@@ -557,8 +560,19 @@ __global__ void __launch_bounds__(256, 2) k_adj_tiles(const AdjParams P) {
             for (int d = 0; d < D; ++d) wt *= oc[d] ? w[d] : 1.f - w[d];
             const int at = (i0[0] + oc[0]) + W0 * (i0[1] + oc[1]) + W01 * (i0[2] + oc[2]);
             atomicAdd(&wi[comp * ws + at], __float2int_rn(wt * v));
+            const float f = sm[(EX + comp) * ws + at] * vb;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+              float dw = oc[d] ? 1.f : -1.f;
+#pragma unroll
+              for (int d2 = 0; d2 < D; ++d2)
+                if (d2 != d) dw *= oc[d2] ? w[d2] : 1.f - w[d2];
+              xb[d] += dw * f;
+            }
           }
         }
+#pragma unroll
+        for (int d = 0; d < D; ++d) S.xbar[d * ld + p] = xb[d];
       }
       __syncthreads();
       if (mb != 0u) {

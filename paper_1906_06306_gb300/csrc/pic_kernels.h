@@ -66,6 +66,10 @@ constexpr bool kFoldGlobal = D == 3 && PIC_X3PAIR != 0;
 #ifndef PIC_BULK_FILTER
 #define PIC_BULK_FILTER 1
 #endif
+// Resident blocks per SM the adjoint's tile pass is compiled for.
+#ifndef PIC_ADJ_MIN_BLOCKS
+#define PIC_ADJ_MIN_BLOCKS 2
+#endif
 // Small periodic FDTD2 lattices take the second B half step and the E update
 // of a step in one launch.
 #ifndef PIC_SMALL_FIELDS

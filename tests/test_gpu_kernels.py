@@ -236,6 +236,45 @@ def test_sort_groups_particles_by_tile(dim, tile):
     sim.close()
 
 
+def test_sort_orders_3d_tiles_by_sub_tile():
+    """3D tiles of 8x8x4 cells are sorted into 4x4x2 sub-tile bins, tile-major
+    (sub-tile x fastest): the bin sequence of the output is the sorted bin
+    sequence of the input, ragged last tiles included, and every bin holds
+    the same particles (bytes)."""
+    nx, ny, nz = 21, 18, 10
+    pl = _plasma(3, (nx, ny, nz), 3, 0.3, 509)
+    rs = np.random.default_rng(510)
+    for s in pl.species:  # scramble the input order
+        p = rs.permutation(s.n)
+        s.cell, s.off, s.u = s.cell[p].copy(), s.off[:, p].copy(), s.u[:, p].copy()
+    from paper_1906_06306_gb300 import Simulation
+
+    sim = Simulation.from_plasma(pl, tuning=dict(tile=[8, 8, 4]))
+    _, spg = sim.download()
+    T, S = (8, 8, 4), (4, 4, 2)
+
+    def bins(cell):
+        cell = np.asarray(cell, dtype=np.int64)
+        i, j, k = cell % nx, (cell // nx) % ny, cell // (nx * ny)
+        tile = oracle.tile_keys(cell, nx, ny, nz, T)
+        ns = [-(-t // u) for t, u in zip(T, S)]
+        sub = ((i % T[0]) // S[0]) + ns[0] * (((j % T[1]) // S[1]) + ns[1] * ((k % T[2]) // S[2]))
+        return tile * (ns[0] * ns[1] * ns[2]) + sub
+
+    for s_in, s_out in zip(pl.species, spg):
+        b_out, b_in = bins(s_out["cell"]), bins(s_in.cell)
+        assert np.array_equal(b_out, np.sort(b_in))
+
+        def rows(cell, off, u):
+            return np.concatenate([np.asarray(cell)[None].view(np.float32), off, u]).T.copy()
+
+        a = rows(s_out["cell"], s_out["off"], s_out["u"]).view(np.int32)
+        b = rows(s_in.cell, s_in.off, s_in.u).view(np.int32)
+        for key in np.unique(b_in):
+            assert np.array_equal(np.unique(a[b_out == key], axis=0), np.unique(b[b_in == key], axis=0))
+    sim.close()
+
+
 @pytest.mark.parametrize("dim", [1, 2, 3])
 def test_higuera_cary_gather_push_matches_oracle(dim):
     nx, ny, nz = SHAPES[dim]
