@@ -21,20 +21,31 @@ NO_SORT = 1 << 30  # sort cadence for adjoint runs: particle slots stay fixed
 
 
 class Adjoint:
-    """Forward run of `sim` with checkpoints every `checkpoint_every` steps and
-    the reverse sweep.  The steps themselves do not sort (the adjoint arrays
-    follow the particle slots); with `tiled` (the default) the particles are
-    tile-sorted in place at each checkpoint by pic_sort_record, which keeps the
-    permutation and the bucket starts: the forward steps and the adjoint's tile
-    pass then run on tile-grouped particles, and the reverse sweep carries the
-    gradients back through each checkpoint's permutation (pic_adjoint_unsort).
-    Without it every adjoint step takes the global-memory pass."""
+    """Forward run of `sim` with a checkpoint every `checkpoint_every` steps
+    and the reverse sweep.  The steps themselves do not sort (the adjoint
+    arrays follow the particle slots); with `tiled` (the default) the
+    particles are tile-sorted in place every `sort_every` steps (a multiple of
+    the checkpoint cadence, so that a sort opens a segment) by
+    pic_sort_record, which keeps the permutation and the bucket starts: the
+    forward steps and the adjoint's tile pass then run on tile-grouped
+    particles, and the reverse sweep carries the gradients back through each
+    sort's permutation (pic_adjoint_unsort).  Without it every adjoint step
+    takes the global-memory pass.
 
-    def __init__(self, sim, checkpoint_every: int = 20, tiled: bool = True):
+    Memory is one state (fields and particles) per checkpoint plus the states
+    of one segment; checkpoint_every=1 keeps every state of the forward run
+    and recomputes nothing in the reverse sweep (for the 256^2 differentiable
+    set-up about 0.1 GB a step)."""
+
+    def __init__(self, sim, checkpoint_every: int = 20, tiled: bool = True,
+                 sort_every: int = 20):
         if checkpoint_every < 1:
             raise ValueError("checkpoint_every must be >= 1")
+        if tiled and (sort_every < 1 or sort_every % checkpoint_every):
+            raise ValueError("sort_every must be a positive multiple of checkpoint_every")
         self.sim = sim
         self.K = int(checkpoint_every)
+        self.S = int(sort_every)
         self.tiled = bool(tiled)
         self.nsteps = 0
         self.ckpt = []
@@ -73,12 +84,12 @@ class Adjoint:
 
     def forward(self, nsteps: int):
         """nsteps steps of the simulation, keeping a checkpoint every K (taken
-        after the checkpoint's tile sort, which it records)."""
+        after the tile sort that opens it every S steps, which it records)."""
         self.nsteps = int(nsteps)
         self.ckpt = []
         for t in range(self.nsteps):
             if t % self.K == 0:
-                rec = self._sort() if self.tiled else None
+                rec = self._sort() if self.tiled and t % self.S == 0 else None
                 self.ckpt.append((self._state(), rec))
             self.sim.step(1)
 
@@ -100,31 +111,38 @@ class Adjoint:
         at the final state."""
         sim = self.sim
         final = self._state()
+        # the grouping each segment's particles are in: that of the last sort
+        # at or before the segment
+        groups, g = [], None
+        for _, rec in self.ckpt:
+            g = rec if rec is not None else g
+            groups.append(g)
         for seg in reversed(range(len(self.ckpt))):
             t0 = seg * self.K
             t1 = min(self.nsteps, t0 + self.K)
             st, rec = self.ckpt[seg]
-            self._restore(st)
-            self._assume(rec)
-            states = []
-            for _ in range(t0, t1):
-                states.append(self._state())
-                sim.step(1)
-            tst = rec[1] if rec is not None else [None] * len(xbar)
+            states = [st]  # the checkpoint is the segment's first state
+            if t1 - t0 > 1:  # recompute the others (not the step past the last)
+                self._restore(st)
+                self._assume(groups[seg])
+                for k in range(t1 - t0 - 1):
+                    sim.step(1)
+                    states.append(self._state())
+            tst = groups[seg][1] if groups[seg] is not None else [None] * len(xbar)
             for F, sp in reversed(states):
                 asp = [B.pic_adjoint_species(c.data_ptr(), o.data_ptr(), u.data_ptr(),
                                              xb.data_ptr(), ub.data_ptr(),
                                              t.data_ptr() if t is not None else None)
                        for (c, o, u), xb, ub, t in zip(sp, xbar, ubar, tst)]
                 B.pic_adjoint_step(sim.ctx, F.data_ptr(), asp, A.data_ptr())
-            if rec is not None:  # back through the checkpoint's sort
+            if rec is not None:  # back through the sort that opened the segment
                 asp = [B.pic_adjoint_species(None, None, None, xb.data_ptr(), ub.data_ptr())
                        for xb, ub in zip(xbar, ubar)]
                 B.pic_adjoint_unsort(sim.ctx, [p.data_ptr() if p is not None else 0
                                                for p in rec[0]], asp)
         self._restore(final)
-        if self.ckpt:
-            self._assume(self.ckpt[-1][1])
+        if groups:
+            self._assume(groups[-1])
         return A, xbar, ubar
 
 
@@ -134,10 +152,11 @@ class MagneticEnergyProblem:
     given, run for nsteps with checkpoints every K.  modes: float32 array
     [M, 3, nz, ny, nx] of B perturbation fields (planes Bx, By, Bz)."""
 
-    def __init__(self, sim, modes, nsteps: int, checkpoint_every: int = 20):
+    def __init__(self, sim, modes, nsteps: int, checkpoint_every: int = 20,
+                 sort_every: int = 20):
         torch = sim.torch
         self.sim = sim
-        self.adj = Adjoint(sim, checkpoint_every)
+        self.adj = Adjoint(sim, checkpoint_every, sort_every=sort_every)
         self.nsteps = int(nsteps)
         self.modes = torch.as_tensor(np.asarray(modes, dtype=np.float32), device=sim.device)
         self.base_fields = sim.fields.clone()

@@ -66,9 +66,12 @@ constexpr bool kFoldGlobal = D == 3 && PIC_X3PAIR != 0;
 #ifndef PIC_BULK_FILTER
 #define PIC_BULK_FILTER 1
 #endif
-// Resident blocks per SM the adjoint's tile pass is compiled for.
+// Resident blocks per SM the 1D/2D adjoint tile pass is compiled for (4: 64
+// registers without spills, 4 x 45 KB of shared memory for a 16x16-tile
+// window; measured 0.38 -> 0.27 ms per adjoint step of the 256^2 box against 2
+// blocks).  The 3D window's 128 KB allow one block, so 3D keeps 2.
 #ifndef PIC_ADJ_MIN_BLOCKS
-#define PIC_ADJ_MIN_BLOCKS 2
+#define PIC_ADJ_MIN_BLOCKS 4
 #endif
 // Small periodic FDTD2 lattices take the second B half step and the E update
 // of a step in one launch.

@@ -247,6 +247,38 @@ def test_magnetic_energy_gradient_matches_oracle_and_differences():
     sim.close()
 
 
+def test_checkpoint_cadences_and_the_global_pass_give_the_same_gradient():
+    """The reverse sweep with every state kept (no recompute), with a
+    checkpoint every 5 steps (recomputed segments) and sorts every 5 or 10
+    steps, and without tile sorts (global pass only): the same gradient, up to
+    the order of floating-point sums."""
+    import torch
+
+    from paper_1906_06306_gb300 import Simulation
+    from paper_1906_06306_gb300.adjoint import MagneticEnergyProblem
+
+    res = []
+    for k, sort_every, tiled in [(1, 5, True), (5, 10, True), (5, 5, True), (5, 20, False)]:
+        pl, mf, amps = workloads.adjoint_box(n=16, ppc=2, theta=0.1, sigma=1.0, modes=3, seed=5)
+        sim = Simulation.from_plasma(pl)
+        prob = MagneticEnergyProblem(sim, mf, nsteps=12, checkpoint_every=k, sort_every=sort_every)
+        prob.adj.tiled = tiled
+        a = torch.tensor(amps, device=sim.device)
+        # the initial state in the caller's slot order, shared by every run
+        if not res:
+            u0 = prob.u0()
+            base = [(c.clone(), o.clone()) for c, o in prob.base]
+        else:
+            prob.base = [(c.clone(), o.clone()) for c, o in base]
+        prob.run(a, u0)
+        g_a, g_u = prob.gradient()
+        res.append((g_a.cpu().numpy(), g_u.cpu().numpy()))
+        sim.close()
+    for g_a, g_u in res[1:]:
+        assert _rel(g_a, res[0][0]) < 1e-4
+        assert _rel(g_u, res[0][1]) < 1e-4
+
+
 def test_full_size_gradient_matches_central_differences_of_the_gpu_run():
     """The differentiable set-up at its benchmark size (256^2 box, 32 particles
     per cell per species, theta 0.1, sigma 1, 64 modes, 200 steps, checkpoints
