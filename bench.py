@@ -1022,9 +1022,11 @@ def run_adjoint(args):
     box of the differentiable set-up: 32 particles per cell per species,
     theta 0.1, sigma 1, 64 seeded modes of dB ~ 0.1 B0) with respect to the 64
     mode amplitudes and every initial four-velocity: forward run keeping every
-    state (tile sorts every 20 steps, recorded), then the reverse sweep of
-    adjoint steps.  value = particle-steps of the forward run per second of
-    forward + reverse.  Replicas only for N > 1."""
+    state where half the free device memory holds them, else a checkpoint
+    every 20 steps (tile sorts every 20 steps, recorded), then the reverse
+    sweep (recomputed segments, if any, and adjoint steps).  value =
+    particle-steps of the forward run per second of forward + reverse.
+    Replicas only for N > 1."""
     import torch
 
     rank, world, local = dist_env()
@@ -1043,10 +1045,13 @@ def run_adjoint(args):
     pl, mf, amps = workloads.adjoint_box(n=n, ppc=32, theta=0.1, sigma=1.0, modes=8, seed=1239)
     dev = torch.device(f"cuda:{local}")
     sim = Simulation.from_plasma(pl, device=f"cuda:{local}")
-    # every state of the forward run is kept (about 0.1 GB a step on the 256^2
-    # box: 20 GB for 200 steps, well inside the GPU's memory), so the reverse
-    # sweep recomputes nothing; tile sorts every 20 steps
-    prob = MagneticEnergyProblem(sim, mf, nsteps=args.warmup, checkpoint_every=1, sort_every=20)
+    # every state of the forward run is kept when half the free device memory
+    # holds them (about 0.1 GB a step on the 256^2 box: 20 GB for 200 steps),
+    # so that the reverse sweep recomputes nothing; else a checkpoint every 20
+    # steps; tile sorts every 20 steps
+    state_bytes = pl.nparticles * 24 + pl.ncells * 36
+    kcp = 1 if (args.steps + 1) * state_bytes <= 0.5 * torch.cuda.mem_get_info(dev)[0] else 20
+    prob = MagneticEnergyProblem(sim, mf, nsteps=args.warmup, checkpoint_every=kcp, sort_every=20)
     a = torch.tensor(amps, device=dev)
     u0 = prob.u0()
     prob.run(a, u0)  # warm-up: a short gradient
@@ -1104,9 +1109,10 @@ def run_adjoint(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": dict(workload="adjoint_2d3v", grid=[n, n], ppc_per_species=32, species=2,
-                       theta=0.1, sigma=1.0, modes=int(mf.shape[0]), checkpoint_every=1,
+                       theta=0.1, sigma=1.0, modes=int(mf.shape[0]), checkpoint_every=kcp,
                        sort_every=20,
-                       states_kept_gb=round((args.steps + 1) * (npart * 24 + pl.ncells * 36) / 1e9, 1),
+                       states_kept_gb=round((-(-args.steps // kcp) + (kcp if kcp > 1 else 0)) *
+                                            state_bytes / 1e9, 1),
                        particles=npart, loss=float(loss),
                        grad_norm_amps=float(g_a.norm()), grad_norm_u0=float(g_u.norm()),
                        forward_ms=ms_f, reverse_ms=ms_b,

@@ -38,9 +38,11 @@ class Adjoint:
     set-up about 0.1 GB a step)."""
 
     def __init__(self, sim, checkpoint_every: int = 20, tiled: bool = True,
-                 sort_every: int = 20):
+                 sort_every: int | None = None):
         if checkpoint_every < 1:
             raise ValueError("checkpoint_every must be >= 1")
+        if sort_every is None:  # the first multiple of the checkpoint cadence from 20 on
+            sort_every = -(-20 // checkpoint_every) * checkpoint_every
         if tiled and (sort_every < 1 or sort_every % checkpoint_every):
             raise ValueError("sort_every must be a positive multiple of checkpoint_every")
         self.sim = sim
@@ -153,7 +155,7 @@ class MagneticEnergyProblem:
     [M, 3, nz, ny, nx] of B perturbation fields (planes Bx, By, Bz)."""
 
     def __init__(self, sim, modes, nsteps: int, checkpoint_every: int = 20,
-                 sort_every: int = 20):
+                 sort_every: int | None = None):
         torch = sim.torch
         self.sim = sim
         self.adj = Adjoint(sim, checkpoint_every, sort_every=sort_every)
