@@ -1054,9 +1054,11 @@ def run_adjoint(args):
     prob = MagneticEnergyProblem(sim, mf, nsteps=args.warmup, checkpoint_every=kcp, sort_every=20)
     a = torch.tensor(amps, device=dev)
     u0 = prob.u0()
-    prob.run(a, u0)  # warm-up: a short gradient
-    prob.gradient()
+    prob.run(a, u0)  # warm-up: a short gradient (--warmup steps), then a full-length one,
+    prob.gradient()  # after which the allocator holds the kept states' memory
     prob.nsteps = args.steps
+    prob.run(a, u0)
+    prob.gradient()
     torch.cuda.synchronize(dev)
     if dist is not None:
         dist.barrier()
