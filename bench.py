@@ -695,6 +695,7 @@ def sub_record(name, steps, warmup, local=0):
         "step_graph": not shock,
         "roofline": {"bound": "hbm", "achieved": alg / avg_push_s / 1e9, "peak": peak,
                      "unit": "GB/s", "frac": alg / avg_push_s / 1e9 / peak,
+                     "traffic": profiled_traffic(name, geo.nx == 1024, avg_n),
                      "kernel": f"k_particles<{w['dim']},{3 if shock else 0}>",
                      "peak_source": peak_kind, "avg_launch_us": avg_push_s * 1e6,
                      "alg_bytes_per_launch": alg, "timed_steps": kt_steps},
