@@ -435,7 +435,7 @@ __device__ __forceinline__ AdjBlock adj_block(const AdjParams& P) {
 }
 // Window-local cell of a particle and whether its stencil (cells b - 1 ..
 // b + 2 on every gridded axis, as in the forward tile kernel) is inside the
-// window; the same test in both tile passes.
+// window.
 template <int D>
 __device__ __forceinline__ bool adj_in_window(const AdjParams& P, const AdjBlock& B, int cell,
                                               int* l) {
@@ -472,7 +472,8 @@ __device__ __forceinline__ void adj_share(const AdjParams& P, const AdjSpecies& 
 // goes to the lattice once per window cell.  A particle whose stencil is not
 // inside the window goes on the species' deferred list for the global pass.
 template <int D>
-__global__ void __launch_bounds__(256, D == 3 ? 2 : PIC_ADJ_MIN_BLOCKS) k_adj_tiles(const AdjParams P) {
+__global__ void __launch_bounds__(256, D == 3 ? 2 : PIC_ADJ_MIN_BLOCKS)
+    k_adj_tiles(const AdjParams P) {
   extern __shared__ __align__(16) float sm[];
   __shared__ unsigned wmax[8];  // per warp of the block (256 threads)
   const AdjBlock B = adj_block<D>(P);
