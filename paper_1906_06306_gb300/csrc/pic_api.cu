@@ -197,7 +197,7 @@ std::string derive_tiles(const pic_grid& grid, const pic_tuning& tun, long long 
       r.T[d] = tun.tile[d] < n ? tun.tile[d] : n;
       r.nt[d] = (n + r.T[d] - 1) / r.T[d];
       r.W[d] = r.T[d] + 2 * r.H + 1;
-      const int ks = grid.dim == 3 ? kSubTile3[d] : kSubTile[d];
+      const int ks = grid.dim == 3 ? kSubTile3[d] : grid.dim == 2 ? kSubTile2[d] : 0;
       const int sub = ks > 0 && ks < r.T[d] ? ks : r.T[d];
       r.S[d] = sub;
       r.ns[d] = (r.T[d] + sub - 1) / sub;

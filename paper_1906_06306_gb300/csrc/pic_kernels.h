@@ -85,23 +85,24 @@ constexpr bool kFoldGlobal = D == 3 && PIC_X3PAIR != 0;
 #ifndef PIC_PREFETCH
 #define PIC_PREFETCH 0
 #endif
-// Sub-tile extents of the sort key (0: the whole tile), for 1D/2D and for 3D.
-// The tile sort orders a tile's particles by sub-tile, so the lanes of a warp
-// gather from and deposit into a small patch of the tile window: fewer shared
-// memory bank conflicts, more sort bins.  Measured on the 2D 16x8 tiles it
-// does not pay (4x4: -1 %); on the 3D 8x8x4 tiles 4x4x2 cut the particle
-// kernel's shared-memory wavefronts by 12 %.
+// Sub-tile extents of the sort key (0: the whole tile), for 2D and for 3D (1D
+// tiles are not subdivided).  The tile sort orders a tile's particles by
+// sub-tile, so the lanes of a warp gather from and deposit into a part of the
+// tile window: fewer shared-memory bank conflicts (coinciding stencil words
+// are broadcasts), more sort bins.  Measured with every other setting fixed
+// (two runs each, 1024^2 turbulence with 16x8 tiles; 1024x128x128 shock with
+// 8x8x4 tiles): in 2D 8x4 took the particle kernel from 0.567 to 0.553 ms
+// (the sort 0.055 -> 0.063 ms, the step 0.634 -> 0.629 ms; 8x8 0.629, 4x8
+// 0.631, 16x4 0.631, 4x4 slower); in 3D 2x4x2 from 5.11 to 5.04 ms (the step
+// 6.59 -> 6.55 ms; 4x4x2 6.59, 4x4x4 6.66, 8x4x2 and 4x8x2 6.65, 4x4x1 6.68).
 #ifndef PIC_SUBTILE_X
-#define PIC_SUBTILE_X 0
+#define PIC_SUBTILE_X 8
 #endif
 #ifndef PIC_SUBTILE_Y
-#define PIC_SUBTILE_Y 0
-#endif
-#ifndef PIC_SUBTILE_Z
-#define PIC_SUBTILE_Z 0
+#define PIC_SUBTILE_Y 4
 #endif
 #ifndef PIC_SUBTILE3_X
-#define PIC_SUBTILE3_X 4
+#define PIC_SUBTILE3_X 2
 #endif
 #ifndef PIC_SUBTILE3_Y
 #define PIC_SUBTILE3_Y 4
@@ -109,7 +110,7 @@ constexpr bool kFoldGlobal = D == 3 && PIC_X3PAIR != 0;
 #ifndef PIC_SUBTILE3_Z
 #define PIC_SUBTILE3_Z 2
 #endif
-constexpr int kSubTile[3] = {PIC_SUBTILE_X, PIC_SUBTILE_Y, PIC_SUBTILE_Z};
+constexpr int kSubTile2[3] = {PIC_SUBTILE_X, PIC_SUBTILE_Y, 0};
 constexpr int kSubTile3[3] = {PIC_SUBTILE3_X, PIC_SUBTILE3_Y, PIC_SUBTILE3_Z};
 // Sort bins of a tiling: sub-tiles of every tile, tile-major.
 inline long long sort_bins(const TileDev& t) { return (long long)t.ntiles * t.nsub; }
