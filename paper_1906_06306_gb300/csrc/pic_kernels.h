@@ -54,8 +54,14 @@ constexpr bool kJ64 = D == 2 && PIC_J64 != 0;
 #ifndef PIC_X3PAIR
 #define PIC_X3PAIR 0
 #endif
+// The 3D fixed-point current folds into the global J planes instead of a
+// float window (a smaller block: 55 KB for the 8x8x4-tile window, four blocks
+// per SM) on its own too.
+#ifndef PIC_FOLD_GLOBAL_3D
+#define PIC_FOLD_GLOBAL_3D 0
+#endif
 template <int D>
-constexpr bool kFoldGlobal = D == 3 && PIC_X3PAIR != 0;
+constexpr bool kFoldGlobal = D == 3 && (PIC_X3PAIR != 0 || PIC_FOLD_GLOBAL_3D != 0);
 // The 2D particle kernel stages the field window of a tile inside the lattice
 // by one tensor copy (TMA) instead of per-thread loads.
 #ifndef PIC_TMA_WINDOW
