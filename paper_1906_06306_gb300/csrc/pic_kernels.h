@@ -21,8 +21,13 @@ constexpr int kMaxSpecies = 4;
 #ifndef PIC_PUSH_MIN_BLOCKS_TMA
 #define PIC_PUSH_MIN_BLOCKS_TMA 5
 #endif
+// 3D: 4 blocks per SM hold the kernel to 64 registers (no spills) and, with
+// the current folded into global J (PIC_FOLD_GLOBAL_3D), a block to 55 KB of
+// shared memory: measured on the 1024x128x128 shock (two runs each) the
+// particle kernel 5.00 -> 4.75 ms a step against 80 registers, a float window
+// and 3 blocks per SM (4.83 ms with the global fold at 3 blocks).
 #ifndef PIC_PUSH_MIN_BLOCKS_3D
-#define PIC_PUSH_MIN_BLOCKS_3D 2
+#define PIC_PUSH_MIN_BLOCKS_3D 4
 #endif
 // Blocks whose tile window lies inside the lattice skip the periodic-wrap
 // arithmetic (window-local indices and the new cell index).
@@ -54,11 +59,11 @@ constexpr bool kJ64 = D == 2 && PIC_J64 != 0;
 #ifndef PIC_X3PAIR
 #define PIC_X3PAIR 0
 #endif
-// The 3D fixed-point current folds into the global J planes instead of a
-// float window (a smaller block: 55 KB for the 8x8x4-tile window, four blocks
-// per SM) on its own too.
+// The 3D fixed-point current folds into the global J planes at every fold
+// instead of into a float window flushed once (a smaller block: 55 KB for the
+// 8x8x4-tile window, four blocks per SM); also without the x-paired window.
 #ifndef PIC_FOLD_GLOBAL_3D
-#define PIC_FOLD_GLOBAL_3D 0
+#define PIC_FOLD_GLOBAL_3D 1
 #endif
 template <int D>
 constexpr bool kFoldGlobal = D == 3 && (PIC_X3PAIR != 0 || PIC_FOLD_GLOBAL_3D != 0);
