@@ -448,7 +448,7 @@ pic_status do_sort(pic_ctx* ctx, bool copy_back, int32_t* const* perm = nullptr)
       float* off_out = (float*)(cell_out + ld);
       float* u_out = off_out + (long long)D * ld;
       r = launch_tile_scatter(P, ctx->sp[s].cell, ctx->sp[s].off, ctx->sp[s].u, n, ld,
-                              ctx->d_cursor, ctx->d_tstart[s], cell_out, off_out, u_out, ctx->st,
+                              ctx->d_cursor, cell_out, off_out, u_out, ctx->st,
                               perm ? perm[s] : nullptr);
       if (r != cudaSuccess) return r;
       if (!copy_back) continue;

@@ -77,10 +77,6 @@ constexpr bool kFoldGlobal = D == 3 && (PIC_X3PAIR != 0 || PIC_FOLD_GLOBAL_3D !=
 #ifndef PIC_BULK_FILTER
 #define PIC_BULK_FILTER 1
 #endif
-// The tile sort spreads each bin's arrivals over the bin (k_tile_scatter).
-#ifndef PIC_SCRAMBLE_BINS
-#define PIC_SCRAMBLE_BINS 1
-#endif
 // Resident blocks per SM the 1D/2D adjoint tile pass is compiled for (4: 64
 // registers without spills, 4 x 45 KB of shared memory for a 16x16-tile
 // window; measured 0.38 -> 0.27 ms per adjoint step of the 256^2 box against 2
@@ -250,12 +246,11 @@ cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* curs
                              cudaStream_t st);
 inline long long scan_scratch(long long n) { return 3 * ((n + 4095) / 4096 + 1); }
 // arrays with rows of ld elements, the first n of which are particles
-// start: the bins' first slots (start[bins] = n); perm (or null): perm[new
-// slot] = old slot
+// perm (or null): perm[new slot] = old slot
 cudaError_t launch_tile_scatter(const SortParams& P, const int* cell, const float* off,
                                 const float* u, long long n, long long ld, int* cursor,
-                                const int* start, int* cell_out, float* off_out, float* u_out,
-                                cudaStream_t st, int* perm = nullptr);
+                                int* cell_out, float* off_out, float* u_out, cudaStream_t st,
+                                int* perm = nullptr);
 // bucket starts t[0..nb] from outside: unless they are a partition of [0, n)
 // they become one bucket, and ST_BAD_BUCKETS is set
 cudaError_t launch_check_buckets(int* tstart, long long nb, long long n, int* status,

@@ -190,22 +190,10 @@ __global__ void __launch_bounds__(1024) k_scan_add(int* start, int* cursor, int 
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) start[n] = part_scan[gridDim.x];
 }
 
-// Slot of the r-th arrival in a bin of `count` slots starting at `start`:
-// with PIC_SCRAMBLE_BINS the arrivals are spread over the bin, r -> r x 1000003
-// mod count (a bijection: the prime is above any bin's count), so that the
-// particles one warp of the scatter carries in (neighbours in the old order,
-// often from one cell) land in different warps of the particle kernel, whose
-// lanes then meet in fewer shared-memory words and banks.
-__device__ __forceinline__ long long bin_slot(int start, int count, long long r) {
-  if (!PIC_SCRAMBLE_BINS || count <= 1) return start + r;
-  return start + (long long)((unsigned long long)r * 1000003ull % (unsigned long long)count);
-}
-
 template <int D>
 __global__ void k_tile_scatter(const SortParams P, const int* __restrict__ cell,
                                const float* __restrict__ off, const float* __restrict__ u,
-                               long long n, long long ld, int* cursor,
-                               const int* __restrict__ start, int* __restrict__ cell_out,
+                               long long n, long long ld, int* cursor, int* __restrict__ cell_out,
                                float* __restrict__ off_out, float* __restrict__ u_out,
                                int* __restrict__ perm) {
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -215,9 +203,7 @@ __global__ void k_tile_scatter(const SortParams P, const int* __restrict__ cell,
     const unsigned active = __ballot_sync(0xffffffffu, act);
     if (act) {
       const int c = cell[p];
-      const int key = tile_key(P, c);
-      const int b0 = start[key];
-      const long long q = bin_slot(b0, start[key + 1] - b0, warp_reserve(cursor, key, active) - b0);
+      const long long q = warp_reserve(cursor, tile_key(P, c), active);
       cell_out[q] = c;
 #pragma unroll
       for (int d = 0; d < D; ++d) off_out[d * ld + q] = off[d * ld + p];
@@ -282,14 +268,14 @@ cudaError_t launch_tile_scan(const int* count, int ntiles, int* start, int* curs
 
 cudaError_t launch_tile_scatter(const SortParams& P, const int* cell, const float* off,
                                 const float* u, long long n, long long ld, int* cursor,
-                                const int* start, int* cell_out, float* off_out, float* u_out,
-                                cudaStream_t st, int* perm) {
+                                int* cell_out, float* off_out, float* u_out, cudaStream_t st,
+                                int* perm) {
   if (n == 0) return cudaSuccess;
   const unsigned nb = blocks_for(n);
   switch (P.g.dim) {
-    case 1: k_tile_scatter<1><<<nb, 256, 0, st>>>(P, cell, off, u, n, ld, cursor, start, cell_out, off_out, u_out, perm); break;
-    case 2: k_tile_scatter<2><<<nb, 256, 0, st>>>(P, cell, off, u, n, ld, cursor, start, cell_out, off_out, u_out, perm); break;
-    case 3: k_tile_scatter<3><<<nb, 256, 0, st>>>(P, cell, off, u, n, ld, cursor, start, cell_out, off_out, u_out, perm); break;
+    case 1: k_tile_scatter<1><<<nb, 256, 0, st>>>(P, cell, off, u, n, ld, cursor, cell_out, off_out, u_out, perm); break;
+    case 2: k_tile_scatter<2><<<nb, 256, 0, st>>>(P, cell, off, u, n, ld, cursor, cell_out, off_out, u_out, perm); break;
+    case 3: k_tile_scatter<3><<<nb, 256, 0, st>>>(P, cell, off, u, n, ld, cursor, cell_out, off_out, u_out, perm); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
