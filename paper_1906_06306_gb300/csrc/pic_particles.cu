@@ -927,6 +927,7 @@ cudaError_t set_particle_smem_limit(int bytes) {
 #undef PIC_SET
   if (e == cudaSuccess) e = set_limit<2, 0, 23, 15>(bytes);
   if (e == cudaSuccess) e = set_limit<2, 0, 23, 23>(bytes);
+  if (e == cudaSuccess) e = set_limit<2, 0, 25, 17>(bytes);
 #if PIC_TMA_RECORDS
   if (e == cudaSuccess) e = set_limit<2, 0, 23, 15, 1, true>(bytes);
   if (e == cudaSuccess) e = set_limit<2, 0, 23, 23, 1, true>(bytes);
@@ -953,8 +954,9 @@ static cudaError_t launch(const PushParams& P, cudaStream_t st) {
   }
   const size_t smem = particle_smem_bytes(D, P.t);
   // fixed-window instantiations: 2D windows of 16x8 and 16x16 tiles with
-  // halo 3 (23 x 15, 23 x 23), the 3D window of 8x8x4 tiles with halo 2
-  // (13 x 13 x 9); any other window takes the generic kernel
+  // halo 3 (23 x 15, 23 x 23) and of 16x8 tiles with halo 4 (25 x 17), the 3D
+  // window of 8x8x4 tiles with halo 2 (13 x 13 x 9); any other window takes
+  // the generic kernel
   const bool w3 = P.t.W[0] == 13 && P.t.W[1] == 13 && P.t.W[2] == 9;
   const bool w37 = P.t.W[0] == 13 && P.t.W[1] == 13 && P.t.W[2] == 7;  // 8x8x2 tiles, halo 2
   // the record stream needs 16-byte aligned rows (bulk copies)
@@ -968,6 +970,8 @@ static cudaError_t launch(const PushParams& P, cudaStream_t st) {
     k_particles<2, 0, 23, 15><<<nblocks, kPushThreads, smem, st>>>(P);
   else if (D == 2 && MODE == 0 && P.t.W[0] == 23 && P.t.W[1] == 23)
     k_particles<2, 0, 23, 23><<<nblocks, kPushThreads, smem, st>>>(P);
+  else if (D == 2 && MODE == 0 && P.t.W[0] == 25 && P.t.W[1] == 17)
+    k_particles<2, 0, 25, 17><<<nblocks, kPushThreads, smem, st>>>(P);
   else if (tma)
     k_particles<D, MODE, 0, 0, 1, kStreamable><<<nblocks, kPushThreads, smem, st>>>(P);
   else if (D == 3 && MODE == 0 && w3)
