@@ -369,7 +369,7 @@ pic_status pic_step_host(pic_ctx* ctx, const pic_host_species* hs, float* host_f
  * max(steps, 2*sort_every) steps (rounded up to whole sort cycles) with CUDA
  * events, and finally keeps the fastest candidate.  candidates == NULL selects
  * a built-in set of 18 for the grid's dimension (three tile shapes around the
- * default, halos 2 and 3, three cadences).  *best_index (may be NULL) receives
+ * default, halos 3 and 4 in 1D/2D or 2 and 3 in 3D, three cadences).  *best_index (may be NULL) receives
  * the chosen candidate's index.  Synchronises.  Candidates that pic_set_tuning
  * rejects are skipped; PIC_ERR_ARG if none is valid. */
 pic_status pic_autotune(pic_ctx* ctx, const pic_tuning* candidates, int ncandidates, int steps,

@@ -1266,7 +1266,9 @@ pic_status pic_autotune(pic_ctx* ctx, const pic_tuning* candidates, int ncandida
   if (candidates) {
     cs.assign(candidates, candidates + ncandidates);
   } else {
-    // built-in candidates: tile shapes around the default, two halos, cadences
+    // built-in candidates: tile shapes around the default, two halos (3 and 4 in
+    // 1D/2D, 2 and 3 in 3D, where the window's shared memory is the limit),
+    // cadences
     const int D = ctx->grid.dim;
     const int tiles1[][3] = {{32, 1, 1}, {64, 1, 1}, {128, 1, 1}};
     const int tiles2[][3] = {{16, 16, 1}, {8, 16, 1}, {16, 8, 1}};
@@ -1274,8 +1276,9 @@ pic_status pic_autotune(pic_ctx* ctx, const pic_tuning* candidates, int ncandida
     const int (*tiles)[3] = D == 1 ? tiles1 : D == 2 ? tiles2 : tiles3;
     const int cad2[] = {5, 10, 20}, cad3[] = {2, 3, 5};
     const int* cad = D == 3 ? cad3 : cad2;
+    const int h0 = D == 3 ? 2 : 3;
     for (int t = 0; t < 3; ++t)
-      for (int h = 2; h <= 3; ++h)
+      for (int h = h0; h <= h0 + 1; ++h)
         for (int k = 0; k < 3; ++k) {
           pic_tuning c{};
           for (int d = 0; d < 3; ++d) c.tile[d] = tiles[t][d];
