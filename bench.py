@@ -750,7 +750,7 @@ def run_ours(args):
     dev = torch.device(f"cuda:{local}")
     autotuned = args.autotune and not shock  # its steps would advance the shock: defaults
     if autotuned:  # untimed: real steps under candidate tunings, keeps the fastest
-        sim.autotune(None, steps=20)
+        sim.autotune(None, steps=40)
     tun = sim.tuning()
     for _ in range(args.warmup):
         sim.step(1)

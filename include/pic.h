@@ -364,14 +364,16 @@ pic_status pic_step_host(pic_ctx* ctx, const pic_host_species* hs, float* host_f
 
 /* Autotuner of the launch parameters (tile size, halo, sort cadence; the
  * filter passes are physics and are kept).  Runs real time steps, which
- * advance the simulation exactly as pic_step does: for each candidate it
- * re-sorts if the tiles change, takes one step, then times
- * max(steps, 2*sort_every) steps (rounded up to whole sort cycles) with CUDA
- * events, and finally keeps the fastest candidate.  candidates == NULL selects
- * a built-in set of 18 for the grid's dimension (three tile shapes around the
- * default, halos 3 and 4 in 1D/2D or 2 and 3 in 3D, three cadences).  *best_index (may be NULL) receives
- * the chosen candidate's index.  Synchronises.  Candidates that pic_set_tuning
- * rejects are skipped; PIC_ERR_ARG if none is valid. */
+ * advance the simulation exactly as pic_step does.  Two passes over the
+ * candidates, the second in reverse order: for each candidate it re-sorts if
+ * the tiles change, takes 2*sort_every untimed steps (which also capture its
+ * step graph), then times max(steps, 2*sort_every) steps (rounded up to whole
+ * sort cycles) with CUDA events; the candidate with the smallest sum of its
+ * two per-step times is kept.  candidates == NULL selects a built-in set of
+ * 18 for the grid's dimension (three tile shapes around the default, halos 3
+ * and 4 in 1D/2D or 2 and 3 in 3D, three cadences).  *best_index (may be
+ * NULL) receives the chosen candidate's index.  Synchronises.  Candidates
+ * that pic_set_tuning rejects are skipped; PIC_ERR_ARG if none is valid. */
 pic_status pic_autotune(pic_ctx* ctx, const pic_tuning* candidates, int ncandidates, int steps,
                         int* best_index);
 

@@ -1291,34 +1291,46 @@ pic_status pic_autotune(pic_ctx* ctx, const pic_tuning* candidates, int ncandida
   cudaEvent_t ea = nullptr, eb = nullptr;
   PIC_CK(ctx, cudaEventCreate(&ea));
   PIC_CK(ctx, cudaEventCreate(&eb));
-  double best_ms = 1e300;
-  int best = -1;
+  // Two passes over the candidates, the second in reverse order, each
+  // candidate's time the sum of both: the plasma keeps evolving while the
+  // candidates run (a heating plasma strays more), and a drift in the step
+  // time then weighs on every candidate alike.  Before each timed run an
+  // untimed one of two sort cycles re-sorts into the new tiles and captures
+  // the new step graph, so that neither lands in the timed interval.
+  std::vector<double> per_step(cs.size(), 0.0);
+  std::vector<char> valid(cs.size(), 1);
   pic_status st = PIC_OK;
-  for (size_t i = 0; i < cs.size() && st == PIC_OK; ++i) {
-    pic_tuning t = cs[i];
-    t.filter_passes = orig.filter_passes;  // physics, not a launch parameter
-    if (t.chunk == 0) t.chunk = orig.chunk;
-    if (pic_set_tuning(ctx, &t) != PIC_OK) continue;  // e.g. window too large: skip
-    const int k = ((std::max(steps, 2 * ctx->tun.sort_every) + ctx->tun.sort_every - 1) /
-                   ctx->tun.sort_every) * ctx->tun.sort_every;
-    if ((st = pic_step(ctx, 1)) != PIC_OK) break;
-    cudaEventRecord(ea, ctx->st);
-    if ((st = pic_step(ctx, k)) != PIC_OK) break;
-    cudaEventRecord(eb, ctx->st);
-    if (cudaEventSynchronize(eb) != cudaSuccess) {
-      st = cuda_fail(ctx, "autotune timing", cudaGetLastError());
-      break;
+  for (int pass = 0; pass < 2 && st == PIC_OK; ++pass)
+    for (size_t j = 0; j < cs.size() && st == PIC_OK; ++j) {
+      const size_t i = pass == 0 ? j : cs.size() - 1 - j;
+      if (!valid[i]) continue;
+      pic_tuning t = cs[i];
+      t.filter_passes = orig.filter_passes;  // physics, not a launch parameter
+      if (t.chunk == 0) t.chunk = orig.chunk;
+      if (pic_set_tuning(ctx, &t) != PIC_OK) {  // e.g. window too large: skip
+        valid[i] = 0;
+        continue;
+      }
+      const int S = ctx->tun.sort_every;
+      const int k = ((std::max(steps, 2 * S) + S - 1) / S) * S;
+      if ((st = pic_step(ctx, 2 * S)) != PIC_OK) break;
+      cudaEventRecord(ea, ctx->st);
+      if ((st = pic_step(ctx, k)) != PIC_OK) break;
+      cudaEventRecord(eb, ctx->st);
+      if (cudaEventSynchronize(eb) != cudaSuccess) {
+        st = cuda_fail(ctx, "autotune timing", cudaGetLastError());
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ea, eb);
+      per_step[i] += ms / k;
     }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ea, eb);
-    if (ms / k < best_ms) {
-      best_ms = ms / k;
-      best = (int)i;
-    }
-  }
   cudaEventDestroy(ea);
   cudaEventDestroy(eb);
   if (st != PIC_OK) return st;
+  int best = -1;
+  for (size_t i = 0; i < cs.size(); ++i)
+    if (valid[i] && (best < 0 || per_step[i] < per_step[best])) best = (int)i;
   if (best < 0) {
     pic_set_tuning(ctx, &orig);
     return set_err(ctx, PIC_ERR_ARG, "no candidate tuning was valid");
