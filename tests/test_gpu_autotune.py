@@ -9,18 +9,29 @@ from gpu_helpers import compare_fields, current_scale, oracle_from_sim
 
 pytestmark = pytest.mark.gpu
 
-CANDIDATES = [dict(tile=[16, 16, 1], halo=3, sort_every=3),
-              dict(tile=[8, 8, 1], halo=2, sort_every=5),
-              dict(tile=[16, 8, 1], halo=2, sort_every=4)]
+# short cadences: the autotuner takes 4 cycles of each candidate (two passes
+# of 2 untimed + 2 timed), 40 steps in all; over many more steps the two runs'
+# float-atomic orders drift apart in the turbulent plasma beyond the tolerance
+CANDIDATES = [dict(tile=[16, 16, 1], halo=3, sort_every=2),
+              dict(tile=[8, 8, 1], halo=2, sort_every=1),
+              dict(tile=[16, 8, 1], halo=2, sort_every=2)]
 
 
-def _steps_taken(cands, steps):
-    # two passes; per candidate 2 sort cycles untimed, then the timed whole cycles
-    total = 0
-    for c in cands:
-        k = c["sort_every"]
-        total += 2 * k + -(-max(steps, 2 * k) // k) * k
-    return 2 * total
+def _replay_autotune(sim, cands, steps, chosen):
+    """The steps pic_autotune documents, taken through set_tuning and step: two
+    passes over the candidates (the second in reverse order), each candidate
+    re-tuned, stepped two sort cycles, then max(steps, 2 cycles) rounded up to
+    whole cycles; at the end the chosen tuning is set."""
+    orig = sim.tuning()
+    for order in (cands, cands[::-1]):
+        for c in order:
+            k = c["sort_every"]
+            sim.set_tuning(tile=c["tile"], halo=c["halo"], sort_every=k,
+                           filter_passes=orig["filter_passes"], chunk=orig["chunk"])
+            sim.step(2 * k)
+            sim.step(-(-max(steps, 2 * k) // k) * k)
+    sim.set_tuning(tile=chosen["tile"], halo=chosen["halo"], sort_every=chosen["sort_every"],
+                   filter_passes=orig["filter_passes"], chunk=orig["chunk"])
 
 
 def test_autotune_advances_the_simulation_like_pic_step():
@@ -30,11 +41,12 @@ def test_autotune_advances_the_simulation_like_pic_step():
     a = Simulation.from_plasma(pl)
     b = Simulation.from_plasma(pl)
     g, _, osp, _ = oracle_from_sim(a)
-    chosen = a.autotune(CANDIDATES, steps=6)
+    chosen = a.autotune(CANDIDATES, steps=2)
     assert any(chosen["tile"][:2] == c["tile"][:2] and chosen["halo"] == c["halo"] and
                chosen["sort_every"] == c["sort_every"] for c in CANDIDATES)
-    nsteps = _steps_taken(CANDIDATES, 6)
-    b.step(nsteps)
+    _replay_autotune(b, CANDIDATES, 2, chosen)
+    assert a.tuning() == b.tuning()
+    nsteps = 2 * sum(4 * c["sort_every"] for c in CANDIDATES)
     a.check()
     b.check()
     Fa, _ = a.download()
