@@ -358,7 +358,15 @@ pic_status pic_wait_probe(pic_ctx* ctx);
  * buffers, runs pic_step(nsteps), copies particles and fields back into the
  * same host buffers and synchronises.  Host rows have the species' cap
  * elements; the counts before the steps are copied in and those after them
- * (pic_particle_counts) copied out. */
+ * (pic_particle_counts) copied out.  Host buffers should be pinned (page-
+ * locked) for the copies to overlap.  On boxes without shock boundaries, with
+ * the event timers off and nsteps >= 1, the copies overlap: in on one stream
+ * of the library's (fields, then species after species), out on another; the
+ * last step sorts (when due) and runs the particle kernel species by species,
+ * each as soon as its particles are in, and each species is copied out as
+ * soon as its push is done while the next is still coming in.  The result
+ * equals pic_step's up to the float rounding of J's sum over the species
+ * (each species' launch adds its own window sums to J). */
 pic_status pic_step_host(pic_ctx* ctx, const pic_host_species* hs, float* host_fields,
                          int nsteps);
 

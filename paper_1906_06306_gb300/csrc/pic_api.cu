@@ -91,6 +91,9 @@ struct pic_ctx {
   pic_tuning step_tun{};
   long long step_phase = -1;
   int step_solver = -1;
+  // pic_step_host's copy streams (in, out) and its events, made on first use
+  cudaStream_t io_st[2] = {nullptr, nullptr};
+  cudaEvent_t io_ev[2 * PIC_MAX_SPECIES + 3] = {};
   bool timing = false;
   std::vector<TimedLaunch> pending;
   std::vector<cudaEvent_t> pool;
@@ -157,6 +160,14 @@ void free_all(pic_ctx* ctx) {
   ctx->step_graph = nullptr;
   if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
   ctx->cap_st = nullptr;
+  for (auto& io : ctx->io_st) {
+    if (io) cudaStreamDestroy(io);
+    io = nullptr;
+  }
+  for (auto& ev : ctx->io_ev) {
+    if (ev) cudaEventDestroy(ev);
+    ev = nullptr;
+  }
   for (auto& t : ctx->pending) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
@@ -429,40 +440,39 @@ PushParams make_params(pic_ctx* ctx) {
 // Sort every species by tile into the sorted buffer.  With copy_back the
 // sorted particles are copied into the caller's arrays; without, the next push
 // reads them from the buffer and writes the caller's arrays (pic_step).
-pic_status do_sort(pic_ctx* ctx, bool copy_back, int32_t* const* perm = nullptr) {
+// The launches that sort species s by tile into its part of the sorted
+// buffer (and, with copy_back, copy it back into the caller's arrays).
+cudaError_t sort_species(pic_ctx* ctx, int s, bool copy_back, int32_t* perm) {
   const SortParams P = make_sort_params(ctx->g, ctx->tile, ctx->d_status);
   const int D = ctx->grid.dim;
-  const cudaError_t e = timed(ctx, PIC_KERNEL_SORT, [&]() -> cudaError_t {
-    for (int s = 0; s < ctx->ns; ++s) {
-      const long long n = ctx->sp[s].n, ld = ctx->cap[s];
-      const int bins = (int)sort_bins(ctx->tile);
-      cudaError_t r = cudaMemsetAsync(ctx->d_count, 0, sizeof(int) * bins, ctx->st);
-      if (r != cudaSuccess) return r;
-      r = launch_tile_count(P, ctx->sp[s].cell, n, ctx->d_count, ctx->st);
-      if (r != cudaSuccess) return r;
-      r = launch_tile_scan(ctx->d_count, bins, ctx->d_tstart[s], ctx->d_cursor,
-                           ctx->d_count + bins, ctx->st);
-      if (r != cudaSuccess) return r;
-      if (n == 0) continue;
-      int* cell_out = (int*)ctx->d_sortbuf + sortbuf_offset(ctx, s);
-      float* off_out = (float*)(cell_out + ld);
-      float* u_out = off_out + (long long)D * ld;
-      r = launch_tile_scatter(P, ctx->sp[s].cell, ctx->sp[s].off, ctx->sp[s].u, n, ld,
-                              ctx->d_cursor, cell_out, off_out, u_out, ctx->st,
-                              perm ? perm[s] : nullptr);
-      if (r != cudaSuccess) return r;
-      if (!copy_back) continue;
-      const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
-      r = copy_rows(ctx->sp[s].cell, cell_out, sizeof(int), n, ld, 1, k, ctx->st);
-      if (r != cudaSuccess) return r;
-      r = copy_rows(ctx->sp[s].off, off_out, sizeof(float), n, ld, D, k, ctx->st);
-      if (r != cudaSuccess) return r;
-      r = copy_rows(ctx->sp[s].u, u_out, sizeof(float), n, ld, 3, k, ctx->st);
-      if (r != cudaSuccess) return r;
-    }
-    return cudaSuccess;
-  });
-  if (e != cudaSuccess) return cuda_fail(ctx, "tile sort", e);
+  const long long n = ctx->sp[s].n, ld = ctx->cap[s];
+  const int bins = (int)sort_bins(ctx->tile);
+  cudaError_t r = cudaMemsetAsync(ctx->d_count, 0, sizeof(int) * bins, ctx->st);
+  if (r != cudaSuccess) return r;
+  r = launch_tile_count(P, ctx->sp[s].cell, n, ctx->d_count, ctx->st);
+  if (r != cudaSuccess) return r;
+  r = launch_tile_scan(ctx->d_count, bins, ctx->d_tstart[s], ctx->d_cursor, ctx->d_count + bins,
+                       ctx->st);
+  if (r != cudaSuccess) return r;
+  if (n == 0) return cudaSuccess;
+  int* cell_out = (int*)ctx->d_sortbuf + sortbuf_offset(ctx, s);
+  float* off_out = (float*)(cell_out + ld);
+  float* u_out = off_out + (long long)D * ld;
+  r = launch_tile_scatter(P, ctx->sp[s].cell, ctx->sp[s].off, ctx->sp[s].u, n, ld, ctx->d_cursor,
+                          cell_out, off_out, u_out, ctx->st, perm);
+  if (r != cudaSuccess) return r;
+  if (!copy_back) return cudaSuccess;
+  const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  r = copy_rows(ctx->sp[s].cell, cell_out, sizeof(int), n, ld, 1, k, ctx->st);
+  if (r != cudaSuccess) return r;
+  r = copy_rows(ctx->sp[s].off, off_out, sizeof(float), n, ld, D, k, ctx->st);
+  if (r != cudaSuccess) return r;
+  return copy_rows(ctx->sp[s].u, u_out, sizeof(float), n, ld, 3, k, ctx->st);
+}
+
+// The context's bookkeeping of a tile sort of every species (at the current
+// step, with or without copy back); launches nothing.
+void sort_done(pic_ctx* ctx, bool copy_back) {
   long long ntot = 0;
   for (int s = 0; s < ctx->ns; ++s) {
     ctx->sorted_n[s] = ctx->sp[s].n;
@@ -480,6 +490,18 @@ pic_status do_sort(pic_ctx* ctx, bool copy_back, int32_t* const* perm = nullptr)
   ctx->snapshot_valid = false;
   ctx->sorted_pending = !copy_back;
   ctx->sorted_step = ctx->steps;
+}
+
+pic_status do_sort(pic_ctx* ctx, bool copy_back, int32_t* const* perm = nullptr) {
+  const cudaError_t e = timed(ctx, PIC_KERNEL_SORT, [&]() -> cudaError_t {
+    for (int s = 0; s < ctx->ns; ++s) {
+      const cudaError_t r = sort_species(ctx, s, copy_back, perm ? perm[s] : nullptr);
+      if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+  });
+  if (e != cudaSuccess) return cuda_fail(ctx, "tile sort", e);
+  sort_done(ctx, copy_back);
   return PIC_OK;
 }
 
@@ -1063,6 +1085,39 @@ pic_status pic_field_update(pic_ctx* ctx, int which) {
   return PIC_OK;
 }
 
+// The conducting wall's field condition after a field update (shock boxes).
+cudaError_t wall_fields(pic_ctx* ctx) {
+  if (!ctx->shock) return cudaSuccess;
+  return timed(ctx, PIC_KERNEL_BOUNDARY, [&]() {
+    return launch_wall_fields(ctx->g, ctx->F, ctx->wall, ctx->i_zero, ctx->st);
+  });
+}
+
+// The field half of a step, after the particles deposited J: the filter
+// passes, the second B half step and the E update.
+pic_status step_fields(pic_ctx* ctx) {
+  cudaError_t e;
+  if (!ctx->shock && fields_small_ok(ctx->g)) {
+    // small periodic lattice: the filter (on J) first, then the second B
+    // half step and the E update in one launch (the B half step touches B
+    // only, the filter J only: the order between them does not matter)
+    const pic_status s = do_filter(ctx, ctx->tun.filter_passes);
+    if (s != PIC_OK) return s;
+    e = timed(ctx, PIC_KERNEL_EUPD, [&]() { return launch_fields_small(ctx->g, ctx->F, ctx->st); });
+    if (e != cudaSuccess) return cuda_fail(ctx, "B half step and E update", e);
+  } else {
+    e = timed(ctx, PIC_KERNEL_BHALF, [&]() { return launch_b_half(ctx->g, ctx->F, 0, ctx->st); });
+    if (e == cudaSuccess) e = wall_fields(ctx);
+    if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
+    const pic_status s = do_filter(ctx, ctx->tun.filter_passes);
+    if (s != PIC_OK) return s;
+    e = timed(ctx, PIC_KERNEL_EUPD, [&]() { return launch_e_update(ctx->g, ctx->F, ctx->st); });
+    if (e == cudaSuccess) e = wall_fields(ctx);
+    if (e != cudaSuccess) return cuda_fail(ctx, "E update", e);
+  }
+  return PIC_OK;
+}
+
 pic_status pic_step(pic_ctx* ctx, int nsteps) {
   if (!ctx) return PIC_ERR_ARG;
   if (nsteps < 0) return set_err(ctx, PIC_ERR_ARG, "nsteps must be >= 0");
@@ -1084,12 +1139,7 @@ pic_status pic_step(pic_ctx* ctx, int nsteps) {
     ctx->snapshot_valid = false;
     nsteps -= full * cyc;
   }
-  const auto wall_bc = [&]() {
-    if (!ctx->shock) return cudaSuccess;
-    return timed(ctx, PIC_KERNEL_BOUNDARY, [&]() {
-      return launch_wall_fields(ctx->g, ctx->F, ctx->wall, ctx->i_zero, ctx->st);
-    });
-  };
+  const auto wall_bc = [&]() { return wall_fields(ctx); };
   for (int it = 0; it < nsteps; ++it) {
     InjectParams IP{};
     long long add[PIC_MAX_SPECIES] = {};
@@ -1114,23 +1164,9 @@ pic_status pic_step(pic_ctx* ctx, int nsteps) {
     if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
     e = timed(ctx, PIC_KERNEL_PUSH, [&]() { return launch_particles(ctx->grid.dim, 0, P, ctx->st); });
     if (e != cudaSuccess) return cuda_fail(ctx, "gather/push/deposit kernel", e);
-    if (!ctx->shock && fields_small_ok(ctx->g)) {
-      // small periodic lattice: the filter (on J) first, then the second B
-      // half step and the E update in one launch (the B half step touches B
-      // only, the filter J only: the order between them does not matter)
-      const pic_status s = do_filter(ctx, ctx->tun.filter_passes);
+    {
+      const pic_status s = step_fields(ctx);
       if (s != PIC_OK) return s;
-      e = timed(ctx, PIC_KERNEL_EUPD, [&]() { return launch_fields_small(ctx->g, ctx->F, ctx->st); });
-      if (e != cudaSuccess) return cuda_fail(ctx, "B half step and E update", e);
-    } else {
-      e = timed(ctx, PIC_KERNEL_BHALF, [&]() { return launch_b_half(ctx->g, ctx->F, 0, ctx->st); });
-      if (e == cudaSuccess) e = wall_bc();
-      if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
-      const pic_status s = do_filter(ctx, ctx->tun.filter_passes);
-      if (s != PIC_OK) return s;
-      e = timed(ctx, PIC_KERNEL_EUPD, [&]() { return launch_e_update(ctx->g, ctx->F, ctx->st); });
-      if (e == cudaSuccess) e = wall_bc();
-      if (e != cudaSuccess) return cuda_fail(ctx, "E update", e);
     }
     if (ctx->shock) {
       if (IP.nruns > 0) {
@@ -1218,12 +1254,99 @@ pic_status pic_wait_probe(pic_ctx* ctx) {
   return PIC_OK;
 }
 
+// pic_step_host overlaps its copies in and out (species by species) with
+// each other and with the last step.
+#ifndef PIC_HOST_OVERLAP
+#define PIC_HOST_OVERLAP 1
+#endif
+
+// pic_step_host with its copies overlapped.  The copies in run on one stream,
+// the fields first and then species after species; the copies out on another.
+// The steps before the last wait for every copy in; the last step sorts (when
+// due) and pushes species after species, each as soon as its particles are
+// in, and sends each species back out as soon as its push is done, while the
+// next species is still coming in: the host link moves data both ways at once
+// faster than one way at a time.  The launches are pic_step's, with the sort
+// and the particle kernel split by species.
+pic_status step_host_overlapped(pic_ctx* ctx, const pic_host_species* hs, float* host_fields,
+                                int nsteps) {
+  const int D = ctx->grid.dim, ns = ctx->ns;
+  const cudaMemcpyKind h2d = cudaMemcpyHostToDevice, d2h = cudaMemcpyDeviceToHost;
+  for (auto& io : ctx->io_st)
+    if (!io) PIC_CK(ctx, cudaStreamCreateWithFlags(&io, cudaStreamNonBlocking));
+  for (auto& ev : ctx->io_ev)
+    if (!ev) PIC_CK(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  const cudaStream_t in = ctx->io_st[0], out = ctx->io_st[1];
+  cudaEvent_t* ev_in = ctx->io_ev;                                 // species s is in
+  cudaEvent_t* ev_pushed = ctx->io_ev + PIC_MAX_SPECIES;           // species s is final
+  const cudaEvent_t ev_go = ctx->io_ev[2 * PIC_MAX_SPECIES];       // earlier work queued
+  const cudaEvent_t ev_fin = ctx->io_ev[2 * PIC_MAX_SPECIES + 1];  // fields are in
+  const cudaEvent_t ev_fout = ctx->io_ev[2 * PIC_MAX_SPECIES + 2];  // fields are final
+  // the copies in overwrite buffers that work queued earlier may still use
+  PIC_CK(ctx, cudaEventRecord(ev_go, ctx->st));
+  PIC_CK(ctx, cudaStreamWaitEvent(in, ev_go, 0));
+  PIC_CK(ctx, cudaMemcpyAsync(ctx->F, host_fields, 36 * ctx->g.plane, h2d, in));
+  PIC_CK(ctx, cudaEventRecord(ev_fin, in));
+  for (int s = 0; s < ns; ++s) {
+    const long long n = ctx->sp[s].n, ld = ctx->cap[s];
+    PIC_CK(ctx, copy_rows(ctx->sp[s].cell, hs[s].cell, 4, n, ld, 1, h2d, in));
+    PIC_CK(ctx, copy_rows(ctx->sp[s].off, hs[s].off, 4, n, ld, D, h2d, in));
+    PIC_CK(ctx, copy_rows(ctx->sp[s].u, hs[s].u, 4, n, ld, 3, h2d, in));
+    PIC_CK(ctx, cudaEventRecord(ev_in[s], in));
+  }
+  PIC_CK(ctx, cudaStreamWaitEvent(ctx->st, ev_fin, 0));
+  if (nsteps > 1) {
+    for (int s = 0; s < ns; ++s) PIC_CK(ctx, cudaStreamWaitEvent(ctx->st, ev_in[s], 0));
+    const pic_status r = pic_step(ctx, nsteps - 1);
+    if (r != PIC_OK) return r;
+  }
+  // the last step: the context's bookkeeping of a due sort comes first, so
+  // that the particle parameters read every species from the sorted buffer
+  const bool sort = ctx->steps % ctx->tun.sort_every == 0 && ctx->sorted_step != ctx->steps;
+  if (sort) sort_done(ctx, false);
+  const PushParams P = make_params(ctx);
+  ctx->sorted_pending = false;
+  cudaError_t e = launch_b_half(ctx->g, ctx->F, 1, ctx->st);
+  if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
+  for (int s = 0; s < ns; ++s) {
+    PIC_CK(ctx, cudaStreamWaitEvent(ctx->st, ev_in[s], 0));
+    if (sort && (e = sort_species(ctx, s, false, nullptr)) != cudaSuccess)
+      return cuda_fail(ctx, "tile sort", e);
+    PushParams Ps = P;  // species s alone; the current's quantum stays the step's
+    Ps.nspecies = 1;
+    Ps.sp[0] = P.sp[s];
+    Ps.dcount = P.sp[s].dcount;
+    if ((e = launch_particles(D, 0, Ps, ctx->st)) != cudaSuccess)
+      return cuda_fail(ctx, "gather/push/deposit kernel", e);
+    PIC_CK(ctx, cudaEventRecord(ev_pushed[s], ctx->st));
+    PIC_CK(ctx, cudaStreamWaitEvent(out, ev_pushed[s], 0));
+    const long long n = ctx->sp[s].n, ld = ctx->cap[s];
+    PIC_CK(ctx, copy_rows(hs[s].cell, ctx->sp[s].cell, 4, n, ld, 1, d2h, out));
+    PIC_CK(ctx, copy_rows(hs[s].off, ctx->sp[s].off, 4, n, ld, D, d2h, out));
+    PIC_CK(ctx, copy_rows(hs[s].u, ctx->sp[s].u, 4, n, ld, 3, d2h, out));
+  }
+  const pic_status r = step_fields(ctx);
+  if (r != PIC_OK) return r;
+  ++ctx->steps;
+  ctx->snapshot_valid = false;
+  PIC_CK(ctx, cudaEventRecord(ev_fout, ctx->st));
+  PIC_CK(ctx, cudaStreamWaitEvent(out, ev_fout, 0));
+  PIC_CK(ctx, cudaMemcpyAsync(host_fields, ctx->F, 36 * ctx->g.plane, d2h, out));
+  PIC_CK(ctx, cudaStreamSynchronize(out));
+  PIC_CK(ctx, cudaStreamSynchronize(ctx->st));
+  return PIC_OK;
+}
+
 pic_status pic_step_host(pic_ctx* ctx, const pic_host_species* hs, float* host_fields, int nsteps) {
   if (!ctx || !hs || !host_fields) return set_err(ctx, PIC_ERR_ARG, "NULL argument");
   const int D = ctx->grid.dim;
   for (int s = 0; s < ctx->ns; ++s)
     if (ctx->sp[s].n > 0 && (!hs[s].cell || !hs[s].off || !hs[s].u))
       return set_err(ctx, PIC_ERR_ARG, "host species buffers are NULL");
+  // boxes without shock boundaries (whose counts the injector changes),
+  // with the event timers off: the overlapped copies
+  if (PIC_HOST_OVERLAP && nsteps >= 1 && !ctx->shock && !ctx->timing)
+    return step_host_overlapped(ctx, hs, host_fields, nsteps);
   const cudaMemcpyKind h2d = cudaMemcpyHostToDevice, d2h = cudaMemcpyDeviceToHost;
   for (int s = 0; s < ctx->ns; ++s) {
     const long long n = ctx->sp[s].n, ld = ctx->cap[s];

@@ -39,8 +39,13 @@ def _oracle_like(sim):
     return oracle.Grid(sim.dim, sim.nx, sim.ny, sim.nz, sim.c)
 
 
-@pytest.mark.parametrize("shock,dim", [(False, 2), (True, 2), (False, 3)])
-def test_step_host_equals_device_steps(shock, dim):
+# (shock, dim, steps, sort cadence): the periodic boxes take the overlapped
+# copies, whose last step sorts and pushes species by species; with a cadence
+# of 2 the last of 3 steps (and the only one of 1) opens a sort cycle
+@pytest.mark.parametrize("shock,dim,nsteps,sort_every",
+                         [(False, 2, 4, 1000), (True, 2, 4, 1000), (False, 3, 4, 1000),
+                          (False, 2, 3, 2), (False, 2, 1, 2), (False, 3, 3, 2)])
+def test_step_host_equals_device_steps(shock, dim, nsteps, sort_every):
     import oracle
 
     from paper_1906_06306_gb300 import Simulation
@@ -56,7 +61,8 @@ def test_step_host_equals_device_steps(shock, dim):
     else:  # hot 3D plasma, halo 1: strays go through the deferred-particle kernel
         pl = workloads.uniform_plasma(3, 21, 19, 13, 0.45, 2, 0.01, 2.0, seed=95)
         cap = None
-    tun = dict(sort_every=1000) if dim == 2 else dict(tile=[4, 4, 4], halo=1, sort_every=1000)
+    tun = (dict(sort_every=sort_every) if dim == 2 else
+           dict(tile=[4, 4, 4], halo=1, sort_every=sort_every))
     sims = []
     for _ in range(2):
         sim = Simulation.from_plasma(pl, capacity=cap, tuning=tun)
@@ -64,8 +70,10 @@ def test_step_host_equals_device_steps(shock, dim):
             sim.set_shock_from_plasma(pl)
         sims.append(sim)
     dev, host = sims
+    if nsteps == 1:  # the set-up sort was at step 0: two steps to reach step 2's sort
+        for sim in sims:
+            sim.step(2)
     hs, keep, hf = _host_buffers(host)
-    nsteps = 4
     B.pic_step_host(host.ctx, hs, hf.data_ptr(), nsteps)
     dev.step(nsteps)
     Fd, spd = dev.download()
