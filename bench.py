@@ -844,6 +844,8 @@ def run_ours(args):
             hs.append(B.pic_host_species(*[a.data_ptr() for a in arrs]))
         hf = torch.from_numpy(F0).pin_memory()
         rec = 4 + 4 * pl.dim + 12
+        if args.host_chunk > 0:
+            B.pic_set_host_chunk(sim.ctx, args.host_chunk)
         B.pic_step_host(sim.ctx, hs, hf.data_ptr(), 1)  # warm-up
         if dist is not None:
             dist.barrier()
@@ -1262,6 +1264,9 @@ def main():
                     help="keep the default tuning instead of autotuning before the timed region")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-chunk", type=int, default=0,
+                    help="particles per chunk of the end-to-end call's overlapped copies "
+                         "(0 = library default)")
     ap.add_argument("--no-sub-records", dest="sub_records", action="store_false",
                     help="skip the bounded 1D Weibel and 3D shock runs of the default line")
     ap.add_argument("--grid", type=int, default=0,

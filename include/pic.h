@@ -353,6 +353,11 @@ pic_status pic_check(pic_ctx* ctx);
  * PIC_ERR_ARG for a NULL context, PIC_ERR_CUDA if the launch fails. */
 pic_status pic_wait_probe(pic_ctx* ctx);
 
+/* Particles per chunk of a species in pic_step_host's overlapped copies
+ * (default 2^21; at most 8 chunks per species).  PIC_ERR_ARG outside
+ * [1, 2^30]. */
+pic_status pic_set_host_chunk(pic_ctx* ctx, int64_t particles);
+
 /* End-to-end step from host memory: copies every species' particles from
  * `hs` and the 9 field planes from `host_fields` into the context's device
  * buffers, runs pic_step(nsteps), copies particles and fields back into the
@@ -360,13 +365,14 @@ pic_status pic_wait_probe(pic_ctx* ctx);
  * elements; the counts before the steps are copied in and those after them
  * (pic_particle_counts) copied out.  Host buffers should be pinned (page-
  * locked) for the copies to overlap.  On boxes without shock boundaries, with
- * the event timers off and nsteps >= 1, the copies overlap: in on one stream
- * of the library's (fields, then species after species), out on another; the
- * last step sorts (when due) and runs the particle kernel species by species,
- * each as soon as its particles are in, and each species is copied out as
- * soon as its push is done while the next is still coming in.  The result
- * equals pic_step's up to the float rounding of J's sum over the species
- * (each species' launch adds its own window sums to J). */
+ * the event timers off and nsteps >= 1, the copies overlap: each species is
+ * cut into chunks of slots (pic_set_host_chunk), copied in on one stream of
+ * the library's (fields first, then chunk after chunk) and out on another;
+ * the last step runs the particle kernel chunk by chunk, each as soon as its
+ * chunk is in (a sort due at that step waits for the whole species), and each
+ * chunk is copied out as soon as its launch is done while later chunks are
+ * still coming in.  The result equals pic_step's up to the float rounding of
+ * J's sum (each launch adds its own window sums to J). */
 pic_status pic_step_host(pic_ctx* ctx, const pic_host_species* hs, float* host_fields,
                          int nsteps);
 

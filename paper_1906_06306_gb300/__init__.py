@@ -23,7 +23,7 @@ Use (device memory and the stream come from PyTorch):
     loss = MagneticEnergy.apply(amps, u0, problem); loss.backward()  # discrete adjoint
 """
 _API = {
-    "PicError", "pic_init", "pic_set_pusher", "pic_set_field_solver", "pic_get_tuning",
+    "PicError", "pic_init", "pic_set_pusher", "pic_set_host_chunk", "pic_set_field_solver", "pic_get_tuning",
     "pic_set_tuning", "pic_set_shock", "pic_particle_counts", "pic_adjoint_step", "pic_sort",
     "pic_sort_bins", "pic_sort_record", "pic_sort_assume", "pic_adjoint_unsort", "pic_gather_push",
     "pic_deposit", "pic_filter_current", "pic_field_update", "pic_step", "pic_energies",

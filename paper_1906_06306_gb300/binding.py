@@ -57,6 +57,7 @@ SIGNATURES = {
     "pic_get_tuning": (c_int, [_P, ctypes.POINTER(pic_tuning)]),
     "pic_set_tuning": (c_int, [_P, ctypes.POINTER(pic_tuning)]),
     "pic_set_pusher": (c_int, [_P, c_int]),
+    "pic_set_host_chunk": (c_int, [_P, c_int64]),
     "pic_set_field_solver": (c_int, [_P, c_int]),
     "pic_set_shock": (c_int, [_P, ctypes.POINTER(pic_shock)]),
     "pic_particle_counts": (c_int, [_P, ctypes.POINTER(c_int64), c_int]),
@@ -150,6 +151,10 @@ def pic_set_field_solver(ctx, order: int) -> None:
 
 def pic_set_pusher(ctx, pusher: int) -> None:
     _check(_lib.pic_set_pusher(ctx, pusher), ctx)
+
+
+def pic_set_host_chunk(ctx, particles: int) -> None:
+    _check(_lib.pic_set_host_chunk(ctx, particles), ctx)
 
 
 def pic_set_shock(ctx, shock: pic_shock) -> None:

@@ -22,6 +22,9 @@ struct TimedLaunch {
 
 thread_local std::string g_init_error;
 
+// most chunks per species of the overlapped pic_step_host
+constexpr int kHostChunks = 8;
+
 }  // namespace
 
 namespace pic {
@@ -91,9 +94,14 @@ struct pic_ctx {
   pic_tuning step_tun{};
   long long step_phase = -1;
   int step_solver = -1;
-  // pic_step_host's copy streams (in, out) and its events, made on first use
+  // pic_step_host's copy streams (in, out), its events (copied in and pushed,
+  // per species and chunk; three more) and clipped bucket starts (one table
+  // per chunk), made on first use
   cudaStream_t io_st[2] = {nullptr, nullptr};
-  cudaEvent_t io_ev[2 * PIC_MAX_SPECIES + 3] = {};
+  cudaEvent_t io_ev[2 * PIC_MAX_SPECIES * kHostChunks + 3] = {};
+  int* d_tclip = nullptr;
+  long long tclip_len = 0;
+  long long host_chunk = 1LL << 21;  // particles per chunk (pic_set_host_chunk)
   bool timing = false;
   std::vector<TimedLaunch> pending;
   std::vector<cudaEvent_t> pool;
@@ -154,6 +162,7 @@ void free_all(pic_ctx* ctx) {
   dfree(ctx->d_dlist);
   dfree(ctx->d_dcount);
   dfree(ctx->d_adjF);
+  dfree(ctx->d_tclip);
   if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
   if (ctx->step_graph) cudaGraphDestroy(ctx->step_graph);
   ctx->step_exec = nullptr;
@@ -794,6 +803,14 @@ pic_status pic_set_pusher(pic_ctx* ctx, int pusher) {
   return PIC_OK;
 }
 
+pic_status pic_set_host_chunk(pic_ctx* ctx, int64_t particles) {
+  if (!ctx) return PIC_ERR_ARG;
+  if (particles < 1 || particles > (1LL << 30))
+    return set_err(ctx, PIC_ERR_ARG, "particles per chunk must be in [1, 2^30]");
+  ctx->host_chunk = particles;
+  return PIC_OK;
+}
+
 pic_status pic_set_shock(pic_ctx* ctx, const pic_shock* sh) {
   if (!ctx) return PIC_ERR_ARG;
   if (!sh) return set_err(ctx, PIC_ERR_ARG, "shock is NULL");
@@ -1254,20 +1271,33 @@ pic_status pic_wait_probe(pic_ctx* ctx) {
   return PIC_OK;
 }
 
-// pic_step_host overlaps its copies in and out (species by species) with
-// each other and with the last step.
+// pic_step_host overlaps its copies in and out (chunk by chunk) with each
+// other and with the last step.
 #ifndef PIC_HOST_OVERLAP
 #define PIC_HOST_OVERLAP 1
 #endif
+// Copy the slots [lo, hi) of `rows` rows of ld elements of `elem` bytes.
+cudaError_t copy_slots(void* dst, const void* src, size_t elem, long long lo, long long hi,
+                       long long ld, int rows, cudaMemcpyKind kind, cudaStream_t st) {
+  if (hi <= lo || rows == 0) return cudaSuccess;
+  char* d = static_cast<char*>(dst) + elem * (size_t)lo;
+  const char* s = static_cast<const char*>(src) + elem * (size_t)lo;
+  if (rows == 1) return cudaMemcpyAsync(d, s, elem * (size_t)(hi - lo), kind, st);
+  return cudaMemcpy2DAsync(d, elem * (size_t)ld, s, elem * (size_t)ld, elem * (size_t)(hi - lo),
+                           (size_t)rows, kind, st);
+}
 
-// pic_step_host with its copies overlapped.  The copies in run on one stream,
-// the fields first and then species after species; the copies out on another.
-// The steps before the last wait for every copy in; the last step sorts (when
-// due) and pushes species after species, each as soon as its particles are
-// in, and sends each species back out as soon as its push is done, while the
-// next species is still coming in: the host link moves data both ways at once
-// faster than one way at a time.  The launches are pic_step's, with the sort
-// and the particle kernel split by species.
+// pic_step_host with its copies overlapped.  Each species is cut into chunks
+// of slots (the context's host_chunk particles each, at most kHostChunks).  The copies in run
+// on one stream, the fields first and then chunk after chunk; the copies out
+// on another.  The steps before the last wait for every copy in.  The last
+// step runs the particle kernel chunk by chunk, each launch over bucket starts
+// clipped to the chunk's slots, as soon as the chunk is in, and sends each
+// chunk back out as soon as its launch is done while later chunks are still
+// coming in: the host link moves data both ways at once faster than one way
+// at a time.  A sort due at the last step waits for the whole species.  The
+// launches are pic_step's, with the sort split by species and the particle
+// kernel by chunk.
 pic_status step_host_overlapped(pic_ctx* ctx, const pic_host_species* hs, float* host_fields,
                                 int nsteps) {
   const int D = ctx->grid.dim, ns = ctx->ns;
@@ -1276,27 +1306,44 @@ pic_status step_host_overlapped(pic_ctx* ctx, const pic_host_species* hs, float*
     if (!io) PIC_CK(ctx, cudaStreamCreateWithFlags(&io, cudaStreamNonBlocking));
   for (auto& ev : ctx->io_ev)
     if (!ev) PIC_CK(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  const long long nb1 = sort_bins(ctx->tile) + 1;
+  if (!ctx->d_tclip || ctx->tclip_len < kHostChunks * nb1) {
+    dfree(ctx->d_tclip);
+    ctx->tclip_len = 0;
+    PIC_CK(ctx, dalloc(&ctx->d_tclip, kHostChunks * nb1));
+    ctx->tclip_len = kHostChunks * nb1;
+  }
+  int nk[PIC_MAX_SPECIES];
+  for (int s = 0; s < ns; ++s)
+    nk[s] = (int)std::min<long long>(
+        kHostChunks, std::max<long long>(1, (ctx->sp[s].n + ctx->host_chunk - 1) /
+                                                ctx->host_chunk));
+  const auto lo_of = [&](int s, int k) { return ctx->sp[s].n * k / nk[s]; };
+  const auto ev_in = [&](int s, int k) { return ctx->io_ev[s * kHostChunks + k]; };
+  const auto ev_pushed = [&](int s, int k) {
+    return ctx->io_ev[(PIC_MAX_SPECIES + s) * kHostChunks + k];
+  };
+  const int e0 = 2 * PIC_MAX_SPECIES * kHostChunks;
   const cudaStream_t in = ctx->io_st[0], out = ctx->io_st[1];
-  cudaEvent_t* ev_in = ctx->io_ev;                                 // species s is in
-  cudaEvent_t* ev_pushed = ctx->io_ev + PIC_MAX_SPECIES;           // species s is final
-  const cudaEvent_t ev_go = ctx->io_ev[2 * PIC_MAX_SPECIES];       // earlier work queued
-  const cudaEvent_t ev_fin = ctx->io_ev[2 * PIC_MAX_SPECIES + 1];  // fields are in
-  const cudaEvent_t ev_fout = ctx->io_ev[2 * PIC_MAX_SPECIES + 2];  // fields are final
+  const cudaEvent_t ev_go = ctx->io_ev[e0];        // earlier work queued
+  const cudaEvent_t ev_fin = ctx->io_ev[e0 + 1];   // fields are in
+  const cudaEvent_t ev_fout = ctx->io_ev[e0 + 2];  // fields are final
   // the copies in overwrite buffers that work queued earlier may still use
   PIC_CK(ctx, cudaEventRecord(ev_go, ctx->st));
   PIC_CK(ctx, cudaStreamWaitEvent(in, ev_go, 0));
   PIC_CK(ctx, cudaMemcpyAsync(ctx->F, host_fields, 36 * ctx->g.plane, h2d, in));
   PIC_CK(ctx, cudaEventRecord(ev_fin, in));
-  for (int s = 0; s < ns; ++s) {
-    const long long n = ctx->sp[s].n, ld = ctx->cap[s];
-    PIC_CK(ctx, copy_rows(ctx->sp[s].cell, hs[s].cell, 4, n, ld, 1, h2d, in));
-    PIC_CK(ctx, copy_rows(ctx->sp[s].off, hs[s].off, 4, n, ld, D, h2d, in));
-    PIC_CK(ctx, copy_rows(ctx->sp[s].u, hs[s].u, 4, n, ld, 3, h2d, in));
-    PIC_CK(ctx, cudaEventRecord(ev_in[s], in));
-  }
+  for (int s = 0; s < ns; ++s)
+    for (int k = 0; k < nk[s]; ++k) {
+      const long long lo = lo_of(s, k), hi = lo_of(s, k + 1), ld = ctx->cap[s];
+      PIC_CK(ctx, copy_slots(ctx->sp[s].cell, hs[s].cell, 4, lo, hi, ld, 1, h2d, in));
+      PIC_CK(ctx, copy_slots(ctx->sp[s].off, hs[s].off, 4, lo, hi, ld, D, h2d, in));
+      PIC_CK(ctx, copy_slots(ctx->sp[s].u, hs[s].u, 4, lo, hi, ld, 3, h2d, in));
+      PIC_CK(ctx, cudaEventRecord(ev_in(s, k), in));
+    }
   PIC_CK(ctx, cudaStreamWaitEvent(ctx->st, ev_fin, 0));
   if (nsteps > 1) {
-    for (int s = 0; s < ns; ++s) PIC_CK(ctx, cudaStreamWaitEvent(ctx->st, ev_in[s], 0));
+    for (int s = 0; s < ns; ++s) PIC_CK(ctx, cudaStreamWaitEvent(ctx->st, ev_in(s, nk[s] - 1), 0));
     const pic_status r = pic_step(ctx, nsteps - 1);
     if (r != PIC_OK) return r;
   }
@@ -1309,21 +1356,33 @@ pic_status step_host_overlapped(pic_ctx* ctx, const pic_host_species* hs, float*
   cudaError_t e = launch_b_half(ctx->g, ctx->F, 1, ctx->st);
   if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
   for (int s = 0; s < ns; ++s) {
-    PIC_CK(ctx, cudaStreamWaitEvent(ctx->st, ev_in[s], 0));
-    if (sort && (e = sort_species(ctx, s, false, nullptr)) != cudaSuccess)
-      return cuda_fail(ctx, "tile sort", e);
-    PushParams Ps = P;  // species s alone; the current's quantum stays the step's
-    Ps.nspecies = 1;
-    Ps.sp[0] = P.sp[s];
-    Ps.dcount = P.sp[s].dcount;
-    if ((e = launch_particles(D, 0, Ps, ctx->st)) != cudaSuccess)
-      return cuda_fail(ctx, "gather/push/deposit kernel", e);
-    PIC_CK(ctx, cudaEventRecord(ev_pushed[s], ctx->st));
-    PIC_CK(ctx, cudaStreamWaitEvent(out, ev_pushed[s], 0));
-    const long long n = ctx->sp[s].n, ld = ctx->cap[s];
-    PIC_CK(ctx, copy_rows(hs[s].cell, ctx->sp[s].cell, 4, n, ld, 1, d2h, out));
-    PIC_CK(ctx, copy_rows(hs[s].off, ctx->sp[s].off, 4, n, ld, D, d2h, out));
-    PIC_CK(ctx, copy_rows(hs[s].u, ctx->sp[s].u, 4, n, ld, 3, d2h, out));
+    if (sort) {  // the count covers the whole species
+      PIC_CK(ctx, cudaStreamWaitEvent(ctx->st, ev_in(s, nk[s] - 1), 0));
+      if ((e = sort_species(ctx, s, false, nullptr)) != cudaSuccess)
+        return cuda_fail(ctx, "tile sort", e);
+    }
+    for (int k = 0; k < nk[s]; ++k) {
+      const long long lo = lo_of(s, k), hi = lo_of(s, k + 1), ld = ctx->cap[s];
+      PIC_CK(ctx, cudaStreamWaitEvent(ctx->st, ev_in(s, k), 0));
+      PushParams Ps = P;  // chunk k of species s; the current's quantum stays the step's
+      Ps.nspecies = 1;
+      Ps.sp[0] = P.sp[s];
+      Ps.dcount = P.sp[s].dcount;
+      if (nk[s] > 1) {
+        int* tk = ctx->d_tclip + k * nb1;
+        PIC_CK(ctx, launch_clip_starts(P.sp[s].tstart, nb1, (int)lo, (int)hi, tk, ctx->st));
+        Ps.sp[0].tstart = tk;
+      }
+      // particles past the last sort (an unsorted tail) lie in the last chunk
+      if (k + 1 < nk[s]) Ps.tail_blocks = 0;
+      if ((e = launch_particles(D, 0, Ps, ctx->st)) != cudaSuccess)
+        return cuda_fail(ctx, "gather/push/deposit kernel", e);
+      PIC_CK(ctx, cudaEventRecord(ev_pushed(s, k), ctx->st));
+      PIC_CK(ctx, cudaStreamWaitEvent(out, ev_pushed(s, k), 0));
+      PIC_CK(ctx, copy_slots(hs[s].cell, ctx->sp[s].cell, 4, lo, hi, ld, 1, d2h, out));
+      PIC_CK(ctx, copy_slots(hs[s].off, ctx->sp[s].off, 4, lo, hi, ld, D, d2h, out));
+      PIC_CK(ctx, copy_slots(hs[s].u, ctx->sp[s].u, 4, lo, hi, ld, 3, d2h, out));
+    }
   }
   const pic_status r = step_fields(ctx);
   if (r != PIC_OK) return r;

@@ -253,6 +253,9 @@ cudaError_t launch_tile_scatter(const SortParams& P, const int* cell, const floa
                                 int* perm = nullptr);
 // bucket starts t[0..nb] from outside: unless they are a partition of [0, n)
 // they become one bucket, and ST_BAD_BUCKETS is set
+// out[i] = tstart[i] clamped to [lo, hi) for i < nb1 (one slot range's buckets)
+cudaError_t launch_clip_starts(const int* tstart, long long nb1, int lo, int hi, int* out,
+                               cudaStream_t st);
 cudaError_t launch_check_buckets(int* tstart, long long nb, long long n, int* status,
                                  cudaStream_t st);
 // out[r * ld + perm[i]] = in[r * ld + i] for i < n, r < rows (entries of perm

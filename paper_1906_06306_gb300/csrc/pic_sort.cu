@@ -302,6 +302,25 @@ cudaError_t launch_check_buckets(int* tstart, long long nb, long long n, int* st
   return cudaGetLastError();
 }
 
+// Bucket starts of one slot range [lo, hi) of a species: out[i] = tstart[i]
+// clamped to [lo, hi), so that bucket i of the clipped starts is bucket i's
+// part inside the range (a particle launch over the clipped starts processes
+// the slots of that range only).
+__global__ void k_clip_starts(const int* __restrict__ t, long long nb1, int lo, int hi,
+                              int* __restrict__ out) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nb1; i += stride)
+    out[i] = min(max(t[i], lo), hi);
+}
+
+cudaError_t launch_clip_starts(const int* tstart, long long nb1, int lo, int hi, int* out,
+                               cudaStream_t st) {
+  if (nb1 <= 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((nb1 + 255) / 256, 4 * 152);
+  k_clip_starts<<<(unsigned)blocks, 256, 0, st>>>(tstart, nb1, lo, hi, out);
+  return cudaGetLastError();
+}
+
 // Adjoint of a sort's permutation: the gradient rows of the particle now in
 // slot i go to the slot it held before the sort, perm[i] (out[perm[i]] =
 // in[i] on each of the `rows` rows of length ld).  An entry outside [0, n)

@@ -39,13 +39,18 @@ def _oracle_like(sim):
     return oracle.Grid(sim.dim, sim.nx, sim.ny, sim.nz, sim.c)
 
 
-# (shock, dim, steps, sort cadence): the periodic boxes take the overlapped
-# copies, whose last step sorts and pushes species by species; with a cadence
-# of 2 the last of 3 steps (and the only one of 1) opens a sort cycle
-@pytest.mark.parametrize("shock,dim,nsteps,sort_every",
-                         [(False, 2, 4, 1000), (True, 2, 4, 1000), (False, 3, 4, 1000),
-                          (False, 2, 3, 2), (False, 2, 1, 2), (False, 3, 3, 2)])
-def test_step_host_equals_device_steps(shock, dim, nsteps, sort_every):
+# (shock, dim, steps, sort cadence, particles per chunk): the periodic boxes
+# take the overlapped copies, whose last step runs the particle kernel chunk
+# by chunk (5000 particles per chunk: 4 chunks of the 2D box's 16,384 per
+# species, 3 of the 3D box's; 2^22: one chunk); with a cadence of 2 the last
+# of 3 steps (and the only one of 1) opens a sort cycle
+@pytest.mark.parametrize("shock,dim,nsteps,sort_every,chunk",
+                         [(False, 2, 4, 1000, 1 << 22), (True, 2, 4, 1000, 1 << 22),
+                          (False, 3, 4, 1000, 1 << 22), (False, 2, 3, 2, 1 << 22),
+                          (False, 2, 4, 1000, 5000), (False, 2, 3, 2, 5000),
+                          (False, 2, 1, 2, 5000), (False, 3, 3, 2, 5000),
+                          (False, 3, 4, 1000, 5000)])
+def test_step_host_equals_device_steps(shock, dim, nsteps, sort_every, chunk):
     import oracle
 
     from paper_1906_06306_gb300 import Simulation
@@ -74,6 +79,7 @@ def test_step_host_equals_device_steps(shock, dim, nsteps, sort_every):
         for sim in sims:
             sim.step(2)
     hs, keep, hf = _host_buffers(host)
+    B.pic_set_host_chunk(host.ctx, chunk)
     B.pic_step_host(host.ctx, hs, hf.data_ptr(), nsteps)
     dev.step(nsteps)
     Fd, spd = dev.download()
