@@ -1298,8 +1298,23 @@ cudaError_t copy_slots(void* dst, const void* src, size_t elem, long long lo, lo
 // at a time.  A sort due at the last step waits for the whole species.  The
 // launches are pic_step's, with the sort split by species and the particle
 // kernel by chunk.
+pic_status step_host_copies(pic_ctx* ctx, const pic_host_species* hs, float* host_fields,
+                            int nsteps);
+
 pic_status step_host_overlapped(pic_ctx* ctx, const pic_host_species* hs, float* host_fields,
                                 int nsteps) {
+  const pic_status r = step_host_copies(ctx, hs, host_fields, nsteps);
+  if (r != PIC_OK) {
+    // no copy to or from the caller's host buffers may outlive the call
+    for (auto io : ctx->io_st)
+      if (io) cudaStreamSynchronize(io);
+    cudaStreamSynchronize(ctx->st);
+  }
+  return r;
+}
+
+pic_status step_host_copies(pic_ctx* ctx, const pic_host_species* hs, float* host_fields,
+                            int nsteps) {
   const int D = ctx->grid.dim, ns = ctx->ns;
   const cudaMemcpyKind h2d = cudaMemcpyHostToDevice, d2h = cudaMemcpyDeviceToHost;
   for (auto& io : ctx->io_st)
@@ -1416,7 +1431,10 @@ pic_status pic_step_host(pic_ctx* ctx, const pic_host_species* hs, float* host_f
   }
   PIC_CK(ctx, cudaMemcpyAsync(ctx->F, host_fields, 36 * ctx->g.plane, h2d, ctx->st));
   const pic_status s = pic_step(ctx, nsteps);
-  if (s != PIC_OK) return s;
+  if (s != PIC_OK) {
+    cudaStreamSynchronize(ctx->st);  // the copies in read the caller's host buffers
+    return s;
+  }
   for (int sp = 0; sp < ctx->ns; ++sp) {
     const long long n = ctx->sp[sp].n, ld = ctx->cap[sp];
     if (n == 0) continue;

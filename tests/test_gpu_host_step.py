@@ -39,18 +39,20 @@ def _oracle_like(sim):
     return oracle.Grid(sim.dim, sim.nx, sim.ny, sim.nz, sim.c)
 
 
-# (shock, dim, steps, sort cadence, particles per chunk): the periodic boxes
-# take the overlapped copies, whose last step runs the particle kernel chunk
-# by chunk (5000 particles per chunk: 4 chunks of the 2D box's 16,384 per
-# species, 3 of the 3D box's; 2^22: one chunk); with a cadence of 2 the last
-# of 3 steps (and the only one of 1) opens a sort cycle
-@pytest.mark.parametrize("shock,dim,nsteps,sort_every,chunk",
-                         [(False, 2, 4, 1000, 1 << 22), (True, 2, 4, 1000, 1 << 22),
-                          (False, 3, 4, 1000, 1 << 22), (False, 2, 3, 2, 1 << 22),
-                          (False, 2, 4, 1000, 5000), (False, 2, 3, 2, 5000),
-                          (False, 2, 1, 2, 5000), (False, 3, 3, 2, 5000),
-                          (False, 3, 4, 1000, 5000)])
-def test_step_host_equals_device_steps(shock, dim, nsteps, sort_every, chunk):
+# (shock, dim, steps, sort cadence, particles per chunk, row padding): the
+# periodic boxes take the overlapped copies, whose last step runs the particle
+# kernel chunk by chunk (5000 particles per chunk: 4 chunks of the 2D box's
+# 16,384 per species, 3 of the 3D box's; 2^22: one chunk); with a cadence of 2
+# the last of 3 steps (and the only one of 1) opens a sort cycle; a padding
+# makes the rows (cap) longer than the particle count
+@pytest.mark.parametrize("shock,dim,nsteps,sort_every,chunk,pad",
+                         [(False, 2, 4, 1000, 1 << 22, 0), (True, 2, 4, 1000, 1 << 22, 0),
+                          (False, 3, 4, 1000, 1 << 22, 0), (False, 2, 3, 2, 1 << 22, 0),
+                          (False, 2, 4, 1000, 5000, 0), (False, 2, 3, 2, 5000, 0),
+                          (False, 2, 1, 2, 5000, 0), (False, 3, 3, 2, 5000, 0),
+                          (False, 3, 4, 1000, 5000, 0), (False, 2, 3, 2, 5000, 77),
+                          (False, 3, 2, 1000, 4096, 131)])
+def test_step_host_equals_device_steps(shock, dim, nsteps, sort_every, chunk, pad):
     import oracle
 
     from paper_1906_06306_gb300 import Simulation
@@ -62,10 +64,10 @@ def test_step_host_equals_device_steps(shock, dim, nsteps, sort_every, chunk):
         cap = [s.n + workloads.injected_count(pl, 6) for s in pl.species]
     elif dim == 2:
         pl = workloads.turbulence_2d(n=64, ppc=4, r_p=4.0, theta=0.3, sigma=10.0, modes=4, seed=94)
-        cap = None
+        cap = [s.n + pad for s in pl.species] if pad else None
     else:  # hot 3D plasma, halo 1: strays go through the deferred-particle kernel
         pl = workloads.uniform_plasma(3, 21, 19, 13, 0.45, 2, 0.01, 2.0, seed=95)
-        cap = None
+        cap = [s.n + pad for s in pl.species] if pad else None
     tun = (dict(sort_every=sort_every) if dim == 2 else
            dict(tile=[4, 4, 4], halo=1, sort_every=sort_every))
     sims = []
