@@ -196,6 +196,10 @@ struct SmemAcc {
 #ifndef PIC_ZZ_PACKED
 #define PIC_ZZ_PACKED 1
 #endif
+// the same for the 3D shared-memory ZigZag (zigzag_smem3)
+#ifndef PIC_ZZ_PACKED3
+#define PIC_ZZ_PACKED3 1
+#endif
 #ifndef PIC_MAGIC_F2I
 #define PIC_MAGIC_F2I 1
 #endif
@@ -586,11 +590,87 @@ __device__ __forceinline__ void zigzag_smem2(const SmemJ& A, const int* b, const
   if (crossed) put(b[0] + dc[0], b[1] + dc[1], i2);
 }
 
+// The 3D shared-memory window path in the same way: both segments' relay
+// points, displacements and weights as (segment 1, segment 2) pairs, and
+// zz_values<3>'s twelve products, with the +-D_b D_c / 12 terms, evaluated on
+// the pairs; the words of a segment in zz_deposit<3>'s order.
+__device__ __forceinline__ void zigzag_smem3(const SmemJ& A, const int* b, const int* dc,
+                                             const float* o1, const float* o2, float q) {
+  float2 Dp[3], Wp[3], Mp[3];
+  bool crossed = false;
+  const float2 one = make_float2(1.0f, 1.0f);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float x1 = o1[d];
+    const float kf = (float)dc[d];
+    const float x2 = kf + o2[d];
+    const float xr = dc[d] != 0 ? fmaxf(kf, 0.0f) : 0.5f * (x1 + x2);
+    const float2 P = make_float2(x1, xr), Q = make_float2(xr, x2);
+    Dp[d] = __fadd2_rn(Q, make_float2(-P.x, -P.y));
+    Wp[d] = __ffma2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(P, Q), make_float2(0.0f, -kf));
+    Mp[d] = __fadd2_rn(one, make_float2(-Wp[d].x, -Wp[d].y));
+    crossed |= dc[d] != 0;
+  }
+  const float2 q2 = make_float2(q, q), c12 = make_float2(1.0f / 12.0f, 1.0f / 12.0f);
+  const float2 f0 = __fmul2_rn(q2, Dp[0]), f1 = __fmul2_rn(q2, Dp[1]), f2 = __fmul2_rn(q2, Dp[2]);
+  const float2 cyz = __fmul2_rn(__fmul2_rn(Dp[1], Dp[2]), c12);
+  const float2 czx = __fmul2_rn(__fmul2_rn(Dp[2], Dp[0]), c12);
+  const float2 cxy = __fmul2_rn(__fmul2_rn(Dp[0], Dp[1]), c12);
+  const float2 nyz = make_float2(-cyz.x, -cyz.y), nzx = make_float2(-czx.x, -czx.y),
+               nxy = make_float2(-cxy.x, -cxy.y);
+  const float2 &wx = Wp[0], &wy = Wp[1], &wz = Wp[2], &mx = Mp[0], &my = Mp[1], &mz = Mp[2];
+  float2 v[12] = {__fmul2_rn(f0, __ffma2_rn(my, mz, cyz)),  __fmul2_rn(f0, __ffma2_rn(wy, mz, nyz)),
+                  __fmul2_rn(f0, __ffma2_rn(my, wz, nyz)),  __fmul2_rn(f0, __ffma2_rn(wy, wz, cyz)),
+                  __fmul2_rn(f1, __ffma2_rn(mz, mx, czx)),  __fmul2_rn(f1, __ffma2_rn(wz, mx, nzx)),
+                  __fmul2_rn(f1, __ffma2_rn(mz, wx, nzx)),  __fmul2_rn(f1, __ffma2_rn(wz, wx, czx)),
+                  __fmul2_rn(f2, __ffma2_rn(mx, my, cxy)),  __fmul2_rn(f2, __ffma2_rn(wx, my, nxy)),
+                  __fmul2_rn(f2, __ffma2_rn(mx, wy, nxy)),  __fmul2_rn(f2, __ffma2_rn(wx, wy, cxy))};
+  if (!crossed) {
+#pragma unroll
+    for (int w = 0; w < 12; ++w) v[w].x += v[w].y;
+  }
+  int i1[12], i2[12];
+#pragma unroll
+  for (int w = 0; w < 12; ++w) {
+#if PIC_MAGIC_F2I
+    const float2 t = __fadd2_rn(v[w], make_float2(12582912.0f, 12582912.0f));
+    i1[w] = __float_as_int(t.x) - 0x4B400000;
+    i2[w] = __float_as_int(t.y) - 0x4B400000;
+#else
+    i1[w] = __float2int_rn(v[w].x);
+    i2[w] = __float2int_rn(v[w].y);
+#endif
+  }
+  // zz_deposit<3>'s words: Jx at (i, j+{0,1}, k+{0,1}), Jy at (i+{0,1}, j,
+  // k+{0,1}), Jz at (i+{0,1}, j+{0,1}, k), second index fastest
+  auto put = [&](int bi, int bj, int bk, const int* iv) {
+    int* J = A.ji + bi + A.W0 * bj + A.W01 * bk;
+    atomicAdd(J, iv[0]);
+    atomicAdd(J + A.W0, iv[1]);
+    atomicAdd(J + A.W01, iv[2]);
+    atomicAdd(J + A.W0 + A.W01, iv[3]);
+    atomicAdd(J + A.wc, iv[4]);
+    atomicAdd(J + A.wc + A.W01, iv[5]);
+    atomicAdd(J + A.wc + 1, iv[6]);
+    atomicAdd(J + A.wc + 1 + A.W01, iv[7]);
+    atomicAdd(J + 2 * A.wc, iv[8]);
+    atomicAdd(J + 2 * A.wc + 1, iv[9]);
+    atomicAdd(J + 2 * A.wc + A.W0, iv[10]);
+    atomicAdd(J + 2 * A.wc + A.W0 + 1, iv[11]);
+  };
+  put(b[0], b[1], b[2], i1);
+  if (crossed) put(b[0] + dc[0], b[1] + dc[1], b[2] + dc[2], i2);
+}
+
 template <int D, class Acc>
 __device__ __forceinline__ void zigzag(const Acc& A, const int* b, const int* dc, const float* o1,
                                        const float* o2, const float* dn, float q) {
   if constexpr (D == 2 && PIC_ZZ_PACKED && std::is_same<Acc, SmemJ>::value) {
     zigzag_smem2(A, b, dc, o1, o2, dn, q);
+    return;
+  }
+  if constexpr (D == 3 && PIC_ZZ_PACKED3 && std::is_same<Acc, SmemJ>::value) {
+    zigzag_smem3(A, b, dc, o1, o2, q);
     return;
   }
   float D1[3], D2[3], W1[3] = {0.f, 0.f, 0.f}, W2[3] = {0.f, 0.f, 0.f};
