@@ -1288,9 +1288,10 @@ cudaError_t copy_slots(void* dst, const void* src, size_t elem, long long lo, lo
 }
 
 // pic_step_host with its copies overlapped.  Each species is cut into chunks
-// of slots (the context's host_chunk particles each, at most kHostChunks).  The copies in run
-// on one stream, the fields first and then chunk after chunk; the copies out
-// on another.  The steps before the last wait for every copy in.  The last
+// of slots (host_chunk particles each, at most kHostChunks; one chunk for a
+// species with an unsorted tail, which the last launch processes).  The copies
+// in run on one stream, the fields first and then chunk after chunk; the
+// copies out on another.  The steps before the last wait for every copy in.  The last
 // step runs the particle kernel chunk by chunk, each launch over bucket starts
 // clipped to the chunk's slots, as soon as the chunk is in, and sends each
 // chunk back out as soon as its launch is done while later chunks are still
@@ -1330,9 +1331,11 @@ pic_status step_host_copies(pic_ctx* ctx, const pic_host_species* hs, float* hos
   }
   int nk[PIC_MAX_SPECIES];
   for (int s = 0; s < ns; ++s)
-    nk[s] = (int)std::min<long long>(
-        kHostChunks, std::max<long long>(1, (ctx->sp[s].n + ctx->host_chunk - 1) /
-                                                ctx->host_chunk));
+    nk[s] = ctx->sp[s].n != ctx->sorted_n[s]
+                ? 1
+                : (int)std::min<long long>(
+                      kHostChunks, std::max<long long>(1, (ctx->sp[s].n + ctx->host_chunk - 1) /
+                                                              ctx->host_chunk));
   const auto lo_of = [&](int s, int k) { return ctx->sp[s].n * k / nk[s]; };
   const auto ev_in = [&](int s, int k) { return ctx->io_ev[s * kHostChunks + k]; };
   const auto ev_pushed = [&](int s, int k) {
@@ -1388,7 +1391,8 @@ pic_status step_host_copies(pic_ctx* ctx, const pic_host_species* hs, float* hos
         PIC_CK(ctx, launch_clip_starts(P.sp[s].tstart, nb1, (int)lo, (int)hi, tk, ctx->st));
         Ps.sp[0].tstart = tk;
       }
-      // particles past the last sort (an unsorted tail) lie in the last chunk
+      // the tail kernel runs with the species' last chunk (with its only one
+      // when the species has an unsorted tail)
       if (k + 1 < nk[s]) Ps.tail_blocks = 0;
       if ((e = launch_particles(D, 0, Ps, ctx->st)) != cudaSuccess)
         return cuda_fail(ctx, "gather/push/deposit kernel", e);
