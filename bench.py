@@ -108,19 +108,21 @@ def kernel_source_hash() -> str:
 
 
 def launches_per_step(sim, shock=False):
-    """Kernels of one pic_step on `sim`'s tuning, and of one tile sort: per
-    step the first B half step, the tile particle kernel, one fused launch per
-    filter pass, the deferred-particle kernel in 3D or with the wall, and the
-    second B half step with the E update (one launch on a periodic FDTD2
-    lattice of at most 4096 points, else two); per sort and species the count,
-    the scan (three kernels past 4096 bins) and the scatter."""
+    """Kernels of a graph-replayed pic_step on `sim`'s tuning, per step and per
+    sort cycle: per step the first B half step, the tile particle kernel, one
+    fused launch per filter pass, the deferred-particle kernel in 3D or with
+    the wall, and the second B half step with the E update (two launches; on a
+    periodic FDTD2 lattice of at most 4096 points one launch that also takes
+    the next step's first B half step, whose launch then opens only each
+    cycle); per sort and species the count, the scan (three kernels past 4096
+    bins) and the scatter."""
     from paper_1906_06306_gb300 import binding as B
 
     tun = sim.tuning()
     cells = sim.nx * sim.ny * sim.nz
-    fields = 2 if (not shock and cells <= 4096) else 3
-    step = fields + 1 + tun["filter_passes"] + (1 if sim.dim == 3 or shock else 0)
-    sort = (3 if B.pic_sort_bins(sim.ctx) <= 4096 else 5) * sim.nspecies
+    small = not shock and cells <= 4096
+    step = (1 if small else 3) + 1 + tun["filter_passes"] + (1 if sim.dim == 3 or shock else 0)
+    sort = (3 if B.pic_sort_bins(sim.ctx) <= 4096 else 5) * sim.nspecies + (1 if small else 0)
     return step, sort
 
 

@@ -1110,9 +1110,16 @@ cudaError_t wall_fields(pic_ctx* ctx) {
   });
 }
 
+// Inside one pic_step call on a small periodic lattice, the single-block
+// field launch of a step also runs the next step's first B half step.
+#ifndef PIC_SMALL_CHAIN
+#define PIC_SMALL_CHAIN 1
+#endif
+
 // The field half of a step, after the particles deposited J: the filter
-// passes, the second B half step and the E update.
-pic_status step_fields(pic_ctx* ctx) {
+// passes, the second B half step and the E update; with `chain` (small
+// periodic lattices only) the next step's first B half step too.
+pic_status step_fields(pic_ctx* ctx, bool chain = false) {
   cudaError_t e;
   if (!ctx->shock && fields_small_ok(ctx->g)) {
     // small periodic lattice: the filter (on J) first, then the second B
@@ -1120,7 +1127,8 @@ pic_status step_fields(pic_ctx* ctx) {
     // only, the filter J only: the order between them does not matter)
     const pic_status s = do_filter(ctx, ctx->tun.filter_passes);
     if (s != PIC_OK) return s;
-    e = timed(ctx, PIC_KERNEL_EUPD, [&]() { return launch_fields_small(ctx->g, ctx->F, ctx->st); });
+    e = timed(ctx, PIC_KERNEL_EUPD,
+              [&]() { return launch_fields_small(ctx->g, ctx->F, ctx->st, chain ? 1 : 0); });
     if (e != cudaSuccess) return cuda_fail(ctx, "B half step and E update", e);
   } else {
     e = timed(ctx, PIC_KERNEL_BHALF, [&]() { return launch_b_half(ctx->g, ctx->F, 0, ctx->st); });
@@ -1157,6 +1165,7 @@ pic_status pic_step(pic_ctx* ctx, int nsteps) {
     nsteps -= full * cyc;
   }
   const auto wall_bc = [&]() { return wall_fields(ctx); };
+  bool b1_done = false;  // this step's first B half step ran with the last field launch
   for (int it = 0; it < nsteps; ++it) {
     InjectParams IP{};
     long long add[PIC_MAX_SPECIES] = {};
@@ -1176,13 +1185,19 @@ pic_status pic_step(pic_ctx* ctx, int nsteps) {
     }
     const PushParams P = make_params(ctx);
     ctx->sorted_pending = false;
-    cudaError_t e = timed(ctx, PIC_KERNEL_BHALF, [&]() { return launch_b_half(ctx->g, ctx->F, 1, ctx->st); });
-    if (e == cudaSuccess) e = wall_bc();
-    if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
+    cudaError_t e = cudaSuccess;
+    if (!b1_done) {
+      e = timed(ctx, PIC_KERNEL_BHALF, [&]() { return launch_b_half(ctx->g, ctx->F, 1, ctx->st); });
+      if (e == cudaSuccess) e = wall_bc();
+      if (e != cudaSuccess) return cuda_fail(ctx, "B half step", e);
+    }
     e = timed(ctx, PIC_KERNEL_PUSH, [&]() { return launch_particles(ctx->grid.dim, 0, P, ctx->st); });
     if (e != cudaSuccess) return cuda_fail(ctx, "gather/push/deposit kernel", e);
+    // small periodic lattice, not the call's last step: the field launch also
+    // takes the next step's first B half step
+    b1_done = PIC_SMALL_CHAIN && it + 1 < nsteps && !ctx->shock && fields_small_ok(ctx->g);
     {
-      const pic_status s = step_fields(ctx);
+      const pic_status s = step_fields(ctx, b1_done);
       if (s != PIC_OK) return s;
     }
     if (ctx->shock) {

@@ -95,9 +95,11 @@ __global__ void k_e_update(float* __restrict__ F, const GridDev g, float c) {
 // global-memory writes before its later reads), every point's E update; the
 // operations of k_b_half and k_e_update point by point, so the same bits.  One
 // launch instead of two where launch latency, not bandwidth, bounds the step.
+// With `chain` set, after another barrier, the next step's first B half step
+// (which clears J for its deposit) as well: one launch instead of three.
 template <int D>
 __global__ void __launch_bounds__(1024) k_fields_small(float* __restrict__ F, const GridDev g,
-                                                       float hc, float c) {
+                                                       float hc, float c, int chain) {
   const int n0 = g.n[0], n1 = g.n[1];
   const int cells = (int)g.plane;
   for (int t = threadIdx.x; t < cells; t += blockDim.x) {
@@ -108,6 +110,12 @@ __global__ void __launch_bounds__(1024) k_fields_small(float* __restrict__ F, co
   for (int t = threadIdx.x; t < cells; t += blockDim.x) {
     const int i = t % n0, r = t / n0;
     e_update_point<D>(F, g, i, r % n1, r / n1, c);
+  }
+  if (!chain) return;
+  __syncthreads();
+  for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+    const int i = t % n0, r = t / n0;
+    b_half_point<D>(F, g, i, r % n1, r / n1, hc, 1);
   }
 }
 
@@ -806,12 +814,12 @@ bool fields_small_ok(const GridDev& g) {
   return PIC_SMALL_FIELDS && g.order == 2 && g.plane <= kSmallFieldCells;
 }
 
-cudaError_t launch_fields_small(const GridDev& g, float* F, cudaStream_t st) {
+cudaError_t launch_fields_small(const GridDev& g, float* F, cudaStream_t st, int chain) {
   const int threads = g.plane < 1024 ? (int)((g.plane + 31) / 32 * 32) : 1024;
   switch (g.dim) {
-    case 1: k_fields_small<1><<<1, threads, 0, st>>>(F, g, 0.5f * g.c, g.c); break;
-    case 2: k_fields_small<2><<<1, threads, 0, st>>>(F, g, 0.5f * g.c, g.c); break;
-    case 3: k_fields_small<3><<<1, threads, 0, st>>>(F, g, 0.5f * g.c, g.c); break;
+    case 1: k_fields_small<1><<<1, threads, 0, st>>>(F, g, 0.5f * g.c, g.c, chain); break;
+    case 2: k_fields_small<2><<<1, threads, 0, st>>>(F, g, 0.5f * g.c, g.c, chain); break;
+    case 3: k_fields_small<3><<<1, threads, 0, st>>>(F, g, 0.5f * g.c, g.c, chain); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -212,10 +212,11 @@ long long window_landing_floats(int dim, const TileDev& t);
 cudaError_t launch_b_half(const GridDev& g, float* F, int zero_j, cudaStream_t st);
 cudaError_t launch_e_update(const GridDev& g, float* F, cudaStream_t st);
 // FDTD2 lattices of at most kSmallFieldCells points: the second B half step
-// and the E update in one single-block launch (the same bits as the two)
+// and the E update in one single-block launch (the same bits as the two);
+// with chain != 0 also the next step's first B half step (clearing J)
 constexpr long long kSmallFieldCells = 4096;
 bool fields_small_ok(const GridDev& g);
-cudaError_t launch_fields_small(const GridDev& g, float* F, cudaStream_t st);
+cudaError_t launch_fields_small(const GridDev& g, float* F, cudaStream_t st, int chain = 0);
 // one Binomial2 sub-pass along gridded axis `axis` over ncomp consecutive planes,
 // src -> dst (a full pass is one sub-pass per gridded axis, x first)
 cudaError_t launch_filter_f32(const GridDev& g, const float* src, float* dst, int ncomp, int axis,

@@ -67,6 +67,34 @@ def test_graph_replay_equals_single_steps(dim):
     b.close()
 
 
+@pytest.mark.parametrize("dim", [1, 2])
+def test_chained_small_lattice_loop_equals_single_steps(dim):
+    """On a periodic FDTD2 lattice of at most 4096 points the field launch of a
+    step also runs the next step's first B half step inside one pic_step call;
+    with the event timers on, pic_step(n) takes the plain loop (no graph), so
+    this is the chained loop against calls of one step (never chained)."""
+    from paper_1906_06306_gb300 import binding as B
+
+    if dim == 1:
+        pl = workloads.weibel_1d(nx=128, ppc=8, seed=64)
+        tun = dict(sort_every=3)
+    else:
+        pl = workloads.turbulence_2d(n=32, ppc=4, r_p=4.0, theta=0.3, sigma=10.0, modes=4, seed=65)
+        tun = dict(tile=[8, 8, 1], sort_every=4, filter_passes=1)
+    a, b = _pair(pl, **tun)
+    B.pic_timing(b.ctx, 1)
+    n = 11
+    for _ in range(n):
+        a.step(1)
+    b.step(n)
+    B.pic_timing(b.ctx, 0)
+    a.check()
+    b.check()
+    _same(a, b, n)
+    a.close()
+    b.close()
+
+
 def test_graph_replay_follows_the_oracle():
     """Many steps through the graph with sorts in between, against the oracle:
     the fields after the run (particle order differs after sorts, fields do
