@@ -117,7 +117,10 @@ typedef struct {
 /* Kernel kinds reported by pic_kernel_times. */
 #define PIC_KERNEL_PUSH 0   /* gather + push + move + deposit (fused) */
 #define PIC_KERNEL_BHALF 1  /* B half step */
-#define PIC_KERNEL_EUPD 2   /* E update with -J */
+#define PIC_KERNEL_EUPD 2   /* E update with -J (on a periodic FDTD2 lattice of
+                               at most 4096 points: with the second B half step,
+                               and inside a multi-step pic_step call with the
+                               next step's first B half step, in one launch) */
 #define PIC_KERNEL_FILTER 3 /* one Binomial2 pass */
 #define PIC_KERNEL_SORT 4   /* tile sort: count + scan + scatter + copy back */
 #define PIC_KERNEL_BOUNDARY 5 /* wall fields and injection (pic_set_shock) */
