@@ -35,6 +35,29 @@ def test_step_bytes_adds_fields_filter_and_amortised_sort():
     assert b.push_bytes_per_launch(pl, 500) == 500 * 56 + 64 * 36
 
 
+def test_launch_counts_per_step_and_per_sort_cycle(monkeypatch):
+    """The claimed launch counts: 4 per step (first B half step, particle
+    kernel, second B half step, E update), one per filter pass, the deferred
+    kernel in 3D or with the wall; on a periodic FDTD2 lattice of at most 4096
+    points 2 per step (particle kernel, one field launch that takes the next
+    step's first B half step) and the first B half step once per sort cycle;
+    per sort and species count, scan (3 kernels past 4096 bins) and scatter."""
+    b = _bench()
+    from paper_1906_06306_gb300 import binding as B
+
+    def sim(dim, n, species, passes, bins):
+        monkeypatch.setattr(B, "pic_sort_bins", lambda ctx: bins)
+        return SimpleNamespace(dim=dim, nx=n[0], ny=n[1], nz=n[2], nspecies=species, ctx=None,
+                               tuning=lambda: dict(filter_passes=passes))
+
+    assert b.launches_per_step(sim(1, (512, 1, 1), 2, 0, 8)) == (2, 3 * 2 + 1)
+    assert b.launches_per_step(sim(2, (1024, 1024, 1), 2, 0, 32768)) == (4, 5 * 2)
+    assert b.launches_per_step(sim(3, (1024, 128, 128), 2, 4, 1 << 20), shock=True) == \
+        (3 + 1 + 4 + 1, 5 * 2)
+    # a small lattice with shock boundaries takes the separate field launches
+    assert b.launches_per_step(sim(2, (48, 8, 1), 2, 0, 24), shock=True) == (3 + 1 + 1, 3 * 2)
+
+
 def test_profiled_traffic_reads_the_summary_only_for_the_current_kernel(tmp_path, monkeypatch):
     b = _bench()
     h = b.kernel_source_hash()
